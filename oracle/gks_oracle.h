@@ -1,0 +1,97 @@
+/*
+ * gks_oracle.h -- plain, slow FP64 CPU oracle for the fifth-order TENO-D
+ * gas-kinetic scheme (GKS) with two-stage fourth-order (S2O4) time stepping.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the CUDA path.  Only
+ * the test suite, the smoke entry and the bench's CPU-baseline leg may load
+ * it.  It shares no code, header, table or constant with the CUDA library.
+ *
+ * Every routine follows the paper's statement of the method:
+ *   Sec. 2.1  BGK model, Maxwellian, compatibility, Eqs. (2.1)-(2.9)
+ *   Sec. 2.2  two-stage fourth-order time stepping, Eqs. (2.10)-(2.20)
+ *   Sec. 3.1  sub-stencil polynomials, smoothness indicators Eq. (3.7)
+ *   Sec. 3.2  derivatives on the stencils, kinetic merge Eqs. (3.25)-(3.26),
+ *             2-D dimension-by-dimension steps
+ *   Sec. 4.2  TENO-D selection Eqs. (4.5)-(4.14)
+ *   Sec. 5    collision time, CFL time step
+ * Readings of garbled or silent passages are listed in the .c file header.
+ */
+#ifndef GKS_ORACLE_H
+#define GKS_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* boundary kinds for ghost layers */
+enum { OR_BC_PERIODIC = 0, OR_BC_ZEROGRAD = 1, OR_BC_SYMMETRY = 2, OR_BC_NOSLIP = 3, OR_BC_REFLECT = 4 };
+/* collision-time models (Sec. 5) */
+enum { OR_TAU_ZERO = 0, OR_TAU_EULER = 1, OR_TAU_NS = 2 };
+
+typedef struct {
+    int dim;              /* 1 or 2 */
+    int nx, ny;           /* interior cells; ny = 1 in 1-D */
+    double dx, dy;        /* cell sizes */
+    int bc[4];            /* x-low, x-high, y-low, y-high */
+    double gamma;         /* ratio of specific heats */
+    double mu;            /* dynamic viscosity (NS) */
+    double Pr;            /* Prandtl number; 1 = no heat-flux correction */
+    int tau_mode;         /* OR_TAU_* */
+    double c1, c2;        /* Euler collision-time constants */
+    double cfl;
+    double eps;           /* TENO-D epsilon, Eq. (4.5) */
+    double qpow;          /* TENO-D power q, Eq. (4.5) */
+    double ct1, ct2;      /* thresholds C_T1, C_T2, normal direction */
+    double ct1_t, ct2_t;  /* thresholds used in the tangential direction */
+    int positivity_fallback; /* 1: first-order state when rho<=0 or p<=0 at a point */
+} or_problem;
+
+/* ---- reconstruction primitives (Sec. 3.1, 3.2, 4.2) ---- */
+/* n x n matrix (row-major) mapping cell averages at integer offsets to the
+ * monomial coefficients c_k of p(xi) = sum c_k xi^k, xi = (x - x_i)/dx. */
+int    or_fit_matrix(int n, const int *offsets, double *minv);
+double or_poly_eval(int deg, const double *c, double xi);
+double or_poly_deriv(int deg, const double *c, double xi);
+/* Eq. (3.7) in the scaled variable: sum_q int_{-1/2}^{1/2} (p^(q))^2 dxi */
+double or_beta(int deg, const double *c);
+/* TENO-D on the 5 cell averages q[0..4] = Qbar_{i-2..i+2}; evaluates the
+ * selected reconstruction and its xi-derivative at the points xs[0..n-1].
+ * Returns delta_{3,1}; sel[0..2] receives delta_{k,2} (0 when large). */
+int    or_teno_d(const double *q5, double eps, double qpow, double ct1, double ct2,
+                 int n, const double *xs, double *val, double *dval, int *sel);
+
+/* ---- kinetic layer (Sec. 2.1) ---- */
+/* u-moments <u^n>, n = 0..nmax, of a 1-D unit-mass Maxwellian with mean U and
+ * lambda; half = 0 full space, +1 over u>0, -1 over u<0. */
+void   or_moments_u(double U, double lam, int half, int nmax, double *m);
+/* micro slope a with M(prim) a = b, M_ab = <psi_a psi_b>; nvar = dim + 2 */
+int    or_micro_slope(int dim, double K, double U, double V, double lam,
+                      const double *b, double *a);
+/* exact time integrals q0..q5 of the coefficients of Eq. (2.5) over [0, delta] */
+void   or_time_coeffs(double delta, double tau, double *q);
+/* time-integrated interface flux (Eq. 2.12) at one point in the local frame
+ * (normal velocity first) for delta = dt and dt/2. Inputs are conserved
+ * variables and their normal / tangential derivatives on both sides.
+ * Returns 1 when the positivity fallback replaced a side, else 0;
+ * -1 on a non-physical state that the fallback could not fix. */
+int    or_flux_point(const or_problem *P,
+                     const double *Wl, const double *Wln, const double *Wlt,
+                     const double *Wr, const double *Wrn, const double *Wrt,
+                     const double *Wcl, const double *Wcr,
+                     double dt, double *Fdt, double *Fhalf);
+
+/* ---- solver (Sec. 2.2, 3.2, 5) ---- */
+/* W and Wout: interior SoA [nvar][ny][nx]; nvar = dim + 2 */
+int    or_stage1(const or_problem *P, const double *W, double dt, double *Wstar, long *nfallback);
+int    or_step(const or_problem *P, const double *W, double dt, double *Wout, long *nfallback);
+double or_dt(const or_problem *P, const double *W);
+/* advance to t_end with CFL time steps, the last one clipped to t_end */
+int    or_run(const or_problem *P, double *W, double t_end, long max_steps,
+              long *steps_done, double *t_out, long *nfallback);
+/* ghost filling exposed for tests: Wg is [nvar][ny+6][nx+6] (1-D: ny+6 -> 1) */
+void   or_fill_ghosts(const or_problem *P, double *Wg);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

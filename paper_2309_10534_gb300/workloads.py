@@ -1,0 +1,288 @@
+"""Seeded synthetic inputs shaped like the paper's test problems.
+
+This module only builds initial conditions (conserved-variable cell averages
+in float64, SoA ``[nvar][ny][nx]``) and problem parameters.  It holds none of
+the scheme's arithmetic; both the CUDA library and the CPU oracle consume
+what it returns.  Random draws use numpy's PCG64 with an explicit seed.
+
+Problems (paper Sec. 5 unless noted):
+  * ``advection_1d``  -- density-perturbation advection, Sec. 5.1
+  * ``advection_2d``  -- diagonal density advection, Sec. 5.5
+  * ``sod``           -- Sod tube, Sec. 5.2 (b)
+  * ``lax``           -- Lax tube, Sec. 5.2 (a)
+  * ``riemann2d``     -- 2-D Riemann configuration 3, Sec. 5.6 (a), split point
+                         a parameter
+  * ``viscous_shock_tube`` -- Sec. 5.8
+  * ``ensemble_1d``   -- many independent 1-D Riemann problems (seeded)
+  * ``isentropic_vortex`` -- smooth periodic vortex (not in the paper; a
+                         standard smooth 2-D Euler solution)
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Setup:
+    dim: int
+    nx: int
+    ny: int
+    lx: float
+    ly: float
+    W: np.ndarray                      # conserved cell averages [nvar][ny][nx]
+    bc: tuple = ("zerograd",) * 4      # x-low, x-high, y-low, y-high
+    gamma: float = 1.4
+    mu: float = 0.0
+    Pr: float = 1.0
+    tau: str = "euler"
+    cfl: float = 0.5
+    t_end: float = 0.0
+    name: str = ""
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def dx(self):
+        return self.lx / self.nx
+
+    @property
+    def dy(self):
+        return self.ly / self.ny if self.dim == 2 else 1.0
+
+    def problem_kwargs(self):
+        return dict(lx=self.lx, ly=self.ly, bc=self.bc, gamma=self.gamma, mu=self.mu, Pr=self.Pr,
+                    tau=self.tau, cfl=self.cfl)
+
+
+def conserved_1d(rho, u, p, gamma):
+    rho = np.asarray(rho, dtype=np.float64)
+    return np.stack([rho, rho * u, p / (gamma - 1.0) + 0.5 * rho * u * u])
+
+
+def conserved_2d(rho, u, v, p, gamma):
+    rho = np.asarray(rho, dtype=np.float64)
+    return np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
+
+
+def advection_1d(n, gamma=1.4):
+    """rho = 1 + 0.2 sin(pi x), U = 1, p = 1 on [0, 2], periodic; exact cell
+    averages (Sec. 5.1).  The exact solution at time t is the same profile
+    shifted by t."""
+    x = np.linspace(0.0, 2.0, n + 1)
+    dx = 2.0 / n
+    rho = 1.0 + 0.2 * (np.cos(np.pi * x[:-1]) - np.cos(np.pi * x[1:])) / (np.pi * dx)
+    W = np.stack([rho, rho, 1.0 / (gamma - 1.0) + 0.5 * rho])[:, None, :]
+    return Setup(1, n, 1, 2.0, 1.0, W, bc=("periodic",) * 4, gamma=gamma, tau="zero", t_end=2.0,
+                 name="advection_1d")
+
+
+def advection_1d_exact_rho(n, t):
+    x = np.linspace(0.0, 2.0, n + 1)
+    dx = 2.0 / n
+    return 1.0 + 0.2 * (np.cos(np.pi * (x[:-1] - t)) - np.cos(np.pi * (x[1:] - t))) / (np.pi * dx)
+
+
+def _sin_sum_cellavg(nx, ny, lx, ly, t):
+    """Exact cell averages of sin(pi (x + y - t)) on a uniform grid."""
+    x = np.linspace(0.0, lx, nx + 1) - t
+    y = np.linspace(0.0, ly, ny + 1)
+    dx, dy = lx / nx, ly / ny
+    X0, Y0 = np.meshgrid(x[:-1], y[:-1])
+    X1, Y1 = np.meshgrid(x[1:], y[1:])
+    s = (np.sin(np.pi * (X1 + Y0)) - np.sin(np.pi * (X0 + Y0)) - np.sin(np.pi * (X1 + Y1))
+         + np.sin(np.pi * (X0 + Y1)))
+    return s / (np.pi ** 2 * dx * dy)
+
+
+def advection_2d(n, gamma=1.4):
+    """rho = 1 + 0.2 sin(pi (x + y)), U = V = 1, p = 1 on [0, 2]^2, periodic
+    (Sec. 5.5); exact cell averages."""
+    rho = 1.0 + 0.2 * _sin_sum_cellavg(n, n, 2.0, 2.0, 0.0)
+    W = np.stack([rho, rho, rho, 1.0 / (gamma - 1.0) + rho])
+    return Setup(2, n, n, 2.0, 2.0, W, bc=("periodic",) * 4, gamma=gamma, tau="zero", t_end=2.0,
+                 name="advection_2d")
+
+
+def advection_2d_exact_rho(n, t):
+    return 1.0 + 0.2 * _sin_sum_cellavg(n, n, 2.0, 2.0, t)
+
+
+def _riemann_1d(n, left, right, x0=0.5, gamma=1.4, length=1.0):
+    """Exact cell averages of a piecewise-constant (rho, u, p) with a jump at x0."""
+    edges = np.linspace(0.0, length, n + 1)
+    frac_left = np.clip((x0 - edges[:-1]) / (edges[1:] - edges[:-1]), 0.0, 1.0)
+    WL = conserved_1d(*left, gamma)
+    WR = conserved_1d(*right, gamma)
+    return (frac_left[None, :] * WL[:, None] + (1.0 - frac_left[None, :]) * WR[:, None])
+
+
+def sod(n=400, gamma=1.4):
+    """Sod tube: (1, 0, 1) | (0.125, 0, 0.1) at x = 0.5 on [0, 1], t = 0.2."""
+    W = _riemann_1d(n, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 0.5, gamma)[:, None, :]
+    return Setup(1, n, 1, 1.0, 1.0, W, gamma=gamma, t_end=0.2, name="sod",
+                 extra=dict(left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1), x0=0.5))
+
+
+def lax(n=100, gamma=1.4):
+    """Lax tube: (0.445, 0.689, 3.528) | (0.5, 0, 0.571) at x = 0.5, t = 0.14."""
+    left, right = (0.445, 0.689, 3.528), (0.5, 0.0, 0.571)
+    W = _riemann_1d(n, left, right, 0.5, gamma)[:, None, :]
+    return Setup(1, n, 1, 1.0, 1.0, W, gamma=gamma, t_end=0.14, name="lax",
+                 extra=dict(left=left, right=right, x0=0.5))
+
+
+RIEMANN_CONFIG3 = {
+    # (rho, u, v, p) per quadrant, Sec. 5.6 (a)
+    "ll": (0.138, 1.206, 1.206, 0.029),   # x < x0, y < y0
+    "lr": (0.5323, 0.0, 1.206, 0.3),      # x >= x0, y < y0
+    "ur": (1.5, 0.0, 0.0, 1.5),           # x >= x0, y >= y0
+    "ul": (0.5323, 1.206, 0.0, 0.3),      # x < x0, y >= y0
+}
+
+
+def riemann2d(n=1024, ny=None, split=0.8, t_end=0.8, gamma=1.4):
+    """Four-quadrant Riemann problem (configuration 3) on [0, 1]^2 with exact
+    cell averages (area fractions of each quadrant)."""
+    ny = n if ny is None else ny
+    xe = np.linspace(0.0, 1.0, n + 1)
+    ye = np.linspace(0.0, 1.0, ny + 1)
+    fx = np.clip((split - xe[:-1]) / (xe[1:] - xe[:-1]), 0.0, 1.0)  # fraction with x < split
+    fy = np.clip((split - ye[:-1]) / (ye[1:] - ye[:-1]), 0.0, 1.0)
+    FX, FY = np.meshgrid(fx, fy)
+    W = np.zeros((4, ny, n))
+    for key, wx, wy in (("ll", FX, FY), ("lr", 1 - FX, FY), ("ur", 1 - FX, 1 - FY),
+                        ("ul", FX, 1 - FY)):
+        W += (wx * wy)[None] * conserved_2d(*RIEMANN_CONFIG3[key], gamma)[:, None, None]
+    return Setup(2, n, ny, 1.0, 1.0, W, bc=("zerograd",) * 4, gamma=gamma, t_end=t_end,
+                 name="riemann2d_config3", extra=dict(split=split))
+
+
+def viscous_shock_tube(nx=2048, ny=1024, Re=200.0, Pr=0.73, gamma=1.4, t_end=1.0, cfl=0.2):
+    """Viscous shock tube (Sec. 5.8) on [0,1] x [0,0.5]: (120, 0, 120/gamma) |
+    (1.2, 0, 1.2/gamma) at x = 0.5; no-slip adiabatic walls on the left,
+    right and bottom, symmetry on the top; mu = 1/Re (constant)."""
+    edges = np.linspace(0.0, 1.0, nx + 1)
+    fl = np.clip((0.5 - edges[:-1]) / (edges[1:] - edges[:-1]), 0.0, 1.0)
+    WL = conserved_2d(120.0, 0.0, 0.0, 120.0 / gamma, gamma)
+    WR = conserved_2d(1.2, 0.0, 0.0, 1.2 / gamma, gamma)
+    row = fl[None, :] * WL[:, None] + (1 - fl[None, :]) * WR[:, None]
+    W = np.repeat(row[:, None, :], ny, axis=1)
+    return Setup(2, nx, ny, 1.0, 0.5, W, bc=("noslip", "noslip", "noslip", "symmetry"),
+                 gamma=gamma, mu=1.0 / Re, Pr=Pr, tau="ns", cfl=cfl, t_end=t_end,
+                 name="viscous_shock_tube", extra=dict(Re=Re))
+
+
+@dataclass
+class Ensemble:
+    ncells: np.ndarray     # int32 per problem
+    offsets: np.ndarray    # int64 start of each problem in the packed array
+    W: np.ndarray          # packed conserved variables [3][sum ncells]
+    left: np.ndarray       # (rho, u, p) per problem
+    right: np.ndarray
+    gamma: float = 1.4
+    t_end: float = 0.15
+    cfl: float = 0.5
+
+
+def ensemble_1d(count=4096, seed=2309, nmin=200, nmax=4000, gamma=1.4, t_end=0.15):
+    """Independent 1-D Riemann problems on [0, 1] with the jump at 0.5:
+    rho, p ~ log-uniform [0.1, 10] and u ~ uniform [-1, 1] per side, cell
+    counts uniform in [nmin, nmax]; zero-gradient ends."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ncells = rng.integers(nmin, nmax + 1, size=count).astype(np.int32)
+    lr = np.exp(rng.uniform(np.log(0.1), np.log(10.0), size=(count, 2)))
+    lp = np.exp(rng.uniform(np.log(0.1), np.log(10.0), size=(count, 2)))
+    lu = rng.uniform(-1.0, 1.0, size=(count, 2))
+    left = np.stack([lr[:, 0], lu[:, 0], lp[:, 0]], axis=1)
+    right = np.stack([lr[:, 1], lu[:, 1], lp[:, 1]], axis=1)
+    offsets = np.zeros(count + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(ncells)
+    W = np.zeros((3, int(offsets[-1])))
+    for k in range(count):
+        W[:, offsets[k]:offsets[k + 1]] = _riemann_1d(int(ncells[k]), tuple(left[k]),
+                                                      tuple(right[k]), 0.5, gamma)
+    return Ensemble(ncells, offsets[:-1].copy(), W, left, right, gamma, t_end)
+
+
+def isentropic_vortex(n=512, strength=5.0, center=(5.0, 5.0), length=10.0, gamma=1.4,
+                      seed=None, amplitude=1e-3, quad=4):
+    """Isentropic vortex on a periodic [0, L]^2 in a (1, 1) mean flow
+    (standard smooth Euler test; not from the paper).  Cell averages by
+    quad x quad Gauss-Legendre points per cell.  With ``seed`` the initial
+    density gets a Gaussian-random perturbation of the given amplitude at
+    fixed (u, v, p), returned in ``extra['delta_rho']``."""
+    h = length / n
+    gx, gw = np.polynomial.legendre.leggauss(quad)
+    gx = 0.5 * gx
+    gw = 0.5 * gw
+    c = (np.arange(n) + 0.5) * h
+    W = np.zeros((4, n, n))
+    for a in range(quad):
+        for b in range(quad):
+            X, Y = np.meshgrid(c + gx[a] * h, c + gx[b] * h)
+            dxr = X - center[0]
+            dyr = Y - center[1]
+            r2 = dxr * dxr + dyr * dyr
+            du = strength / (2 * math.pi) * np.exp(0.5 * (1 - r2))
+            u = 1.0 - du * dyr
+            v = 1.0 + du * dxr
+            T = 1.0 - (gamma - 1.0) * strength ** 2 / (8 * gamma * math.pi ** 2) * np.exp(1 - r2)
+            rho = T ** (1.0 / (gamma - 1.0))
+            p = rho * T
+            W += gw[a] * gw[b] * conserved_2d(rho, u, v, p, gamma)
+    extra = {}
+    if seed is not None:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        drho = amplitude * rng.standard_normal((n, n))
+        rho = W[0]
+        u = W[1] / rho
+        v = W[2] / rho
+        p = (gamma - 1.0) * (W[3] - 0.5 * rho * (u * u + v * v))
+        W = conserved_2d(rho + drho, u, v, p, gamma)
+        extra["delta_rho"] = drho
+    return Setup(2, n, n, length, length, W, bc=("periodic",) * 4, gamma=gamma, tau="zero",
+                 t_end=2.0, name="isentropic_vortex", extra=extra)
+
+
+def random_smooth_2d(nx, ny, seed, gamma=1.4, amp=0.1, modes=3):
+    """Seeded smooth periodic state (few Fourier modes per field) for parity
+    tests of the smooth branch."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    X, Y = np.meshgrid(x, y)
+
+    def field_(base):
+        f = np.full_like(X, base)
+        for _ in range(modes):
+            kx, ky = rng.integers(1, 4, size=2)
+            ph = rng.uniform(0, 2 * np.pi)
+            f += amp * rng.uniform(-1, 1) * np.sin(2 * np.pi * (kx * X + ky * Y) + ph)
+        return f
+
+    rho = field_(1.0)
+    u = field_(0.3)
+    v = field_(-0.2)
+    p = field_(1.0)
+    return conserved_2d(rho, u, v, p, gamma)
+
+
+def random_rough_2d(nx, ny, seed, gamma=1.4):
+    """Seeded piecewise-constant blocks plus noise: exercises every TENO-D
+    branch.  Positive density and pressure."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    bx = rng.integers(2, 6)
+    by = rng.integers(2, 6)
+    rho = np.exp(rng.uniform(np.log(0.2), np.log(5.0), size=(by, bx)))
+    p = np.exp(rng.uniform(np.log(0.2), np.log(5.0), size=(by, bx)))
+    u = rng.uniform(-1, 1, size=(by, bx))
+    v = rng.uniform(-1, 1, size=(by, bx))
+    iy = (np.arange(ny) * by) // ny
+    ix = (np.arange(nx) * bx) // nx
+
+    def expand(a):
+        return a[iy][:, ix] * (1.0 + 0.02 * rng.standard_normal((ny, nx)))
+
+    return conserved_2d(expand(rho), expand(u) , expand(v), expand(p), gamma)
