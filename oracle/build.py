@@ -1,7 +1,10 @@
 """Build the FP64 CPU oracle (test infrastructure) into oracle/liboracle.so.
 
 Compiled with -ffp-contract=off so that x86-64 and aarch64 hosts round the
-same expressions the same way (no fused multiply-add contraction).
+same expressions the same way (no fused multiply-add contraction), and with
+-fno-strict-aliasing: gcc 13 at -O2 on aarch64 mis-assembled the moment
+matrix of the polynomial helpers under type-based alias analysis (the same
+source was correct at -O1, with -fno-strict-aliasing, and on x86-64).
 """
 import os
 import subprocess
@@ -18,7 +21,7 @@ def build(force: bool = False) -> str:
     ):
         return OUT
     tmp = OUT + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-strict-aliasing", "-fno-fast-math", "-fPIC", "-shared",
            "-D_DEFAULT_SOURCE", "-Wall", "-o", tmp, SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, OUT)

@@ -330,23 +330,21 @@ static void apsi_poly(const double *a, upoly *p)
     pterm(p, 0.5 * a[3], 0, 0, 1);
 }
 
-/* product of two polynomials (terms are not merged; the moment is linear) */
+/* product of two polynomials (terms are not merged; the moment is linear);
+ * r must be neither a nor b */
 static void pmul(const upoly *a, const upoly *b, upoly *r)
 {
-    upoly t;
-    pzero(&t);
+    pzero(r);
     for (int x = 0; x < a->n; ++x)
         for (int y = 0; y < b->n; ++y)
-            pterm(&t, a->c[x] * b->c[y], a->i[x] + b->i[y], a->j[x] + b->j[y], a->k[x] + b->k[y]);
-    *r = t;
+            pterm(r, a->c[x] * b->c[y], a->i[x] + b->i[y], a->j[x] + b->j[y], a->k[x] + b->k[y]);
 }
 
-/* multiply by u^ku v^kv */
+/* multiply by u^ku v^kv (r must not be a) */
 static void pshift(const upoly *a, int ku, int kv, upoly *r)
 {
-    upoly t = *a;
-    for (int x = 0; x < t.n; ++x) { t.i[x] += ku; t.j[x] += kv; }
-    *r = t;
+    pzero(r);
+    for (int x = 0; x < a->n; ++x) pterm(r, a->c[x], a->i[x] + ku, a->j[x] + kv, a->k[x]);
 }
 
 /* <p> = sum c <u^i> <v^j> <xi^2k> (independent Gaussian factors) */
@@ -366,11 +364,11 @@ static void moment_vec(int dim, const mom_t *m, int ku, int kv, const upoly *w, 
 {
     int nv = dim + 2;
     for (int a = 0; a < nv; ++a) {
-        upoly ps, t;
+        upoly ps, prod, shifted;
         psi_poly(active_alpha(dim, a), &ps);
-        if (w) pmul(w, &ps, &t); else t = ps;
-        pshift(&t, ku, kv, &t);
-        out[a] = pmoment(&t, m);
+        if (w) pmul(w, &ps, &prod);
+        pshift(w ? &prod : &ps, ku, kv, &shifted);
+        out[a] = pmoment(&shifted, m);
     }
 }
 
