@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Throughput of the TENO-D gas-kinetic scheme on one GB300 (or N replicas).
+
+Workload: 2-D Riemann problem, configuration 3 (paper Sec. 5.6 (a)) on a
+1024 x 1024 grid with the split at (0.8, 0.8), zero-gradient boundaries,
+CFL 0.5, Euler collision time.  A step is one full S2O4 step (both stages,
+both directions) of the whole grid with the CFL time step computed on the
+device.  Metric: cell-updates per second (cells x steps / time).
+
+Primary value: float32 reconstruction + flux with float64 state and S2O4
+accumulation; the float64 path is timed on the same GPU and reported under
+"fp64".  Timing: W warm-up steps, then K steps, each bracketed by CUDA
+events on the library's stream with a 256 MB L2 flush between steps (outside
+the events).  The sweep kernels are also timed individually by the
+library's event profiler for the roofline.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_GRID = 1024
+METRIC = "TENO-D GKS cell-updates/s (2-D Riemann configuration 3, 1024^2)"
+UNIT = "cell-updates/s"
+# GB300: 152 SMs x 128 FP32 lanes, 2 flops per fused multiply-add
+SMS, FP32_LANES = 152, 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--cpu-sample", type=int, default=96, help="grid of the oracle's bounded sample")
+    return p.parse_args()
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def sweep_traffic_from_profiles():
+    """DRAM bytes per sweep launch from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "sweep_fp32_riemann1024.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    return float(m.group(1)) if m else None
+
+
+def cpu_baseline(steps_budget_s=15.0, n=96):
+    """The oracle as it stands, on the host cores, on a bounded sample: the
+    same problem on an n x n grid, CFL steps until ~steps_budget_s."""
+    import oracle as O
+    from paper_2309_10534_gb300 import workloads as WL
+
+    s = WL.riemann2d(n, split=0.8)
+    P = O.make_problem(2, n, n, **s.problem_kwargs())
+    W = s.W
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        W = O.step(P, W, O.dt(P, W))
+        steps += 1
+        if time.perf_counter() - t0 > steps_budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n * n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%dx%d grid of the same problem, %d CFL steps, single thread" % (n, n, steps)}
+
+
+def run_reference(args):
+    rank, _, world = rank_info()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2309_10534_gb300 import workloads as WL
+
+    n = 64
+    s = WL.riemann2d(n, split=0.8)
+    P = O.make_problem(2, n, n, **s.problem_kwargs())
+    W = s.W
+    for _ in range(args.warmup):
+        W = O.step(P, W, O.dt(P, W))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        W = O.step(P, W, O.dt(P, W))
+    el = time.perf_counter() - t0
+    value = n * n * args.steps / el
+    sample = "%dx%d grid of the same problem per step (bounded sample), single thread" % (n, n)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "riemann2d_config3", "grid": "%dx%d" % (n, n),
+                                            "note": "FP64 CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, local_rank, world = rank_info()
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(local_rank)
+    from paper_2309_10534_gb300 import build
+
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    from paper_2309_10534_gb300 import gks
+    from paper_2309_10534_gb300 import workloads as WL
+
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    s = WL.riemann2d(N_GRID, split=0.8, t_end=0.8)
+    cells = N_GRID * N_GRID
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def solver(precision):
+        S = gks.solver_for(s, precision)
+        S.set_stream(stream.cuda_stream)
+        return S
+
+    def timed(S, K, W):
+        for _ in range(W):
+            S.step(0.0)
+        torch.cuda.synchronize()
+        S.profile(True)
+        S.profile_read(0)
+        S.profile_read(1)
+        S.profile_read(2)
+        L0 = S.kernel_launches()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            S.step(0.0)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        launches = S.kernel_launches() - L0
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        sweep_n, sweep_ms = S.profile_read(0)
+        S.profile(False)
+        return ms, launches, sweep_n, sweep_ms
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    S32 = solver("fp32")
+    ms32, launches32, sn32, sms32 = timed(S32, args.steps, args.warmup)
+    S64 = solver("fp64")
+    k64 = max(1, args.fp64_steps)
+    ms64, launches64, sn64, sms64 = timed(S64, k64, min(args.warmup, 3))
+    clk = clocks.stop()
+
+    # same number of steps on both paths from the same state: relative L1 of fp32 vs fp64
+    S32b = solver("fp32")
+    for _ in range(args.warmup + k64):
+        S32b.step(0.0)
+    W32 = S32b.get_state()
+    W64 = S64.get_state()
+    rel_l1 = float(np.abs(W32 - W64).sum() / np.abs(W64).sum())
+    S32b.close()
+
+    # end to end through the public API with host buffers (pinned)
+    host_in = torch.from_numpy(np.ascontiguousarray(s.W)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    Se = solver("fp32")
+    Se.set_state(host_in.numpy())
+    Se.step(0.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Se.set_state(host_in.numpy())          # H2D of the step's input (synchronising)
+        Se.step(0.0)
+        Se.get_state_into(host_out.numpy())    # D2H of the step's result (synchronising)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    Se.close()
+
+    times = torch.tensor([ms32, ms64, e2e_s], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    ms32, ms64, e2e_s = times.tolist()
+    if rank != 0:
+        dist.barrier() if dist else None
+        return
+
+    fm = gks.count_flops(2, "fp32", "euler", 1.0)
+    fm64 = gks.count_flops(2, "fp64", "euler", 1.0)
+    sweep_avg_ms = sms32 / max(sn32, 1)
+    flops_per_launch = fm["flops_per_cell_sweep"] * cells
+    achieved = flops_per_launch / (sweep_avg_ms * 1e-3) / 1e12
+    peak = SMS * FP32_LANES * 2 * 2.070e9 / 1e12
+    value = cells * args.steps * world / (ms32 * 1e-3)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms32 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "riemann2d_config3", "grid": "%dx%d" % (N_GRID, N_GRID),
+                   "precision": "fp32 reconstruction+flux, fp64 state and S2O4 accumulation",
+                   "cfl": 0.5, "split": 0.8, "l2": "256 MB flush between timed steps",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "fp64": {"value": cells * k64 * world / (ms64 * 1e-3), "unit": UNIT, "steps": k64,
+                 "ms_per_step": ms64 / k64, "flops_per_cell_update": fm64["flops_per_cell_update"]},
+        "fp32_rel_l1_vs_fp64": rel_l1,
+        "gpu_launches": launches32,
+        "e2e": {"value": cells * args.steps * world / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(s.W.nbytes), "d2h_bytes_per_step": int(s.W.nbytes)},
+        "roofline": {"bound": "alu", "kernel": "k2d_sweep<float>", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": sweep_traffic_from_profiles(),
+                     "flops_per_launch": flops_per_launch, "launch_ms": sweep_avg_ms,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)",
+                     "sweep_share_of_step": sms32 / ms32 if ms32 else None},
+        "flops_per_cell_update": fm["flops_per_cell_update"],
+        "clocks": clk,
+    }
+    if world == 1:
+        line["cpu_baseline"] = cpu_baseline(n=args.cpu_sample)
+    print(json.dumps(line))
+    if dist:
+        dist.barrier()
+
+
+if __name__ == "__main__":
+    main()

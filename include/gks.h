@@ -1,0 +1,170 @@
+/*
+ * gks.h -- C ABI of the GB300 library for the fifth-order TENO-D gas-kinetic
+ * scheme (GKS) with two-stage fourth-order (S2O4) time stepping on structured
+ * 1-D and 2-D grids.
+ *
+ * The problem solved is the conservation law W_t = -div F(W), W(0,x) = W0(x)
+ * (paper Sec. 2.2) for the Euler and Navier-Stokes equations of an ideal gas,
+ * with W = (rho, rho U, rho V, rho E) in 2-D and (rho, rho U, rho E) in 1-D.
+ * One S2O4 step = two stages; each stage reconstructs every cell interface
+ * with TENO-D (Sec. 4.2, Eqs. 4.5-4.14; 2-D by the dimension-by-dimension
+ * steps of Sec. 3.2 at two Gauss points), merges the two sides into the
+ * equilibrium state (Eqs. 2.6, 3.25, 3.26), evaluates the time-dependent BGK
+ * flux (Eqs. 2.5, 2.7, 2.9, 2.12) and updates the cells (Sec. 2.2).
+ *
+ * Conventions for every call:
+ *   - Return value: GKS_OK or an error code; gks_last_error() gives text.
+ *     No call throws or aborts across this boundary.
+ *   - Arrays of cell data are conserved variables, float64, interior cells
+ *     only, layout SoA [nvar][ny][nx] row-major (x fastest); nvar = dim + 2,
+ *     ny = 1 in 1-D.  The library keeps its own ghosted device copy.
+ *   - on_device = 0: pointer is host memory (pageable or pinned); the call
+ *     copies and synchronises.  on_device = 1: pointer is device memory owned
+ *     by the caller (e.g. a torch tensor's data_ptr) on the current device;
+ *     it must stay valid until the call returns.
+ *   - All device work is ordered on the context stream (gks_set_stream; the
+ *     default is the legacy default stream).  Calls that return host data
+ *     synchronise that stream.
+ *   - A context is not thread safe; separate contexts are independent.
+ *   - The library owns and frees all device memory it allocates.
+ */
+#ifndef GKS_H
+#define GKS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gks_ctx gks_ctx;
+
+typedef enum {
+    GKS_OK = 0,
+    GKS_EINVAL = 1,          /* bad argument (null pointer, size, enum value) */
+    GKS_ENOMEM = 2,          /* device or host allocation failed */
+    GKS_ECUDA = 3,           /* a CUDA runtime call failed */
+    GKS_ENONPHYSICAL = 4,    /* rho <= 0, p <= 0 or non-finite state seen by a kernel */
+    GKS_ETIMEOUT = 5,        /* a bounded device-side wait gave up */
+    GKS_EUNSUPPORTED = 6     /* valid request this build does not implement */
+} gks_status;
+
+/* ghost-layer boundary conditions (paper Sec. 5: periodic, non-reflecting,
+ * reflective, symmetric, no-slip adiabatic walls) */
+typedef enum {
+    GKS_BC_PERIODIC = 0,
+    GKS_BC_ZEROGRAD = 1,     /* "non-reflecting": copy of the edge cell */
+    GKS_BC_SYMMETRY = 2,     /* mirror, normal velocity negated */
+    GKS_BC_NOSLIP = 3,       /* mirror, both velocity components negated (adiabatic wall) */
+    GKS_BC_REFLECT = 4       /* same ghost rule as GKS_BC_SYMMETRY */
+} gks_bc;
+
+typedef enum {
+    GKS_FP64 = 0,            /* every step in float64 */
+    GKS_FP32_FLUX = 1        /* reconstruction + flux in float32, state and S2O4 accumulation in float64 */
+} gks_precision;
+
+/* collision time (Sec. 5): 0 -> tau = 0 (smooth inviscid tests),
+ * Euler: tau = c1 dt + c2 |pl-pr|/(pl+pr) dt, NS: tau = mu/p + c2 |pl-pr|/(pl+pr) dt */
+typedef enum { GKS_TAU_ZERO = 0, GKS_TAU_EULER = 1, GKS_TAU_NS = 2 } gks_tau_mode;
+
+typedef struct {
+    int dim;                 /* 1 or 2 */
+    int nx, ny;              /* interior cells; ny ignored (= 1) in 1-D; each >= 3 */
+    double x0, x1, y0, y1;   /* domain; uniform cells dx = (x1-x0)/nx, dy = (y1-y0)/ny */
+    int bc[4];               /* gks_bc for x-low, x-high, y-low, y-high */
+    int precision;           /* gks_precision */
+} gks_grid_desc;
+
+typedef struct {
+    double gamma;            /* ratio of specific heats (default 1.4) */
+    double mu;               /* dynamic viscosity, used by GKS_TAU_NS and the viscous time step */
+    double Pr;               /* Prandtl number; 1 disables the heat-flux correction */
+} gks_gas;
+
+typedef struct {
+    double cfl;              /* dt = cfl * min(h/(|U|+a), h^2/(4 nu)), h = min(dx,dy)  (Sec. 5) */
+    double c1, c2;           /* collision-time constants (Sec. 5; defaults 0.01, 1) */
+    double ct1, ct2;         /* TENO-D cut-offs C_T1, C_T2 normal to the face (Eqs. 4.7, 4.12) */
+    double ct1_t, ct2_t;     /* cut-offs of the tangential (Gauss-point) reconstruction */
+    double eps;              /* epsilon of Eq. (4.5) (default 1e-40; float32 path clamps to FLT_MIN) */
+    int q;                   /* power of Eq. (4.5), integer >= 1 (default 7) */
+    int tau_mode;            /* gks_tau_mode */
+    int positivity_fallback; /* 1: a reconstructed point state with rho<=0 or p<=0 is replaced
+                                by the adjacent cell average with zero slopes (not in the paper) */
+} gks_scheme;
+
+typedef struct {
+    unsigned int error_word; /* bit 0: non-physical state after an update; bit 1: fallback failed */
+    long long fallbacks;     /* positivity fallbacks taken since the state was last set */
+    double t;                /* simulation time of the stored state */
+    long long steps;         /* S2O4 steps taken since the state was last set */
+    double dt;               /* the time step the next gks_advance_to step will use */
+} gks_diag;
+
+/* Create a context for one grid; allocates the ghosted device state.
+ * Defaults: gamma 1.4, mu 0, Pr 1, cfl 0.5, c1 0.01, c2 1, C_T 1e-7/1e-5 in
+ * both directions, eps 1e-40, q 7, tau Euler, positivity fallback on. */
+gks_status gks_create(const gks_grid_desc *desc, gks_ctx **out);
+void       gks_destroy(gks_ctx *ctx);
+gks_status gks_set_gas(gks_ctx *ctx, const gks_gas *gas);
+gks_status gks_set_scheme(gks_ctx *ctx, const gks_scheme *scheme);
+/* cudaStream_t passed as void*; NULL = legacy default stream */
+gks_status gks_set_stream(gks_ctx *ctx, void *stream);
+
+/* Copy conserved cell averages in / out ([nvar][ny][nx], float64).
+ * gks_set_state resets t, step count, fallback count and the error word. */
+gks_status gks_set_state(gks_ctx *ctx, const double *W, int on_device);
+gks_status gks_get_state(gks_ctx *ctx, double *W, int on_device);
+/* which: 0 = W (state), 1 = W* (stage-1 output), 2 = stage accumulator
+ * W^n - dt/dx dF(W^n) (Sec. 2.2); same layout as gks_get_state */
+gks_status gks_get_buffer(gks_ctx *ctx, int which, double *W, int on_device);
+
+/* CFL time step of the current state (Sec. 5); synchronises. */
+gks_status gks_compute_dt(gks_ctx *ctx, double *dt);
+/* One S2O4 stage with step dt > 0: stage 1 reads W and writes W* and the
+ * accumulator; stage 2 reads W* and the accumulator and writes W. */
+gks_status gks_stage(gks_ctx *ctx, int stage, double dt);
+/* One S2O4 step; dt <= 0 uses the CFL time step of the current state.
+ * Asynchronous; errors flagged by kernels surface at the next synchronising call. */
+gks_status gks_step(gks_ctx *ctx, double dt);
+/* Advance with CFL steps until t_end (last step clipped to t_end) or
+ * max_steps (<= 0: no limit).  Time and step are kept on the device; the
+ * loop runs as CUDA-graph replays.  Synchronises. */
+gks_status gks_advance_to(gks_ctx *ctx, double t_end, long long max_steps,
+                          long long *steps_done, double *t_out);
+gks_status gks_get_diagnostics(gks_ctx *ctx, gks_diag *out);
+/* Text of the last error on this context (never NULL). */
+const char *gks_last_error(const gks_ctx *ctx);
+const char *gks_status_string(int status);
+/* Number of kernel launches this context has issued (graph replays count
+ * every kernel node). */
+long long  gks_kernel_launches(const gks_ctx *ctx);
+
+/* ---- measurement helpers (not part of the paper's method) ---- */
+
+/* Per-kernel timing with CUDA events recorded on the context stream around
+ * every directly launched kernel (not inside CUDA graphs).  kind: 0 = stage
+ * kernels (2-D sweeps, 1-D stage), 1 = ghost fill, 2 = other (CFL
+ * reduction, time commit, parameter kernels).  gks_profile_read synchronises,
+ * returns launches and summed milliseconds since the last read, and clears. */
+gks_status gks_profile_enable(gks_ctx *ctx, int enable);
+gks_status gks_profile_read(gks_ctx *ctx, int kind, long long *launches, double *total_ms);
+
+/* Algorithmic operation count of this library's own stage arithmetic, per
+ * cell, obtained by replaying the device functions on the host with a
+ * counting scalar (smooth-data branch: large stencil, closed-form time
+ * coefficients).  Flops = add/sub + mul + div + sqrt (a fused multiply-add
+ * counts 2); exp and erfc are counted separately. */
+typedef struct {
+    double flops_per_cell_update;            /* one full S2O4 step of one cell */
+    double flops_per_cell_sweep;             /* one 2-D sweep (1-D: one stage) kernel, per cell */
+    double transcendentals_per_cell_update;  /* exp + erfc */
+    double divides_per_cell_update;
+    double sqrt_per_cell_update;
+    double fp64_flops_per_cell_update;       /* float64 share (all flops on the float64 path) */
+} gks_flop_model;
+gks_status gks_count_flops(int dim, int precision, int tau_mode, double Pr, gks_flop_model *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GKS_H */

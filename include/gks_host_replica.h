@@ -1,0 +1,46 @@
+/*
+ * gks_host_replica.h -- host compilations of the library's per-point device
+ * arithmetic, for unit tests on machines without a GPU.
+ *
+ * Each call runs the same templated source as the CUDA kernels (compiled for
+ * the host CPU) on ONE stencil or ONE interface point.  There is no
+ * grid-level entry here: stepping a grid always runs on the GPU.
+ * precision: 0 = float64 arithmetic, 1 = float32 arithmetic (inputs and
+ * outputs are passed as float64 either way).  Return 0, or -1 on a bad
+ * argument.
+ */
+#ifndef GKS_HOST_REPLICA_H
+#define GKS_HOST_REPLICA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Folded time coefficients of Sec. 2.2 applied to the time integrals of
+ * Eq. (2.5), as functions of s = dt/tau: cF[0..5], cD[0..5] with
+ * F = sum cF_k dt^{p_k-1} (.), dF/dt = sum 4 cD_k dt^{p_k-2} (.),
+ * p = (1,2,2,1,2,2). */
+int gks_host_time_coeffs(int precision, double s, double *cF, double *cD);
+
+/* TENO-D (Sec. 4.2) on five cell averages q[0..4] = Qbar_{i-2..i+2}:
+ * faces[0..3] = value and xi-derivative at xi = +1/2, then at xi = -1/2;
+ * gauss[0..3] = value and xi-derivative at xi = -1/(2 sqrt 3), then +1/(2 sqrt 3);
+ * returns the large-stencil flag (1/0) or -1. */
+int gks_host_teno(int precision, const double *q, double eps, int qpow, double ct1, double ct2,
+                  double *faces, double *gauss);
+
+/* F and dF/dt (per unit time, Sec. 2.2) at one interface point in the local
+ * frame from the two sides' conserved variables and their normal (n) and
+ * tangential (t) derivatives; 4 slots each, slot 2 unused in 1-D.
+ * tau_mode as gks_tau_mode; Pr applies with tau_mode = 2.  No positivity
+ * fallback here: both sides must be physical. */
+int gks_host_point_flux(int dim, int precision, int tau_mode, double gamma, double mu, double Pr,
+                        double c1, double c2, double dt,
+                        const double *Wl, const double *Wln, const double *Wlt,
+                        const double *Wr, const double *Wrn, const double *Wrt,
+                        double *F, double *dF);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,621 @@
+// gks_api.cu -- host runtime and C ABI (include/gks.h) of the TENO-D
+// gas-kinetic scheme library.
+//
+// The context owns three ghosted float64 device arrays (state W, stage state
+// W*, stage accumulator A), a device-resident DevState (t, dt, CFL rate,
+// error word, counters) and, once advance_to has run, a CUDA graph of
+// GRAPH_STEPS consecutive S2O4 steps.  Time, time step and completion live
+// on the device, so a replayed graph needs no host round trip per step;
+// the host reads the completion flag once per replay.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/gks.h"
+#include "gks_aux.cuh"
+#include "gks_launch.h"
+
+using namespace gks;
+
+namespace {
+constexpr int GRAPH_STEPS = 8;
+}
+
+struct gks_ctx {
+    gks_grid_desc desc{};
+    GridDev g{};
+    gks_gas gas{};
+    gks_scheme sch{};
+    int nv = 0;
+    double *W = nullptr, *Ws = nullptr, *Ac = nullptr;
+    size_t arr_bytes = 0;
+    DevState* ds = nullptr;      // device
+    DevState* hs = nullptr;      // pinned host mirror
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    long long graph_nodes = 0;
+    unsigned long long param_version = 1, graph_version = 0;
+    long long launches = 0;
+    std::string err;
+    // per-kernel event timing (gks_profile_enable)
+    bool prof = false, capturing = false;
+    struct EvPair {
+        cudaEvent_t a, b;
+        int kind;
+    };
+    std::vector<EvPair> ev;
+    size_t ev_used = 0;
+    long long prof_n[3] = {0, 0, 0};
+    double prof_ms[3] = {0, 0, 0};
+};
+
+namespace {
+
+gks_status fail(gks_ctx* c, gks_status s, const char* fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CK(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return fail(c, GKS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+double internal_dof(int dim, double gamma)
+{
+    // 2-D: K = (5 - 3 gamma)/(gamma - 1) + 1 (Sec. 2.1); 1-D: K = (3 - gamma)/(gamma - 1)
+    return dim == 2 ? (5.0 - 3.0 * gamma) / (gamma - 1.0) + 1.0 : (3.0 - gamma) / (gamma - 1.0);
+}
+
+HostFlux host_flux(const gks_ctx* c)
+{
+    HostFlux h;
+    h.gamma = c->gas.gamma;
+    h.K = internal_dof(c->desc.dim, c->gas.gamma);
+    h.ntot = h.K + c->desc.dim;
+    h.c1 = c->sch.c1;
+    h.c2 = c->sch.c2;
+    h.mu = c->gas.mu;
+    h.prfac = (c->sch.tau_mode == GKS_TAU_NS) ? 1.0 / c->gas.Pr - 1.0 : 0.0;
+    h.tau_mode = c->sch.tau_mode;
+    return h;
+}
+
+TenoParams teno_params(const gks_ctx* c, bool tangential)
+{
+    TenoParams t;
+    t.eps = c->sch.eps;
+    t.q = c->sch.q;
+    t.ct1 = tangential ? c->sch.ct1_t : c->sch.ct1;
+    t.ct2 = tangential ? c->sch.ct2_t : c->sch.ct2;
+    return t;
+}
+
+bool prepared_f32 = false, prepared_f64 = false;
+
+// ---------------------------------------------------------------- profiling
+// Returns the index of an event pair whose start was recorded, or -1.
+int prof_begin(gks_ctx* c, cudaStream_t st, int kind)
+{
+    if (!c->prof || c->capturing) return -1;
+    if (c->ev_used == c->ev.size()) {
+        if (c->ev.size() >= 8192) return -1;
+        gks_ctx::EvPair p{};
+        if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) return -1;
+        c->ev.push_back(p);
+    }
+    gks_ctx::EvPair& p = c->ev[c->ev_used];
+    p.kind = kind;
+    if (cudaEventRecord(p.a, st) != cudaSuccess) return -1;
+    return (int)c->ev_used++;
+}
+
+void prof_end(gks_ctx* c, cudaStream_t st, int idx)
+{
+    if (idx >= 0) cudaEventRecord(c->ev[idx].b, st);
+}
+
+// fold the recorded pairs into per-kind totals and recycle the events
+cudaError_t prof_harvest(gks_ctx* c)
+{
+    if (!c->ev_used) return cudaSuccess;
+    cudaError_t e = cudaEventSynchronize(c->ev[c->ev_used - 1].b);
+    if (e != cudaSuccess) return e;
+    for (size_t k = 0; k < c->ev_used; ++k) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, c->ev[k].a, c->ev[k].b);
+        if (e != cudaSuccess) return e;
+        c->prof_n[c->ev[k].kind] += 1;
+        c->prof_ms[c->ev[k].kind] += ms;
+    }
+    c->ev_used = 0;
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- launches
+gks_status enqueue_ghosts(gks_ctx* c, double* arr, cudaStream_t st)
+{
+    const int gx = c->desc.nx + 2 * NG;
+    const int n = (c->desc.dim == 1) ? 2 * NG : 2 * NG * gx + 2 * NG * c->desc.ny;
+    const int pi = prof_begin(c, st, 1);
+    k_fill_ghosts<<<(n + 127) / 128, 128, 0, st>>>(c->g, arr, c->ds);
+    CK(cudaGetLastError());
+    prof_end(c, st, pi);
+    ++c->launches;
+    return GKS_OK;
+}
+
+gks_status enqueue_stage(gks_ctx* c, int stage, int with_sigma, cudaStream_t st)
+{
+    const HostFlux hf = host_flux(c);
+    const TenoParams tn = teno_params(c, false), tt = teno_params(c, true);
+    const bool f32 = c->desc.precision == GKS_FP32_FLUX;
+    if (c->desc.dim == 1) {
+        Stage1DArgs a{};
+        a.stage = stage;
+        a.with_sigma = with_sigma;
+        if (stage == 1) { a.src = c->W; a.out0 = c->Ws; a.out1 = c->Ac; }
+        else { a.src = c->Ws; a.out0 = c->W; a.acc = c->Ac; }
+        const int pi = prof_begin(c, st, 0);
+        CK(launch_stage1d(f32, c->g, a, hf, tn, c->ds, st));
+        prof_end(c, st, pi);
+        ++c->launches;
+        return GKS_OK;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+        SweepArgs a{};
+        a.stage = stage;
+        a.pass = pass;
+        a.dirn = pass;  // x faces first, then y faces
+        a.src = (stage == 1) ? c->W : c->Ws;
+        a.base = (stage == 1) ? c->W : c->Ac;
+        a.out0 = (stage == 1) ? c->Ws : c->W;
+        a.out1 = (stage == 1) ? c->Ac : nullptr;
+        if (pass == 0) {
+            a.nn = c->desc.nx; a.nt = c->desc.ny; a.sn = 1; a.st = c->g.pitch; a.hn = c->g.dx; a.ht = c->g.dy;
+        } else {
+            a.nn = c->desc.ny; a.nt = c->desc.nx; a.sn = c->g.pitch; a.st = 1; a.hn = c->g.dy; a.ht = c->g.dx;
+        }
+        a.with_sigma = (pass == 1) ? with_sigma : 0;
+        const int pi = prof_begin(c, st, 0);
+        cudaError_t e = f32 ? launch_sweep_f32(c->g, a, hf, tn, tt, c->ds, st)
+                            : launch_sweep_f64(c->g, a, hf, tn, tt, c->ds, st);
+        CK(e);
+        prof_end(c, st, pi);
+        ++c->launches;
+    }
+    return GKS_OK;
+}
+
+__global__ void k_prepare(DevState* ds, int mode, double dt, double t_end, long long max_steps)
+{
+    // mode 0: fixed dt, no t_end; 1: CFL dt towards t_end; 2: reset t, counters
+    // and error word; 3: CFL dt, no t_end
+    if (threadIdx.x || blockIdx.x) return;
+    if (mode == 2) {
+        ds->t = 0.0;
+        ds->steps = 0;
+        ds->fallbacks = 0;
+        ds->err = 0;
+    }
+    ds->done = 0;
+    ds->sigma = 0;
+    ds->max_steps = max_steps;
+    if (mode == 0) {
+        ds->dt = dt;
+        ds->fixed_dt = 1;
+        ds->t_end = INFINITY;
+    } else {
+        ds->fixed_dt = 0;
+        ds->t_end = (mode == 1) ? t_end : INFINITY;
+    }
+}
+
+gks_status enqueue_sigma(gks_ctx* c, cudaStream_t st)
+{
+    const long long ncell = (long long)c->desc.nx * (c->desc.dim == 2 ? c->desc.ny : 1);
+    int blocks = (int)((ncell + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    const int pi = prof_begin(c, st, 2);
+    if (c->desc.precision == GKS_FP32_FLUX) k_sigma<float><<<blocks, 256, 0, st>>>(c->g, c->W, c->ds);
+    else k_sigma<double><<<blocks, 256, 0, st>>>(c->g, c->W, c->ds);
+    CK(cudaGetLastError());
+    prof_end(c, st, pi);
+    ++c->launches;
+    return GKS_OK;
+}
+
+gks_status enqueue_commit(gks_ctx* c, int init, cudaStream_t st)
+{
+    const int pi = prof_begin(c, st, 2);
+    k_commit<<<1, 32, 0, st>>>(c->ds, init);
+    CK(cudaGetLastError());
+    prof_end(c, st, pi);
+    ++c->launches;
+    return GKS_OK;
+}
+
+// one S2O4 step: ghosts(W), stage 1, ghosts(W*), stage 2 (+ CFL rate), commit
+gks_status enqueue_step(gks_ctx* c, cudaStream_t st)
+{
+    gks_status s;
+    if ((s = enqueue_ghosts(c, c->W, st))) return s;
+    if ((s = enqueue_stage(c, 1, 0, st))) return s;
+    if ((s = enqueue_ghosts(c, c->Ws, st))) return s;
+    if ((s = enqueue_stage(c, 2, 1, st))) return s;
+    return enqueue_commit(c, 0, st);
+}
+
+gks_status sync_state(gks_ctx* c)
+{
+    CK(cudaMemcpyAsync(c->hs, c->ds, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return GKS_OK;
+}
+
+gks_status check_err(gks_ctx* c)
+{
+    if (c->hs->err & 2u)
+        return fail(c, GKS_ENONPHYSICAL, "positivity fallback failed: an adjacent cell state is non-physical");
+    if (c->hs->err & 1u)
+        return fail(c, GKS_ENONPHYSICAL, "non-physical or non-finite state after an update (t = %.17g)",
+                    c->hs->t);
+    return GKS_OK;
+}
+
+gks_status copy_interior(gks_ctx* c, double* arr, const double* W, int on_device, bool in)
+{
+    const int nx = c->desc.nx, ny = (c->desc.dim == 2) ? c->desc.ny : 1;
+    const size_t spitch = (size_t)nx * sizeof(double), dpitch = (size_t)c->g.pitch * sizeof(double);
+    const long long row0 = (c->desc.dim == 2) ? NG : 0;
+    for (int v = 0; v < c->nv; ++v) {
+        double* dev = arr + (long long)v * c->g.plane + row0 * c->g.pitch + NG;
+        const double* hostv = W + (size_t)v * nx * ny;
+        if (in) {
+            CK(cudaMemcpy2DAsync(dev, dpitch, hostv, spitch, spitch, ny,
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+        } else {
+            CK(cudaMemcpy2DAsync((double*)hostv, spitch, dev, dpitch, spitch, ny,
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+        }
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return GKS_OK;
+}
+
+gks_status build_graph(gks_ctx* c)
+{
+    if (c->graph && c->graph_version == c->param_version) return GKS_OK;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    const long long before = c->launches;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    gks_status s = GKS_OK;
+    for (int k = 0; k < GRAPH_STEPS && s == GKS_OK; ++k) s = enqueue_step(c, c->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    c->capturing = false;
+    c->graph_nodes = c->launches - before;
+    c->launches = before;  // captured, not launched
+    if (s != GKS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    CK(e);
+    e = cudaGraphInstantiate(&c->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    c->graph_version = c->param_version;
+    return GKS_OK;
+}
+
+gks_status prepare_kernels(gks_ctx* c)
+{
+    cudaError_t e = cudaSuccess;
+    if (c->desc.dim == 2 && c->desc.precision == GKS_FP32_FLUX && !prepared_f32) {
+        e = prepare_sweep_f32();
+        prepared_f32 = (e == cudaSuccess);
+    }
+    if (c->desc.dim == 2 && c->desc.precision == GKS_FP64 && !prepared_f64) {
+        e = prepare_sweep_f64();
+        prepared_f64 = (e == cudaSuccess);
+    }
+    CK(e);
+    return GKS_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* gks_status_string(int s)
+{
+    switch (s) {
+    case GKS_OK: return "ok";
+    case GKS_EINVAL: return "invalid argument";
+    case GKS_ENOMEM: return "out of memory";
+    case GKS_ECUDA: return "CUDA error";
+    case GKS_ENONPHYSICAL: return "non-physical state";
+    case GKS_ETIMEOUT: return "device wait timed out";
+    case GKS_EUNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+const char* gks_last_error(const gks_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+long long gks_kernel_launches(const gks_ctx* c) { return c ? c->launches : 0; }
+
+gks_status gks_create(const gks_grid_desc* d, gks_ctx** out)
+{
+    if (!d || !out) return GKS_EINVAL;
+    *out = nullptr;
+    if (d->dim != 1 && d->dim != 2) return GKS_EINVAL;
+    if (d->nx < 3 || (d->dim == 2 && d->ny < 3)) return GKS_EINVAL;
+    if (!(d->x1 > d->x0) || (d->dim == 2 && !(d->y1 > d->y0))) return GKS_EINVAL;
+    if (d->precision != GKS_FP64 && d->precision != GKS_FP32_FLUX) return GKS_EINVAL;
+    for (int k = 0; k < 4; ++k)
+        if (d->bc[k] < GKS_BC_PERIODIC || d->bc[k] > GKS_BC_REFLECT) return GKS_EINVAL;
+    if ((d->bc[0] == GKS_BC_PERIODIC) != (d->bc[1] == GKS_BC_PERIODIC)) return GKS_EINVAL;
+    if (d->dim == 2 && (d->bc[2] == GKS_BC_PERIODIC) != (d->bc[3] == GKS_BC_PERIODIC)) return GKS_EINVAL;
+    if ((long long)d->nx * (d->dim == 2 ? d->ny : 1) > (1ll << 31)) return GKS_EINVAL;
+
+    gks_ctx* c = new (std::nothrow) gks_ctx();
+    if (!c) return GKS_ENOMEM;
+    c->desc = *d;
+    if (d->dim == 1) c->desc.ny = 1;
+    c->nv = d->dim + 2;
+    c->gas = {1.4, 0.0, 1.0};
+    c->sch.cfl = 0.5;
+    c->sch.c1 = 0.01;
+    c->sch.c2 = 1.0;
+    c->sch.ct1 = c->sch.ct1_t = 1e-7;
+    c->sch.ct2 = c->sch.ct2_t = 1e-5;
+    c->sch.eps = 1e-40;
+    c->sch.q = 7;
+    c->sch.tau_mode = GKS_TAU_EULER;
+    c->sch.positivity_fallback = 1;
+
+    GridDev& g = c->g;
+    g.dim = d->dim;
+    g.nx = d->nx;
+    g.ny = c->desc.ny;
+    g.pitch = ((d->nx + 2 * NG + 15) / 16) * 16;
+    g.gy = (d->dim == 2) ? d->ny + 2 * NG : 1;
+    g.plane = (long long)g.gy * g.pitch;
+    g.dx = (d->x1 - d->x0) / d->nx;
+    g.dy = (d->dim == 2) ? (d->y1 - d->y0) / d->ny : 1.0;
+    for (int k = 0; k < 4; ++k) g.bc[k] = d->bc[k];
+    g.gamma = c->gas.gamma;
+    g.mu = c->gas.mu;
+
+    c->arr_bytes = (size_t)c->nv * g.plane * sizeof(double);
+    cudaError_t e1 = cudaMalloc(&c->W, c->arr_bytes);
+    cudaError_t e2 = cudaMalloc(&c->Ws, c->arr_bytes);
+    cudaError_t e3 = cudaMalloc(&c->Ac, c->arr_bytes);
+    cudaError_t e4 = cudaMalloc(&c->ds, sizeof(DevState));
+    cudaError_t e5 = cudaMallocHost(&c->hs, sizeof(DevState));
+    if (e1 || e2 || e3 || e4 || e5) {
+        gks_destroy(c);
+        cudaGetLastError();
+        return GKS_ENOMEM;
+    }
+    cudaMemset(c->W, 0, c->arr_bytes);
+    cudaMemset(c->Ws, 0, c->arr_bytes);
+    cudaMemset(c->Ac, 0, c->arr_bytes);
+    memset(c->hs, 0, sizeof(DevState));
+    c->hs->cfl = c->sch.cfl;
+    c->hs->t_end = INFINITY;
+    if (cudaMemcpy(c->ds, c->hs, sizeof(DevState), cudaMemcpyHostToDevice) != cudaSuccess ||
+        prepare_kernels(c) != GKS_OK) {
+        gks_destroy(c);
+        return GKS_ECUDA;
+    }
+    *out = c;
+    return GKS_OK;
+}
+
+void gks_destroy(gks_ctx* c)
+{
+    if (!c) return;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (auto& p : c->ev) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    cudaFree(c->W);
+    cudaFree(c->Ws);
+    cudaFree(c->Ac);
+    cudaFree(c->ds);
+    if (c->hs) cudaFreeHost(c->hs);
+    delete c;
+}
+
+gks_status gks_set_gas(gks_ctx* c, const gks_gas* gas)
+{
+    if (!c || !gas) return GKS_EINVAL;
+    if (!(gas->gamma > 1.0 && gas->gamma < 3.0) || !(gas->mu >= 0.0) || !(gas->Pr > 0.0))
+        return fail(c, GKS_EINVAL, "gas parameters out of range");
+    c->gas = *gas;
+    c->g.gamma = gas->gamma;
+    c->g.mu = gas->mu;
+    ++c->param_version;
+    return GKS_OK;
+}
+
+gks_status gks_set_scheme(gks_ctx* c, const gks_scheme* s)
+{
+    if (!c || !s) return GKS_EINVAL;
+    if (!(s->cfl > 0.0) || s->q < 1 || s->q > 32 || !(s->eps >= 0.0) || !(s->ct1 >= 0.0) || !(s->ct2 >= 0.0) ||
+        !(s->ct1_t >= 0.0) || !(s->ct2_t >= 0.0) || s->tau_mode < 0 || s->tau_mode > 2)
+        return fail(c, GKS_EINVAL, "scheme parameters out of range");
+    if (!s->positivity_fallback)
+        return fail(c, GKS_EUNSUPPORTED, "the kernels always apply the positivity fallback");
+    c->sch = *s;
+    ++c->param_version;
+    // cfl lives in the device state
+    c->hs->cfl = s->cfl;
+    CK(cudaMemcpyAsync(&c->ds->cfl, &c->hs->cfl, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return GKS_OK;
+}
+
+gks_status gks_set_stream(gks_ctx* c, void* stream)
+{
+    if (!c) return GKS_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return GKS_OK;
+}
+
+gks_status gks_set_state(gks_ctx* c, const double* W, int on_device)
+{
+    if (!c || !W) return GKS_EINVAL;
+    gks_status s = copy_interior(c, c->W, W, on_device, true);
+    if (s) return s;
+    k_prepare<<<1, 32, 0, c->stream>>>(c->ds, 2, 0.0, INFINITY, 0);
+    CK(cudaGetLastError());
+    ++c->launches;
+    return sync_state(c);
+}
+
+gks_status gks_get_state(gks_ctx* c, double* W, int on_device)
+{
+    if (!c || !W) return GKS_EINVAL;
+    return copy_interior(c, c->W, W, on_device, false);
+}
+
+gks_status gks_get_buffer(gks_ctx* c, int which, double* W, int on_device)
+{
+    if (!c || !W || which < 0 || which > 2) return GKS_EINVAL;
+    double* arr = which == 0 ? c->W : (which == 1 ? c->Ws : c->Ac);
+    return copy_interior(c, arr, W, on_device, false);
+}
+
+gks_status gks_compute_dt(gks_ctx* c, double* dt)
+{
+    if (!c || !dt) return GKS_EINVAL;
+    CK(cudaMemsetAsync(&c->ds->sigma, 0, sizeof(unsigned long long), c->stream));
+    gks_status s = enqueue_sigma(c, c->stream);
+    if (s) return s;
+    if ((s = sync_state(c))) return s;
+    if ((s = check_err(c))) return s;
+    double sig;
+    memcpy(&sig, &c->hs->sigma, sizeof sig);
+    *dt = c->sch.cfl / sig;
+    CK(cudaMemsetAsync(&c->ds->sigma, 0, sizeof(unsigned long long), c->stream));
+    return GKS_OK;
+}
+
+gks_status gks_stage(gks_ctx* c, int stage, double dt)
+{
+    if (!c || (stage != 1 && stage != 2) || !(dt > 0.0) || !std::isfinite(dt)) return GKS_EINVAL;
+    k_prepare<<<1, 32, 0, c->stream>>>(c->ds, 0, dt, 0.0, 0);
+    CK(cudaGetLastError());
+    ++c->launches;
+    gks_status s = enqueue_ghosts(c, stage == 1 ? c->W : c->Ws, c->stream);
+    if (s) return s;
+    return enqueue_stage(c, stage, 0, c->stream);
+}
+
+gks_status gks_step(gks_ctx* c, double dt)
+{
+    if (!c || !std::isfinite(dt)) return GKS_EINVAL;
+    gks_status s;
+    if (dt > 0.0) {
+        k_prepare<<<1, 32, 0, c->stream>>>(c->ds, 0, dt, 0.0, 0);
+        CK(cudaGetLastError());
+        ++c->launches;
+    } else {
+        k_prepare<<<1, 32, 0, c->stream>>>(c->ds, 3, 0.0, 0.0, 0);
+        CK(cudaGetLastError());
+        ++c->launches;
+        if ((s = enqueue_sigma(c, c->stream))) return s;
+        if ((s = enqueue_commit(c, 1, c->stream))) return s;
+    }
+    return enqueue_step(c, c->stream);
+}
+
+gks_status gks_advance_to(gks_ctx* c, double t_end, long long max_steps, long long* steps_done, double* t_out)
+{
+    if (!c || !std::isfinite(t_end)) return GKS_EINVAL;
+    gks_status s;
+    if ((s = sync_state(c))) return s;
+    const long long steps0 = c->hs->steps;
+    if (!(c->hs->t < t_end)) {
+        if (steps_done) *steps_done = 0;
+        if (t_out) *t_out = c->hs->t;
+        return GKS_OK;
+    }
+    const long long limit = max_steps > 0 ? steps0 + max_steps : 0;
+    k_prepare<<<1, 32, 0, c->stream>>>(c->ds, 1, 0.0, t_end, limit);
+    CK(cudaGetLastError());
+    ++c->launches;
+    if ((s = enqueue_sigma(c, c->stream))) return s;
+    if ((s = enqueue_commit(c, 1, c->stream))) return s;
+    if ((s = build_graph(c))) return s;
+    for (;;) {
+        CK(cudaGraphLaunch(c->graph, c->stream));
+        c->launches += c->graph_nodes;
+        if ((s = sync_state(c))) return s;
+        if ((s = check_err(c))) return s;
+        if (c->hs->done) break;
+    }
+    if (steps_done) *steps_done = c->hs->steps - steps0;
+    if (t_out) *t_out = c->hs->t;
+    return GKS_OK;
+}
+
+gks_status gks_get_diagnostics(gks_ctx* c, gks_diag* out)
+{
+    if (!c || !out) return GKS_EINVAL;
+    gks_status s = sync_state(c);
+    if (s) return s;
+    out->error_word = c->hs->err;
+    out->fallbacks = (long long)c->hs->fallbacks;
+    out->t = c->hs->t;
+    out->steps = c->hs->steps;
+    out->dt = c->hs->dt;
+    return check_err(c);
+}
+
+gks_status gks_profile_enable(gks_ctx* c, int enable)
+{
+    if (!c) return GKS_EINVAL;
+    c->prof = enable != 0;
+    return GKS_OK;
+}
+
+gks_status gks_profile_read(gks_ctx* c, int kind, long long* launches, double* total_ms)
+{
+    if (!c || kind < 0 || kind > 2) return GKS_EINVAL;
+    CK(prof_harvest(c));
+    if (launches) *launches = c->prof_n[kind];
+    if (total_ms) *total_ms = c->prof_ms[kind];
+    c->prof_n[kind] = 0;
+    c->prof_ms[kind] = 0.0;
+    return GKS_OK;
+}
+
+}  // extern "C"

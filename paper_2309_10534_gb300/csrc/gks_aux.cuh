@@ -1,0 +1,115 @@
+// gks_aux.cuh -- small kernels of the step loop: ghost-layer filling, the
+// CFL-rate reduction of a state, and the device-side time commit.  Included
+// by the runtime translation unit only.
+#pragma once
+
+#include "gks_kernels.cuh"
+
+namespace gks {
+
+// ------------------------------------------------------------------ ghosts
+// source index of ghost position g (ghosted coordinate) along a line of n
+// interior cells, and the velocity flips the rule implies
+__device__ __forceinline__ int ghost_src(int bc, int n, int g, bool& flip_n, bool& flip_all)
+{
+    flip_n = flip_all = false;
+    if (g >= NG && g < NG + n) return g;
+    const bool low = g < NG;
+    switch (bc) {
+    case 0:  // periodic
+        return NG + (((g - NG) % n) + n) % n;
+    case 1:  // zero gradient
+        return low ? NG : NG + n - 1;
+    case 3:  // no-slip adiabatic wall
+        flip_all = true;
+        return low ? 2 * NG - 1 - g : 2 * (NG + n) - 1 - g;
+    default:  // symmetry / reflect
+        flip_n = true;
+        return low ? 2 * NG - 1 - g : 2 * (NG + n) - 1 - g;
+    }
+}
+
+// One thread per ghost cell.  x ghosts of interior rows use the x rule; rows
+// of y ghosts use the y rule to pick an interior row, then the x rule for
+// x-ghost columns (the same values as filling x first, then y over the full
+// ghosted width).
+__global__ void k_fill_ghosts(GridDev g, double* __restrict__ W, const DevState* ds)
+{
+    if (ds && ds->done) return;
+    const int gx = g.nx + 2 * NG;
+    const int nv = g.dim + 2;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int i, j;
+    if (g.dim == 1) {
+        if (idx >= 2 * NG) return;
+        j = 0;
+        i = idx < NG ? idx : g.nx + idx;  // 0,1,2 and nx+3.. nx+5
+    } else {
+        const int band = 2 * NG * gx;
+        if (idx < band) {
+            j = idx / gx;
+            i = idx % gx;
+            if (j >= NG) j = g.ny + j;  // rows ny+3 .. ny+5
+        } else {
+            idx -= band;
+            if (idx >= 2 * NG * g.ny) return;
+            j = NG + idx / (2 * NG);
+            int k = idx % (2 * NG);
+            i = k < NG ? k : g.nx + k;
+        }
+    }
+    bool fxn, fxa, fyn = false, fya = false;
+    int sj = j;
+    if (g.dim == 2) sj = ghost_src(g.bc[2 + (j >= NG + g.ny)], g.ny, j, fyn, fya);
+    int si = ghost_src(g.bc[(i >= NG + g.nx)], g.nx, i, fxn, fxa);
+    for (int v = 0; v < nv; ++v) {
+        double val = W[(long long)v * g.plane + (long long)sj * g.pitch + si];
+        // x rule flips the x velocity (v=1) for symmetry, both for no-slip
+        const int vx = 1, vy = (g.dim == 2) ? 2 : -1;
+        bool neg = false;
+        if (v == vx && (fxn || fxa)) neg = !neg;
+        if (v == vy && fxa) neg = !neg;
+        if (v == vy && (fyn || fya)) neg = !neg;
+        if (v == vx && fya) neg = !neg;
+        W[(long long)v * g.plane + (long long)j * g.pitch + i] = neg ? -val : val;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sigma(GridDev g, const double* __restrict__ W, DevState* ds)
+{
+    double s = 0.0;
+    unsigned int err = 0;
+    const int nv = g.dim + 2;
+    const double h = (g.dim == 2) ? fmin(g.dx, g.dy) : g.dx;
+    const long long ncell = (long long)g.nx * (g.dim == 2 ? g.ny : 1);
+    for (long long c = blockIdx.x * 256ll + threadIdx.x; c < ncell; c += 256ll * gridDim.x) {
+        const int i = (int)(c % g.nx), j = (int)(c / g.nx);
+        const long long off = (long long)(g.dim == 2 ? j + NG : 0) * g.pitch + i + NG;
+        double w[4];
+        for (int v = 0; v < nv; ++v) w[v] = W[(long long)v * g.plane + off];
+        s = fmax(s, cell_sigma<T>(w, g.dim, g.gamma, g.mu, h, err));
+    }
+    block_commit_sigma<256>(s, err, 0ull, ds);
+}
+
+// After the last kernel of a step: advance t by dt, pick the next dt
+// (CFL from the reduced sigma, clipped to t_end), detect completion.
+// init = 1: only pick dt from sigma (before the first step).
+__global__ void k_commit(DevState* ds, int init)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (ds->done) return;
+    if (!init) {
+        ds->t += ds->dt;
+        ds->steps += 1;
+    }
+    const double sig = __longlong_as_double((long long)ds->sigma);
+    ds->sigma = 0ull;
+    double dt = ds->fixed_dt ? ds->dt : ds->cfl / sig;
+    if (ds->t + dt > ds->t_end) dt = ds->t_end - ds->t;
+    ds->dt = dt;
+    if (!(ds->t < ds->t_end) || (ds->max_steps > 0 && ds->steps >= ds->max_steps)) ds->done = 1u;
+}
+
+}  // namespace gks

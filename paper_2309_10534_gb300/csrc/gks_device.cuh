@@ -1,0 +1,585 @@
+// gks_device.cuh -- device arithmetic of the TENO-D gas-kinetic scheme.
+//
+// Everything here runs per cell or per interface point in registers:
+//   * TENO-D reconstruction of one 5-cell stencil (paper Sec. 4.2), written
+//     with the Legendre-type coefficients of the quartic and the (b, c)
+//     coefficients of the three quadratics, evaluated at the cell faces
+//     (xi = +-1/2) or at the Gauss points xi = +-1/(2 sqrt 3);
+//   * Maxwellian moments, the closed-form micro-slope solve, kinetic merge
+//     and the time-dependent BGK flux at one point (Sec. 2.1, Eqs. 2.5-2.9),
+//     with the two time integrals of Sec. 2.2 folded into F and dF/dt.
+// Templated on the arithmetic type T (float or double) and the dimension.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#define GKS_HD __host__ __device__ __forceinline__
+
+namespace gks {
+
+// ------------------------------------------------------------------ math
+template <typename T> struct M;
+template <> struct M<float> {
+    static GKS_HD float erfc_(float x) { return erfcf(x); }
+    static GKS_HD float exp_(float x) { return expf(x); }
+    static GKS_HD float sqrt_(float x) { return sqrtf(x); }
+    static GKS_HD float rcp(float x) { return 1.0f / x; }
+    static constexpr float tiny = 1.17549435e-38f;  // FLT_MIN: smallest eps kept normal
+    static constexpr int nseries = 16;               // terms of the time-coefficient series
+    static constexpr float s_series = 2.0f;          // series below, closed form above
+};
+template <> struct M<double> {
+    static GKS_HD double erfc_(double x) { return erfc(x); }
+    static GKS_HD double exp_(double x) { return exp(x); }
+    static GKS_HD double sqrt_(double x) { return sqrt(x); }
+    static GKS_HD double rcp(double x) { return 1.0 / x; }
+    static constexpr double tiny = 0.0;
+    static constexpr int nseries = 22;
+    static constexpr double s_series = 1.0;
+};
+
+// integer power by squaring (q of Eq. 4.5 is a small positive integer)
+template <typename T>
+GKS_HD T ipow(T x, int q)
+{
+    T r = T(1);
+    while (q) {
+        if (q & 1) r *= x;
+        x *= x;
+        q >>= 1;
+    }
+    return r;
+}
+
+// ------------------------------------------------------------------ TENO-D
+struct TenoParams {
+    double eps;
+    int q;
+    double ct1, ct2;  // thresholds of the first / second selection
+};
+
+// Result of the TENO-D selection on one 5-cell stencil: either the large
+// stencil, or the equal-weight (d_k = 1/3) average of the kept sub-stencils.
+template <typename T> struct TenoSel {
+    T q2;               // centre cell average
+    T b[3], c[3];       // quadratic k: p = q2 - c/12 + b xi + c xi^2
+    T u1, u2, u3, u4;   // quartic in the Legendre-type basis
+    T w[3];             // sub-stencil weights (0 when the large stencil is used)
+    bool large;
+};
+
+// beta_k of Eq. (3.7): quadratics b^2 + 13/3 c^2; the quartic in Balsara's
+// Legendre form.  Selection of Eqs. (4.5)-(4.7) and (4.11)-(4.12) evaluated
+// in ratio form chi_k >= C  <=>  sum_j ((beta_k+eps)/(beta_j+eps))^q <= 1/C,
+// which needs no (beta+eps)^-q and cannot overflow into a wrong decision.
+template <typename T>
+GKS_HD void teno_select(const T q[5], const TenoParams& P, TenoSel<T>& S)
+{
+    const T q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3], q4 = q[4];
+    S.q2 = q2;
+    S.b[0] = T(0.5) * (q0 - T(4) * q1 + T(3) * q2);
+    S.c[0] = T(0.5) * (q0 - T(2) * q1 + q2);
+    S.b[1] = T(0.5) * (q3 - q1);
+    S.c[1] = T(0.5) * (q1 - T(2) * q2 + q3);
+    S.b[2] = T(0.5) * (T(-3) * q2 + T(4) * q3 - q4);
+    S.c[2] = T(0.5) * (q2 - T(2) * q3 + q4);
+    S.u1 = (T(11) * q0 - T(82) * q1 + T(82) * q3 - T(11) * q4) * T(1.0 / 120.0);
+    S.u2 = (T(-3) * q0 + T(40) * q1 - T(74) * q2 + T(40) * q3 - T(3) * q4) * T(1.0 / 56.0);
+    S.u3 = (-q0 + T(2) * q1 - T(2) * q3 + q4) * T(1.0 / 12.0);
+    S.u4 = (q0 - T(4) * q1 + T(6) * q2 - T(4) * q3 + q4) * T(1.0 / 24.0);
+
+    T eps = (T)P.eps;
+    if (eps < M<T>::tiny) eps = M<T>::tiny;
+    T t[4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t[k] = S.b[k] * S.b[k] + T(13.0 / 3.0) * S.c[k] * S.c[k] + eps;
+    {
+        T a = S.u1 + T(0.1) * S.u3, bq = S.u2 + T(123.0 / 455.0) * S.u4;
+        t[3] = a * a + T(13.0 / 3.0) * bq * bq + T(781.0 / 20.0) * S.u3 * S.u3
+             + T(1421461.0 / 2275.0) * S.u4 * S.u4 + eps;
+    }
+    // first selection: keep the large stencil when chi_{3,1} >= C_T1
+    T s1 = T(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s1 += ipow(t[3] / t[j], P.q);
+    S.large = (s1 * (T)P.ct1 <= T(1));
+    if (S.large) {
+        S.w[0] = S.w[1] = S.w[2] = T(0);
+        return;
+    }
+    // second selection among the small stencils, d_k = 1/3 (cancels)
+    T d[3], dsum = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        T s2 = T(0);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) s2 += ipow(t[k] / t[j], P.q);
+        d[k] = (s2 * (T)P.ct2 <= T(1)) ? T(1) : T(0);
+        dsum += d[k];
+    }
+    T inv = T(1) / dsum;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) S.w[k] = d[k] * inv;
+}
+
+// values and xi-derivatives at the faces xi = +1/2 (vp, dp) and -1/2 (vm, dm)
+template <typename T>
+GKS_HD void teno_faces(const T q[5], const TenoSel<T>& S, T& vp, T& dp, T& vm, T& dm)
+{
+    if (S.large) {  // Eqs. (4.8), (4.9) and their mirror at x_{i-1/2}
+        vp = (T(2) * q[0] - T(13) * q[1] + T(47) * q[2] + T(27) * q[3] - T(3) * q[4]) * T(1.0 / 60.0);
+        dp = (q[1] - T(15) * q[2] + T(15) * q[3] - q[4]) * T(1.0 / 12.0);
+        vm = (T(-3) * q[0] + T(27) * q[1] + T(47) * q[2] - T(13) * q[3] + T(2) * q[4]) * T(1.0 / 60.0);
+        dm = (q[0] - T(15) * q[1] + T(15) * q[2] - q[3]) * T(1.0 / 12.0);
+        return;
+    }
+    // Eqs. (4.13), (4.14): p_k(+-1/2) = q2 +- b/2 + c/6, p_k'(+-1/2) = b +- c
+    vp = dp = vm = dm = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        T w = S.w[k], bh = T(0.5) * S.b[k], c6 = S.c[k] * T(1.0 / 6.0);
+        vp += w * (bh + c6);
+        vm += w * (c6 - bh);
+        dp += w * (S.b[k] + S.c[k]);
+        dm += w * (S.b[k] - S.c[k]);
+    }
+    vp += S.q2;
+    vm += S.q2;
+}
+
+// value and xi-derivative at the Gauss point xi = g (g = +-1/(2 sqrt 3), xi^2 = 1/12)
+template <typename T>
+GKS_HD void teno_gauss(const TenoSel<T>& S, T g, T& v, T& d)
+{
+    if (S.large) {
+        // P2(g) = 0, P3(g) = -g/15, P4(g) = -1/180; P3'(g) = 1/10, P4'(g) = -2g/21
+        v = S.q2 + S.u1 * g - S.u3 * g * T(1.0 / 15.0) - S.u4 * T(1.0 / 180.0);
+        d = S.u1 + T(2) * S.u2 * g + T(0.1) * S.u3 - T(2.0 / 21.0) * S.u4 * g;
+        return;
+    }
+    v = S.q2;
+    d = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        v += S.w[k] * S.b[k] * g;
+        d += S.w[k] * (S.b[k] + T(2) * S.c[k] * g);
+    }
+}
+
+// ------------------------------------------------------------------ kinetic layer
+// Moments of a unit-mass Maxwellian: <u^n> (n = 0..6), <v^m> (m = 0..5),
+// <xi^2>, <xi^4>.  In 1-D there is no v: <v^0> = 1, <v^m> = 0.
+template <typename T, int DIM>
+GKS_HD void u_recursion(T* u, T U, T inv2l)
+{
+#pragma unroll
+    for (int n = 0; n < 5; ++n) u[n + 2] = U * u[n + 1] + T(n + 1) * inv2l * u[n];
+}
+
+template <typename T, int DIM>
+GKS_HD void v_moments(T* v, T V, T inv2l)
+{
+    if constexpr (DIM == 2) {
+        v[0] = T(1);
+        v[1] = V;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) v[n + 2] = V * v[n + 1] + T(n + 1) * inv2l * v[n];
+    } else {
+        v[0] = T(1);
+#pragma unroll
+        for (int n = 1; n < 6; ++n) v[n] = T(0);
+    }
+}
+
+// <u^k v^m psi_a>, psi = (1, u, v, (u^2+v^2+xi^2)/2)
+template <int k, int m, typename T>
+GKS_HD void psim(const T* u, const T* v, T xi2, T* o)
+{
+    o[0] = u[k] * v[m];
+    o[1] = u[k + 1] * v[m];
+    o[2] = u[k] * v[m + 1];
+    o[3] = T(0.5) * (u[k + 2] * v[m] + u[k] * v[m + 2] + u[k] * v[m] * xi2);
+}
+// <u^k v^m xi^2 psi_a>
+template <int k, int m, typename T>
+GKS_HD void psim_xi(const T* u, const T* v, T xi2, T xi4, T* o)
+{
+    o[0] = u[k] * v[m] * xi2;
+    o[1] = u[k + 1] * v[m] * xi2;
+    o[2] = u[k] * v[m + 1] * xi2;
+    o[3] = T(0.5) * ((u[k + 2] * v[m] + u[k] * v[m + 2]) * xi2 + u[k] * v[m] * xi4);
+}
+// <u^k v^m (a . psi) psi_a>
+template <int k, int m, typename T>
+GKS_HD void apsim(const T* u, const T* v, T xi2, T xi4, const T* a, T* o)
+{
+    T t0[4], t1[4], t2[4], t3[4], t4[4], t5[4];
+    psim<k, m>(u, v, xi2, t0);
+    psim<k + 1, m>(u, v, xi2, t1);
+    psim<k, m + 1>(u, v, xi2, t2);
+    psim<k + 2, m>(u, v, xi2, t3);
+    psim<k, m + 2>(u, v, xi2, t4);
+    psim_xi<k, m>(u, v, xi2, xi4, t5);
+    const T h = T(0.5) * a[3];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) o[i] = a[0] * t0[i] + a[1] * t1[i] + a[2] * t2[i] + h * (t3[i] + t4[i] + t5[i]);
+}
+// 1-D variant: v == 0, so only the m = 0 terms survive and no v-moments are read
+template <int k, typename T>
+GKS_HD void apsim1(const T* u, T xi2, T xi4, const T* a, T* o)
+{
+    // psi = (1, u, 0, (u^2+xi^2)/2); a[2] is zero in 1-D
+    T t0[4], t1[4], t3[4], t5[4];
+    const T one[6] = {T(1), T(0), T(0), T(0), T(0), T(0)};
+    psim<k, 0>(u, one, xi2, t0);
+    psim<k + 1, 0>(u, one, xi2, t1);
+    psim<k + 2, 0>(u, one, xi2, t3);
+    psim_xi<k, 0>(u, one, xi2, xi4, t5);
+    const T h = T(0.5) * a[3];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) o[i] = a[0] * t0[i] + a[1] * t1[i] + h * (t3[i] + t5[i]);
+}
+
+template <int k, int m, typename T, int DIM>
+GKS_HD void apsi(const T* u, const T* v, T xi2, T xi4, const T* a, T* o)
+{
+    if constexpr (DIM == 2) apsim<k, m>(u, v, xi2, xi4, a, o);
+    else apsim1<k>(u, xi2, xi4, a, o);
+}
+
+// Micro slope: <a psi> = b with the full-space moments of a Maxwellian
+// (Eq. 2.7), solved in closed form.  ntot = K + DIM degrees of freedom
+// besides... (all translational + internal); inv2l = 1/(2 lambda).
+template <typename T, int DIM>
+GKS_HD void micro_slope(const T* b, T U, T V, T lam, T inv2l, T ntot, T* a)
+{
+    const T E = T(0.5) * (U * U + V * V + ntot * inv2l);
+    const T R2 = b[1] - U * b[0];
+    const T R3 = (DIM == 2) ? b[2] - V * b[0] : T(0);
+    const T R4 = T(2) * (b[3] - E * b[0]);
+    const T tl = T(2) * lam;
+    a[3] = tl * tl / ntot * (R4 - T(2) * U * R2 - T(2) * V * R3);
+    a[2] = (DIM == 2) ? tl * R3 - V * a[3] : T(0);
+    a[1] = tl * R2 - U * a[3];
+    a[0] = b[0] - U * a[1] - V * a[2] - E * a[3];
+}
+
+// ------------------------------------------------------------------ time coefficients
+// With s = dt/tau, the time integrals of Eq. (2.5) over [0, delta] are
+// q_k = tau^{p_k} phi_k(delta/tau), p = (1,2,2,1,2,2).  The flux and its time
+// derivative (Sec. 2.2) need F = (4 F(dt/2) - F(dt))/dt and
+// dF = 4 (F(dt) - 2 F(dt/2))/dt^2, i.e. per coefficient
+//   cF_k = (4 phi_k(s/2) - phi_k(s)) / s^{p_k}
+//   cD_k = (phi_k(s) - 2 phi_k(s/2)) / s^{p_k}
+// and then  qF_k = cF_k * dt^{p_k-1},  qD_k = 4 cD_k * dt^{p_k-2}.
+// Small s: power series (coefficients generated at compile time from the
+// Taylor series of exp, plus the 1/s terms of cF_4, cF_5); large s: closed
+// forms in y = exp(-s/2) with the polynomial parts cancelled analytically.
+struct SeriesTable {
+    double c[12][24];
+};
+
+constexpr double cx_fact(int n) { return n <= 1 ? 1.0 : n * cx_fact(n - 1); }
+constexpr double cx_pow2neg(int n) { return n == 0 ? 1.0 : 0.5 * cx_pow2neg(n - 1); }
+// Taylor coefficient a_n of phi_k(x) = sum a_n x^n
+constexpr double cx_phi(int k, int n)
+{
+    const double e = ((n % 2) ? -1.0 : 1.0) / cx_fact(n);  // (-1)^n / n!
+    switch (k) {
+    case 0: return n >= 2 ? e : 0.0;                   // x - 1 + e^-x
+    case 1: return n >= 3 ? (n - 2) * e : 0.0;         // 2 - x - (x+2) e^-x
+    case 2: return n >= 3 ? -e : 0.0;                  // x^2/2 - x + 1 - e^-x
+    case 3: return n >= 1 ? -e : 0.0;                  // 1 - e^-x
+    case 4: return n >= 1 ? (2 - n) * e : 0.0;         // -2 + (x+2) e^-x
+    default: return n >= 1 ? e : 0.0;                  // -(1 - e^-x)
+    }
+}
+constexpr int cx_p(int k) { return (k == 0 || k == 3) ? 1 : 2; }
+constexpr SeriesTable make_series_table()
+{
+    SeriesTable t{};
+    for (int k = 0; k < 6; ++k)
+        for (int m = 0; m < 24; ++m) {
+            const int n = m + cx_p(k);  // coefficient of s^m after dividing by s^p
+            const double w2 = cx_pow2neg(n);
+            t.c[k][m] = cx_phi(k, n) * (4.0 * w2 - 1.0);       // cF_k
+            t.c[6 + k][m] = cx_phi(k, n) * (1.0 - 2.0 * w2);   // cD_k
+        }
+    return t;
+}
+__constant__ SeriesTable kSeries = make_series_table();
+constexpr SeriesTable kSeriesHost = make_series_table();  // host replay (operation counting)
+
+template <typename T>
+GKS_HD void time_coeffs(T s, T* cF, T* cD)
+{
+    if (s < M<T>::s_series) {
+        const int n = (s < T(0.25)) ? (M<T>::nseries / 2) : M<T>::nseries;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            T acc = T(0);
+#ifdef __CUDA_ARCH__
+            for (int m = n - 1; m >= 0; --m) acc = acc * s + (T)kSeries.c[k][m];
+#else
+            for (int m = n - 1; m >= 0; --m) acc = acc * s + (T)kSeriesHost.c[k][m];
+#endif
+            if (k < 6) cF[k] = acc; else cD[k - 6] = acc;
+        }
+        // phi_4 and phi_5 start at -x: their x^1 terms leave -1/s in cF_4, cF_5
+        // (they cancel in cD); the table holds the powers s^0 and up.
+        const T is = T(1) / s;
+        cF[4] -= is;
+        cF[5] -= is;
+        return;
+    }
+    const T y = M<T>::exp_(T(-0.5) * s), y2 = y * y;
+    const T is = T(1) / s, is2 = is * is;
+    const T omy = T(1) - y;
+    cF[0] = (s - T(3) + T(4) * y - y2) * is;
+    cD[0] = omy * omy * is;
+    cF[1] = (T(6) - s - (T(2) * s + T(8)) * y + (s + T(2)) * y2) * is2;
+    cD[1] = (T(-2) + (s + T(4)) * y - (s + T(2)) * y2) * is2;
+    cF[2] = (T(3) - s - T(4) * y + y2) * is2;
+    cD[2] = (T(0.25) * s * s - T(1) + T(2) * y - y2) * is2;
+    cF[3] = omy * (T(3) - y) * is;
+    cD[3] = -omy * omy * is;
+    cF[4] = (T(-6) + (T(2) * s + T(8)) * y - (s + T(2)) * y2) * is2;
+    cD[4] = (T(2) - (s + T(4)) * y + (s + T(2)) * y2) * is2;
+    cF[5] = -omy * (T(3) - y) * is2;
+    cD[5] = omy * omy * is2;
+}
+
+// ------------------------------------------------------------------ flux at a point
+template <typename T> struct FluxParams {
+    T gm1;        // gamma - 1
+    T K;          // internal degrees of freedom of this dimension
+    T ntot;       // K + DIM
+    T dt;
+    T c1, c2, mu; // collision time (Sec. 5)
+    T prfac;      // 1/Pr - 1
+    int tau_mode; // 0 zero, 1 Euler, 2 NS
+};
+
+template <typename T> struct Side {  // one reconstructed side (local frame, 4 slots; 1-D slot 2 = 0)
+    T W[4], Wn[4], Wt[4];
+};
+
+template <typename T, int DIM>
+GKS_HD bool physical(const T* W, T gm1)
+{
+    const T r = W[0];
+    const T ke = (DIM == 2) ? (W[1] * W[1] + W[2] * W[2]) : W[1] * W[1];
+    const T p = gm1 * (W[3] - T(0.5) * ke / r);
+    return r > T(0) && p > T(0) && isfinite(p);
+}
+
+// Accumulated contributions of the non-equilibrium side terms and of the
+// equilibrium state, built side by side to keep few values alive.
+template <typename T, int DIM, bool NONEQ, bool PRFIX>
+GKS_HD void side_terms(const Side<T>& S, bool upper, const FluxParams<T>& P,
+                                           T* W0, T* W0n, T* W0t, T* S3, T* S4, T* S5,
+                                           T* N4, T* N5, T& pside)
+{
+    const T r = S.W[0], ir = T(1) / r;
+    const T U = S.W[1] * ir;
+    const T V = (DIM == 2) ? S.W[2] * ir : T(0);
+    const T p = P.gm1 * (S.W[3] - T(0.5) * r * (U * U + V * V));
+    pside = p;
+    const T inv2l = p * ir;           // 1/(2 lambda)
+    const T lam = T(0.5) * r / p;     // lambda = rho/(2p)
+    const T sl = M<T>::sqrt_(lam);
+    const T xi2 = P.K * inv2l, xi4 = P.K * (P.K + T(2)) * inv2l * inv2l;
+
+    // half-space u-moments: upper = u > 0 (left state), else u < 0 (right state)
+    T uh[7], v[6];
+    const T sg = upper ? T(1) : T(-1);
+    uh[0] = T(0.5) * M<T>::erfc_(-sg * sl * U);
+    uh[1] = U * uh[0] + sg * T(0.28209479177387814) * M<T>::exp_(-lam * U * U) / sl;  // e/(2 sqrt(pi lam))
+    u_recursion<T, DIM>(uh, U, inv2l);
+    v_moments<T, DIM>(v, V, inv2l);
+
+    // micro slopes, Eq. (2.7)
+    T an[4], at[4] = {T(0), T(0), T(0), T(0)}, b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = S.Wn[i] * ir;
+    micro_slope<T, DIM>(b, U, V, lam, inv2l, P.ntot, an);
+    if constexpr (DIM == 2) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] = S.Wt[i] * ir;
+        micro_slope<T, DIM>(b, U, V, lam, inv2l, P.ntot, at);
+    }
+
+    // kinetic merge, Eqs. (2.6), (3.25), (3.26)
+    T t[4];
+    psim<0, 0>(uh, v, xi2, t);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) W0[i] += r * t[i];
+    apsi<0, 0, T, DIM>(uh, v, xi2, xi4, an, t);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) W0n[i] += r * t[i];
+    if constexpr (DIM == 2) {
+        apsi<0, 0, T, DIM>(uh, v, xi2, xi4, at, t);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) W0t[i] += r * t[i];
+    }
+
+    if constexpr (NONEQ) {
+        // time derivative of the side's Maxwellian from <a_n u + a_t v + A> = 0
+        T uf[7];
+        uf[0] = T(1);
+        uf[1] = U;
+        u_recursion<T, DIM>(uf, U, inv2l);
+        T x1[4], A[4];
+        apsi<1, 0, T, DIM>(uf, v, xi2, xi4, an, x1);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] = -x1[i];
+        if constexpr (DIM == 2) {
+            apsi<0, 1, T, DIM>(uf, v, xi2, xi4, at, x1);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) b[i] -= x1[i];
+        }
+        micro_slope<T, DIM>(b, U, V, lam, inv2l, P.ntot, A);
+
+        // flux moments of the side terms of Eq. (2.5) over the half space
+        psim<1, 0>(uh, v, xi2, t);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) S3[i] += r * t[i];
+        apsi<2, 0, T, DIM>(uh, v, xi2, xi4, an, t);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) S4[i] += r * t[i];
+        if constexpr (DIM == 2) {
+            apsi<1, 1, T, DIM>(uh, v, xi2, xi4, at, t);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) S4[i] += r * t[i];
+        }
+        apsi<1, 0, T, DIM>(uh, v, xi2, xi4, A, t);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) S5[i] += r * t[i];
+        if constexpr (PRFIX) {
+            // density moments (weight 1 instead of u) for the heat flux
+            apsi<1, 0, T, DIM>(uh, v, xi2, xi4, an, t);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) N4[i] += r * t[i];
+            if constexpr (DIM == 2) {
+                apsi<0, 1, T, DIM>(uh, v, xi2, xi4, at, t);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) N4[i] += r * t[i];
+            }
+            apsi<0, 0, T, DIM>(uh, v, xi2, xi4, A, t);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) N5[i] += r * t[i];
+        }
+    }
+}
+
+// F and dF/dt (per unit time; Sec. 2.2) at one interface point in the local
+// frame.  Both sides must be physical (the caller applies the fallback).
+template <typename T, int DIM, bool NONEQ, bool PRFIX>
+GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& P,
+                                           T* F, T* dF)
+{
+    T W0[4] = {0, 0, 0, 0}, W0n[4] = {0, 0, 0, 0}, W0t[4] = {0, 0, 0, 0};
+    T S3[4] = {0, 0, 0, 0}, S4[4] = {0, 0, 0, 0}, S5[4] = {0, 0, 0, 0};
+    T N4[4] = {0, 0, 0, 0}, N5[4] = {0, 0, 0, 0};
+    T pl, pr;
+    side_terms<T, DIM, NONEQ, PRFIX>(L, true, P, W0, W0n, W0t, S3, S4, S5, N4, N5, pl);
+    side_terms<T, DIM, NONEQ, PRFIX>(R, false, P, W0, W0n, W0t, S3, S4, S5, N4, N5, pr);
+
+    // equilibrium state g0
+    const T r0 = W0[0], ir0 = T(1) / r0;
+    const T U0 = W0[1] * ir0;
+    const T V0 = (DIM == 2) ? W0[2] * ir0 : T(0);
+    const T p0 = P.gm1 * (W0[3] - T(0.5) * r0 * (U0 * U0 + V0 * V0));
+    const T inv2l = p0 * ir0, lam = T(0.5) * r0 / p0;
+    const T xi2 = P.K * inv2l, xi4 = P.K * (P.K + T(2)) * inv2l * inv2l;
+    T u[7], v[6];
+    u[0] = T(1);
+    u[1] = U0;
+    u_recursion<T, DIM>(u, U0, inv2l);
+    v_moments<T, DIM>(v, V0, inv2l);
+
+    T an[4], at[4] = {T(0), T(0), T(0), T(0)}, A0[4], b[4], x1[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = W0n[i] * ir0;
+    micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, an);
+    if constexpr (DIM == 2) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] = W0t[i] * ir0;
+        micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, at);
+    }
+    apsi<1, 0, T, DIM>(u, v, xi2, xi4, an, x1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = -x1[i];
+    if constexpr (DIM == 2) {
+        apsi<0, 1, T, DIM>(u, v, xi2, xi4, at, x1);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] -= x1[i];
+    }
+    micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, A0);
+
+    T T0[4], T1[4] = {0, 0, 0, 0}, T2[4];
+    psim<1, 0>(u, v, xi2, T0);
+    apsi<1, 0, T, DIM>(u, v, xi2, xi4, A0, T2);
+
+    // collision time and time coefficients
+    T cF[6], cD[6];
+    if (P.tau_mode == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            F[i] = r0 * T0[i];
+            dF[i] = r0 * T2[i];
+        }
+        return;
+    }
+    const T jump = fabs(pl - pr) / (pl + pr);
+    T s;
+    if (P.tau_mode == 1) s = T(1) / (P.c1 + P.c2 * jump);               // dt / tau
+    else s = P.dt / (P.mu / p0 + P.c2 * jump * P.dt);
+    time_coeffs<T>(s, cF, cD);
+
+    if constexpr (NONEQ) {
+        apsi<2, 0, T, DIM>(u, v, xi2, xi4, an, T1);
+        if constexpr (DIM == 2) {
+            apsi<1, 1, T, DIM>(u, v, xi2, xi4, at, x1);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) T1[i] += x1[i];
+        }
+    }
+    const T dt = P.dt, idt = T(1) / dt;
+    // qF_k = cF_k dt^{p_k - 1}, qD_k = 4 cD_k dt^{p_k - 2}
+    const T qF0 = cF[0], qF1 = cF[1] * dt, qF2 = cF[2] * dt, qF3 = cF[3], qF4 = cF[4] * dt, qF5 = cF[5] * dt;
+    const T qD0 = T(4) * cD[0] * idt, qD1 = T(4) * cD[1], qD2 = T(4) * cD[2], qD3 = T(4) * cD[3] * idt;
+    const T qD4 = T(4) * cD[4], qD5 = T(4) * cD[5];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        F[i] = r0 * (qF0 * T0[i] + qF1 * T1[i] + qF2 * T2[i]) + qF3 * S3[i] + qF4 * S4[i] + qF5 * S5[i];
+        dF[i] = r0 * (qD0 * T0[i] + qD1 * T1[i] + qD2 * T2[i]) + qD3 * S3[i] + qD4 * S4[i] + qD5 * S5[i];
+    }
+    if constexpr (PRFIX) {
+        // Prandtl correction: F_E += (1/Pr - 1) q, q the heat flux relative to
+        // (U0, V0) expanded in raw moments of the same time-dependent f.
+        // Density moments: g0 terms N0 = <psi>, N1 = <(a_n u + a_t v) psi>,
+        // N2 = <A0 psi> = -N1; side terms N3 = W0 / rho, N4, N5 (accumulated).
+        T N0[4], N1[4];
+        psim<0, 0>(u, v, xi2, N0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) N1[i] = -b[i];
+        const T ke = T(0.5) * (U0 * U0 + V0 * V0);
+        const T cf = ke + U0 * U0;
+        T MF[4], MD[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            MF[i] = r0 * (qF0 * N0[i] + (qF1 - qF2) * N1[i]) + qF3 * W0[i] + qF4 * N4[i] + qF5 * N5[i];
+            MD[i] = r0 * (qD0 * N0[i] + (qD1 - qD2) * N1[i]) + qD3 * W0[i] + qD4 * N4[i] + qD5 * N5[i];
+        }
+        const T qh = F[3] - U0 * F[1] - V0 * F[2] + cf * F[0] + U0 * V0 * MF[2] - U0 * MF[3] - U0 * ke * MF[0];
+        const T qd = dF[3] - U0 * dF[1] - V0 * dF[2] + cf * dF[0] + U0 * V0 * MD[2] - U0 * MD[3]
+                   - U0 * ke * MD[0];
+        F[3] += P.prfac * qh;
+        dF[3] += P.prfac * qd;
+    }
+}
+
+}  // namespace gks

@@ -1,0 +1,104 @@
+// gks_host_replica.cu -- host compilations of the per-point device arithmetic
+// (include/gks_host_replica.h), used by unit tests without a GPU.
+#include "../../include/gks_host_replica.h"
+#include "gks_device.cuh"
+
+namespace {
+
+template <typename T>
+int time_coeffs_t(double s, double* cF, double* cD)
+{
+    T f[6], d[6];
+    gks::time_coeffs<T>((T)s, f, d);
+    for (int k = 0; k < 6; ++k) { cF[k] = (double)f[k]; cD[k] = (double)d[k]; }
+    return 0;
+}
+
+template <typename T>
+int teno_t(const double* q, double eps, int qpow, double ct1, double ct2, double* faces, double* gauss)
+{
+    T qq[5];
+    for (int k = 0; k < 5; ++k) qq[k] = (T)q[k];
+    gks::TenoParams P{eps, qpow, ct1, ct2};
+    gks::TenoSel<T> S;
+    gks::teno_select(qq, P, S);
+    T vp, dp, vm, dm;
+    gks::teno_faces(qq, S, vp, dp, vm, dm);
+    faces[0] = vp; faces[1] = dp; faces[2] = vm; faces[3] = dm;
+    T v, d;
+    gks::teno_gauss(S, T(-0.28867513459481288), v, d);
+    gauss[0] = v; gauss[1] = d;
+    gks::teno_gauss(S, T(0.28867513459481288), v, d);
+    gauss[2] = v; gauss[3] = d;
+    return S.large ? 1 : 0;
+}
+
+template <typename T, int DIM, bool NONEQ, bool PRFIX>
+int flux_t(int tau_mode, double gamma, double mu, double Pr, double c1, double c2, double dt,
+           const double* Wl, const double* Wln, const double* Wlt, const double* Wr, const double* Wrn,
+           const double* Wrt, double* F, double* dF)
+{
+    const double K = DIM == 2 ? (5.0 - 3.0 * gamma) / (gamma - 1.0) + 1.0 : (3.0 - gamma) / (gamma - 1.0);
+    gks::FluxParams<T> p;
+    p.gm1 = (T)(gamma - 1.0);
+    p.K = (T)K;
+    p.ntot = (T)(K + DIM);
+    p.dt = (T)dt;
+    p.c1 = (T)c1;
+    p.c2 = (T)c2;
+    p.mu = (T)mu;
+    p.prfac = (T)(1.0 / Pr - 1.0);
+    p.tau_mode = tau_mode;
+    gks::Side<T> L, R;
+    for (int k = 0; k < 4; ++k) {
+        L.W[k] = (T)Wl[k]; L.Wn[k] = (T)Wln[k]; L.Wt[k] = (T)(Wlt ? Wlt[k] : 0.0);
+        R.W[k] = (T)Wr[k]; R.Wn[k] = (T)Wrn[k]; R.Wt[k] = (T)(Wrt ? Wrt[k] : 0.0);
+    }
+    if (DIM == 1) { L.W[2] = L.Wn[2] = L.Wt[2] = R.W[2] = R.Wn[2] = R.Wt[2] = T(0); }
+    T f[4], d[4];
+    gks::point_flux<T, DIM, NONEQ, PRFIX>(L, R, p, f, d);
+    for (int k = 0; k < 4; ++k) { F[k] = (double)f[k]; dF[k] = (double)d[k]; }
+    return 0;
+}
+
+template <typename T, int DIM>
+int flux_dispatch(int tau_mode, double gamma, double mu, double Pr, double c1, double c2, double dt,
+                  const double* Wl, const double* Wln, const double* Wlt, const double* Wr,
+                  const double* Wrn, const double* Wrt, double* F, double* dF)
+{
+    if (tau_mode == 0)
+        return flux_t<T, DIM, false, false>(tau_mode, gamma, mu, Pr, c1, c2, dt, Wl, Wln, Wlt, Wr, Wrn, Wrt, F, dF);
+    if (tau_mode == 2 && Pr != 1.0)
+        return flux_t<T, DIM, true, true>(tau_mode, gamma, mu, Pr, c1, c2, dt, Wl, Wln, Wlt, Wr, Wrn, Wrt, F, dF);
+    return flux_t<T, DIM, true, false>(tau_mode, gamma, mu, Pr, c1, c2, dt, Wl, Wln, Wlt, Wr, Wrn, Wrt, F, dF);
+}
+
+}  // namespace
+
+extern "C" int gks_host_time_coeffs(int precision, double s, double* cF, double* cD)
+{
+    if (!cF || !cD || !(s > 0.0)) return -1;
+    return precision == 1 ? time_coeffs_t<float>(s, cF, cD) : time_coeffs_t<double>(s, cF, cD);
+}
+
+extern "C" int gks_host_teno(int precision, const double* q, double eps, int qpow, double ct1, double ct2,
+                             double* faces, double* gauss)
+{
+    if (!q || !faces || !gauss || qpow < 1) return -1;
+    return precision == 1 ? teno_t<float>(q, eps, qpow, ct1, ct2, faces, gauss)
+                          : teno_t<double>(q, eps, qpow, ct1, ct2, faces, gauss);
+}
+
+extern "C" int gks_host_point_flux(int dim, int precision, int tau_mode, double gamma, double mu, double Pr,
+                                   double c1, double c2, double dt, const double* Wl, const double* Wln,
+                                   const double* Wlt, const double* Wr, const double* Wrn, const double* Wrt,
+                                   double* F, double* dF)
+{
+    if ((dim != 1 && dim != 2) || tau_mode < 0 || tau_mode > 2 || !Wl || !Wln || !Wr || !Wrn || !F || !dF)
+        return -1;
+    if (dim == 2)
+        return precision == 1 ? flux_dispatch<float, 2>(tau_mode, gamma, mu, Pr, c1, c2, dt, Wl, Wln, Wlt, Wr, Wrn, Wrt, F, dF)
+                              : flux_dispatch<double, 2>(tau_mode, gamma, mu, Pr, c1, c2, dt, Wl, Wln, Wlt, Wr, Wrn, Wrt, F, dF);
+    return precision == 1 ? flux_dispatch<float, 1>(tau_mode, gamma, mu, Pr, c1, c2, dt, Wl, Wln, Wlt, Wr, Wrn, Wrt, F, dF)
+                          : flux_dispatch<double, 1>(tau_mode, gamma, mu, Pr, c1, c2, dt, Wl, Wln, Wlt, Wr, Wrn, Wrt, F, dF);
+}

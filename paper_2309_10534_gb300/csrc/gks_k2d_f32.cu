@@ -1,0 +1,44 @@
+// gks_k2d_f32.cu -- instantiations and launcher of the 2-D sweep in float.
+#include "gks_launch.h"
+
+namespace gks {
+
+namespace {
+template <bool NONEQ, bool PRFIX>
+cudaError_t launch_one(const GridDev& g, const SweepArgs& a, const FluxParams<float>& fp, const TenoParams& tn,
+                       const TenoParams& tt, DevState* ds, cudaStream_t st)
+{
+    constexpr int TN = SWEEP_TN, TT = SWEEP_TT;
+    auto kern = k2d_sweep<float, NONEQ, PRFIX, TN, TT>;
+    const size_t smem = sizeof(SweepSmem<float, TN, TT>);
+    dim3 grid((a.nn + TN - 1) / TN, (a.nt + TT - 1) / TT);
+    kern<<<grid, SWEEP_THREADS, smem, st>>>(g, a, fp, tn, tt, ds);
+    return cudaGetLastError();
+}
+template <bool NONEQ, bool PRFIX>
+cudaError_t set_smem()
+{
+    return cudaFuncSetAttribute(k2d_sweep<float, NONEQ, PRFIX, SWEEP_TN, SWEEP_TT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(SweepSmem<float, SWEEP_TN, SWEEP_TT>));
+}
+}  // namespace
+
+cudaError_t prepare_sweep_f32()
+{
+    cudaError_t e = set_smem<false, false>();
+    if (e == cudaSuccess) e = set_smem<true, false>();
+    if (e == cudaSuccess) e = set_smem<true, true>();
+    return e;
+}
+
+cudaError_t launch_sweep_f32(const GridDev& g, const SweepArgs& a, const HostFlux& hf, const TenoParams& tn,
+                             const TenoParams& tt, DevState* ds, cudaStream_t st)
+{
+    const FluxParams<float> fp = make_flux_params<float>(hf);
+    if (hf.tau_mode == 0) return launch_one<false, false>(g, a, fp, tn, tt, ds, st);
+    if (hf.prfac != 0.0 && hf.tau_mode == 2) return launch_one<true, true>(g, a, fp, tn, tt, ds, st);
+    return launch_one<true, false>(g, a, fp, tn, tt, ds, st);
+}
+
+}  // namespace gks

@@ -1,0 +1,403 @@
+// gks_kernels.cuh -- kernels of one S2O4 step of the TENO-D gas-kinetic scheme.
+//
+// Data layout (HBM): conserved variables, float64, SoA with three ghost
+// layers: W[v][j][i], v < nvar, j < gy = ny + 6 (1-D: gy = 1), i < pitch
+// (pitch >= nx + 6, a multiple of 16 doubles).  Interior cell (0, 0) sits at
+// (j, i) = (3, 3) (1-D: i = 3).  Three such arrays live on the device:
+//   W  -- the state W^n (and W^{n+1} after stage 2)
+//   Ws -- the stage state W*
+//   Ac -- the stage accumulator W^n - dt/dx d(F + dt/6 dF)   (Sec. 2.2)
+// Kernels of one step (2-D): ghost(W), sweep-x s1, sweep-y s1, ghost(Ws),
+// sweep-x s2, sweep-y s2 (+ CFL reduction), commit.  1-D: ghost, stage 1,
+// ghost, stage 2, commit.  A sweep computes every face flux of its tile
+// once, in shared memory, so both neighbours of a face apply bit-identical
+// values and the update is conservative.
+#pragma once
+
+#include "gks_device.cuh"
+
+namespace gks {
+
+constexpr int NG = 3;
+
+struct DevState {
+    double t, dt, t_end, cfl;
+    unsigned long long sigma;      // max over cells of the signal rate, as ordered bits
+    unsigned long long fallbacks;  // positivity fallbacks taken
+    long long steps, max_steps;
+    unsigned int err;              // bit 0 non-physical update, bit 1 fallback failed
+    unsigned int done;             // 1: t_end or max_steps reached; kernels return early
+    unsigned int fixed_dt;         // 1: keep dt (caller-given), 0: CFL time step
+    unsigned int pad;
+};
+
+struct GridDev {
+    int dim, nx, ny, pitch, gy;
+    long long plane;   // elements per variable plane = gy * pitch
+    double dx, dy;
+    int bc[4];
+    double gamma, mu;
+};
+
+// ------------------------------------------------------------------ CFL rate
+// sigma = max((|U| + a)/h, 4 nu / h^2), dt = cfl / sigma  (Sec. 5)
+template <typename T>
+__device__ __forceinline__ double cell_sigma(const double* w, int dim, double gamma, double mu, double h,
+                                             unsigned int& err)
+{
+    const double r = w[0];
+    const double U = w[1] / r, V = (dim == 2) ? w[2] / r : 0.0;
+    const double E = w[dim + 1];
+    if constexpr (sizeof(T) == 8) {
+        const double p = (gamma - 1.0) * (E - 0.5 * r * (U * U + V * V));
+        if (!(r > 0.0 && p > 0.0 && isfinite(p))) err |= 1u;
+        const double a = sqrt(gamma * p / r);
+        double s = (sqrt(U * U + V * V) + a) / h;
+        if (mu > 0.0) s = fmax(s, 4.0 * mu / (r * h * h));
+        return s;
+    } else {
+        const float rf = (float)r, Uf = (float)U, Vf = (float)V;
+        const float p = (float)((gamma - 1.0) * (E - 0.5 * r * (U * U + V * V)));
+        if (!(rf > 0.0f && p > 0.0f && isfinite(p))) err |= 1u;
+        const float a = sqrtf((float)gamma * p / rf);
+        float s = (sqrtf(Uf * Uf + Vf * Vf) + a) / (float)h;
+        if (mu > 0.0) s = fmaxf(s, 4.0f * (float)mu / (rf * (float)(h * h)));
+        return (double)s;
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void block_commit_sigma(double s, unsigned int err, unsigned long long nfb,
+                                                   DevState* ds)
+{
+    __shared__ double red_s[NT / 32];
+    __shared__ unsigned int red_e[NT / 32];
+    __shared__ unsigned long long red_f[NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+        err |= __shfl_xor_sync(0xffffffffu, err, o);
+        nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { red_s[w] = s; red_e[w] = err; red_f[w] = nfb; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < NT / 32; ++k) { s = fmax(s, red_s[k]); err |= red_e[k]; nfb += red_f[k]; }
+        if (s > 0.0 || s != s) atomicMax(&ds->sigma, (unsigned long long)__double_as_longlong(s));
+        if (err) atomicOr(&ds->err, err);
+        if (nfb) atomicAdd(&ds->fallbacks, nfb);
+    }
+}
+
+// ------------------------------------------------------------------ 1-D stage
+struct Stage1DArgs {
+    const double* src;   // reconstruction input (W for stage 1, W* for stage 2), ghosts filled
+    double* out0;        // stage 1: W*; stage 2: W (new state)
+    double* out1;        // stage 1: accumulator A; stage 2: unused
+    const double* acc;   // stage 2: accumulator A; stage 1: unused
+    int stage;
+    int with_sigma;      // stage 2: reduce the CFL rate of the new state
+};
+
+template <typename T, bool NONEQ, bool PRFIX, int TN>
+__global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, FluxParams<T> fp, TenoParams tn,
+                                                    DevState* ds)
+{
+    if (ds->done) return;
+    constexpr int NT = TN + 1;
+    const double dt = ds->dt;
+    fp.dt = (T)dt;
+    __shared__ T sq[3][TN + 6];
+    __shared__ T sL[3][2][TN + 1], sR[3][2][TN + 1];  // [var][value, slope][face]
+    __shared__ T sG[2][3][TN + 1];                     // face fluxes for the update
+    const int i0 = blockIdx.x * TN;
+    const int tid = threadIdx.x;
+    const int gx = g.nx + 2 * NG;
+    const int slot[3] = {0, 1, 3};
+
+    for (int k = tid; k < 3 * (TN + 6); k += NT) {
+        const int v = k / (TN + 6), c = k % (TN + 6);
+        const int gi = i0 + c;  // ghosted index of cell i0 - 3 + c
+        sq[v][c] = gi < gx ? (T)a.src[(long long)v * g.plane + gi] : T(0);
+    }
+    __syncthreads();
+    const T idx_ = T(1.0 / g.dx);
+    // phase 1: TENO-D per cell c (interior i0 - 1 + c), both faces
+    for (int c = tid; c < TN + 2; c += NT) {
+        for (int v = 0; v < 3; ++v) {
+            T q[5];
+#pragma unroll
+            for (int s = 0; s < 5; ++s) q[s] = sq[v][c + s];
+            TenoSel<T> S;
+            teno_select(q, tn, S);
+            T vp, dp, vm, dm;
+            teno_faces(q, S, vp, dp, vm, dm);
+            if (c <= TN) { sL[v][0][c] = vp; sL[v][1][c] = dp * idx_; }
+            if (c >= 1) { sR[v][0][c - 1] = vm; sR[v][1][c - 1] = dm * idx_; }
+        }
+    }
+    __syncthreads();
+    // phase 2: flux at face f (between interior i0+f-1 and i0+f)
+    unsigned long long nfb = 0;
+    unsigned int err = 0;
+    for (int f = tid; f <= TN; f += NT) {
+        if (i0 + f > g.nx) continue;  // padding past the last face
+        Side<T> L, R;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { L.W[k] = L.Wn[k] = L.Wt[k] = R.W[k] = R.Wn[k] = R.Wt[k] = T(0); }
+        for (int v = 0; v < 3; ++v) {
+            L.W[slot[v]] = sL[v][0][f];
+            L.Wn[slot[v]] = sL[v][1][f];
+            R.W[slot[v]] = sR[v][0][f];
+            R.Wn[slot[v]] = sR[v][1][f];
+        }
+        if (!physical<T, 1>(L.W, fp.gm1)) {
+            for (int v = 0; v < 3; ++v) { L.W[slot[v]] = sq[v][f + 2]; L.Wn[slot[v]] = T(0); }
+            ++nfb;
+            if (!physical<T, 1>(L.W, fp.gm1)) err |= 2u;
+        }
+        if (!physical<T, 1>(R.W, fp.gm1)) {
+            for (int v = 0; v < 3; ++v) { R.W[slot[v]] = sq[v][f + 3]; R.Wn[slot[v]] = T(0); }
+            ++nfb;
+            if (!physical<T, 1>(R.W, fp.gm1)) err |= 2u;
+        }
+        T F[4], dF[4];
+        point_flux<T, 1, NONEQ, PRFIX>(L, R, fp, F, dF);
+        const T tdt = (T)dt;
+        for (int v = 0; v < 3; ++v) {
+            const int s = slot[v];
+            if (a.stage == 1) {
+                sG[0][v][f] = T(0.5) * F[s] + T(0.125) * tdt * dF[s];
+                sG[1][v][f] = F[s] + tdt * T(1.0 / 6.0) * dF[s];
+            } else {
+                sG[0][v][f] = tdt * T(1.0 / 3.0) * dF[s];
+            }
+        }
+    }
+    __syncthreads();
+    // phase 3: update
+    double sig = 0.0;
+    const double cx = dt / g.dx;
+    for (int c = tid; c < TN; c += NT) {
+        const int i = i0 + c;
+        if (i >= g.nx) continue;
+        const long long o = i + NG;
+        if (a.stage == 1) {
+            for (int v = 0; v < 3; ++v) {
+                const double w = a.src[(long long)v * g.plane + o];
+                a.out0[(long long)v * g.plane + o] = w - cx * (double)(sG[0][v][c + 1] - sG[0][v][c]);
+                a.out1[(long long)v * g.plane + o] = w - cx * (double)(sG[1][v][c + 1] - sG[1][v][c]);
+            }
+        } else {
+            double w[4];
+            for (int v = 0; v < 3; ++v) {
+                const double r = a.acc[(long long)v * g.plane + o] - cx * (double)(sG[0][v][c + 1] - sG[0][v][c]);
+                a.out0[(long long)v * g.plane + o] = r;
+                w[v] = r;
+            }
+            if (a.with_sigma) sig = fmax(sig, cell_sigma<T>(w, 1, g.gamma, g.mu, g.dx, err));
+        }
+    }
+    if (NT % 32 == 0) block_commit_sigma<NT>(sig, err, nfb, ds);
+}
+
+// ------------------------------------------------------------------ 2-D sweep
+struct SweepArgs {
+    const double* src;   // reconstruction input (W or W*), ghosts filled
+    const double* base;  // first sweep: W (stage 1) or A (stage 2); second sweep: ignored
+    double* out0;        // stage 1: W*; stage 2: W
+    double* out1;        // stage 1: A
+    int stage, pass;     // pass 0: x sweep (first), 1: y sweep (second)
+    int dirn;            // 0: faces normal to x, 1: faces normal to y
+    int nn, nt;          // cells along the normal / tangential direction
+    long long sn, st;    // element strides along normal / tangential
+    double hn, ht;       // cell sizes along normal / tangential
+    int with_sigma;
+};
+
+template <typename T, int TN, int TT> struct SweepSmem {
+    T w[4][TT + 4][TN + 6];           // cells: tangential rows t0-2.., normal n0-3..
+    T rec[4][4][TT + 4][TN + 1];      // [vL, sL, vR, sR][var][row][face]
+    T gp[24][TT * (TN + 1)][2];       // Gauss-point states [quantity][pair][gp]
+};
+
+template <typename T, bool NONEQ, bool PRFIX, int TN, int TT>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4) ? 2 : 1)
+k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoParams tnn, TenoParams tnt, DevState* ds)
+{
+    if (ds->done) return;
+    constexpr int NT = 256;
+    constexpr int NF = TN + 1;           // faces per tile row
+    constexpr int NP = TT * NF;          // (face, row) pairs
+    static_assert(NP == NT, "one (face,row) pair per thread");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SweepSmem<T, TN, TT>& sm = *reinterpret_cast<SweepSmem<T, TN, TT>*>(smem_raw);
+    T* sF = &sm.rec[0][0][0][0];         // reused after the Gauss-point phase: [k][row][face]
+
+    const double dt = ds->dt;
+    fp.dt = (T)dt;
+    const int tid = threadIdx.x;
+    const int n0 = blockIdx.x * TN, t0 = blockIdx.y * TT;
+    const int perm[4] = {0, a.dirn == 0 ? 1 : 2, a.dirn == 0 ? 2 : 1, 3};
+    const long long org = (long long)NG * g.pitch + NG;  // interior (0,0)
+
+    // load cells (normal n0-3 .. n0+TN+2, tangential t0-2 .. t0+TT+1); the
+    // thread index runs fastest along the unit-stride direction
+    {
+        constexpr int CN = TN + 6, CT = TT + 4, NCELL = CN * CT;
+        for (int k = tid; k < 4 * NCELL; k += NT) {
+            const int v = k / NCELL, e = k % NCELL;
+            int cn, ct;
+            if (a.dirn == 0) { ct = e / CN; cn = e % CN; } else { cn = e / CT; ct = e % CT; }
+            const int in = n0 - 3 + cn, it = t0 - 2 + ct;
+            T val = T(0);
+            if (in < a.nn + 3 && it < a.nt + 2)  // ghosted extent (negative side is covered by ghosts)
+                val = (T)a.src[(long long)perm[v] * g.plane + org + in * a.sn + it * a.st];
+            sm.w[v][ct][cn] = val;
+        }
+    }
+    __syncthreads();
+
+    // phase 1: normal TENO-D per (cell, row, var): cell c <-> normal n0-1+c
+    {
+        const T ih = T(1.0 / a.hn);
+        constexpr int NC = TN + 2, NR = TT + 4;
+        for (int k = tid; k < 4 * NC * NR; k += NT) {
+            const int v = k / (NC * NR), e = k % (NC * NR);
+            const int r = e / NC, c = e % NC;
+            T q[5];
+#pragma unroll
+            for (int s = 0; s < 5; ++s) q[s] = sm.w[v][r][c + s];
+            TenoSel<T> S;
+            teno_select(q, tnn, S);
+            T vp, dp, vm, dm;
+            teno_faces(q, S, vp, dp, vm, dm);
+            if (c <= TN) { sm.rec[0][v][r][c] = vp; sm.rec[1][v][r][c] = dp * ih; }
+            if (c >= 1) { sm.rec[2][v][r][c - 1] = vm; sm.rec[3][v][r][c - 1] = dm * ih; }
+        }
+    }
+    __syncthreads();
+
+    // phase 2a: tangential TENO-D of the line averages to the two Gauss points
+    {
+        const int r = tid / NF, f = tid % NF;  // pair = tid
+        const T ih = T(1.0 / a.ht);
+        const T g0 = T(-0.28867513459481288), g1 = T(0.28867513459481288);  // -+1/(2 sqrt 3)
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                T q[5];
+                TenoSel<T> S;
+                T va, da, vb, db;
+#pragma unroll
+                for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * side][v][r + s][f];
+                teno_select(q, tnt, S);
+                teno_gauss(S, g0, va, da);
+                teno_gauss(S, g1, vb, db);
+                sm.gp[12 * side + v][tid][0] = va;
+                sm.gp[12 * side + v][tid][1] = vb;
+                sm.gp[12 * side + 8 + v][tid][0] = da * ih;
+                sm.gp[12 * side + 8 + v][tid][1] = db * ih;
+#pragma unroll
+                for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * side + 1][v][r + s][f];
+                teno_select(q, tnt, S);
+                teno_gauss(S, g0, va, da);
+                teno_gauss(S, g1, vb, db);
+                sm.gp[12 * side + 4 + v][tid][0] = va;
+                sm.gp[12 * side + 4 + v][tid][1] = vb;
+            }
+        }
+    }
+    __syncthreads();
+
+    // phase 2b: merge + flux at each Gauss point; thread pairs hold the two
+    // Gauss points of one face segment and average them (weights 1/2)
+    unsigned long long nfb = 0;
+    unsigned int err = 0;
+    const T tdt = (T)dt;
+    for (int task = tid; task < 2 * NP; task += NT) {
+        const int pair = task >> 1, gpi = task & 1;
+        const int r = pair / NF, f = pair % NF;
+        // faces n0+f <= nn on rows t0+r < nt exist; the rest of the tile is padding
+        const bool valid = (n0 + f <= a.nn) && (t0 + r < a.nt);
+        Side<T> L, R;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            L.W[v] = sm.gp[v][pair][gpi];
+            L.Wn[v] = sm.gp[4 + v][pair][gpi];
+            L.Wt[v] = sm.gp[8 + v][pair][gpi];
+            R.W[v] = sm.gp[12 + v][pair][gpi];
+            R.Wn[v] = sm.gp[16 + v][pair][gpi];
+            R.Wt[v] = sm.gp[20 + v][pair][gpi];
+        }
+        T F[4] = {T(0), T(0), T(0), T(0)}, dF[4] = {T(0), T(0), T(0), T(0)};
+        if (valid) {
+            if (!physical<T, 2>(L.W, fp.gm1)) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) { L.W[v] = sm.w[v][r + 2][f + 2]; L.Wn[v] = L.Wt[v] = T(0); }
+                ++nfb;
+                if (!physical<T, 2>(L.W, fp.gm1)) err |= 2u;
+            }
+            if (!physical<T, 2>(R.W, fp.gm1)) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) { R.W[v] = sm.w[v][r + 2][f + 3]; R.Wn[v] = R.Wt[v] = T(0); }
+                ++nfb;
+                if (!physical<T, 2>(R.W, fp.gm1)) err |= 2u;
+            }
+            point_flux<T, 2, NONEQ, PRFIX>(L, R, fp, F, dF);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            F[v] = T(0.5) * (F[v] + __shfl_xor_sync(0xffffffffu, F[v], 1));
+            dF[v] = T(0.5) * (dF[v] + __shfl_xor_sync(0xffffffffu, dF[v], 1));
+        }
+        if (gpi == 0) {  // rec was last read before the barrier ending phase 2a
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                if (a.stage == 1) {
+                    sF[(v * TT + r) * NF + f] = T(0.5) * F[v] + T(0.125) * tdt * dF[v];
+                    sF[((4 + v) * TT + r) * NF + f] = F[v] + tdt * T(1.0 / 6.0) * dF[v];
+                } else {
+                    sF[(v * TT + r) * NF + f] = tdt * T(1.0 / 3.0) * dF[v];
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // phase 3: flux divergence into the float64 state
+    double sig = 0.0;
+    const double cn = dt / a.hn;
+    const double h = fmin(g.dx, g.dy);
+    if (tid < TN * TT) {
+        const int r = tid / TN, c = tid % TN;
+        const int in = n0 + c, it = t0 + r;
+        if (in < a.nn && it < a.nt) {
+            const long long o = org + in * a.sn + it * a.st;
+            double wn[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const long long go = (long long)perm[v] * g.plane + o;
+                const double d0 = (double)(sF[(v * TT + r) * NF + c + 1] - sF[(v * TT + r) * NF + c]);
+                if (a.stage == 1) {
+                    const double d1 = (double)(sF[((4 + v) * TT + r) * NF + c + 1] - sF[((4 + v) * TT + r) * NF + c]);
+                    const double b0 = a.pass == 0 ? a.base[go] : a.out0[go];
+                    const double b1 = a.pass == 0 ? a.base[go] : a.out1[go];
+                    a.out0[go] = b0 - cn * d0;
+                    a.out1[go] = b1 - cn * d1;
+                } else {
+                    const double b0 = a.pass == 0 ? a.base[go] : a.out0[go];
+                    const double res = b0 - cn * d0;
+                    a.out0[go] = res;
+                    wn[perm[v]] = res;
+                }
+            }
+            if (a.with_sigma) sig = cell_sigma<T>(wn, 2, g.gamma, g.mu, h, err);
+        }
+    }
+    block_commit_sigma<NT>(sig, err, nfb, ds);
+}
+
+}  // namespace gks

@@ -1,0 +1,50 @@
+// gks_launch.h -- host-side launchers of the stage kernels, one translation
+// unit per precision so the heavy instantiations compile in parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "gks_kernels.cuh"
+
+namespace gks {
+
+// tile of the 2-D sweep: TN cells along the face normal (TN + 1 faces) x TT rows
+constexpr int SWEEP_TN = 31;
+constexpr int SWEEP_TT = 8;
+constexpr int SWEEP_THREADS = 256;
+// cells per block of the 1-D stage (TN + 1 threads, one per face)
+constexpr int STAGE1D_TN = 127;
+
+struct HostFlux {
+    double gamma, K, ntot, c1, c2, mu, prfac;
+    int tau_mode;
+};
+
+cudaError_t launch_sweep_f32(const GridDev& g, const SweepArgs& a, const HostFlux& hf, const TenoParams& tn,
+                             const TenoParams& tt, DevState* ds, cudaStream_t st);
+cudaError_t launch_sweep_f64(const GridDev& g, const SweepArgs& a, const HostFlux& hf, const TenoParams& tn,
+                             const TenoParams& tt, DevState* ds, cudaStream_t st);
+// raise the dynamic shared-memory limit of every 2-D sweep instantiation
+// (current device); call once before the first launch
+cudaError_t prepare_sweep_f32();
+cudaError_t prepare_sweep_f64();
+cudaError_t launch_stage1d(int fp32, const GridDev& g, const Stage1DArgs& a, const HostFlux& hf,
+                           const TenoParams& tn, DevState* ds, cudaStream_t st);
+
+template <typename T>
+inline FluxParams<T> make_flux_params(const HostFlux& h)
+{
+    FluxParams<T> p;
+    p.gm1 = (T)(h.gamma - 1.0);
+    p.K = (T)h.K;
+    p.ntot = (T)h.ntot;
+    p.dt = (T)0;
+    p.c1 = (T)h.c1;
+    p.c2 = (T)h.c2;
+    p.mu = (T)h.mu;
+    p.prfac = (T)h.prfac;
+    p.tau_mode = h.tau_mode;
+    return p;
+}
+
+}  // namespace gks

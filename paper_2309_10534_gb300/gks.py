@@ -1,0 +1,312 @@
+"""ctypes binding of libgks.so (include/gks.h): the same entry points, plus a
+small ``Solver`` class that only marshals arguments.
+
+Every computation runs in the CUDA library; there is no CPU path.  Loading
+fails loudly when ``libgks.so`` has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgks.so")
+
+GKS_OK, GKS_EINVAL, GKS_ENOMEM, GKS_ECUDA, GKS_ENONPHYSICAL, GKS_ETIMEOUT, GKS_EUNSUPPORTED = range(7)
+BC = {"periodic": 0, "zerograd": 1, "symmetry": 2, "noslip": 3, "reflect": 4}
+PRECISION = {"fp64": 0, "fp32": 1}
+TAU = {"zero": 0, "euler": 1, "ns": 2}
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
+                ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
+                ("bc", C.c_int * 4), ("precision", C.c_int)]
+
+
+class Gas(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("mu", C.c_double), ("Pr", C.c_double)]
+
+
+class Scheme(C.Structure):
+    _fields_ = [("cfl", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
+                ("ct1", C.c_double), ("ct2", C.c_double), ("ct1_t", C.c_double), ("ct2_t", C.c_double),
+                ("eps", C.c_double), ("q", C.c_int), ("tau_mode", C.c_int),
+                ("positivity_fallback", C.c_int)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("error_word", C.c_uint), ("fallbacks", C.c_longlong), ("t", C.c_double),
+                ("steps", C.c_longlong), ("dt", C.c_double)]
+
+
+class FlopModel(C.Structure):
+    _fields_ = [("flops_per_cell_update", C.c_double), ("flops_per_cell_sweep", C.c_double),
+                ("transcendentals_per_cell_update", C.c_double), ("divides_per_cell_update", C.c_double),
+                ("sqrt_per_cell_update", C.c_double), ("fp64_flops_per_cell_update", C.c_double)]
+
+
+class GKSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d): %s" % (_status_string(status), status, msg))
+        self.status = status
+
+
+_lib = None
+_vp = C.c_void_p
+_dp = C.POINTER(C.c_double)
+
+
+def lib():
+    """Load libgks.so; raises if it is missing (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libgks.so is not built (run paper_2309_10534_gb300/build.py)")
+        L = C.CDLL(LIB_PATH)
+        sig = {
+            "gks_create": ([C.POINTER(GridDesc), C.POINTER(_vp)], C.c_int),
+            "gks_destroy": ([_vp], None),
+            "gks_set_gas": ([_vp, C.POINTER(Gas)], C.c_int),
+            "gks_set_scheme": ([_vp, C.POINTER(Scheme)], C.c_int),
+            "gks_set_stream": ([_vp, _vp], C.c_int),
+            "gks_set_state": ([_vp, _vp, C.c_int], C.c_int),
+            "gks_get_state": ([_vp, _vp, C.c_int], C.c_int),
+            "gks_get_buffer": ([_vp, C.c_int, _vp, C.c_int], C.c_int),
+            "gks_compute_dt": ([_vp, _dp], C.c_int),
+            "gks_stage": ([_vp, C.c_int, C.c_double], C.c_int),
+            "gks_step": ([_vp, C.c_double], C.c_int),
+            "gks_advance_to": ([_vp, C.c_double, C.c_longlong, C.POINTER(C.c_longlong), _dp], C.c_int),
+            "gks_get_diagnostics": ([_vp, C.POINTER(Diag)], C.c_int),
+            "gks_last_error": ([_vp], C.c_char_p),
+            "gks_status_string": ([C.c_int], C.c_char_p),
+            "gks_kernel_launches": ([_vp], C.c_longlong),
+            "gks_profile_enable": ([_vp, C.c_int], C.c_int),
+            "gks_profile_read": ([_vp, C.c_int, C.POINTER(C.c_longlong), _dp], C.c_int),
+            "gks_count_flops": ([C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(FlopModel)], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _status_string(s):
+    try:
+        return lib().gks_status_string(s).decode()
+    except Exception:  # pragma: no cover - only when the library is absent
+        return "status"
+
+
+def default_scheme(**kw) -> Scheme:
+    s = Scheme(cfl=0.5, c1=0.01, c2=1.0, ct1=1e-7, ct2=1e-5, ct1_t=1e-7, ct2_t=1e-5, eps=1e-40, q=7,
+               tau_mode=TAU["euler"], positivity_fallback=1)
+    for k, v in kw.items():
+        if k == "tau" or k == "tau_mode":
+            v = TAU[v] if isinstance(v, str) else int(v)
+            k = "tau_mode"
+        setattr(s, k, v)
+    if "ct1" in kw and "ct1_t" not in kw:
+        s.ct1_t = kw["ct1"]
+    if "ct2" in kw and "ct2_t" not in kw:
+        s.ct2_t = kw["ct2"]
+    return s
+
+
+class Solver:
+    """One grid context.  Arrays: conserved variables, float64,
+    [nvar][ny][nx] (1-D: [3][1][nx] or [3][nx]); numpy (host) or a CUDA
+    torch tensor (device, passed by data_ptr)."""
+
+    def __init__(self, dim, nx, ny=1, *, lx=1.0, ly=1.0, bc=("zerograd",) * 4, precision="fp64",
+                 gamma=1.4, mu=0.0, Pr=1.0, tau="euler", cfl=0.5, **scheme):
+        L = lib()
+        d = GridDesc()
+        d.dim, d.nx, d.ny = dim, nx, (ny if dim == 2 else 1)
+        d.x0, d.x1, d.y0, d.y1 = 0.0, lx, 0.0, (ly if dim == 2 else 1.0)
+        for k in range(4):
+            d.bc[k] = BC[bc[k]] if isinstance(bc[k], str) else int(bc[k])
+        d.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        h = _vp()
+        self._check(L.gks_create(C.byref(d), C.byref(h)), None)
+        self.h = h
+        self.dim, self.nx, self.ny = dim, nx, d.ny
+        self.nvar = dim + 2
+        self.set_gas(gamma=gamma, mu=mu, Pr=Pr)
+        self.set_scheme(cfl=cfl, tau=tau, **scheme)
+
+    # -- plumbing
+    def _check(self, status, h="self"):
+        if status != GKS_OK:
+            handle = self.h if h == "self" else h
+            msg = lib().gks_last_error(handle).decode() if handle else ""
+            raise GKSError(status, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gks_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.nvar, self.ny, self.nx)
+
+    def _host(self, W):
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        if W.size != self.nvar * self.ny * self.nx:
+            raise ValueError("state has %d values, expected %d" % (W.size, self.nvar * self.ny * self.nx))
+        return W
+
+    # -- API
+    def set_gas(self, gamma=1.4, mu=0.0, Pr=1.0):
+        self._check(lib().gks_set_gas(self.h, C.byref(Gas(gamma, mu, Pr))))
+
+    def set_scheme(self, **kw):
+        self._check(lib().gks_set_scheme(self.h, C.byref(default_scheme(**kw))))
+
+    def set_stream(self, stream_handle: int):
+        self._check(lib().gks_set_stream(self.h, _vp(stream_handle)))
+
+    def set_state(self, W):
+        if hasattr(W, "data_ptr"):  # torch tensor on the device
+            self._check(lib().gks_set_state(self.h, _vp(W.data_ptr()), 1))
+        else:
+            W = self._host(W)
+            self._check(lib().gks_set_state(self.h, W.ctypes.data_as(_vp), 0))
+
+    def get_state(self, out=None):
+        if out is not None and hasattr(out, "data_ptr"):
+            self._check(lib().gks_get_state(self.h, _vp(out.data_ptr()), 1))
+            return out
+        W = np.empty(self.shape)
+        self._check(lib().gks_get_state(self.h, W.ctypes.data_as(_vp), 0))
+        return W
+
+    def get_state_into(self, out):
+        """Copy the state into a caller-owned contiguous float64 host array."""
+        if not (out.dtype == np.float64 and out.flags.c_contiguous and out.size == self.nvar * self.ny * self.nx):
+            raise ValueError("need a contiguous float64 array of the state's size")
+        self._check(lib().gks_get_state(self.h, out.ctypes.data_as(_vp), 0))
+        return out
+
+    def get_buffer(self, which):
+        W = np.empty(self.shape)
+        self._check(lib().gks_get_buffer(self.h, int(which), W.ctypes.data_as(_vp), 0))
+        return W
+
+    def compute_dt(self):
+        dt = C.c_double(0.0)
+        self._check(lib().gks_compute_dt(self.h, C.byref(dt)))
+        return dt.value
+
+    def stage(self, stage, dt):
+        self._check(lib().gks_stage(self.h, int(stage), float(dt)))
+
+    def step(self, dt=0.0):
+        self._check(lib().gks_step(self.h, float(dt)))
+
+    def advance_to(self, t_end, max_steps=0):
+        n = C.c_longlong(0)
+        t = C.c_double(0.0)
+        self._check(lib().gks_advance_to(self.h, float(t_end), int(max_steps), C.byref(n), C.byref(t)))
+        return n.value, t.value
+
+    def diagnostics(self):
+        d = Diag()
+        self._check(lib().gks_get_diagnostics(self.h, C.byref(d)))
+        return d
+
+    def kernel_launches(self):
+        return lib().gks_kernel_launches(self.h)
+
+    def profile(self, enable=True):
+        """Record CUDA events around every directly launched kernel."""
+        self._check(lib().gks_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_read(self, kind=0):
+        """(launches, total ms) of kernel kind 0 stage, 1 ghost, 2 other; clears."""
+        n = C.c_longlong(0)
+        ms = C.c_double(0.0)
+        self._check(lib().gks_profile_read(self.h, int(kind), C.byref(n), C.byref(ms)))
+        return n.value, ms.value
+
+
+def count_flops(dim, precision="fp32", tau="euler", Pr=1.0):
+    """Algorithmic operation count of the library's stage arithmetic per cell."""
+    m = FlopModel()
+    st = lib().gks_count_flops(int(dim), PRECISION[precision] if isinstance(precision, str) else int(precision),
+                               TAU[tau] if isinstance(tau, str) else int(tau), float(Pr), C.byref(m))
+    if st != GKS_OK:
+        raise GKSError(st, "gks_count_flops")
+    return {k: getattr(m, k) for k, _ in FlopModel._fields_}
+
+
+def solver_for(setup, precision="fp64", **kw) -> Solver:
+    """Solver configured from a ``workloads.Setup``."""
+    args = dict(lx=setup.lx, ly=setup.ly, bc=setup.bc, precision=precision, gamma=setup.gamma,
+                mu=setup.mu, Pr=setup.Pr, tau=setup.tau, cfl=setup.cfl)
+    args.update(kw)
+    s = Solver(setup.dim, setup.nx, setup.ny, **args)
+    s.set_state(setup.W)
+    return s
+
+
+# ---------------------------------------------------------------- host replicas
+def _replica():
+    L = lib()
+    if not getattr(L, "_replica_declared", False):
+        L.gks_host_time_coeffs.argtypes = [C.c_int, C.c_double, _dp, _dp]
+        L.gks_host_teno.argtypes = [C.c_int, _dp, C.c_double, C.c_int, C.c_double, C.c_double, _dp, _dp]
+        L.gks_host_point_flux.argtypes = [C.c_int, C.c_int, C.c_int] + [C.c_double] * 6 + [_dp] * 8
+        for f in (L.gks_host_time_coeffs, L.gks_host_teno, L.gks_host_point_flux):
+            f.restype = C.c_int
+        L._replica_declared = True
+    return L
+
+
+def _arr(a, n):
+    x = np.zeros(n) if a is None else np.ascontiguousarray(a, dtype=np.float64)
+    return x, x.ctypes.data_as(_dp)
+
+
+def host_time_coeffs(s, precision="fp64"):
+    """Folded time coefficients (cF, cD) from the host build of the device code."""
+    cF, pF = _arr(None, 6)
+    cD, pD = _arr(None, 6)
+    if _replica().gks_host_time_coeffs(PRECISION[precision], float(s), pF, pD):
+        raise ValueError("bad argument")
+    return cF, cD
+
+
+def host_teno(q, precision="fp64", eps=1e-40, q_pow=7, ct1=1e-7, ct2=1e-5):
+    """(faces[vp, dp, vm, dm], gauss[v-, d-, v+, d+], large) for one stencil."""
+    qq, pq = _arr(q, 5)
+    f, pf = _arr(None, 4)
+    g, pg = _arr(None, 4)
+    r = _replica().gks_host_teno(PRECISION[precision], pq, eps, q_pow, ct1, ct2, pf, pg)
+    if r < 0:
+        raise ValueError("bad argument")
+    return f, g, bool(r)
+
+
+def host_point_flux(dim, Wl, Wln, Wlt, Wr, Wrn, Wrt, dt, precision="fp64", tau="euler", gamma=1.4,
+                    mu=0.0, Pr=1.0, c1=0.01, c2=1.0):
+    """(F, dF/dt) at one point from the host build of the device code; 4 slots."""
+    keep = [_arr(a, 4) for a in (Wl, Wln, Wlt, Wr, Wrn, Wrt)]
+    F, pF = _arr(None, 4)
+    dF, pD = _arr(None, 4)
+    r = _replica().gks_host_point_flux(dim, PRECISION[precision], TAU[tau] if isinstance(tau, str) else tau,
+                                       gamma, mu, Pr, c1, c2, dt, *[k[1] for k in keep], pF, pD)
+    if r:
+        raise ValueError("bad argument")
+    return F, dF

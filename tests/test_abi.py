@@ -1,0 +1,70 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, and
+exports every entry point include/gks.h declares.  No compute calls."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gks.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gks_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2309_10534_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("gks_create", "gks_destroy", "gks_set_gas", "gks_set_scheme", "gks_set_stream",
+                 "gks_set_state", "gks_get_state", "gks_compute_dt", "gks_stage", "gks_step",
+                 "gks_advance_to", "gks_get_diagnostics", "gks_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.gks_status_string.restype = ctypes.c_char_p
+    assert lib.gks_status_string(0) == b"ok"
+    assert lib.gks_status_string(4) == b"non-physical state"
+
+
+def test_create_rejects_bad_descriptors_before_touching_the_device(libpath):
+    from paper_2309_10534_gb300 import gks
+    L = gks.lib()
+    d = gks.GridDesc()
+    d.dim, d.nx, d.ny = 3, 10, 10  # bad dim
+    d.x0, d.x1, d.y0, d.y1 = 0, 1, 0, 1
+    h = ctypes.c_void_p()
+    assert L.gks_create(ctypes.byref(d), ctypes.byref(h)) == gks.GKS_EINVAL
+    d.dim, d.nx = 2, 2  # too few cells
+    assert L.gks_create(ctypes.byref(d), ctypes.byref(h)) == gks.GKS_EINVAL
+    d.nx = 10
+    d.bc[0], d.bc[1] = 0, 1  # periodic on one side only
+    assert L.gks_create(ctypes.byref(d), ctypes.byref(h)) == gks.GKS_EINVAL
+    assert L.gks_create(None, ctypes.byref(h)) == gks.GKS_EINVAL
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2309_10534_gb300 import gks
+    monkeypatch.setattr(gks, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(gks, "_lib", None)
+    with pytest.raises(ImportError):
+        gks.lib()

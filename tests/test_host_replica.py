@@ -1,0 +1,103 @@
+"""The library's per-point device arithmetic, compiled for the host, against
+the FP64 oracle and high-precision quadrature (CPU only; the GPU parity tests
+check the kernels themselves)."""
+import shutil
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+mp = pytest.importorskip("mpmath")
+
+
+@pytest.fixture(scope="module")
+def G():
+    import os
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2309_10534_gb300 import build, gks
+    build.build()
+    return gks
+
+
+def _phi(k, x):
+    e = mp.e ** (-x)
+    return [x - 1 + e, 2 - x - (x + 2) * e, x * x / 2 - x + 1 - e, 1 - e, -2 + (x + 2) * e, -(1 - e)][k]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 2e-15), ("fp32", 3e-7)])
+def test_time_coefficients_all_branches(G, precision, tol):
+    """Folded coefficients (Sec. 2.2 applied to the integrals of Eq. 2.5)
+    against 50-digit evaluation, across the series / closed-form switch."""
+    mp.mp.dps = 50
+    p = [1, 2, 2, 1, 2, 2]
+    for s in [1e-4, 3e-3, 0.05, 0.24, 0.26, 0.7, 0.99, 1.01, 1.5, 1.99, 2.01, 3.0, 10.0, 99.0, 1e3]:
+        cF, cD = G.host_time_coeffs(s, precision)
+        S = mp.mpf(s)
+        for k in range(6):
+            eF = (4 * _phi(k, S / 2) - _phi(k, S)) / S ** p[k]
+            eD = (_phi(k, S) - 2 * _phi(k, S / 2)) / S ** p[k]
+            scale = max(abs(eF), abs(eD), 1)
+            assert abs(cF[k] - eF) / scale < tol, (s, k, "F", cF[k], float(eF))
+            assert abs(cD[k] - eD) / scale < tol, (s, k, "D", cD[k], float(eD))
+
+
+def test_teno_matches_oracle(G):
+    rng = np.random.default_rng(3)
+    xs = [0.5, -0.5, -0.5 / np.sqrt(3), 0.5 / np.sqrt(3)]
+    cases = [np.sin(0.3 * np.arange(5) + ph) + 2 for ph in rng.uniform(0, 6, 10)]
+    cases += [rng.normal(size=5) for _ in range(30)]
+    cases += [np.where(np.arange(5) < k, 1.0, 0.2) + 0.01 * rng.normal(size=5) for k in range(1, 5)]
+    cases += [np.array([3.0] * 5), np.array([1.0, 1.0, 1.0, 2.0, 3.0])]
+    for q in cases:
+        val, dval, large, _ = O.teno_d(q, xs)
+        faces, gauss, glarge = G.host_teno(q)
+        assert glarge == large, q
+        assert np.allclose(faces, [val[0], dval[0], val[1], dval[1]], rtol=0, atol=1e-13), q
+        assert np.allclose(gauss, [val[2], dval[2], val[3], dval[3]], rtol=0, atol=1e-13), q
+        f32, g32, l32 = G.host_teno(q, "fp32")
+        if l32 == large:
+            assert np.allclose(f32, faces, rtol=0, atol=2e-5 * (1 + abs(q).max()))
+
+
+def _state(dim, rng, rho=None):
+    r = rho if rho is not None else np.exp(rng.uniform(-0.5, 0.5))
+    U, V = rng.uniform(-0.8, 0.8, 2)
+    p = np.exp(rng.uniform(-0.5, 0.5))
+    E = p / 0.4 + 0.5 * r * (U * U + (V * V if dim == 2 else 0))
+    return np.array([r, r * U, r * V if dim == 2 else 0.0, E])
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("tau,Pr", [("zero", 1.0), ("euler", 1.0), ("ns", 1.0), ("ns", 0.73)])
+def test_point_flux_matches_oracle(G, dim, tau, Pr):
+    """F and dF/dt of one point: the device arithmetic (closed-form slopes,
+    folded time coefficients) against the oracle (moment-matrix solves,
+    F(dt) and F(dt/2) combined as Sec. 2.2 prints)."""
+    rng = np.random.default_rng(7 + dim)
+    P = O.make_problem(dim, 8, 8, tau=tau, mu=0.02, Pr=Pr)
+    sl = [0, 1, 2, 3] if dim == 2 else [0, 1, 3]
+    for trial in range(12):
+        Wl, Wr = _state(dim, rng), _state(dim, rng)
+        Wln, Wlt, Wrn, Wrt = (0.3 * rng.normal(size=4) for _ in range(4))
+        if dim == 1:
+            for a in (Wln, Wlt, Wrn, Wrt):
+                a[2] = 0.0
+            Wlt[:] = 0
+            Wrt[:] = 0
+        dt = 10 ** rng.uniform(-4, -2)
+        Fd, Fh, rc = O.flux_point(P, Wl[sl], Wln[sl], Wlt[sl] if dim == 2 else None, Wr[sl], Wrn[sl],
+                                  Wrt[sl] if dim == 2 else None, dt)
+        assert rc == 0
+        Fo = (4 * Fh - Fd) / dt
+        dFo = 4 * (Fd - 2 * Fh) / dt ** 2
+        F, dF = G.host_point_flux(dim, Wl, Wln, Wlt, Wr, Wrn, Wrt, dt, tau=tau, mu=0.02, Pr=Pr)
+        scale = np.abs(Fo).max()
+        assert np.allclose(F[sl], Fo, rtol=0, atol=1e-12 * scale), (trial, F[sl], Fo)
+        # the oracle's dF/dt is a difference of two time integrals: its own
+        # rounding is ~ eps |F| / dt
+        assert np.allclose(dF[sl], dFo, rtol=1e-9, atol=1e-13 * scale / dt), (trial, dF[sl], dFo)
+        F32, dF32 = G.host_point_flux(dim, Wl, Wln, Wlt, Wr, Wrn, Wrt, dt, precision="fp32", tau=tau,
+                                      mu=0.02, Pr=Pr)
+        assert np.allclose(F32[sl], Fo, rtol=0, atol=3e-6 * scale)
