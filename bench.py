@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--fp64-steps", type=int, default=3)
     p.add_argument("--cpu-sample", type=int, default=96, help="grid of the oracle's bounded sample")
+    p.add_argument("--skip-cpu", action="store_true", help="omit the CPU-oracle baseline (profiling runs)")
     return p.parse_args()
 
 
@@ -312,7 +313,7 @@ def main():
         "flops_per_cell_update": fm["flops_per_cell_update"],
         "clocks": clk,
     }
-    if world == 1:
+    if world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(n=args.cpu_sample)
     print(json.dumps(line))
     if dist:
