@@ -164,6 +164,36 @@ typedef struct {
 } gks_flop_model;
 gks_status gks_count_flops(int dim, int precision, int tau_mode, double Pr, gks_flop_model *out);
 
+/* ---- allocation-free 1-D step (the paper has no counterpart) ---- */
+
+/* Largest grid gks_step1d_noalloc accepts. */
+#define GKS_NOALLOC_MAX_NX 16384
+
+/* One S2O4 step of a 1-D problem that allocates no device memory, for
+ * callers that cannot call cudaMalloc: a host whose device memory belongs to
+ * another allocator (a framework's caching allocator or a fixed budget) or a
+ * latency-critical loop that cannot take cudaMalloc's implicit device-wide
+ * synchronisation.  It computes what gks_create + gks_set_state + gks_step(dt)
+ * would, without a context.
+ *   W_in, W_out: caller-owned device arrays, conserved variables [3][nx]
+ *                float64 (rho, rho U, rho E); may not overlap.
+ *   dx > 0, dt > 0 (no CFL choice here), bc[2] = x-low, x-high (gks_bc),
+ *   gas and scheme as for gks_set_gas / gks_set_scheme, precision as gks_grid_desc.
+ *   stream: cudaStream_t or NULL; the call synchronises it before returning.
+ *   error_word (may be NULL): the step's error word (see gks_diag).
+ * Working buffers live in one file-scope static device array sized for
+ * GKS_NOALLOC_MAX_NX cells (about 1.6 MB on every GPU that loads the
+ * library, kept until the process exits).  nx > GKS_NOALLOC_MAX_NX returns
+ * GKS_EUNSUPPORTED; bad arguments GKS_EINVAL; a non-physical result
+ * GKS_ENONPHYSICAL.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call reuses the same array and
+ * resets what must start at zero, so calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller. */
+gks_status gks_step1d_noalloc(const double *W_in, double *W_out, int nx, double dx, const int *bc,
+                              const gks_gas *gas, const gks_scheme *scheme, int precision, double dt,
+                              void *stream, unsigned int *error_word);
+
 #ifdef __cplusplus
 }
 #endif

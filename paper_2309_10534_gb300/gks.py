@@ -310,3 +310,26 @@ def host_point_flux(dim, Wl, Wln, Wlt, Wr, Wrn, Wrt, dt, precision="fp64", tau="
     if r:
         raise ValueError("bad argument")
     return F, dF
+
+
+def step1d_noalloc(W_in, W_out, dx, dt, bc=("zerograd", "zerograd"), precision="fp64", gamma=1.4, mu=0.0,
+                   Pr=1.0, stream=0, **scheme):
+    """One 1-D S2O4 step through gks_step1d_noalloc (no device allocation by
+    the library).  W_in, W_out: contiguous float64 CUDA tensors [3][nx] (or
+    [3][1][nx]).  Returns the error word; raises GKSError on a bad status."""
+    L = lib()
+    if not getattr(L, "_noalloc_declared", False):
+        L.gks_step1d_noalloc.argtypes = [_vp, _vp, C.c_int, C.c_double, C.POINTER(C.c_int), C.POINTER(Gas),
+                                         C.POINTER(Scheme), C.c_int, C.c_double, _vp, C.POINTER(C.c_uint)]
+        L.gks_step1d_noalloc.restype = C.c_int
+        L._noalloc_declared = True
+    nx = W_in.shape[-1]
+    bcs = (C.c_int * 2)(*[BC[b] if isinstance(b, str) else int(b) for b in bc])
+    err = C.c_uint(0)
+    st = L.gks_step1d_noalloc(_vp(W_in.data_ptr()), _vp(W_out.data_ptr()), int(nx), float(dx), bcs,
+                              C.byref(Gas(gamma, mu, Pr)), C.byref(default_scheme(**scheme)),
+                              PRECISION[precision] if isinstance(precision, str) else int(precision),
+                              float(dt), _vp(stream), C.byref(err))
+    if st != GKS_OK:
+        raise GKSError(st, "gks_step1d_noalloc")
+    return err.value
