@@ -38,11 +38,17 @@ def _sources():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(inc, f) for f in os.listdir(inc)]
 
 
+# float32 device arithmetic: flush denormals, approximate divide and square
+# root (these flags do not touch float64 operations)
+FAST_F32 = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+EXTRA = {"gks_k2d_f32": FAST_F32, "gks_k1d": FAST_F32}
+
+
 def _compile(unit):
     src = os.path.join(CSRC, unit + ".cu")
     obj = os.path.join(BUILD, unit + ".o")
     log = os.path.join(BUILD, unit + ".log")
-    cmd = [_nvcc()] + ARCH + COMMON + ["-c", src, "-o", obj]
+    cmd = [_nvcc()] + ARCH + COMMON + EXTRA.get(unit, []) + ["-c", src, "-o", obj]
     with open(log, "w") as f:
         r = subprocess.run(cmd, stdout=f, stderr=subprocess.STDOUT)
     if r.returncode:

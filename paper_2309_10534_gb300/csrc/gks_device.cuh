@@ -71,9 +71,9 @@ template <typename T> struct TenoSel {
 };
 
 // beta_k of Eq. (3.7): quadratics b^2 + 13/3 c^2; the quartic in Balsara's
-// Legendre form.  Selection of Eqs. (4.5)-(4.7) and (4.11)-(4.12) evaluated
-// in ratio form chi_k >= C  <=>  sum_j ((beta_k+eps)/(beta_j+eps))^q <= 1/C,
-// which needs no (beta+eps)^-q and cannot overflow into a wrong decision.
+// Legendre form.  Selection of Eqs. (4.5)-(4.7) and (4.11)-(4.12) on powers
+// normalised by the smallest beta + eps (below), without divisions and
+// without (beta+eps)^-q, which would overflow in float32.
 template <typename T>
 GKS_HD void teno_select(const T q[5], const TenoParams& P, TenoSel<T>& S)
 {
@@ -100,26 +100,40 @@ GKS_HD void teno_select(const T q[5], const TenoParams& P, TenoSel<T>& S)
         t[3] = a * a + T(13.0 / 3.0) * bq * bq + T(781.0 / 20.0) * S.u3 * S.u3
              + T(1421461.0 / 2275.0) * S.u4 * S.u4 + eps;
     }
-    // first selection: keep the large stencil when chi_{3,1} >= C_T1
-    T s1 = T(0);
+    // chi_k = t_k^-q / sum_j t_j^-q.  With m = min_j t_j and r_j = m / t_j in
+    // (0, 1], chi_k = r_k^q / sum_j r_j^q: nothing overflows, and an r^q that
+    // underflows belongs to a chi far below any cut-off.  The same powers
+    // serve both selections (the second normalises over k = 0..2 only).
+    T m = t[0] < t[1] ? t[0] : t[1];
+    m = m < t[2] ? m : t[2];
+    m = m < t[3] ? m : t[3];
+    T p[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) s1 += ipow(t[3] / t[j], P.q);
-    S.large = (s1 * (T)P.ct1 <= T(1));
+    for (int j = 0; j < 4; ++j) {
+        const T r = m * (T(1) / t[j]);
+        if (P.q == 7) {
+            const T r2 = r * r, r3 = r2 * r;
+            p[j] = r3 * r3 * r;
+        } else {
+            p[j] = ipow(r, P.q);
+        }
+    }
+    const T s012 = p[0] + p[1] + p[2];
+    // first selection (Eqs. 4.6, 4.7): keep the large stencil when chi_{3,1} >= C_T1
+    S.large = (p[3] >= (T)P.ct1 * (s012 + p[3]));
     if (S.large) {
         S.w[0] = S.w[1] = S.w[2] = T(0);
         return;
     }
-    // second selection among the small stencils, d_k = 1/3 (cancels)
+    // second selection among the small stencils (Eqs. 4.11, 4.12), d_k = 1/3 cancels
     T d[3], dsum = T(0);
+    const T thr = (T)P.ct2 * s012;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        T s2 = T(0);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) s2 += ipow(t[k] / t[j], P.q);
-        d[k] = (s2 * (T)P.ct2 <= T(1)) ? T(1) : T(0);
+        d[k] = (p[k] >= thr) ? T(1) : T(0);
         dsum += d[k];
     }
-    T inv = T(1) / dsum;
+    const T inv = T(1) / dsum;
 #pragma unroll
     for (int k = 0; k < 3; ++k) S.w[k] = d[k] * inv;
 }
@@ -249,18 +263,46 @@ GKS_HD void apsi(const T* u, const T* v, T xi2, T xi4, const T* a, T* o)
     else apsim1<k>(u, xi2, xi4, a, o);
 }
 
+// Start of the half-space moments: h0 = 1/2 erfc(-sg z) (the mass fraction
+// on the side sg of u = 0, z = sqrt(lambda) U) and g = exp(-z^2).
+// float64: the math library's erfc and exp.  float32: erfc by Abramowitz &
+// Stegun 7.1.26 (Hastings' rational approximation, |error| <= 1.5e-7 on
+// x >= 0), which reuses g = exp(-z^2), so one exponential serves both.
+template <typename T>
+GKS_HD void half_space_start(T z, T sg, T& h0, T& g)
+{
+    h0 = T(0.5) * M<T>::erfc_(-sg * z);
+    g = M<T>::exp_(-z * z);
+}
+template <>
+GKS_HD void half_space_start<float>(float z, float sg, float& h0, float& g)
+{
+    const float x = fabsf(z);
+#ifdef __CUDA_ARCH__
+    g = __expf(-x * x);
+    const float t = __frcp_rn(1.0f + 0.3275911f * x);
+#else
+    g = expf(-x * x);
+    const float t = 1.0f / (1.0f + 0.3275911f * x);
+#endif
+    const float poly = t * (0.254829592f + t * (-0.284496736f + t * (1.421413741f + t * (-1.453152027f
+                     + t * 1.061405429f))));
+    const float h = 0.5f * poly * g;  // 1/2 erfc(|z|)
+    h0 = (sg * z >= 0.0f) ? 1.0f - h : h;
+}
+
 // Micro slope: <a psi> = b with the full-space moments of a Maxwellian
 // (Eq. 2.7), solved in closed form.  ntot = K + DIM degrees of freedom
 // besides... (all translational + internal); inv2l = 1/(2 lambda).
 template <typename T, int DIM>
-GKS_HD void micro_slope(const T* b, T U, T V, T lam, T inv2l, T ntot, T* a)
+GKS_HD void micro_slope(const T* b, T U, T V, T lam, T inv2l, T ntot, T inv_ntot, T* a)
 {
     const T E = T(0.5) * (U * U + V * V + ntot * inv2l);
     const T R2 = b[1] - U * b[0];
     const T R3 = (DIM == 2) ? b[2] - V * b[0] : T(0);
     const T R4 = T(2) * (b[3] - E * b[0]);
     const T tl = T(2) * lam;
-    a[3] = tl * tl / ntot * (R4 - T(2) * U * R2 - T(2) * V * R3);
+    a[3] = tl * tl * inv_ntot * (R4 - T(2) * U * R2 - T(2) * V * R3);
     a[2] = (DIM == 2) ? tl * R3 - V * a[3] : T(0);
     a[1] = tl * R2 - U * a[3];
     a[0] = b[0] - U * a[1] - V * a[2] - E * a[3];
@@ -356,6 +398,7 @@ template <typename T> struct FluxParams {
     T gm1;        // gamma - 1
     T K;          // internal degrees of freedom of this dimension
     T ntot;       // K + DIM
+    T inv_ntot;   // 1 / ntot
     T dt;
     T c1, c2, mu; // collision time (Sec. 5)
     T prfac;      // 1/Pr - 1
@@ -395,8 +438,8 @@ GKS_HD void side_terms(const Side<T>& S, bool upper, const FluxParams<T>& P,
     // half-space u-moments: upper = u > 0 (left state), else u < 0 (right state)
     T uh[7], v[6];
     const T sg = upper ? T(1) : T(-1);
-    uh[0] = T(0.5) * M<T>::erfc_(-sg * sl * U);
-    uh[1] = U * uh[0] + sg * T(0.28209479177387814) * M<T>::exp_(-lam * U * U) / sl;  // e/(2 sqrt(pi lam))
+    half_space_start<T>(sl * U, sg, uh[0], uh[1]);
+    uh[1] = U * uh[0] + sg * T(0.28209479177387814) * uh[1] / sl;  // + e^{-lam U^2} / (2 sqrt(pi lam))
     u_recursion<T, DIM>(uh, U, inv2l);
     v_moments<T, DIM>(v, V, inv2l);
 
@@ -404,11 +447,11 @@ GKS_HD void side_terms(const Side<T>& S, bool upper, const FluxParams<T>& P,
     T an[4], at[4] = {T(0), T(0), T(0), T(0)}, b[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) b[i] = S.Wn[i] * ir;
-    micro_slope<T, DIM>(b, U, V, lam, inv2l, P.ntot, an);
+    micro_slope<T, DIM>(b, U, V, lam, inv2l, P.ntot, P.inv_ntot, an);
     if constexpr (DIM == 2) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) b[i] = S.Wt[i] * ir;
-        micro_slope<T, DIM>(b, U, V, lam, inv2l, P.ntot, at);
+        micro_slope<T, DIM>(b, U, V, lam, inv2l, P.ntot, P.inv_ntot, at);
     }
 
     // kinetic merge, Eqs. (2.6), (3.25), (3.26)
@@ -440,7 +483,7 @@ GKS_HD void side_terms(const Side<T>& S, bool upper, const FluxParams<T>& P,
 #pragma unroll
             for (int i = 0; i < 4; ++i) b[i] -= x1[i];
         }
-        micro_slope<T, DIM>(b, U, V, lam, inv2l, P.ntot, A);
+        micro_slope<T, DIM>(b, U, V, lam, inv2l, P.ntot, P.inv_ntot, A);
 
         // flux moments of the side terms of Eq. (2.5) over the half space
         psim<1, 0>(uh, v, xi2, t);
@@ -503,11 +546,11 @@ GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& 
     T an[4], at[4] = {T(0), T(0), T(0), T(0)}, A0[4], b[4], x1[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) b[i] = W0n[i] * ir0;
-    micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, an);
+    micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, P.inv_ntot, an);
     if constexpr (DIM == 2) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) b[i] = W0t[i] * ir0;
-        micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, at);
+        micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, P.inv_ntot, at);
     }
     apsi<1, 0, T, DIM>(u, v, xi2, xi4, an, x1);
 #pragma unroll
@@ -517,7 +560,7 @@ GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& 
 #pragma unroll
         for (int i = 0; i < 4; ++i) b[i] -= x1[i];
     }
-    micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, A0);
+    micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, P.inv_ntot, A0);
 
     T T0[4], T1[4] = {0, 0, 0, 0}, T2[4];
     psim<1, 0>(u, v, xi2, T0);

@@ -43,6 +43,7 @@ int flux_t(int tau_mode, double gamma, double mu, double Pr, double c1, double c
     p.gm1 = (T)(gamma - 1.0);
     p.K = (T)K;
     p.ntot = (T)(K + DIM);
+    p.inv_ntot = (T)(1.0 / (K + DIM));
     p.dt = (T)dt;
     p.c1 = (T)c1;
     p.c2 = (T)c2;

@@ -216,6 +216,9 @@ struct SweepArgs {
     int with_sigma;
 };
 
+// global variable index of local variable v (swap: faces normal to y)
+__device__ __forceinline__ int gvar(int v, bool swap) { return (swap && (v == 1 || v == 2)) ? 3 - v : v; }
+
 template <typename T, int TN, int TT> struct SweepSmem {
     T w[4][TT + 4][TN + 6];           // cells: tangential rows t0-2.., normal n0-3..
     T rec[4][4][TT + 4][TN + 1];      // [vL, sL, vR, sR][var][row][face]
@@ -239,7 +242,8 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoParams tnn, TenoParams t
     fp.dt = (T)dt;
     const int tid = threadIdx.x;
     const int n0 = blockIdx.x * TN, t0 = blockIdx.y * TT;
-    const int perm[4] = {0, a.dirn == 0 ? 1 : 2, a.dirn == 0 ? 2 : 1, 3};
+    // local frame: normal momentum first; y faces swap the two momentum components
+    const bool swap = a.dirn != 0;
     const long long org = (long long)NG * g.pitch + NG;  // interior (0,0)
 
     // load cells (normal n0-3 .. n0+TN+2, tangential t0-2 .. t0+TT+1); the
@@ -253,7 +257,7 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoParams tnn, TenoParams t
             const int in = n0 - 3 + cn, it = t0 - 2 + ct;
             T val = T(0);
             if (in < a.nn + 3 && it < a.nt + 2)  // ghosted extent (negative side is covered by ghosts)
-                val = (T)a.src[(long long)perm[v] * g.plane + org + in * a.sn + it * a.st];
+                val = (T)a.src[(long long)gvar(v, swap) * g.plane + org + in * a.sn + it * a.st];
             sm.w[v][ct][cn] = val;
         }
     }
@@ -284,7 +288,7 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoParams tnn, TenoParams t
         const int r = tid / NF, f = tid % NF;  // pair = tid
         const T ih = T(1.0 / a.ht);
         const T g0 = T(-0.28867513459481288), g1 = T(0.28867513459481288);  // -+1/(2 sqrt 3)
-#pragma unroll
+#pragma unroll 1
         for (int side = 0; side < 2; ++side) {
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
@@ -317,6 +321,7 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoParams tnn, TenoParams t
     unsigned long long nfb = 0;
     unsigned int err = 0;
     const T tdt = (T)dt;
+#pragma unroll 1
     for (int task = tid; task < 2 * NP; task += NT) {
         const int pair = task >> 1, gpi = task & 1;
         const int r = pair / NF, f = pair % NF;
@@ -379,7 +384,7 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoParams tnn, TenoParams t
             double wn[4];
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                const long long go = (long long)perm[v] * g.plane + o;
+                const long long go = (long long)gvar(v, swap) * g.plane + o;
                 const double d0 = (double)(sF[(v * TT + r) * NF + c + 1] - sF[(v * TT + r) * NF + c]);
                 if (a.stage == 1) {
                     const double d1 = (double)(sF[((4 + v) * TT + r) * NF + c + 1] - sF[((4 + v) * TT + r) * NF + c]);
@@ -391,7 +396,7 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoParams tnn, TenoParams t
                     const double b0 = a.pass == 0 ? a.base[go] : a.out0[go];
                     const double res = b0 - cn * d0;
                     a.out0[go] = res;
-                    wn[perm[v]] = res;
+                    wn[v] = res;  // local order; the CFL rate only needs |U|
                 }
             }
             if (a.with_sigma) sig = cell_sigma<T>(wn, 2, g.gamma, g.mu, h, err);

@@ -38,6 +38,7 @@ inline FluxParams<T> make_flux_params(const HostFlux& h)
     p.gm1 = (T)(h.gamma - 1.0);
     p.K = (T)h.K;
     p.ntot = (T)h.ntot;
+    p.inv_ntot = (T)(1.0 / h.ntot);
     p.dt = (T)0;
     p.c1 = (T)h.c1;
     p.c2 = (T)h.c2;

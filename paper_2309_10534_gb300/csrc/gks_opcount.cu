@@ -98,6 +98,7 @@ void count(int tau_mode, double Pr, gks_flop_model* out)
     fp.gm1 = T(gamma - 1.0);
     fp.K = T(K);
     fp.ntot = T(K + DIM);
+    fp.inv_ntot = T(1.0 / (K + DIM));
     fp.dt = T(1e-3);
     fp.c1 = T(0.01);
     fp.c2 = T(1.0);
