@@ -164,6 +164,13 @@ typedef struct {
 } gks_flop_model;
 gks_status gks_count_flops(int dim, int precision, int tau_mode, double Pr, gks_flop_model *out);
 
+/* Measured arithmetic peak of the current device: fused multiply-adds in 16
+ * independent chains per thread on 8 blocks of 256 threads per SM, one launch
+ * grown to about target_ms; *tflops counts 2 flops per FMA.  precision:
+ * GKS_FP32_FLUX measures float32, GKS_FP64 float64.  Allocates and frees a
+ * small output buffer; synchronises the device. */
+gks_status gks_alu_peak(int precision, double target_ms, double *tflops);
+
 /* ---- allocation-free 1-D step (the paper has no counterpart) ---- */
 
 /* Largest grid gks_step1d_noalloc accepts. */

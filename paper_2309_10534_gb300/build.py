@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 OUT = os.path.join(HERE, "libgks.so")
 ROOT = os.path.dirname(HERE)
 
-UNITS = ["gks_api", "gks_k1d", "gks_k2d_f32", "gks_k2d_f64", "gks_opcount", "gks_host_replica", "gks_noalloc"]
+UNITS = ["gks_api", "gks_k1d", "gks_k2d_f32", "gks_k2d_f64", "gks_opcount", "gks_host_replica", "gks_noalloc", "gks_probe"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
           "-I" + os.path.join(ROOT, "include")]

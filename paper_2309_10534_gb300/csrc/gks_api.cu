@@ -34,6 +34,8 @@ struct gks_ctx {
     gks_scheme sch{};
     int nv = 0;
     double *W = nullptr, *Ws = nullptr, *Ac = nullptr;
+    void *inc0 = nullptr, *inc1 = nullptr;  // x-sweep increments (2-D), working precision
+    float *Wf = nullptr, *Wsf = nullptr;     // float32 shadows of W, W* (2-D float32 path)
     size_t arr_bytes = 0;
     DevState* ds = nullptr;      // device
     DevState* hs = nullptr;      // pinned host mirror
@@ -149,12 +151,19 @@ cudaError_t prof_harvest(gks_ctx* c)
 }
 
 // ---------------------------------------------------------------- launches
+// Ghost layers of W or W*.  On the 2-D float32 path the sweeps read only the
+// float32 shadow, so its ghosts are filled instead of the float64 ones.
 gks_status enqueue_ghosts(gks_ctx* c, double* arr, cudaStream_t st)
 {
     const int gx = c->desc.nx + 2 * NG;
     const int n = (c->desc.dim == 1) ? 2 * NG : 2 * NG * gx + 2 * NG * c->desc.ny;
     const int pi = prof_begin(c, st, 1);
-    k_fill_ghosts<<<(n + 127) / 128, 128, 0, st>>>(c->g, arr, c->ds);
+    if (c->Wf) {
+        float* shadow = (arr == c->W) ? c->Wf : c->Wsf;
+        k_fill_ghosts<float><<<(n + 127) / 128, 128, 0, st>>>(c->g, shadow, c->ds);
+    } else {
+        k_fill_ghosts<double><<<(n + 127) / 128, 128, 0, st>>>(c->g, arr, c->ds);
+    }
     CK(cudaGetLastError());
     prof_end(c, st, pi);
     ++c->launches;
@@ -170,6 +179,7 @@ gks_status enqueue_stage(gks_ctx* c, int stage, int with_sigma, cudaStream_t st)
         Stage1DArgs a{};
         a.stage = stage;
         a.with_sigma = with_sigma;
+        a.idx = 1.0 / c->g.dx;
         if (stage == 1) { a.src = c->W; a.out0 = c->Ws; a.out1 = c->Ac; }
         else { a.src = c->Ws; a.out0 = c->W; a.acc = c->Ac; }
         const int pi = prof_begin(c, st, 0);
@@ -184,13 +194,20 @@ gks_status enqueue_stage(gks_ctx* c, int stage, int with_sigma, cudaStream_t st)
         a.pass = pass;
         a.dirn = pass;  // x faces first, then y faces
         a.src = (stage == 1) ? c->W : c->Ws;
+        a.srcf = (stage == 1) ? c->Wf : c->Wsf;
         a.base = (stage == 1) ? c->W : c->Ac;
         a.out0 = (stage == 1) ? c->Ws : c->W;
+        a.out0f = (stage == 1) ? c->Wsf : c->Wf;
         a.out1 = (stage == 1) ? c->Ac : nullptr;
+        a.inc0 = c->inc0;
+        a.inc1 = c->inc1;
+        a.hmin = fmin(c->g.dx, c->g.dy);
         if (pass == 0) {
-            a.nn = c->desc.nx; a.nt = c->desc.ny; a.sn = 1; a.st = c->g.pitch; a.hn = c->g.dx; a.ht = c->g.dy;
+            a.nn = c->desc.nx; a.nt = c->desc.ny; a.sn = 1; a.st = c->g.pitch;
+            a.ihn = 1.0 / c->g.dx; a.iht = 1.0 / c->g.dy;
         } else {
-            a.nn = c->desc.ny; a.nt = c->desc.nx; a.sn = c->g.pitch; a.st = 1; a.hn = c->g.dy; a.ht = c->g.dx;
+            a.nn = c->desc.ny; a.nt = c->desc.nx; a.sn = c->g.pitch; a.st = 1;
+            a.ihn = 1.0 / c->g.dy; a.iht = 1.0 / c->g.dx;
         }
         a.with_sigma = (pass == 1) ? with_sigma : 0;
         const int pi = prof_begin(c, st, 0);
@@ -416,7 +433,18 @@ gks_status gks_create(const gks_grid_desc* d, gks_ctx** out)
     cudaError_t e3 = cudaMalloc(&c->Ac, c->arr_bytes);
     cudaError_t e4 = cudaMalloc(&c->ds, sizeof(DevState));
     cudaError_t e5 = cudaMallocHost(&c->hs, sizeof(DevState));
-    if (e1 || e2 || e3 || e4 || e5) {
+    cudaError_t e6 = cudaSuccess, e7 = cudaSuccess;
+    if (d->dim == 2) {
+        const size_t inc_bytes = (size_t)c->nv * g.plane * (d->precision == GKS_FP32_FLUX ? 4 : 8);
+        e6 = cudaMalloc(&c->inc0, inc_bytes);
+        e7 = cudaMalloc(&c->inc1, inc_bytes);
+        if (d->precision == GKS_FP32_FLUX && e6 == cudaSuccess && e7 == cudaSuccess) {
+            const size_t fb = (size_t)c->nv * g.plane * sizeof(float);
+            e6 = cudaMalloc(&c->Wf, fb);
+            if (e6 == cudaSuccess) e6 = cudaMalloc(&c->Wsf, fb);
+        }
+    }
+    if (e1 || e2 || e3 || e4 || e5 || e6 || e7) {
         gks_destroy(c);
         cudaGetLastError();
         return GKS_ENOMEM;
@@ -448,6 +476,10 @@ void gks_destroy(gks_ctx* c)
     cudaFree(c->W);
     cudaFree(c->Ws);
     cudaFree(c->Ac);
+    cudaFree(c->inc0);
+    cudaFree(c->inc1);
+    cudaFree(c->Wf);
+    cudaFree(c->Wsf);
     cudaFree(c->ds);
     if (c->hs) cudaFreeHost(c->hs);
     delete c;
@@ -494,6 +526,12 @@ gks_status gks_set_state(gks_ctx* c, const double* W, int on_device)
     if (!c || !W) return GKS_EINVAL;
     gks_status s = copy_interior(c, c->W, W, on_device, true);
     if (s) return s;
+    if (c->Wf) {
+        const long long n = (long long)c->nv * c->g.plane;
+        k_to_float<<<(int)((n + 255) / 256 > 4096 ? 4096 : (n + 255) / 256), 256, 0, c->stream>>>(c->W, c->Wf, n);
+        CK(cudaGetLastError());
+        ++c->launches;
+    }
     k_prepare<<<1, 32, 0, c->stream>>>(c->ds, 2, 0.0, INFINITY, 0);
     CK(cudaGetLastError());
     ++c->launches;

@@ -33,7 +33,8 @@ __device__ __forceinline__ int ghost_src(int bc, int n, int g, bool& flip_n, boo
 // of y ghosts use the y rule to pick an interior row, then the x rule for
 // x-ghost columns (the same values as filling x first, then y over the full
 // ghosted width).
-__global__ void k_fill_ghosts(GridDev g, double* __restrict__ W, const DevState* ds)
+template <typename E>
+__global__ void k_fill_ghosts(GridDev g, E* __restrict__ W, const DevState* ds)
 {
     if (ds && ds->done) return;
     const int gx = g.nx + 2 * NG;
@@ -63,7 +64,7 @@ __global__ void k_fill_ghosts(GridDev g, double* __restrict__ W, const DevState*
     if (g.dim == 2) sj = ghost_src(g.bc[2 + (j >= NG + g.ny)], g.ny, j, fyn, fya);
     int si = ghost_src(g.bc[(i >= NG + g.nx)], g.nx, i, fxn, fxa);
     for (int v = 0; v < nv; ++v) {
-        double val = W[(long long)v * g.plane + (long long)sj * g.pitch + si];
+        E val = W[(long long)v * g.plane + (long long)sj * g.pitch + si];
         // x rule flips the x velocity (v=1) for symmetry, both for no-slip
         const int vx = 1, vy = (g.dim == 2) ? 2 : -1;
         bool neg = false;
@@ -78,7 +79,7 @@ __global__ void k_fill_ghosts(GridDev g, double* __restrict__ W, const DevState*
 template <typename T>
 __global__ void __launch_bounds__(256) k_sigma(GridDev g, const double* __restrict__ W, DevState* ds)
 {
-    double s = 0.0;
+    T s = T(0);
     unsigned int err = 0;
     const int nv = g.dim + 2;
     const double h = (g.dim == 2) ? fmin(g.dx, g.dy) : g.dx;
@@ -88,9 +89,15 @@ __global__ void __launch_bounds__(256) k_sigma(GridDev g, const double* __restri
         const long long off = (long long)(g.dim == 2 ? j + NG : 0) * g.pitch + i + NG;
         double w[4];
         for (int v = 0; v < nv; ++v) w[v] = W[(long long)v * g.plane + off];
-        s = fmax(s, cell_sigma<T>(w, g.dim, g.gamma, g.mu, h, err));
+        s = fmax(s, cell_sigma<T>(w, g.dim, (T)g.gamma, (T)g.mu, (T)h, err));
     }
-    block_commit_sigma<256>(s, err, 0ull, ds);
+    block_commit<256, T>(s, true, err, 0u, ds);
+}
+
+// float32 shadow of a float64 array (same layout)
+__global__ void k_to_float(const double* __restrict__ W, float* __restrict__ Wf, long long n)
+{
+    for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += 256ll * gridDim.x) Wf[i] = (float)W[i];
 }
 
 // After the last kernel of a step: advance t by dt, pick the next dt

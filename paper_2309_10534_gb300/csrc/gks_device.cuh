@@ -60,6 +60,26 @@ struct TenoParams {
     double ct1, ct2;  // thresholds of the first / second selection
 };
 
+// the same parameters in the arithmetic type of the kernel (no conversions
+// from double inside the hot loop); eps is clamped to the smallest normal
+// float in float32
+template <typename T> struct TenoT {
+    T eps, ct1, ct2;
+    int q;
+};
+
+template <typename T>
+inline TenoT<T> teno_t(const TenoParams& P)
+{
+    TenoT<T> t;
+    t.eps = (T)P.eps;
+    if (t.eps < (T)M<T>::tiny) t.eps = (T)M<T>::tiny;
+    t.ct1 = (T)P.ct1;
+    t.ct2 = (T)P.ct2;
+    t.q = P.q;
+    return t;
+}
+
 // Result of the TENO-D selection on one 5-cell stencil: either the large
 // stencil, or the equal-weight (d_k = 1/3) average of the kept sub-stencils.
 template <typename T> struct TenoSel {
@@ -75,7 +95,7 @@ template <typename T> struct TenoSel {
 // normalised by the smallest beta + eps (below), without divisions and
 // without (beta+eps)^-q, which would overflow in float32.
 template <typename T>
-GKS_HD void teno_select(const T q[5], const TenoParams& P, TenoSel<T>& S)
+GKS_HD void teno_select(const T q[5], const TenoT<T>& P, TenoSel<T>& S)
 {
     const T q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3], q4 = q[4];
     S.q2 = q2;
@@ -90,8 +110,7 @@ GKS_HD void teno_select(const T q[5], const TenoParams& P, TenoSel<T>& S)
     S.u3 = (-q0 + T(2) * q1 - T(2) * q3 + q4) * T(1.0 / 12.0);
     S.u4 = (q0 - T(4) * q1 + T(6) * q2 - T(4) * q3 + q4) * T(1.0 / 24.0);
 
-    T eps = (T)P.eps;
-    if (eps < M<T>::tiny) eps = M<T>::tiny;
+    const T eps = P.eps;
     T t[4];
 #pragma unroll
     for (int k = 0; k < 3; ++k) t[k] = S.b[k] * S.b[k] + T(13.0 / 3.0) * S.c[k] * S.c[k] + eps;
@@ -120,14 +139,14 @@ GKS_HD void teno_select(const T q[5], const TenoParams& P, TenoSel<T>& S)
     }
     const T s012 = p[0] + p[1] + p[2];
     // first selection (Eqs. 4.6, 4.7): keep the large stencil when chi_{3,1} >= C_T1
-    S.large = (p[3] >= (T)P.ct1 * (s012 + p[3]));
+    S.large = (p[3] >= P.ct1 * (s012 + p[3]));
     if (S.large) {
         S.w[0] = S.w[1] = S.w[2] = T(0);
         return;
     }
     // second selection among the small stencils (Eqs. 4.11, 4.12), d_k = 1/3 cancels
     T d[3], dsum = T(0);
-    const T thr = (T)P.ct2 * s012;
+    const T thr = P.ct2 * s012;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         d[k] = (p[k] >= thr) ? T(1) : T(0);
@@ -207,60 +226,116 @@ GKS_HD void v_moments(T* v, T V, T inv2l)
     }
 }
 
-// <u^k v^m psi_a>, psi = (1, u, v, (u^2+v^2+xi^2)/2)
-template <int k, int m, typename T>
-GKS_HD void psim(const T* u, const T* v, T xi2, T* o)
+// Moment matrix H^(k,m)_ab = <u^k v^m psi_a psi_b>, psi = (1, u, v, (u^2+v^2+xi^2)/2),
+// of a unit-mass Maxwellian from its moment tables; 10 unique entries
+// (H00 H01 H02 H03 H11 H12 H13 H22 H23 H33).  <u^k v^m (a.psi) psi> = H a.
+// 1-D: v == 0, so only m = 0 occurs and the v entries vanish.
+template <int k, int m, typename T, int DIM>
+GKS_HD void hmat(const T* u, const T* v, T xi2, T xi4, T* H)
 {
-    o[0] = u[k] * v[m];
-    o[1] = u[k + 1] * v[m];
-    o[2] = u[k] * v[m + 1];
-    o[3] = T(0.5) * (u[k + 2] * v[m] + u[k] * v[m + 2] + u[k] * v[m] * xi2);
-}
-// <u^k v^m xi^2 psi_a>
-template <int k, int m, typename T>
-GKS_HD void psim_xi(const T* u, const T* v, T xi2, T xi4, T* o)
-{
-    o[0] = u[k] * v[m] * xi2;
-    o[1] = u[k + 1] * v[m] * xi2;
-    o[2] = u[k] * v[m + 1] * xi2;
-    o[3] = T(0.5) * ((u[k + 2] * v[m] + u[k] * v[m + 2]) * xi2 + u[k] * v[m] * xi4);
-}
-// <u^k v^m (a . psi) psi_a>
-template <int k, int m, typename T>
-GKS_HD void apsim(const T* u, const T* v, T xi2, T xi4, const T* a, T* o)
-{
-    T t0[4], t1[4], t2[4], t3[4], t4[4], t5[4];
-    psim<k, m>(u, v, xi2, t0);
-    psim<k + 1, m>(u, v, xi2, t1);
-    psim<k, m + 1>(u, v, xi2, t2);
-    psim<k + 2, m>(u, v, xi2, t3);
-    psim<k, m + 2>(u, v, xi2, t4);
-    psim_xi<k, m>(u, v, xi2, xi4, t5);
-    const T h = T(0.5) * a[3];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) o[i] = a[0] * t0[i] + a[1] * t1[i] + a[2] * t2[i] + h * (t3[i] + t4[i] + t5[i]);
-}
-// 1-D variant: v == 0, so only the m = 0 terms survive and no v-moments are read
-template <int k, typename T>
-GKS_HD void apsim1(const T* u, T xi2, T xi4, const T* a, T* o)
-{
-    // psi = (1, u, 0, (u^2+xi^2)/2); a[2] is zero in 1-D
-    T t0[4], t1[4], t3[4], t5[4];
-    const T one[6] = {T(1), T(0), T(0), T(0), T(0), T(0)};
-    psim<k, 0>(u, one, xi2, t0);
-    psim<k + 1, 0>(u, one, xi2, t1);
-    psim<k + 2, 0>(u, one, xi2, t3);
-    psim_xi<k, 0>(u, one, xi2, xi4, t5);
-    const T h = T(0.5) * a[3];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) o[i] = a[0] * t0[i] + a[1] * t1[i] + h * (t3[i] + t5[i]);
+    if constexpr (DIM == 2) {
+        H[0] = u[k] * v[m];
+        H[1] = u[k + 1] * v[m];
+        H[2] = u[k] * v[m + 1];
+        H[4] = u[k + 2] * v[m];
+        H[5] = u[k + 1] * v[m + 1];
+        H[7] = u[k] * v[m + 2];
+        H[3] = T(0.5) * (H[4] + H[7] + H[0] * xi2);
+        H[6] = T(0.5) * (u[k + 3] * v[m] + u[k + 1] * v[m + 2] + H[1] * xi2);
+        H[8] = T(0.5) * (u[k + 2] * v[m + 1] + u[k] * v[m + 3] + H[2] * xi2);
+        H[9] = T(0.25) * (u[k + 4] * v[m] + u[k] * v[m + 4] + H[0] * xi4
+                          + T(2) * (u[k + 2] * v[m + 2] + (H[4] + H[7]) * xi2));
+    } else {
+        static_assert(m == 0, "1-D has no v moments");
+        H[0] = u[k];
+        H[1] = u[k + 1];
+        H[4] = u[k + 2];
+        H[3] = T(0.5) * (H[4] + H[0] * xi2);
+        H[6] = T(0.5) * (u[k + 3] + H[1] * xi2);
+        H[9] = T(0.25) * (u[k + 4] + H[0] * xi4 + T(2) * H[4] * xi2);
+        H[2] = H[5] = H[7] = H[8] = T(0);
+    }
 }
 
-template <int k, int m, typename T, int DIM>
-GKS_HD void apsi(const T* u, const T* v, T xi2, T xi4, const T* a, T* o)
+// o = H a for the symmetric moment matrix of hmat
+template <typename T, int DIM>
+GKS_HD void hmv(const T* H, const T* a, T* o)
 {
-    if constexpr (DIM == 2) apsim<k, m>(u, v, xi2, xi4, a, o);
-    else apsim1<k>(u, xi2, xi4, a, o);
+    if constexpr (DIM == 2) {
+        o[0] = H[0] * a[0] + H[1] * a[1] + H[2] * a[2] + H[3] * a[3];
+        o[1] = H[1] * a[0] + H[4] * a[1] + H[5] * a[2] + H[6] * a[3];
+        o[2] = H[2] * a[0] + H[5] * a[1] + H[7] * a[2] + H[8] * a[3];
+        o[3] = H[3] * a[0] + H[6] * a[1] + H[8] * a[2] + H[9] * a[3];
+    } else {
+        o[0] = H[0] * a[0] + H[1] * a[1] + H[3] * a[3];
+        o[1] = H[1] * a[0] + H[4] * a[1] + H[6] * a[3];
+        o[2] = T(0);
+        o[3] = H[3] * a[0] + H[6] * a[1] + H[9] * a[3];
+    }
+}
+
+// Euler flux rho <u psi> of a Maxwellian state (local frame, normal first):
+// (m, m U + p, m V, U (E + p))
+template <typename T, int DIM>
+GKS_HD void euler_flux(const T* W, T U, T p, T* F)
+{
+    F[0] = W[1];
+    F[1] = W[1] * U + p;
+    F[2] = (DIM == 2) ? W[1] * W[2] / W[0] : T(0);
+    F[3] = U * (W[3] + p);
+}
+
+// Jacobian-vector products of the Euler fluxes.  For the micro slope a of a
+// state derivative dW (<a psi> rho = dW), chain rule through the Maxwellian
+// gives rho <u (a.psi) psi> = (dF/dW) dW and rho <v (a.psi) psi> = (dG/dW) dW,
+// with F, G the normal and tangential Euler fluxes of an ideal gas whose
+// gamma matches K.  h = (E + p)/rho.
+template <typename T, int DIM>
+GKS_HD void euler_jvp(const T* dW, T U, T V, T h, T gm1, T* dF, T* dG)
+{
+    const T q = T(0.5) * (U * U + V * V);
+    if constexpr (DIM == 2) {
+        const T dp = gm1 * (dW[3] - U * dW[1] - V * dW[2] + q * dW[0]);
+        const T cross = V * dW[1] + U * dW[2] - U * V * dW[0];
+        if (dF) {
+            dF[0] = dW[1];
+            dF[1] = T(2) * U * dW[1] - U * U * dW[0] + dp;
+            dF[2] = cross;
+            dF[3] = U * (dW[3] + dp) + h * (dW[1] - U * dW[0]);
+        }
+        if (dG) {
+            dG[0] = dW[2];
+            dG[1] = cross;
+            dG[2] = T(2) * V * dW[2] - V * V * dW[0] + dp;
+            dG[3] = V * (dW[3] + dp) + h * (dW[2] - V * dW[0]);
+        }
+    } else {
+        const T dp = gm1 * (dW[3] - U * dW[1] + q * dW[0]);
+        if (dF) {
+            dF[0] = dW[1];
+            dF[1] = T(2) * U * dW[1] - U * U * dW[0] + dp;
+            dF[2] = T(0);
+            dF[3] = U * (dW[3] + dp) + h * (dW[1] - U * dW[0]);
+        }
+        if (dG) dG[0] = dG[1] = dG[2] = dG[3] = T(0);
+    }
+}
+
+// -rho <(a_n u + a_t v) psi> = -(dF/dW Wn + dG/dW Wt): the conserved time
+// derivative that the compatibility condition <a_n u + a_t v + A> = 0 gives
+template <typename T, int DIM>
+GKS_HD void compat_time_derivative(const T* Wn, const T* Wt, T U, T V, T h, T gm1, T* Wtime)
+{
+    T x[4], y[4];
+    euler_jvp<T, DIM>(Wn, U, V, h, gm1, x, nullptr);
+    if constexpr (DIM == 2) {
+        euler_jvp<T, DIM>(Wt, U, V, h, gm1, nullptr, y);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) Wtime[i] = -(x[i] + y[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) Wtime[i] = -x[i];
+    }
 }
 
 // Start of the half-space moments: h0 = 1/2 erfc(-sg z) (the mass fraction
@@ -319,8 +394,8 @@ GKS_HD void micro_slope(const T* b, T U, T V, T lam, T inv2l, T ntot, T inv_ntot
 // Small s: power series (coefficients generated at compile time from the
 // Taylor series of exp, plus the 1/s terms of cF_4, cF_5); large s: closed
 // forms in y = exp(-s/2) with the polynomial parts cancelled analytically.
-struct SeriesTable {
-    double c[12][24];
+template <typename E> struct SeriesTable {
+    E c[12][24];
 };
 
 constexpr double cx_fact(int n) { return n <= 1 ? 1.0 : n * cx_fact(n - 1); }
@@ -339,20 +414,45 @@ constexpr double cx_phi(int k, int n)
     }
 }
 constexpr int cx_p(int k) { return (k == 0 || k == 3) ? 1 : 2; }
-constexpr SeriesTable make_series_table()
+template <typename E>
+constexpr SeriesTable<E> make_series_table()
 {
-    SeriesTable t{};
+    SeriesTable<E> t{};
     for (int k = 0; k < 6; ++k)
         for (int m = 0; m < 24; ++m) {
             const int n = m + cx_p(k);  // coefficient of s^m after dividing by s^p
             const double w2 = cx_pow2neg(n);
-            t.c[k][m] = cx_phi(k, n) * (4.0 * w2 - 1.0);       // cF_k
-            t.c[6 + k][m] = cx_phi(k, n) * (1.0 - 2.0 * w2);   // cD_k
+            t.c[k][m] = (E)(cx_phi(k, n) * (4.0 * w2 - 1.0));       // cF_k
+            t.c[6 + k][m] = (E)(cx_phi(k, n) * (1.0 - 2.0 * w2));   // cD_k
         }
     return t;
 }
-__constant__ SeriesTable kSeries = make_series_table();
-constexpr SeriesTable kSeriesHost = make_series_table();  // host replay (operation counting)
+__constant__ SeriesTable<double> kSeriesD = make_series_table<double>();
+__constant__ SeriesTable<float> kSeriesF = make_series_table<float>();
+// host copies (operation counting, host replicas)
+constexpr SeriesTable<double> kSeriesHostD = make_series_table<double>();
+constexpr SeriesTable<float> kSeriesHostF = make_series_table<float>();
+
+template <typename T> struct SeriesOf {
+    static GKS_HD T c(int k, int m)
+    {
+#ifdef __CUDA_ARCH__
+        return (T)kSeriesD.c[k][m];
+#else
+        return (T)kSeriesHostD.c[k][m];
+#endif
+    }
+};
+template <> struct SeriesOf<float> {
+    static GKS_HD float c(int k, int m)
+    {
+#ifdef __CUDA_ARCH__
+        return kSeriesF.c[k][m];
+#else
+        return kSeriesHostF.c[k][m];
+#endif
+    }
+};
 
 template <typename T>
 GKS_HD void time_coeffs(T s, T* cF, T* cD)
@@ -362,11 +462,7 @@ GKS_HD void time_coeffs(T s, T* cF, T* cD)
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             T acc = T(0);
-#ifdef __CUDA_ARCH__
-            for (int m = n - 1; m >= 0; --m) acc = acc * s + (T)kSeries.c[k][m];
-#else
-            for (int m = n - 1; m >= 0; --m) acc = acc * s + (T)kSeriesHost.c[k][m];
-#endif
+            for (int m = n - 1; m >= 0; --m) acc = acc * s + SeriesOf<T>::c(k, m);
             if (k < 6) cF[k] = acc; else cD[k - 6] = acc;
         }
         // phi_4 and phi_5 start at -x: their x^1 terms leave -1/s in cF_4, cF_5
@@ -422,8 +518,7 @@ GKS_HD bool physical(const T* W, T gm1)
 // equilibrium state, built side by side to keep few values alive.
 template <typename T, int DIM, bool NONEQ, bool PRFIX>
 GKS_HD void side_terms(const Side<T>& S, bool upper, const FluxParams<T>& P,
-                                           T* W0, T* W0n, T* W0t, T* S3, T* S4, T* S5,
-                                           T* N4, T* N5, T& pside)
+                       T* W0, T* W0n, T* W0t, T* S3, T* S4, T* S5, T* N4, T* N5, T& pside)
 {
     const T r = S.W[0], ir = T(1) / r;
     const T U = S.W[1] * ir;
@@ -431,7 +526,7 @@ GKS_HD void side_terms(const Side<T>& S, bool upper, const FluxParams<T>& P,
     const T p = P.gm1 * (S.W[3] - T(0.5) * r * (U * U + V * V));
     pside = p;
     const T inv2l = p * ir;           // 1/(2 lambda)
-    const T lam = T(0.5) * r / p;     // lambda = rho/(2p)
+    const T lam = T(0.5) / inv2l;     // lambda = rho/(2p)
     const T sl = M<T>::sqrt_(lam);
     const T xi2 = P.K * inv2l, xi4 = P.K * (P.K + T(2)) * inv2l * inv2l;
 
@@ -454,65 +549,66 @@ GKS_HD void side_terms(const Side<T>& S, bool upper, const FluxParams<T>& P,
         micro_slope<T, DIM>(b, U, V, lam, inv2l, P.ntot, P.inv_ntot, at);
     }
 
-    // kinetic merge, Eqs. (2.6), (3.25), (3.26)
-    T t[4];
-    psim<0, 0>(uh, v, xi2, t);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) W0[i] += r * t[i];
-    apsi<0, 0, T, DIM>(uh, v, xi2, xi4, an, t);
+    // kinetic merge, Eqs. (2.6), (3.25), (3.26): W0 += rho <psi>_half,
+    // W0_n += rho <(a_n.psi) psi>_half, W0_t += rho <(a_t.psi) psi>_half
+    T H[10], t[4];
+    hmat<0, 0, T, DIM>(uh, v, xi2, xi4, H);
+    W0[0] += r * H[0];
+    W0[1] += r * H[1];
+    W0[2] += r * H[2];
+    W0[3] += r * H[3];
+    hmv<T, DIM>(H, an, t);
 #pragma unroll
     for (int i = 0; i < 4; ++i) W0n[i] += r * t[i];
+    T A[4];
     if constexpr (DIM == 2) {
-        apsi<0, 0, T, DIM>(uh, v, xi2, xi4, at, t);
+        hmv<T, DIM>(H, at, t);
 #pragma unroll
         for (int i = 0; i < 4; ++i) W0t[i] += r * t[i];
     }
 
     if constexpr (NONEQ) {
-        // time derivative of the side's Maxwellian from <a_n u + a_t v + A> = 0
-        T uf[7];
-        uf[0] = T(1);
-        uf[1] = U;
-        u_recursion<T, DIM>(uf, U, inv2l);
-        T x1[4], A[4];
-        apsi<1, 0, T, DIM>(uf, v, xi2, xi4, an, x1);
+        // time derivative of the side's Maxwellian: <a_n u + a_t v + A> = 0
+        const T h = (S.W[3] + p) * ir;
+        T Wtime[4];
+        compat_time_derivative<T, DIM>(S.Wn, S.Wt, U, V, h, P.gm1, Wtime);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) b[i] = -x1[i];
-        if constexpr (DIM == 2) {
-            apsi<0, 1, T, DIM>(uf, v, xi2, xi4, at, x1);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) b[i] -= x1[i];
-        }
+        for (int i = 0; i < 4; ++i) b[i] = Wtime[i] * ir;
         micro_slope<T, DIM>(b, U, V, lam, inv2l, P.ntot, P.inv_ntot, A);
-
-        // flux moments of the side terms of Eq. (2.5) over the half space
-        psim<1, 0>(uh, v, xi2, t);
+        if constexpr (PRFIX) {  // density moments of the A and slope terms, for the heat flux
+            hmv<T, DIM>(H, A, t);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) S3[i] += r * t[i];
-        apsi<2, 0, T, DIM>(uh, v, xi2, xi4, an, t);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) S4[i] += r * t[i];
-        if constexpr (DIM == 2) {
-            apsi<1, 1, T, DIM>(uh, v, xi2, xi4, at, t);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) S4[i] += r * t[i];
+            for (int i = 0; i < 4; ++i) N5[i] += r * t[i];
         }
-        apsi<1, 0, T, DIM>(uh, v, xi2, xi4, A, t);
+        // flux moments of the side terms of Eq. (2.5) over the half space
+        hmat<1, 0, T, DIM>(uh, v, xi2, xi4, H);
+        S3[0] += r * H[0];
+        S3[1] += r * H[1];
+        S3[2] += r * H[2];
+        S3[3] += r * H[3];
+        hmv<T, DIM>(H, A, t);
 #pragma unroll
         for (int i = 0; i < 4; ++i) S5[i] += r * t[i];
         if constexpr (PRFIX) {
-            // density moments (weight 1 instead of u) for the heat flux
-            apsi<1, 0, T, DIM>(uh, v, xi2, xi4, an, t);
+            hmv<T, DIM>(H, an, t);
 #pragma unroll
             for (int i = 0; i < 4; ++i) N4[i] += r * t[i];
             if constexpr (DIM == 2) {
-                apsi<0, 1, T, DIM>(uh, v, xi2, xi4, at, t);
+                hmat<0, 1, T, DIM>(uh, v, xi2, xi4, H);
+                hmv<T, DIM>(H, at, t);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) N4[i] += r * t[i];
             }
-            apsi<0, 0, T, DIM>(uh, v, xi2, xi4, A, t);
+        }
+        hmat<2, 0, T, DIM>(uh, v, xi2, xi4, H);
+        hmv<T, DIM>(H, an, t);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) N5[i] += r * t[i];
+        for (int i = 0; i < 4; ++i) S4[i] += r * t[i];
+        if constexpr (DIM == 2) {
+            hmat<1, 1, T, DIM>(uh, v, xi2, xi4, H);
+            hmv<T, DIM>(H, at, t);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) S4[i] += r * t[i];
         }
     }
 }
@@ -520,8 +616,7 @@ GKS_HD void side_terms(const Side<T>& S, bool upper, const FluxParams<T>& P,
 // F and dF/dt (per unit time; Sec. 2.2) at one interface point in the local
 // frame.  Both sides must be physical (the caller applies the fallback).
 template <typename T, int DIM, bool NONEQ, bool PRFIX>
-GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& P,
-                                           T* F, T* dF)
+GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& P, T* F, T* dF)
 {
     T W0[4] = {0, 0, 0, 0}, W0n[4] = {0, 0, 0, 0}, W0t[4] = {0, 0, 0, 0};
     T S3[4] = {0, 0, 0, 0}, S4[4] = {0, 0, 0, 0}, S5[4] = {0, 0, 0, 0};
@@ -530,64 +625,59 @@ GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& 
     side_terms<T, DIM, NONEQ, PRFIX>(L, true, P, W0, W0n, W0t, S3, S4, S5, N4, N5, pl);
     side_terms<T, DIM, NONEQ, PRFIX>(R, false, P, W0, W0n, W0t, S3, S4, S5, N4, N5, pr);
 
-    // equilibrium state g0
+    // equilibrium state g0: rho0 <u psi>_0 is the Euler flux of W0 and
+    // rho0 <u A0 psi>_0 = (dF/dW) W0_time with W0_time = rho0 <A0 psi>_0 from
+    // the compatibility condition, so A0 itself is never formed
     const T r0 = W0[0], ir0 = T(1) / r0;
     const T U0 = W0[1] * ir0;
     const T V0 = (DIM == 2) ? W0[2] * ir0 : T(0);
     const T p0 = P.gm1 * (W0[3] - T(0.5) * r0 * (U0 * U0 + V0 * V0));
-    const T inv2l = p0 * ir0, lam = T(0.5) * r0 / p0;
-    const T xi2 = P.K * inv2l, xi4 = P.K * (P.K + T(2)) * inv2l * inv2l;
-    T u[7], v[6];
-    u[0] = T(1);
-    u[1] = U0;
-    u_recursion<T, DIM>(u, U0, inv2l);
-    v_moments<T, DIM>(v, V0, inv2l);
+    const T h0 = (W0[3] + p0) * ir0;
+    T F0[4], W0time[4], F2[4];
+    euler_flux<T, DIM>(W0, U0, p0, F0);
+    compat_time_derivative<T, DIM>(W0n, W0t, U0, V0, h0, P.gm1, W0time);
+    euler_jvp<T, DIM>(W0time, U0, V0, h0, P.gm1, F2, nullptr);
 
-    T an[4], at[4] = {T(0), T(0), T(0), T(0)}, A0[4], b[4], x1[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) b[i] = W0n[i] * ir0;
-    micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, P.inv_ntot, an);
-    if constexpr (DIM == 2) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) b[i] = W0t[i] * ir0;
-        micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, P.inv_ntot, at);
-    }
-    apsi<1, 0, T, DIM>(u, v, xi2, xi4, an, x1);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) b[i] = -x1[i];
-    if constexpr (DIM == 2) {
-        apsi<0, 1, T, DIM>(u, v, xi2, xi4, at, x1);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) b[i] -= x1[i];
-    }
-    micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, P.inv_ntot, A0);
-
-    T T0[4], T1[4] = {0, 0, 0, 0}, T2[4];
-    psim<1, 0>(u, v, xi2, T0);
-    apsi<1, 0, T, DIM>(u, v, xi2, xi4, A0, T2);
-
-    // collision time and time coefficients
-    T cF[6], cD[6];
     if (P.tau_mode == 0) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            F[i] = r0 * T0[i];
-            dF[i] = r0 * T2[i];
+            F[i] = F0[i];
+            dF[i] = F2[i];
         }
         return;
     }
+    // collision time and time coefficients
+    T cF[6], cD[6];
     const T jump = fabs(pl - pr) / (pl + pr);
     T s;
     if (P.tau_mode == 1) s = T(1) / (P.c1 + P.c2 * jump);               // dt / tau
     else s = P.dt / (P.mu / p0 + P.c2 * jump * P.dt);
     time_coeffs<T>(s, cF, cD);
 
+    T F1[4] = {T(0), T(0), T(0), T(0)};  // rho0 <u (a0n u + a0t v) psi>_0
     if constexpr (NONEQ) {
-        apsi<2, 0, T, DIM>(u, v, xi2, xi4, an, T1);
-        if constexpr (DIM == 2) {
-            apsi<1, 1, T, DIM>(u, v, xi2, xi4, at, x1);
+        const T inv2l = p0 * ir0, lam = T(0.5) / inv2l;
+        const T xi2 = P.K * inv2l, xi4 = P.K * (P.K + T(2)) * inv2l * inv2l;
+        T u[7], v[6], an[4], at[4] = {T(0), T(0), T(0), T(0)}, b[4], H[10], t[4];
+        u[0] = T(1);
+        u[1] = U0;
+        u_recursion<T, DIM>(u, U0, inv2l);
+        v_moments<T, DIM>(v, V0, inv2l);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) T1[i] += x1[i];
+        for (int i = 0; i < 4; ++i) b[i] = W0n[i] * ir0;
+        micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, P.inv_ntot, an);
+        hmat<2, 0, T, DIM>(u, v, xi2, xi4, H);
+        hmv<T, DIM>(H, an, t);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) F1[i] = r0 * t[i];
+        if constexpr (DIM == 2) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) b[i] = W0t[i] * ir0;
+            micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, P.inv_ntot, at);
+            hmat<1, 1, T, DIM>(u, v, xi2, xi4, H);
+            hmv<T, DIM>(H, at, t);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) F1[i] += r0 * t[i];
         }
     }
     const T dt = P.dt, idt = T(1) / dt;
@@ -597,25 +687,21 @@ GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& 
     const T qD4 = T(4) * cD[4], qD5 = T(4) * cD[5];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        F[i] = r0 * (qF0 * T0[i] + qF1 * T1[i] + qF2 * T2[i]) + qF3 * S3[i] + qF4 * S4[i] + qF5 * S5[i];
-        dF[i] = r0 * (qD0 * T0[i] + qD1 * T1[i] + qD2 * T2[i]) + qD3 * S3[i] + qD4 * S4[i] + qD5 * S5[i];
+        F[i] = qF0 * F0[i] + qF1 * F1[i] + qF2 * F2[i] + qF3 * S3[i] + qF4 * S4[i] + qF5 * S5[i];
+        dF[i] = qD0 * F0[i] + qD1 * F1[i] + qD2 * F2[i] + qD3 * S3[i] + qD4 * S4[i] + qD5 * S5[i];
     }
     if constexpr (PRFIX) {
         // Prandtl correction: F_E += (1/Pr - 1) q, q the heat flux relative to
         // (U0, V0) expanded in raw moments of the same time-dependent f.
-        // Density moments: g0 terms N0 = <psi>, N1 = <(a_n u + a_t v) psi>,
-        // N2 = <A0 psi> = -N1; side terms N3 = W0 / rho, N4, N5 (accumulated).
-        T N0[4], N1[4];
-        psim<0, 0>(u, v, xi2, N0);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) N1[i] = -b[i];
+        // Density moments: rho0 <psi>_0 = W0, rho0 <(a_n u + a_t v) psi>_0 =
+        // -W0_time, rho0 <A0 psi>_0 = W0_time; side terms W0, N4, N5.
         const T ke = T(0.5) * (U0 * U0 + V0 * V0);
         const T cf = ke + U0 * U0;
         T MF[4], MD[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            MF[i] = r0 * (qF0 * N0[i] + (qF1 - qF2) * N1[i]) + qF3 * W0[i] + qF4 * N4[i] + qF5 * N5[i];
-            MD[i] = r0 * (qD0 * N0[i] + (qD1 - qD2) * N1[i]) + qD3 * W0[i] + qD4 * N4[i] + qD5 * N5[i];
+            MF[i] = qF0 * W0[i] + (qF2 - qF1) * W0time[i] + qF3 * W0[i] + qF4 * N4[i] + qF5 * N5[i];
+            MD[i] = qD0 * W0[i] + (qD2 - qD1) * W0time[i] + qD3 * W0[i] + qD4 * N4[i] + qD5 * N5[i];
         }
         const T qh = F[3] - U0 * F[1] - V0 * F[2] + cf * F[0] + U0 * V0 * MF[2] - U0 * MF[3] - U0 * ke * MF[0];
         const T qd = dF[3] - U0 * dF[1] - V0 * dF[2] + cf * dF[0] + U0 * V0 * MD[2] - U0 * MD[3]

@@ -19,9 +19,9 @@ int teno_t(const double* q, double eps, int qpow, double ct1, double ct2, double
 {
     T qq[5];
     for (int k = 0; k < 5; ++k) qq[k] = (T)q[k];
-    gks::TenoParams P{eps, qpow, ct1, ct2};
+    const gks::TenoParams P{eps, qpow, ct1, ct2};
     gks::TenoSel<T> S;
-    gks::teno_select(qq, P, S);
+    gks::teno_select(qq, gks::teno_t<T>(P), S);
     T vp, dp, vm, dm;
     gks::teno_faces(qq, S, vp, dp, vm, dm);
     faces[0] = vp; faces[1] = dp; faces[2] = vm; faces[3] = dm;

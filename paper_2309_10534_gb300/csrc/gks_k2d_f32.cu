@@ -12,7 +12,7 @@ cudaError_t launch_one(const GridDev& g, const SweepArgs& a, const FluxParams<fl
     auto kern = k2d_sweep<float, NONEQ, PRFIX, TN, TT>;
     const size_t smem = sizeof(SweepSmem<float, TN, TT>);
     dim3 grid((a.nn + TN - 1) / TN, (a.nt + TT - 1) / TT);
-    kern<<<grid, SWEEP_THREADS, smem, st>>>(g, a, fp, tn, tt, ds);
+    kern<<<grid, SWEEP_THREADS, smem, st>>>(g, a, fp, teno_t<float>(tn), teno_t<float>(tt), ds);
     return cudaGetLastError();
 }
 template <bool NONEQ, bool PRFIX>

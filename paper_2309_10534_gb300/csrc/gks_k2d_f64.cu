@@ -12,7 +12,7 @@ cudaError_t launch_one(const GridDev& g, const SweepArgs& a, const FluxParams<do
     auto kern = k2d_sweep<double, NONEQ, PRFIX, TN, TT>;
     const size_t smem = sizeof(SweepSmem<double, TN, TT>);
     dim3 grid((a.nn + TN - 1) / TN, (a.nt + TT - 1) / TT);
-    kern<<<grid, SWEEP_THREADS, smem, st>>>(g, a, fp, tn, tt, ds);
+    kern<<<grid, SWEEP_THREADS, smem, st>>>(g, a, fp, teno_t<double>(tn), teno_t<double>(tt), ds);
     return cudaGetLastError();
 }
 template <bool NONEQ, bool PRFIX>

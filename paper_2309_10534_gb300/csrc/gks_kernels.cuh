@@ -40,42 +40,34 @@ struct GridDev {
 };
 
 // ------------------------------------------------------------------ CFL rate
-// sigma = max((|U| + a)/h, 4 nu / h^2), dt = cfl / sigma  (Sec. 5)
+// sigma = max((|U| + a)/h, 4 nu / h^2), dt = cfl / sigma  (Sec. 5), in the
+// kernel's arithmetic type (the float32 path takes its time step in float32;
+// only the state and its accumulation are float64)
 template <typename T>
-__device__ __forceinline__ double cell_sigma(const double* w, int dim, double gamma, double mu, double h,
-                                             unsigned int& err)
+__device__ __forceinline__ T cell_sigma(const double* w, int dim, T gamma, T mu, T h, unsigned int& err)
 {
-    const double r = w[0];
-    const double U = w[1] / r, V = (dim == 2) ? w[2] / r : 0.0;
-    const double E = w[dim + 1];
-    if constexpr (sizeof(T) == 8) {
-        const double p = (gamma - 1.0) * (E - 0.5 * r * (U * U + V * V));
-        if (!(r > 0.0 && p > 0.0 && isfinite(p))) err |= 1u;
-        const double a = sqrt(gamma * p / r);
-        double s = (sqrt(U * U + V * V) + a) / h;
-        if (mu > 0.0) s = fmax(s, 4.0 * mu / (r * h * h));
-        return s;
-    } else {
-        const float rf = (float)r, Uf = (float)U, Vf = (float)V;
-        const float p = (float)((gamma - 1.0) * (E - 0.5 * r * (U * U + V * V)));
-        if (!(rf > 0.0f && p > 0.0f && isfinite(p))) err |= 1u;
-        const float a = sqrtf((float)gamma * p / rf);
-        float s = (sqrtf(Uf * Uf + Vf * Vf) + a) / (float)h;
-        if (mu > 0.0) s = fmaxf(s, 4.0f * (float)mu / (rf * (float)(h * h)));
-        return (double)s;
-    }
+    const T r = (T)w[0], ir = T(1) / r;
+    const T U = (T)w[1] * ir, V = (dim == 2) ? (T)w[2] * ir : T(0);
+    const T E = (T)w[dim + 1];
+    const T p = (gamma - T(1)) * (E - T(0.5) * r * (U * U + V * V));
+    if (!(r > T(0) && p > T(0) && isfinite(p))) err |= 1u;
+    const T a = sqrt(gamma * p * ir);
+    const T ih = T(1) / h;
+    T s = (sqrt(U * U + V * V) + a) * ih;
+    if (mu > T(0)) s = fmax(s, T(4) * mu * ir * ih * ih);
+    return s;
 }
 
-template <int NT>
-__device__ __forceinline__ void block_commit_sigma(double s, unsigned int err, unsigned long long nfb,
-                                                   DevState* ds)
+// Block reduction of the CFL rate (only when with_sigma), the error word and
+// the fallback count; one atomic of each per block.
+template <int NT, typename T>
+__device__ __forceinline__ void block_commit(T s, bool with_sigma, unsigned int err, unsigned int nfb, DevState* ds)
 {
-    __shared__ double red_s[NT / 32];
-    __shared__ unsigned int red_e[NT / 32];
-    __shared__ unsigned long long red_f[NT / 32];
+    __shared__ T red_s[NT / 32];
+    __shared__ unsigned int red_e[NT / 32], red_f[NT / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+        if (with_sigma) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
         err |= __shfl_xor_sync(0xffffffffu, err, o);
         nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
     }
@@ -83,10 +75,16 @@ __device__ __forceinline__ void block_commit_sigma(double s, unsigned int err, u
     if (l == 0) { red_s[w] = s; red_e[w] = err; red_f[w] = nfb; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 1; k < NT / 32; ++k) { s = fmax(s, red_s[k]); err |= red_e[k]; nfb += red_f[k]; }
-        if (s > 0.0 || s != s) atomicMax(&ds->sigma, (unsigned long long)__double_as_longlong(s));
+        for (int k = 1; k < NT / 32; ++k) {
+            if (with_sigma) s = fmax(s, red_s[k]);
+            err |= red_e[k];
+            nfb += red_f[k];
+        }
+        const double sd = (double)s;
+        if (with_sigma && (sd > 0.0 || sd != sd))
+            atomicMax(&ds->sigma, (unsigned long long)__double_as_longlong(sd));
         if (err) atomicOr(&ds->err, err);
-        if (nfb) atomicAdd(&ds->fallbacks, nfb);
+        if (nfb) atomicAdd(&ds->fallbacks, (unsigned long long)nfb);
     }
 }
 
@@ -98,10 +96,11 @@ struct Stage1DArgs {
     const double* acc;   // stage 2: accumulator A; stage 1: unused
     int stage;
     int with_sigma;      // stage 2: reduce the CFL rate of the new state
+    double idx;          // 1 / dx
 };
 
 template <typename T, bool NONEQ, bool PRFIX, int TN>
-__global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, FluxParams<T> fp, TenoParams tn,
+__global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, FluxParams<T> fp, TenoT<T> tn,
                                                     DevState* ds)
 {
     if (ds->done) return;
@@ -122,7 +121,7 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
         sq[v][c] = gi < gx ? (T)a.src[(long long)v * g.plane + gi] : T(0);
     }
     __syncthreads();
-    const T idx_ = T(1.0 / g.dx);
+    const T idx_ = (T)a.idx;
     // phase 1: TENO-D per cell c (interior i0 - 1 + c), both faces
     for (int c = tid; c < TN + 2; c += NT) {
         for (int v = 0; v < 3; ++v) {
@@ -139,8 +138,7 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
     }
     __syncthreads();
     // phase 2: flux at face f (between interior i0+f-1 and i0+f)
-    unsigned long long nfb = 0;
-    unsigned int err = 0;
+    unsigned int nfb = 0, err = 0;
     for (int f = tid; f <= TN; f += NT) {
         if (i0 + f > g.nx) continue;  // padding past the last face
         Side<T> L, R;
@@ -177,8 +175,8 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
     }
     __syncthreads();
     // phase 3: update
-    double sig = 0.0;
-    const double cx = dt / g.dx;
+    T sig = T(0);
+    const double cx = dt * a.idx;
     for (int c = tid; c < TN; c += NT) {
         const int i = i0 + c;
         if (i >= g.nx) continue;
@@ -196,23 +194,33 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
                 a.out0[(long long)v * g.plane + o] = r;
                 w[v] = r;
             }
-            if (a.with_sigma) sig = fmax(sig, cell_sigma<T>(w, 1, g.gamma, g.mu, g.dx, err));
+            if (a.with_sigma) sig = fmax(sig, cell_sigma<T>(w, 1, (T)g.gamma, (T)g.mu, (T)g.dx, err));
         }
     }
-    if (NT % 32 == 0) block_commit_sigma<NT>(sig, err, nfb, ds);
+    if (NT % 32 == 0) block_commit<NT, T>(sig, a.with_sigma != 0, err, nfb, ds);
 }
 
 // ------------------------------------------------------------------ 2-D sweep
+// One stage = x sweep (pass 0) then y sweep (pass 1).  The x sweep stores its
+// flux-divergence increments dt/dx dG in the kernel's arithmetic type (inc0,
+// inc1); the y sweep adds its own and applies ONE float64 update per value:
+//   stage 1: W* = W - (inc0 + dt/dy dG1),  A = W - (inc1 + dt/dy dG2)
+//   stage 2: W  = A - (inc0 + dt/dy dG)
 struct SweepArgs {
     const double* src;   // reconstruction input (W or W*), ghosts filled
-    const double* base;  // first sweep: W (stage 1) or A (stage 2); second sweep: ignored
-    double* out0;        // stage 1: W*; stage 2: W
-    double* out1;        // stage 1: A
+    const float* srcf;   // float32 path: float32 shadow of src (ghosts filled)
+    const double* base;  // y sweep: W (stage 1) or A (stage 2)
+    double* out0;        // y sweep, stage 1: W*; stage 2: W
+    float* out0f;        // float32 path, y sweep: float32 shadow of out0
+    double* out1;        // y sweep, stage 1: A
+    void* inc0;          // increments, arithmetic type, same ghosted layout
+    void* inc1;          // (stage 1 only)
     int stage, pass;     // pass 0: x sweep (first), 1: y sweep (second)
     int dirn;            // 0: faces normal to x, 1: faces normal to y
     int nn, nt;          // cells along the normal / tangential direction
     long long sn, st;    // element strides along normal / tangential
-    double hn, ht;       // cell sizes along normal / tangential
+    double ihn, iht;     // inverse cell sizes along normal / tangential
+    double hmin;         // min(dx, dy) for the CFL rate
     int with_sigma;
 };
 
@@ -227,7 +235,7 @@ template <typename T, int TN, int TT> struct SweepSmem {
 
 template <typename T, bool NONEQ, bool PRFIX, int TN, int TT>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4) ? 2 : 1)
-k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoParams tnn, TenoParams tnt, DevState* ds)
+k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, DevState* ds)
 {
     if (ds->done) return;
     constexpr int NT = 256;
@@ -256,8 +264,11 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoParams tnn, TenoParams t
             if (a.dirn == 0) { ct = e / CN; cn = e % CN; } else { cn = e / CT; ct = e % CT; }
             const int in = n0 - 3 + cn, it = t0 - 2 + ct;
             T val = T(0);
-            if (in < a.nn + 3 && it < a.nt + 2)  // ghosted extent (negative side is covered by ghosts)
-                val = (T)a.src[(long long)gvar(v, swap) * g.plane + org + in * a.sn + it * a.st];
+            if (in < a.nn + 3 && it < a.nt + 2) {  // ghosted extent (negative side is covered by ghosts)
+                const long long gi = (long long)gvar(v, swap) * g.plane + org + in * a.sn + it * a.st;
+                if constexpr (sizeof(T) == 4) val = a.srcf[gi];
+                else val = a.src[gi];
+            }
             sm.w[v][ct][cn] = val;
         }
     }
@@ -265,7 +276,7 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoParams tnn, TenoParams t
 
     // phase 1: normal TENO-D per (cell, row, var): cell c <-> normal n0-1+c
     {
-        const T ih = T(1.0 / a.hn);
+        const T ih = (T)a.ihn;
         constexpr int NC = TN + 2, NR = TT + 4;
         for (int k = tid; k < 4 * NC * NR; k += NT) {
             const int v = k / (NC * NR), e = k % (NC * NR);
@@ -286,7 +297,7 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoParams tnn, TenoParams t
     // phase 2a: tangential TENO-D of the line averages to the two Gauss points
     {
         const int r = tid / NF, f = tid % NF;  // pair = tid
-        const T ih = T(1.0 / a.ht);
+        const T ih = (T)a.iht;
         const T g0 = T(-0.28867513459481288), g1 = T(0.28867513459481288);  // -+1/(2 sqrt 3)
 #pragma unroll 1
         for (int side = 0; side < 2; ++side) {
@@ -318,8 +329,7 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoParams tnn, TenoParams t
 
     // phase 2b: merge + flux at each Gauss point; thread pairs hold the two
     // Gauss points of one face segment and average them (weights 1/2)
-    unsigned long long nfb = 0;
-    unsigned int err = 0;
+    unsigned int nfb = 0, err = 0;
     const T tdt = (T)dt;
 #pragma unroll 1
     for (int task = tid; task < 2 * NP; task += NT) {
@@ -372,37 +382,44 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoParams tnn, TenoParams t
     }
     __syncthreads();
 
-    // phase 3: flux divergence into the float64 state
-    double sig = 0.0;
-    const double cn = dt / a.hn;
-    const double h = fmin(g.dx, g.dy);
+    // phase 3: flux divergence; the y sweep updates the float64 state
+    T sig = T(0);
+    const T cn = (T)(dt * a.ihn);
     if (tid < TN * TT) {
         const int r = tid / TN, c = tid % TN;
         const int in = n0 + c, it = t0 + r;
         if (in < a.nn && it < a.nt) {
             const long long o = org + in * a.sn + it * a.st;
+            T* inc0 = static_cast<T*>(a.inc0);
+            T* inc1 = static_cast<T*>(a.inc1);
             double wn[4];
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 const long long go = (long long)gvar(v, swap) * g.plane + o;
-                const double d0 = (double)(sF[(v * TT + r) * NF + c + 1] - sF[(v * TT + r) * NF + c]);
-                if (a.stage == 1) {
-                    const double d1 = (double)(sF[((4 + v) * TT + r) * NF + c + 1] - sF[((4 + v) * TT + r) * NF + c]);
-                    const double b0 = a.pass == 0 ? a.base[go] : a.out0[go];
-                    const double b1 = a.pass == 0 ? a.base[go] : a.out1[go];
-                    a.out0[go] = b0 - cn * d0;
-                    a.out1[go] = b1 - cn * d1;
-                } else {
-                    const double b0 = a.pass == 0 ? a.base[go] : a.out0[go];
-                    const double res = b0 - cn * d0;
+                const T d0 = cn * (sF[(v * TT + r) * NF + c + 1] - sF[(v * TT + r) * NF + c]);
+                const T d1 = (a.stage == 1)
+                           ? cn * (sF[((4 + v) * TT + r) * NF + c + 1] - sF[((4 + v) * TT + r) * NF + c])
+                           : T(0);
+                if (a.pass == 0) {
+                    inc0[go] = d0;
+                    if (a.stage == 1) inc1[go] = d1;
+                } else if (a.stage == 1) {
+                    const double w = a.base[go];
+                    const double res = w - (double)(inc0[go] + d0);
                     a.out0[go] = res;
+                    a.out1[go] = w - (double)(inc1[go] + d1);
+                    if constexpr (sizeof(T) == 4) a.out0f[go] = (float)res;
+                } else {
+                    const double res = a.base[go] - (double)(inc0[go] + d0);
+                    a.out0[go] = res;
+                    if constexpr (sizeof(T) == 4) a.out0f[go] = (float)res;
                     wn[v] = res;  // local order; the CFL rate only needs |U|
                 }
             }
-            if (a.with_sigma) sig = cell_sigma<T>(wn, 2, g.gamma, g.mu, h, err);
+            if (a.with_sigma) sig = cell_sigma<T>(wn, 2, (T)g.gamma, (T)g.mu, (T)a.hmin, err);
         }
     }
-    block_commit_sigma<NT>(sig, err, nfb, ds);
+    block_commit<NT, T>(sig, a.with_sigma != 0, err, nfb, ds);
 }
 
 }  // namespace gks

@@ -169,6 +169,7 @@ extern "C" gks_status gks_step1d_noalloc(const double* W_in, double* W_out, int 
 
     k_load<<<(nx + 2 * NG + 127) / 128, 128, 0, st>>>(W_in, W, nx, bc[0], bc[1], ds, dt);
     Stage1DArgs a1{};
+    a1.idx = 1.0 / dx;
     a1.src = W;
     a1.out0 = Ws;
     a1.out1 = Ac;
@@ -176,6 +177,7 @@ extern "C" gks_status gks_step1d_noalloc(const double* W_in, double* W_out, int 
     if (launch_stage1d(f32, g, a1, hf, tn, ds, st) != cudaSuccess) return GKS_ECUDA;
     k_ghosts<<<1, 32, 0, st>>>(Ws, nx, bc[0], bc[1]);
     Stage1DArgs a2{};
+    a2.idx = 1.0 / dx;
     a2.src = Ws;
     a2.out0 = Wn;
     a2.acc = Ac;

@@ -105,7 +105,12 @@ void count(int tau_mode, double Pr, gks_flop_model* out)
     fp.mu = T(tau_mode == 2 ? 1e-4 : 0.0);
     fp.prfac = T(1.0 / Pr - 1.0);
     fp.tau_mode = tau_mode;
-    TenoParams tp{1e-40, 7, 1e-7, 1e-5};
+    const TenoParams tp0{1e-40, 7, 1e-7, 1e-5};
+    TenoT<T> tp;
+    tp.eps = T(1e-40);
+    tp.ct1 = T(1e-7);
+    tp.ct2 = T(1e-5);
+    tp.q = tp0.q;
 
     const T q[5] = {T(1.00), T(1.011), T(1.023), T(1.036), T(1.050)};
     const Counts recon = measure([&] {

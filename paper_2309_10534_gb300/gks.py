@@ -241,6 +241,18 @@ class Solver:
         return n.value, ms.value
 
 
+def alu_peak(precision="fp32", target_ms=200.0):
+    """Measured FMA-chain throughput (TFLOP/s, 2 flops per FMA) of the device."""
+    L = lib()
+    L.gks_alu_peak.argtypes = [C.c_int, C.c_double, _dp]
+    L.gks_alu_peak.restype = C.c_int
+    v = C.c_double(0.0)
+    st = L.gks_alu_peak(PRECISION[precision], float(target_ms), C.byref(v))
+    if st != GKS_OK:
+        raise GKSError(st, "gks_alu_peak")
+    return v.value
+
+
 def count_flops(dim, precision="fp32", tau="euler", Pr=1.0):
     """Algorithmic operation count of the library's stage arithmetic per cell."""
     m = FlopModel()
