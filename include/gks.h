@@ -115,7 +115,9 @@ gks_status gks_set_stream(gks_ctx *ctx, void *stream);
 gks_status gks_set_state(gks_ctx *ctx, const double *W, int on_device);
 gks_status gks_get_state(gks_ctx *ctx, double *W, int on_device);
 /* which: 0 = W (state), 1 = W* (stage-1 output), 2 = stage accumulator
- * W^n - dt/dx dF(W^n) (Sec. 2.2); same layout as gks_get_state */
+ * W^n - dt/dx dF(W^n) (Sec. 2.2); same layout as gks_get_state.  On the 2-D
+ * GKS_FP32_FLUX path W* is held in float32 and the accumulator as a float32
+ * increment of W; this call widens them (valid between stage 1 and stage 2). */
 gks_status gks_get_buffer(gks_ctx *ctx, int which, double *W, int on_device);
 
 /* CFL time step of the current state (Sec. 5); synchronises. */

@@ -45,6 +45,9 @@ struct gks_ctx {
     long long graph_nodes = 0;
     unsigned long long param_version = 1, graph_version = 0;
     long long launches = 0;
+    // the device already holds the CFL time step of the current state (set by
+    // a CFL step's commit, cleared by anything else that changes W or dt)
+    bool cfl_dt_ready = false;
     std::string err;
     // per-kernel event timing (gks_profile_enable)
     bool prof = false, capturing = false;
@@ -195,7 +198,10 @@ gks_status enqueue_stage(gks_ctx* c, int stage, int with_sigma, cudaStream_t st)
         a.dirn = pass;  // x faces first, then y faces
         a.src = (stage == 1) ? c->W : c->Ws;
         a.srcf = (stage == 1) ? c->Wf : c->Wsf;
-        a.base = (stage == 1) ? c->W : c->Ac;
+        a.basef = c->Wf;
+        // float64 path: stage 2 starts from the accumulator; float32 path: from W
+        // (its accumulator is the increment inc1)
+        a.base = (stage == 1 || f32) ? c->W : c->Ac;
         a.out0 = (stage == 1) ? c->Ws : c->W;
         a.out0f = (stage == 1) ? c->Wsf : c->Wf;
         a.out1 = (stage == 1) ? c->Ac : nullptr;
@@ -491,6 +497,7 @@ gks_status gks_set_gas(gks_ctx* c, const gks_gas* gas)
     if (!(gas->gamma > 1.0 && gas->gamma < 3.0) || !(gas->mu >= 0.0) || !(gas->Pr > 0.0))
         return fail(c, GKS_EINVAL, "gas parameters out of range");
     c->gas = *gas;
+    c->cfl_dt_ready = false;
     c->g.gamma = gas->gamma;
     c->g.mu = gas->mu;
     ++c->param_version;
@@ -507,6 +514,7 @@ gks_status gks_set_scheme(gks_ctx* c, const gks_scheme* s)
         return fail(c, GKS_EUNSUPPORTED, "the kernels always apply the positivity fallback");
     c->sch = *s;
     ++c->param_version;
+    c->cfl_dt_ready = false;
     // cfl lives in the device state
     c->hs->cfl = s->cfl;
     CK(cudaMemcpyAsync(&c->ds->cfl, &c->hs->cfl, sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -524,6 +532,7 @@ gks_status gks_set_stream(gks_ctx* c, void* stream)
 gks_status gks_set_state(gks_ctx* c, const double* W, int on_device)
 {
     if (!c || !W) return GKS_EINVAL;
+    c->cfl_dt_ready = false;
     gks_status s = copy_interior(c, c->W, W, on_device, true);
     if (s) return s;
     if (c->Wf) {
@@ -548,6 +557,15 @@ gks_status gks_get_buffer(gks_ctx* c, int which, double* W, int on_device)
 {
     if (!c || !W || which < 0 || which > 2) return GKS_EINVAL;
     double* arr = which == 0 ? c->W : (which == 1 ? c->Ws : c->Ac);
+    if (c->Wf && which > 0) {
+        // float32 path: W* lives in float32, the accumulator as an increment
+        const long long n = (long long)c->nv * c->g.plane;
+        const int blocks = (int)((n + 255) / 256 > 4096 ? 4096 : (n + 255) / 256);
+        if (which == 1) k_widen<<<blocks, 256, 0, c->stream>>>(c->Wsf, c->Ws, n);
+        else k_accumulator<<<blocks, 256, 0, c->stream>>>(c->W, static_cast<const float*>(c->inc1), c->Ac, n);
+        CK(cudaGetLastError());
+        ++c->launches;
+    }
     return copy_interior(c, arr, W, on_device, false);
 }
 
@@ -569,6 +587,7 @@ gks_status gks_compute_dt(gks_ctx* c, double* dt)
 gks_status gks_stage(gks_ctx* c, int stage, double dt)
 {
     if (!c || (stage != 1 && stage != 2) || !(dt > 0.0) || !std::isfinite(dt)) return GKS_EINVAL;
+    c->cfl_dt_ready = false;
     k_prepare<<<1, 32, 0, c->stream>>>(c->ds, 0, dt, 0.0, 0);
     CK(cudaGetLastError());
     ++c->launches;
@@ -582,22 +601,27 @@ gks_status gks_step(gks_ctx* c, double dt)
     if (!c || !std::isfinite(dt)) return GKS_EINVAL;
     gks_status s;
     if (dt > 0.0) {
+        c->cfl_dt_ready = false;
         k_prepare<<<1, 32, 0, c->stream>>>(c->ds, 0, dt, 0.0, 0);
         CK(cudaGetLastError());
         ++c->launches;
-    } else {
+    } else if (!c->cfl_dt_ready) {
         k_prepare<<<1, 32, 0, c->stream>>>(c->ds, 3, 0.0, 0.0, 0);
         CK(cudaGetLastError());
         ++c->launches;
         if ((s = enqueue_sigma(c, c->stream))) return s;
         if ((s = enqueue_commit(c, 1, c->stream))) return s;
     }
-    return enqueue_step(c, c->stream);
+    // else: the previous CFL step's commit already chose dt from this state
+    s = enqueue_step(c, c->stream);
+    c->cfl_dt_ready = (s == GKS_OK && !(dt > 0.0));
+    return s;
 }
 
 gks_status gks_advance_to(gks_ctx* c, double t_end, long long max_steps, long long* steps_done, double* t_out)
 {
     if (!c || !std::isfinite(t_end)) return GKS_EINVAL;
+    c->cfl_dt_ready = false;
     gks_status s;
     if ((s = sync_state(c))) return s;
     const long long steps0 = c->hs->steps;

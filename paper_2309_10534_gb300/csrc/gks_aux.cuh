@@ -100,6 +100,18 @@ __global__ void k_to_float(const double* __restrict__ W, float* __restrict__ Wf,
     for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += 256ll * gridDim.x) Wf[i] = (float)W[i];
 }
 
+// float64 views of the float32 path's stage buffers (gks_get_buffer):
+// W* from its float32 form, the accumulator from W and its increment
+__global__ void k_widen(const float* __restrict__ src, double* __restrict__ dst, long long n)
+{
+    for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += 256ll * gridDim.x) dst[i] = (double)src[i];
+}
+__global__ void k_accumulator(const double* __restrict__ W, const float* __restrict__ inc, double* __restrict__ A,
+                              long long n)
+{
+    for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += 256ll * gridDim.x) A[i] = W[i] - (double)inc[i];
+}
+
 // After the last kernel of a step: advance t by dt, pick the next dt
 // (CFL from the reduced sigma, clipped to t_end), detect completion.
 // init = 1: only pick dt from sigma (before the first step).

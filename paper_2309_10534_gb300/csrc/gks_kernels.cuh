@@ -203,12 +203,19 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
 // ------------------------------------------------------------------ 2-D sweep
 // One stage = x sweep (pass 0) then y sweep (pass 1).  The x sweep stores its
 // flux-divergence increments dt/dx dG in the kernel's arithmetic type (inc0,
-// inc1); the y sweep adds its own and applies ONE float64 update per value:
+// inc1); the y sweep adds its own.
+// float64 path (one float64 update per value):
 //   stage 1: W* = W - (inc0 + dt/dy dG1),  A = W - (inc1 + dt/dy dG2)
 //   stage 2: W  = A - (inc0 + dt/dy dG)
+// float32 path: W* is only the stage-2 reconstruction input, so it is formed
+// in float32 from the float32 shadow of W, and the accumulator stays an
+// increment; the only float64 arithmetic is the final update of W:
+//   stage 1: W*f = Wf - (inc0 + dt/dy dG1),  inc1 <- inc1 + dt/dy dG2
+//   stage 2: W   = W - (inc1 + inc0 + dt/dy dG)   (and its shadow Wf)
 struct SweepArgs {
     const double* src;   // reconstruction input (W or W*), ghosts filled
     const float* srcf;   // float32 path: float32 shadow of src (ghosts filled)
+    const float* basef;  // float32 path, y sweep of stage 1: float32 shadow of W
     const double* base;  // y sweep: W (stage 1) or A (stage 2)
     double* out0;        // y sweep, stage 1: W*; stage 2: W
     float* out0f;        // float32 path, y sweep: float32 shadow of out0
@@ -403,16 +410,23 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
                 if (a.pass == 0) {
                     inc0[go] = d0;
                     if (a.stage == 1) inc1[go] = d1;
+                } else if constexpr (sizeof(T) == 4) {
+                    if (a.stage == 1) {
+                        a.out0f[go] = a.basef[go] - (inc0[go] + d0);
+                        inc1[go] = inc1[go] + d1;
+                    } else {
+                        const double res = a.base[go] - (double)(inc1[go] + inc0[go] + d0);
+                        a.out0[go] = res;
+                        a.out0f[go] = (float)res;
+                        wn[v] = res;  // local order; the CFL rate only needs |U|
+                    }
                 } else if (a.stage == 1) {
                     const double w = a.base[go];
-                    const double res = w - (double)(inc0[go] + d0);
-                    a.out0[go] = res;
+                    a.out0[go] = w - (double)(inc0[go] + d0);
                     a.out1[go] = w - (double)(inc1[go] + d1);
-                    if constexpr (sizeof(T) == 4) a.out0f[go] = (float)res;
                 } else {
                     const double res = a.base[go] - (double)(inc0[go] + d0);
                     a.out0[go] = res;
-                    if constexpr (sizeof(T) == 4) a.out0f[go] = (float)res;
                     wn[v] = res;  // local order; the CFL rate only needs |U|
                 }
             }
