@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=3)
     p.add_argument("--cpu-sample", type=int, default=96, help="grid of the oracle's bounded sample")
     p.add_argument("--skip-cpu", action="store_true", help="omit the CPU-oracle baseline (profiling runs)")
+    p.add_argument("--no-ensemble", dest="ensemble", action="store_false",
+                   help="omit the batched 1-D ensemble leg")
     return p.parse_args()
 
 
@@ -173,6 +175,48 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def ensemble_leg(gks, WL, stream, peak32):
+    """4096 independent 1-D Riemann problems (200..4000 cells, seeded) to
+    t = 0.15 in one persistent launch, float32 flux / float64 state, launch
+    shape from the autotuner.  One untimed run captures the graph; the timed
+    run replays it from the same initial state.  Cell-updates = sum over
+    problems of cells x steps taken (a problem flagged non-physical stops
+    early and counts only its own steps)."""
+    import numpy as np
+    import torch
+    E = WL.ensemble_1d()
+    B = gks.Batch(E.ncells, np.ones(E.ncells.size), precision="fp32")
+    B.set_stream(stream.cuda_stream)
+    B.set_state(E.W)
+    th, bp, _ = B.tune(0.005, use_cache=False)
+    B.advance_to(E.t_end, allow_failed=True)
+    B.set_state(E.W)
+    L0 = B.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    nbad = B.advance_to(E.t_end, allow_failed=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    t, steps, err, _ = B.progress()
+    cu = float((E.ncells.astype(np.float64) * steps).sum())
+    fpc = gks.count_flops(1, "fp32", "euler", 1.0)["flops_per_cell_update"]
+    tf = fpc * cu / (ms * 1e-3) / 1e12
+    launches = B.launches() - L0   # graph replays, one kernel each
+    B.close()
+    return {"value": cu / (ms * 1e-3), "unit": UNIT, "workload": "ensemble_1d_riemann",
+            "problems": int(E.ncells.size), "cells": int(E.ncells.sum()), "t_end": E.t_end,
+            "ms": ms, "cell_updates": cu, "max_steps_per_problem": int(steps.max()),
+            "flagged_nonphysical": int(nbad), "launch": {"threads": th, "blocks_per_sm": bp},
+            "gpu_launches": launches,
+            "precision": "fp32 reconstruction+flux, fp64 state and S2O4 accumulation",
+            "flops_per_cell_update": fpc,
+            "roofline": {"bound": "alu", "kernel": "k_batch<float>", "achieved": tf, "peak": peak32,
+                         "unit": "TFLOP/s", "frac": tf / peak32,
+                         "basis": "whole launch vs measured FP32 FMA peak"}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -243,6 +287,7 @@ def main():
     S64 = solver("fp64")
     k64 = max(1, args.fp64_steps)
     ms64, launches64, sn64, sms64 = timed(S64, k64, min(args.warmup, 3))
+    ens = ensemble_leg(gks, WL, stream, peak32) if args.ensemble else None
     clk = clocks.stop()
 
     # same number of steps on both paths from the same state: relative L1 of fp32 vs fp64
@@ -321,6 +366,8 @@ def main():
         "flops_per_cell_update": fm["flops_per_cell_update"],
         "clocks": clk,
     }
+    if ens:
+        line["ensemble"] = ens
     if world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(n=args.cpu_sample)
     print(json.dumps(line))

@@ -141,6 +141,49 @@ const char *gks_status_string(int status);
  * every kernel node). */
 long long  gks_kernel_launches(const gks_ctx *ctx);
 
+/* ---- batched ensemble of independent 1-D problems ---- */
+
+/* A batch holds `count` independent 1-D problems, problem k on [0, lengths[k]]
+ * with ncells[k] >= 3 uniform cells and zero-gradient ("non-reflecting",
+ * Sec. 5.2) ends, all with the same gas and scheme.  gks_batch_advance_to
+ * advances every problem to t_end with its own CFL time steps (Sec. 5) in ONE
+ * persistent kernel launch, replayed as a CUDA graph: each block takes the
+ * next problem from an atomic queue ordered by decreasing estimated cost
+ * (n^2 * max signal speed / length) and runs it to t_end alone.
+ * States are packed [3][sum ncells] float64 (rho, rho U, rho E), problem k
+ * starting at cell sum_{j<k} ncells[j]; on_device as for gks_set_state. */
+typedef struct gks_batch gks_batch;
+gks_status gks_batch_create(int count, const int *ncells, const double *lengths, int precision,
+                            gks_batch **out);
+void       gks_batch_destroy(gks_batch *b);
+gks_status gks_batch_set_gas(gks_batch *b, const gks_gas *gas);
+gks_status gks_batch_set_scheme(gks_batch *b, const gks_scheme *scheme);
+gks_status gks_batch_set_stream(gks_batch *b, void *stream);
+/* resets every problem's time, steps, error word; recomputes the cost order */
+gks_status gks_batch_set_state(gks_batch *b, const double *W, int on_device);
+gks_status gks_batch_get_state(gks_batch *b, double *W, int on_device);
+/* max_steps: per problem and call (<= 0: none).  Synchronises.  A problem
+ * whose cell averages leave the physical set (rho <= 0 or p <= 0) stops at the
+ * end of the step that produced them, keeping that state, its time and step
+ * count, with bit 0 of its error word set; the other problems still advance to
+ * t_end.  Returns GKS_ENONPHYSICAL if any problem is flagged (count in
+ * gks_batch_last_error; which ones in gks_batch_get_progress). */
+gks_status gks_batch_advance_to(gks_batch *b, double t_end, long long max_steps);
+/* per-problem arrays of length count (any may be NULL) */
+gks_status gks_batch_get_progress(gks_batch *b, double *t, long long *steps, unsigned int *err,
+                                  long long *fallbacks);
+/* launch shape: threads per block 128 or 256, blocks per SM 1..16 */
+gks_status gks_batch_set_launch(gks_batch *b, int threads, int blocks_per_sm);
+/* Autotuner: times every launch shape (threads 128/256 x 1/2/4/8 blocks per
+ * SM) advancing the stored state to t_probe, restores the state, applies the
+ * fastest and appends it to a cache file ($GKS_TUNE_CACHE, else
+ * ~/.cache/gks_batch_tune.txt) keyed by device, precision, collision model,
+ * count and total cells; use_cache = 1 applies a cached entry without timing. */
+gks_status gks_batch_tune(gks_batch *b, double t_probe, int use_cache, int *threads, int *blocks_per_sm,
+                          double *best_ms);
+const char *gks_batch_last_error(const gks_batch *b);
+long long  gks_batch_launches(const gks_batch *b);
+
 /* ---- measurement helpers (not part of the paper's method) ---- */
 
 /* Per-kernel timing with CUDA events recorded on the context stream around

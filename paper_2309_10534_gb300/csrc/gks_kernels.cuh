@@ -48,7 +48,7 @@ __device__ __forceinline__ T cell_sigma(const double* w, int dim, T gamma, T mu,
 {
     const T r = (T)w[0], ir = T(1) / r;
     const T U = (T)w[1] * ir, V = (dim == 2) ? (T)w[2] * ir : T(0);
-    const T E = (T)w[dim + 1];
+    const T E = (T)(dim == 2 ? w[3] : w[2]);  // no dynamic index: keeps w in registers
     const T p = (gamma - T(1)) * (E - T(0.5) * r * (U * U + V * V));
     if (!(r > T(0) && p > T(0) && isfinite(p))) err |= 1u;
     const T a = sqrt(gamma * p * ir);
@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
     const T idx_ = (T)a.idx;
     // phase 1: TENO-D per cell c (interior i0 - 1 + c), both faces
     for (int c = tid; c < TN + 2; c += NT) {
+#pragma unroll
         for (int v = 0; v < 3; ++v) {
             T q[5];
 #pragma unroll
@@ -144,6 +145,7 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
         Side<T> L, R;
 #pragma unroll
         for (int k = 0; k < 4; ++k) { L.W[k] = L.Wn[k] = L.Wt[k] = R.W[k] = R.Wn[k] = R.Wt[k] = T(0); }
+#pragma unroll
         for (int v = 0; v < 3; ++v) {
             L.W[slot[v]] = sL[v][0][f];
             L.Wn[slot[v]] = sL[v][1][f];
@@ -151,11 +153,13 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
             R.Wn[slot[v]] = sR[v][1][f];
         }
         if (!physical<T, 1>(L.W, fp.gm1)) {
+#pragma unroll
             for (int v = 0; v < 3; ++v) { L.W[slot[v]] = sq[v][f + 2]; L.Wn[slot[v]] = T(0); }
             ++nfb;
             if (!physical<T, 1>(L.W, fp.gm1)) err |= 2u;
         }
         if (!physical<T, 1>(R.W, fp.gm1)) {
+#pragma unroll
             for (int v = 0; v < 3; ++v) { R.W[slot[v]] = sq[v][f + 3]; R.Wn[slot[v]] = T(0); }
             ++nfb;
             if (!physical<T, 1>(R.W, fp.gm1)) err |= 2u;
@@ -163,6 +167,7 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
         T F[4], dF[4];
         point_flux<T, 1, NONEQ, PRFIX>(L, R, fp, F, dF);
         const T tdt = (T)dt;
+#pragma unroll
         for (int v = 0; v < 3; ++v) {
             const int s = slot[v];
             if (a.stage == 1) {
@@ -182,6 +187,7 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
         if (i >= g.nx) continue;
         const long long o = i + NG;
         if (a.stage == 1) {
+#pragma unroll
             for (int v = 0; v < 3; ++v) {
                 const double w = a.src[(long long)v * g.plane + o];
                 a.out0[(long long)v * g.plane + o] = w - cx * (double)(sG[0][v][c + 1] - sG[0][v][c]);
@@ -189,6 +195,7 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
             }
         } else {
             double w[4];
+#pragma unroll
             for (int v = 0; v < 3; ++v) {
                 const double r = a.acc[(long long)v * g.plane + o] - cx * (double)(sG[0][v][c + 1] - sG[0][v][c]);
                 a.out0[(long long)v * g.plane + o] = r;
@@ -306,7 +313,7 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
         const int r = tid / NF, f = tid % NF;  // pair = tid
         const T ih = (T)a.iht;
         const T g0 = T(-0.28867513459481288), g1 = T(0.28867513459481288);  // -+1/(2 sqrt 3)
-#pragma unroll 1
+#pragma unroll1
         for (int side = 0; side < 2; ++side) {
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
@@ -338,7 +345,7 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
     // Gauss points of one face segment and average them (weights 1/2)
     unsigned int nfb = 0, err = 0;
     const T tdt = (T)dt;
-#pragma unroll 1
+#pragma unroll1
     for (int task = tid; task < 2 * NP; task += NT) {
         const int pair = task >> 1, gpi = task & 1;
         const int r = pair / NF, f = pair % NF;

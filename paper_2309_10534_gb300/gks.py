@@ -345,3 +345,112 @@ def step1d_noalloc(W_in, W_out, dx, dt, bc=("zerograd", "zerograd"), precision="
     if st != GKS_OK:
         raise GKSError(st, "gks_step1d_noalloc")
     return err.value
+
+
+class Batch:
+    """Independent 1-D problems advanced in one persistent launch (gks_batch_*).
+    W: packed [3][sum ncells] float64."""
+
+    def __init__(self, ncells, lengths, precision="fp32", gamma=1.4, mu=0.0, Pr=1.0, tau="euler", cfl=0.5,
+                 **scheme):
+        L = lib()
+        if not getattr(L, "_batch_declared", False):
+            sig = {
+                "gks_batch_create": ([C.c_int, C.POINTER(C.c_int), _dp, C.c_int, C.POINTER(_vp)], C.c_int),
+                "gks_batch_destroy": ([_vp], None),
+                "gks_batch_set_gas": ([_vp, C.POINTER(Gas)], C.c_int),
+                "gks_batch_set_scheme": ([_vp, C.POINTER(Scheme)], C.c_int),
+                "gks_batch_set_stream": ([_vp, _vp], C.c_int),
+                "gks_batch_set_state": ([_vp, _vp, C.c_int], C.c_int),
+                "gks_batch_get_state": ([_vp, _vp, C.c_int], C.c_int),
+                "gks_batch_advance_to": ([_vp, C.c_double, C.c_longlong], C.c_int),
+                "gks_batch_get_progress": ([_vp, _dp, C.POINTER(C.c_longlong), C.POINTER(C.c_uint),
+                                            C.POINTER(C.c_longlong)], C.c_int),
+                "gks_batch_set_launch": ([_vp, C.c_int, C.c_int], C.c_int),
+                "gks_batch_tune": ([_vp, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp],
+                                   C.c_int),
+                "gks_batch_last_error": ([_vp], C.c_char_p),
+                "gks_batch_launches": ([_vp], C.c_longlong),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            L._batch_declared = True
+        n = np.ascontiguousarray(ncells, dtype=np.int32)
+        lens = np.ascontiguousarray(lengths, dtype=np.float64)
+        self.count = len(n)
+        self.total = int(n.sum())
+        h = _vp()
+        st = L.gks_batch_create(self.count, n.ctypes.data_as(C.POINTER(C.c_int)), lens.ctypes.data_as(_dp),
+                                PRECISION[precision] if isinstance(precision, str) else int(precision), C.byref(h))
+        if st != GKS_OK:
+            raise GKSError(st, "gks_batch_create")
+        self.h = h
+        self._check(L.gks_batch_set_gas(h, C.byref(Gas(gamma, mu, Pr))))
+        self._check(L.gks_batch_set_scheme(h, C.byref(default_scheme(cfl=cfl, tau=tau, **scheme))))
+
+    def _check(self, st):
+        if st != GKS_OK:
+            raise GKSError(st, lib().gks_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gks_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_handle):
+        self._check(lib().gks_batch_set_stream(self.h, _vp(stream_handle)))
+
+    def set_state(self, W):
+        if hasattr(W, "data_ptr"):
+            self._check(lib().gks_batch_set_state(self.h, _vp(W.data_ptr()), 1))
+        else:
+            W = np.ascontiguousarray(W, dtype=np.float64)
+            if W.size != 3 * self.total:
+                raise ValueError("packed state must have 3 x %d values" % self.total)
+            self._check(lib().gks_batch_set_state(self.h, W.ctypes.data_as(_vp), 0))
+
+    def get_state(self):
+        W = np.empty((3, self.total))
+        self._check(lib().gks_batch_get_state(self.h, W.ctypes.data_as(_vp), 0))
+        return W
+
+    def advance_to(self, t_end, max_steps=0, allow_failed=False):
+        """Advance every problem to t_end.  A problem that produced a
+        non-physical cell average stops there and is flagged in progress();
+        with allow_failed that is not an error and the number of flagged
+        problems is returned."""
+        st = lib().gks_batch_advance_to(self.h, float(t_end), int(max_steps))
+        if st == GKS_ENONPHYSICAL and allow_failed:
+            return int(np.count_nonzero(self.progress()[2]))
+        self._check(st)
+        return 0
+
+    def progress(self):
+        t = np.zeros(self.count)
+        steps = np.zeros(self.count, dtype=np.int64)
+        err = np.zeros(self.count, dtype=np.uint32)
+        fb = C.c_longlong(0)
+        self._check(lib().gks_batch_get_progress(self.h, t.ctypes.data_as(_dp),
+                                                 steps.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                                 err.ctypes.data_as(C.POINTER(C.c_uint)), C.byref(fb)))
+        return t, steps, err, fb.value
+
+    def set_launch(self, threads, blocks_per_sm):
+        self._check(lib().gks_batch_set_launch(self.h, int(threads), int(blocks_per_sm)))
+
+    def tune(self, t_probe, use_cache=True):
+        th, bp, ms = C.c_int(0), C.c_int(0), C.c_double(0.0)
+        self._check(lib().gks_batch_tune(self.h, float(t_probe), 1 if use_cache else 0, C.byref(th), C.byref(bp),
+                                         C.byref(ms)))
+        return th.value, bp.value, ms.value
+
+    def launches(self):
+        return lib().gks_batch_launches(self.h)
