@@ -184,6 +184,39 @@ gks_status gks_batch_tune(gks_batch *b, double t_probe, int use_cache, int *thre
 const char *gks_batch_last_error(const gks_batch *b);
 long long  gks_batch_launches(const gks_batch *b);
 
+/* ---- discrete adjoint (2-D, collision-free flux) ---- */
+
+/* Hand-written reverse mode of the 2-D S2O4 step with fixed dt (Sec. 2.2)
+ * for the collision-free flux (tau_mode = GKS_TAU_ZERO, the paper's setting
+ * for smooth inviscid flow, Sec. 5.1 and 5.5): the transposed Jacobians of
+ * the two stages, of the Gauss-point flux (kinetic merge, Euler flux and its
+ * compatibility time derivative) and of the TENO-D reconstructions with the
+ * stencil selection of the forward pass held fixed, and of the ghost fill.
+ * An adjoint object belongs to one context (2-D, tau_mode zero; otherwise
+ * GKS_EUNSUPPORTED) and uses that context's state and stream.
+ * checkpoint_every = k >= 1: the forward pass keeps W every k steps (device
+ * memory: ceil(nsteps/k) + k + 8 state-sized arrays plus scratch of about
+ * 116 x nx x ny values of the working precision); the backward pass
+ * recomputes one k-step segment at a time. */
+typedef struct gks_adjoint gks_adjoint;
+gks_status gks_adjoint_create(gks_ctx *ctx, int checkpoint_every, gks_adjoint **out);
+void       gks_adjoint_destroy(gks_adjoint *adj);
+/* nsteps steps of fixed dt from the context's current state, keeping
+ * checkpoints; leaves the final state W_N in the context.  Synchronises;
+ * GKS_ENONPHYSICAL as gks_step. */
+gks_status gks_adjoint_forward(gks_adjoint *adj, int nsteps, double dt);
+/* gW0 = (dW_N/dW_0)^T gWN for the last forward pass; gWN, gW0 interior
+ * [nv][ny][nx] float64 (host, or device with on_device = 1).  Leaves the
+ * context at W_N.  Synchronises. */
+gks_status gks_adjoint_backward(gks_adjoint *adj, const double *gWN, double *gW0, int on_device);
+/* kernel launches issued by the adjoint's own kernels (forward steps not counted) */
+long long  gks_adjoint_launches(const gks_adjoint *adj);
+/* One step's vector-Jacobian product: gin = (dS/dW)^T gout for the S2O4 step
+ * S of fixed dt at state W (interior layout as above).  Sets the context's
+ * state to S(W).  Allocates and frees a temporary adjoint object. */
+gks_status gks_vjp_step(gks_ctx *ctx, const double *W, const double *gout, double *gin, double dt,
+                        int on_device);
+
 /* ---- measurement helpers (not part of the paper's method) ---- */
 
 /* Per-kernel timing with CUDA events recorded on the context stream around

@@ -40,6 +40,21 @@ int gks_host_point_flux(int dim, int precision, int tau_mode, double gamma, doub
                         const double *Wr, const double *Wrn, const double *Wrt,
                         double *F, double *dF);
 
+/* Transpose of TENO-D with the selection of q held fixed (the adjoint's
+ * frozen selection; with it the reconstruction is linear in q): the
+ * cotangents gfaces[0..3] of faces[] and ggauss[0..3] of gauss[] as in
+ * gks_host_teno -> gq[0..4].  Returns the large-stencil flag or -1. */
+int gks_host_teno_vjp(int precision, const double *q, double eps, int qpow, double ct1, double ct2,
+                      const double *gfaces, const double *ggauss, double *gq);
+
+/* Vector-Jacobian product of the 2-D collision-free (tau = 0) point flux:
+ * cotangents gF[4], gdF[4] of F and dF/dt -> gl[12], gr[12], the cotangents
+ * of (W, Wn, Wt) of the left and right side. */
+int gks_host_point_flux_vjp(int precision, double gamma,
+                            const double *Wl, const double *Wln, const double *Wlt,
+                            const double *Wr, const double *Wrn, const double *Wrt,
+                            const double *gF, const double *gdF, double *gl, double *gr);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,686 @@
+// gks_adjoint.cu -- hand-written discrete adjoint of the 2-D S2O4 step
+// (collision-free flux, tau = 0) with checkpointing (include/gks.h,
+// gks_adjoint_* and gks_vjp_step).
+//
+// One step of the scheme (Sec. 2.2, dimension by dimension, fixed dt):
+//   W*      = W^n - dt/h  d(F/2 + dt/8 dF)(W^n)     (both directions)
+//   A       = W^n - dt/h  d(F + dt/6 dF)(W^n)
+//   W^{n+1} = A   - dt/h  d(dt/3 dF)(W*)
+// where d is the face difference and (F, dF) the Gauss-averaged face flux
+// and its time derivative.  Given lam = dJ/dW^{n+1}, the adjoint step is
+//   lam*  = [d dF/dW*]^T (dt^2/(3h) Delta lam)
+//   lam^n = lam + lam* + [dF/dW^n]^T (dt/h Delta(lam + lam*/2))
+//                      + [d dF/dW^n]^T (dt^2/h Delta(lam/6 + lam*/8))
+// with Delta lam the difference of lam across a face (zero outside the
+// interior).  The transposed flux Jacobian of one direction is applied by
+// four kernels on the stage input:
+//   k_adj_lines   normal TENO-D per cell -> face-line values and slopes
+//                 (the forward sweep's phase 1)
+//   k_adj_gauss   per face segment and Gauss point: tangential TENO-D to the
+//                 Gauss point (forward), the reverse of the point flux, then
+//                 the transposed tangential reconstruction; writes, per face
+//                 segment, its contributions to the five line rows of its
+//                 tangential stencil
+//   k_adj_normal  per cell: gathers the line cotangents of its two faces and
+//                 applies the transposed normal reconstruction; writes its
+//                 contributions to the five cells of its stencil
+//   k_adj_gather  per cell: sums the contributions it received
+// and the ghost layers are folded back onto the interior cells they copy
+// (the transpose of the ghost fill).  TENO-D selections are recomputed from
+// the same stage inputs as in the forward pass, i.e. frozen at the forward
+// pass's choice.  Every sum is a gather in a fixed order, so the result does
+// not depend on scheduling (only the positivity fallback, which smooth flows
+// do not take, adds with atomics).
+//
+// Checkpointing: gks_adjoint_forward keeps W every k steps; the backward pass
+// recomputes each k-step segment from its checkpoint, keeping its states, and
+// runs the segment's adjoint steps in reverse.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "../../include/gks.h"
+#include "gks_adjoint.cuh"
+#include "gks_ctx.h"
+
+using namespace gks;
+
+namespace {
+
+constexpr int NQ = 16;  // line quantities per face segment: [vL, sL, vR, sR] x 4 variables
+
+// One direction of one stage.  Orientation: dirn 0 = faces normal to x
+// (normal index = x, unit stride), dirn 1 = faces normal to y.  Scratch
+// arrays are laid out with the unit-stride grid direction fastest.
+struct AdjDir {
+    const double* src;    // stage input, float64 path (ghosts filled)
+    const float* srcf;    // stage input, float32 path (float32 shadow, ghosts filled)
+    const double* lam1;   // cotangent fields (ghosted; interior used)
+    const double* lam2;   // may be null
+    double cF1, cD1, cF2, cD2;
+    void* lines;          // [NQ][faces nn+1][rows nt+4]
+    void* contrib;        // [5][NQ][faces nn+1][rows nt]
+    void* dcell;          // [5][4][cells nn+2][rows nt+4]
+    double* gW;           // ghosted gradient accumulator
+    int dirn, nn, nt;
+    long long sn, st;     // element strides along normal / tangential
+    double ihn, iht;
+};
+
+__device__ __forceinline__ int gvar_(int v, bool swap) { return (swap && (v == 1 || v == 2)) ? 3 - v : v; }
+
+// scratch indices: faces f in [0, nn], line rows r in [-2, nt+2), Gauss rows
+// in [0, nt), cells i in [-1, nn]
+__device__ __forceinline__ long long lidx(const AdjDir& a, int f, int r)
+{
+    return a.dirn == 0 ? (long long)(r + 2) * (a.nn + 1) + f : (long long)f * (a.nt + 4) + (r + 2);
+}
+__device__ __forceinline__ long long cidx(const AdjDir& a, int f, int r)
+{
+    return a.dirn == 0 ? (long long)r * (a.nn + 1) + f : (long long)f * a.nt + r;
+}
+__device__ __forceinline__ long long didx(const AdjDir& a, int i, int r)
+{
+    return a.dirn == 0 ? (long long)(r + 2) * (a.nn + 2) + (i + 1) : (long long)(i + 1) * (a.nt + 4) + (r + 2);
+}
+
+template <typename T>
+__device__ __forceinline__ T load_src(const AdjDir& a, long long gi)
+{
+    if constexpr (sizeof(T) == 4) return a.srcf[gi];
+    else return a.src[gi];
+}
+
+// map the launch to (normal index, tangential index): the unit-stride grid
+// direction runs along threadIdx.x
+__device__ __forceinline__ void map2(const AdjDir& a, int& n, int& t, int n0, int t0)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (a.dirn == 0) { n = n0 + x; t = t0 + y; }
+    else { n = n0 + y; t = t0 + x; }
+}
+
+// ---- phase 1: normal TENO-D of the stage input (as the forward sweep)
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_lines(GridDev g, AdjDir a, TenoT<T> tn)
+{
+    int i, r;
+    map2(a, i, r, -1, -2);
+    if (i > a.nn || r >= a.nt + 2) return;
+    const bool swap = a.dirn != 0;
+    const long long org = (long long)NG * g.pitch + NG;
+    const long long LP = (long long)(a.nn + 1) * (a.nt + 4);
+    T* L = static_cast<T*>(a.lines);
+    const T ih = (T)a.ihn;
+#pragma unroll 1
+    for (int v = 0; v < 4; ++v) {
+        const long long base = (long long)gvar_(v, swap) * g.plane + org + r * a.st;
+        T q[5];
+#pragma unroll
+        for (int s = 0; s < 5; ++s) q[s] = load_src<T>(a, base + (i - 2 + s) * a.sn);
+        TenoSel<T> S;
+        teno_select(q, tn, S);
+        T vp, dp, vm, dm;
+        teno_faces(q, S, vp, dp, vm, dm);
+        if (i + 1 <= a.nn) {
+            L[(0 * 4 + v) * LP + lidx(a, i + 1, r)] = vp;
+            L[(1 * 4 + v) * LP + lidx(a, i + 1, r)] = dp * ih;
+        }
+        if (i >= 0) {
+            L[(2 * 4 + v) * LP + lidx(a, i, r)] = vm;
+            L[(3 * 4 + v) * LP + lidx(a, i, r)] = dm * ih;
+        }
+    }
+}
+
+// frozen selection as 4 bits: large, and the kept small stencils
+template <typename T>
+__device__ __forceinline__ unsigned sel_code(const TenoSel<T>& S)
+{
+    if (S.large) return 1u;
+    return (S.w[0] > T(0) ? 2u : 0u) | (S.w[1] > T(0) ? 4u : 0u) | (S.w[2] > T(0) ? 8u : 0u);
+}
+template <typename T>
+__device__ __forceinline__ void sel_decode(unsigned c, TenoSel<T>& S)
+{
+    S.large = (c & 1u) != 0;
+    const T d0 = (c & 2u) ? T(1) : T(0), d1 = (c & 4u) ? T(1) : T(0), d2 = (c & 8u) ? T(1) : T(0);
+    const T dsum = d0 + d1 + d2;
+    const T inv = S.large ? T(0) : T(1) / dsum;  // as teno_select: d_k / sum d
+    S.w[0] = d0 * inv;
+    S.w[1] = d1 * inv;
+    S.w[2] = d2 * inv;
+}
+
+// ---- Gauss points: forward tangential TENO-D, reverse point flux, transposed
+// tangential TENO-D.  Two adjacent lanes hold the two Gauss points of one face
+// segment; lane 0 finishes the left side's quantities, lane 1 the right's.
+template <typename T>
+__global__ void __launch_bounds__(128) k_adj_gauss(GridDev g, AdjDir a, FluxParams<T> fp, TenoT<T> tt)
+{
+    const int gp = threadIdx.x & 1;
+    const int x = (blockIdx.x * blockDim.x + threadIdx.x) >> 1, y = blockIdx.y * blockDim.y + threadIdx.y;
+    int f, r;
+    if (a.dirn == 0) { f = x; r = y; }
+    else { f = y; r = x; }
+    const bool valid = f <= a.nn && r < a.nt;
+    const int fc = valid ? f : 0, rc = valid ? r : 0;  // in-range indices for the idle lanes' loads
+    const bool swap = a.dirn != 0;
+    const long long org = (long long)NG * g.pitch + NG;
+    const long long LP = (long long)(a.nn + 1) * (a.nt + 4);
+    const long long CP = (long long)(a.nn + 1) * a.nt;
+    const T* Lq = static_cast<const T*>(a.lines);
+    const T gpos = gp ? T(0.28867513459481288) : T(-0.28867513459481288);
+    const T iht = (T)a.iht;
+
+    // forward: the Gauss-point states of both sides at this lane's point
+    Side<T> L, R;
+    unsigned long long codes = 0;  // 4 bits per quantity q = 4 k + v
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            T q[5];
+#pragma unroll
+            for (int s = 0; s < 5; ++s) q[s] = Lq[(k * 4 + v) * LP + lidx(a, fc, rc - 2 + s)];
+            TenoSel<T> S;
+            teno_select(q, tt, S);
+            T val, der;
+            teno_gauss(S, gpos, val, der);
+            codes |= (unsigned long long)sel_code(S) << (4 * (k * 4 + v));
+            Side<T>& X = (k < 2) ? L : R;
+            if ((k & 1) == 0) { X.W[v] = val; X.Wt[v] = der * iht; }
+            else X.Wn[v] = val;
+        }
+    }
+    // positivity fallback, as the forward: the adjacent cell average, zero slopes
+    const bool fbL = valid && !physical<T, 2>(L.W, fp.gm1);
+    const bool fbR = valid && !physical<T, 2>(R.W, fp.gm1);
+    if (fbL || fbR) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const long long b = (long long)gvar_(v, swap) * g.plane + org + rc * a.st;
+            if (fbL) { L.W[v] = load_src<T>(a, b + (fc - 1) * a.sn); L.Wn[v] = L.Wt[v] = T(0); }
+            if (fbR) { R.W[v] = load_src<T>(a, b + fc * a.sn); R.Wn[v] = R.Wt[v] = T(0); }
+        }
+    }
+    // face cotangents (each Gauss point carries weight 1/2)
+    T gF[4], gdF[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const long long b = (long long)gvar_(v, swap) * g.plane + org + rc * a.st;
+        double d1 = 0.0, d2 = 0.0;
+        if (fc < a.nn) {
+            d1 += a.lam1[b + fc * a.sn];
+            if (a.lam2) d2 += a.lam2[b + fc * a.sn];
+        }
+        if (fc >= 1) {
+            d1 -= a.lam1[b + (fc - 1) * a.sn];
+            if (a.lam2) d2 -= a.lam2[b + (fc - 1) * a.sn];
+        }
+        gF[v] = (T)(0.5 * (a.cF1 * d1 + a.cF2 * d2));
+        gdF[v] = (T)(0.5 * (a.cD1 * d1 + a.cD2 * d2));
+    }
+    Side<T> gL, gR;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) gL.W[v] = gL.Wn[v] = gL.Wt[v] = gR.W[v] = gR.Wn[v] = gR.Wt[v] = T(0);
+    if (valid) point_flux_vjp(L, R, fp, gF, gdF, gL, gR);
+    if (fbL || fbR) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const long long b = (long long)gvar_(v, swap) * g.plane + org + rc * a.st;
+            if (fbL) {
+                atomicAdd(&a.gW[b + (fc - 1) * a.sn], (double)gL.W[v]);
+                gL.W[v] = gL.Wn[v] = gL.Wt[v] = T(0);
+            }
+            if (fbR) {
+                atomicAdd(&a.gW[b + fc * a.sn], (double)gR.W[v]);
+                gR.W[v] = gR.Wn[v] = gR.Wt[v] = T(0);
+            }
+        }
+    }
+    // exchange: lane 0 keeps the left side (receives its + point), lane 1 the right
+    Side<T>& mine = gp ? gR : gL;
+    const Side<T>& other = gp ? gL : gR;
+    T oW[4], oWn[4], oWt[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        oW[v] = __shfl_xor_sync(0xffffffffu, other.W[v], 1);
+        oWn[v] = __shfl_xor_sync(0xffffffffu, other.Wn[v], 1);
+        oWt[v] = __shfl_xor_sync(0xffffffffu, other.Wt[v], 1);
+    }
+    if (!valid) return;
+    const unsigned long long pcodes = codes;  // both lanes computed the same selections
+    const T gm = T(-0.28867513459481288), gpl = T(0.28867513459481288);
+    T* C = static_cast<T*>(a.contrib);
+#pragma unroll 1
+    for (int kk = 0; kk < 2; ++kk) {
+        const int k = 2 * gp + kk;  // lane 0: k = 0, 1 (left), lane 1: k = 2, 3 (right)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int qi = k * 4 + v;
+            TenoSel<T> S;
+            sel_decode((unsigned)(pcodes >> (4 * qi)) & 15u, S);
+            // cotangents at the - point and the + point
+            T gvm, gdm, gvp, gdp;
+            if (kk == 0) {
+                const T a0 = mine.W[v], d0 = mine.Wt[v] * iht, a1 = oW[v], d1 = oWt[v] * iht;
+                gvm = gp ? a1 : a0; gdm = gp ? d1 : d0;
+                gvp = gp ? a0 : a1; gdp = gp ? d0 : d1;
+            } else {
+                gvm = gp ? oWn[v] : mine.Wn[v];
+                gvp = gp ? mine.Wn[v] : oWn[v];
+                gdm = gdp = T(0);
+            }
+            T gq[5] = {T(0), T(0), T(0), T(0), T(0)};
+            teno_gauss_T(S, gm, gvm, gdm, gq);
+            teno_gauss_T(S, gpl, gvp, gdp, gq);
+#pragma unroll
+            for (int s = 0; s < 5; ++s) C[(long long)(s * NQ + qi) * CP + cidx(a, f, r)] = gq[s];
+        }
+    }
+}
+
+// ---- per cell: line cotangents of its faces -> transposed normal TENO-D
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_normal(GridDev g, AdjDir a, TenoT<T> tn)
+{
+    int i, r;
+    map2(a, i, r, -1, -2);
+    if (i > a.nn || r >= a.nt + 2) return;
+    const bool swap = a.dirn != 0;
+    const long long org = (long long)NG * g.pitch + NG;
+    const long long CP = (long long)(a.nn + 1) * a.nt;
+    const long long DP = (long long)(a.nn + 2) * (a.nt + 4);
+    const T* C = static_cast<const T*>(a.contrib);
+    T* D = static_cast<T*>(a.dcell);
+    const T ih = (T)a.ihn;
+    // line row r receives from Gauss row r - s + 2 at stencil position s
+    auto gline = [&](int q, int f) {
+        T acc = T(0);
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const int rg = r - s + 2;
+            if (rg >= 0 && rg < a.nt) acc += C[(long long)(s * NQ + q) * CP + cidx(a, f, rg)];
+        }
+        return acc;
+    };
+#pragma unroll 1
+    for (int v = 0; v < 4; ++v) {
+        T gvp = T(0), gdp = T(0), gvm = T(0), gdm = T(0);
+        if (i + 1 <= a.nn) {
+            gvp = gline(0 * 4 + v, i + 1);
+            gdp = gline(1 * 4 + v, i + 1) * ih;
+        }
+        if (i >= 0) {
+            gvm = gline(2 * 4 + v, i);
+            gdm = gline(3 * 4 + v, i) * ih;
+        }
+        const long long base = (long long)gvar_(v, swap) * g.plane + org + r * a.st;
+        T q[5];
+#pragma unroll
+        for (int s = 0; s < 5; ++s) q[s] = load_src<T>(a, base + (i - 2 + s) * a.sn);
+        TenoSel<T> S;
+        teno_select(q, tn, S);
+        T gq[5] = {T(0), T(0), T(0), T(0), T(0)};
+        teno_faces_T(S, gvp, gdp, gvm, gdm, gq);
+#pragma unroll
+        for (int s = 0; s < 5; ++s) D[(long long)(s * 4 + v) * DP + didx(a, i, r)] = gq[s];
+    }
+}
+
+// ---- per cell: sum of the contributions of the cells whose stencil holds it
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_gather(GridDev g, AdjDir a)
+{
+    int j, r;
+    map2(a, j, r, -3, -2);
+    if (j > a.nn + 2 || r >= a.nt + 2) return;
+    const bool swap = a.dirn != 0;
+    const long long org = (long long)NG * g.pitch + NG;
+    const long long DP = (long long)(a.nn + 2) * (a.nt + 4);
+    const T* D = static_cast<const T*>(a.dcell);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        T acc = T(0);
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const int i = j + 2 - s;  // cell i's stencil position s is cell i - 2 + s = j
+            if (i >= -1 && i <= a.nn) acc += D[(long long)(s * 4 + v) * DP + didx(a, i, r)];
+        }
+        a.gW[(long long)gvar_(v, swap) * g.plane + org + j * a.sn + r * a.st] += (double)acc;
+    }
+}
+
+// ---- transpose of the ghost fill: y ghost rows first (over the full ghosted
+// width), then the x ghost columns of the interior rows.  One thread per
+// column (row) walks its six ghost cells in a fixed order.
+__global__ void k_fold_y(GridDev g, double* gW)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gx = g.nx + 2 * NG;
+    if (i >= gx) return;
+    for (int k = 0; k < 2 * NG; ++k) {
+        const int j = k < NG ? k : g.ny + k;
+        bool fn, fa;
+        const int sj = ghost_src(g.bc[2 + (j >= NG + g.ny)], g.ny, j, fn, fa);
+        for (int v = 0; v < 4; ++v) {
+            const bool neg = (v == 2 && (fn || fa)) || (v == 1 && fa);
+            double* p = gW + (long long)v * g.plane + (long long)j * g.pitch + i;
+            gW[(long long)v * g.plane + (long long)sj * g.pitch + i] += neg ? -*p : *p;
+            *p = 0.0;
+        }
+    }
+}
+
+__global__ void k_fold_x(GridDev g, double* gW)
+{
+    const int j = NG + blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= NG + g.ny) return;
+    for (int k = 0; k < 2 * NG; ++k) {
+        const int i = k < NG ? k : g.nx + k;
+        bool fn, fa;
+        const int si = ghost_src(g.bc[(i >= NG + g.nx)], g.nx, i, fn, fa);
+        for (int v = 0; v < 4; ++v) {
+            const bool neg = (v == 1 && (fn || fa)) || (v == 2 && fa);
+            double* p = gW + (long long)v * g.plane + (long long)j * g.pitch + i;
+            gW[(long long)v * g.plane + (long long)j * g.pitch + si] += neg ? -*p : *p;
+            *p = 0.0;
+        }
+    }
+}
+
+// out = a + b + c (whole ghosted arrays)
+__global__ void k_sum3(const double* __restrict__ a, const double* __restrict__ b, const double* __restrict__ c,
+                       double* __restrict__ out, long long n)
+{
+    for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += 256ll * gridDim.x) out[i] = a[i] + b[i] + c[i];
+}
+
+__global__ void k_shadow(const double* __restrict__ W, float* __restrict__ Wf, long long n)
+{
+    for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += 256ll * gridDim.x) Wf[i] = (float)W[i];
+}
+
+int blocks_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 4096); }
+
+}  // namespace
+
+struct gks_adjoint {
+    gks_ctx* c = nullptr;
+    int k = 1;
+    int nsteps = 0;
+    double dt = 0.0;
+    bool have_forward = false;
+    std::vector<double*> ckpt;   // W at steps 0, k, 2k, ... (ghosted)
+    std::vector<double*> seg;    // W of the segment being reversed
+    double* WN = nullptr;        // final state of the forward pass
+    double *lam = nullptr, *lams = nullptr, *gacc = nullptr, *nxt = nullptr;
+    void *lines = nullptr, *contrib = nullptr, *dcell = nullptr;
+    long long launches = 0;
+};
+
+namespace {
+
+gks_status adj_alloc(gks_adjoint* A, double** p)
+{
+    gks_ctx* c = A->c;
+    if (!*p) CK(cudaMalloc(p, c->arr_bytes));
+    return GKS_OK;
+}
+
+gks_status adj_scratch(gks_adjoint* A)
+{
+    gks_ctx* c = A->c;
+    if (A->lines) return GKS_OK;
+    const long long nx = c->desc.nx, ny = c->desc.ny;
+    const size_t es = c->desc.precision == GKS_FP32_FLUX ? 4 : 8;
+    const long long lines = std::max((nx + 1) * (ny + 4), (ny + 1) * (nx + 4)) * NQ;
+    const long long contrib = std::max((nx + 1) * ny, (ny + 1) * nx) * 5 * NQ;
+    const long long dcell = std::max((nx + 2) * (ny + 4), (ny + 2) * (nx + 4)) * 20;
+    CK(cudaMalloc(&A->lines, lines * es));
+    CK(cudaMalloc(&A->contrib, contrib * es));
+    CK(cudaMalloc(&A->dcell, dcell * es));
+    gks_status s;
+    if ((s = adj_alloc(A, &A->lam)) || (s = adj_alloc(A, &A->lams)) || (s = adj_alloc(A, &A->gacc)) ||
+        (s = adj_alloc(A, &A->nxt)))
+        return s;
+    return GKS_OK;
+}
+
+// load a ghosted float64 state into the context's W (and its float32 shadow)
+gks_status load_state(gks_adjoint* A, const double* Wg)
+{
+    gks_ctx* c = A->c;
+    CK(cudaMemcpyAsync(c->W, Wg, c->arr_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->Wf) {
+        const long long n = (long long)c->nv * c->g.plane;
+        k_shadow<<<blocks_for(n), 256, 0, c->stream>>>(c->W, c->Wf, n);
+        CK(cudaGetLastError());
+        ++A->launches;
+    }
+    return GKS_OK;
+}
+
+template <typename T>
+gks_status sweep_vjp_t(gks_adjoint* A, AdjDir d)
+{
+    gks_ctx* c = A->c;
+    const HostFlux hf = rt::host_flux(c);
+    const FluxParams<T> fp = make_flux_params<T>(hf);
+    const TenoT<T> tn = teno_t<T>(rt::teno_params(c, false)), tt = teno_t<T>(rt::teno_params(c, true));
+    const GridDev& g = c->g;
+    cudaStream_t st = c->stream;
+    // launch shapes: x along the unit-stride direction
+    auto grid_for = [&](int nnorm, int ntan, dim3 blk, int xmul) {
+        const int ex = d.dirn == 0 ? nnorm : ntan, ey = d.dirn == 0 ? ntan : nnorm;
+        return dim3((unsigned)((ex * xmul + blk.x - 1) / blk.x), (unsigned)((ey + blk.y - 1) / blk.y));
+    };
+    const dim3 b256(32, 8), b128(32, 4);
+    k_adj_lines<T><<<grid_for(d.nn + 2, d.nt + 4, b256, 1), b256, 0, st>>>(g, d, tn);
+    k_adj_gauss<T><<<grid_for(d.nn + 1, d.nt, b128, 2), b128, 0, st>>>(g, d, fp, tt);
+    k_adj_normal<T><<<grid_for(d.nn + 2, d.nt + 4, b256, 1), b256, 0, st>>>(g, d, tn);
+    k_adj_gather<T><<<grid_for(d.nn + 6, d.nt + 4, b256, 1), b256, 0, st>>>(g, d);
+    CK(cudaGetLastError());
+    A->launches += 4;
+    return GKS_OK;
+}
+
+// adds to A->gacc the transposed flux Jacobian of both directions at the
+// stage input (src), with face cotangents from lam1, lam2
+gks_status stage_vjp(gks_adjoint* A, bool stage2_input, const double* lam1, const double* lam2, double cF1,
+                     double cD1, double cF2, double cD2)
+{
+    gks_ctx* c = A->c;
+    const bool f32 = c->desc.precision == GKS_FP32_FLUX;
+    for (int dirn = 0; dirn < 2; ++dirn) {
+        AdjDir d{};
+        d.src = stage2_input ? c->Ws : c->W;
+        d.srcf = stage2_input ? c->Wsf : c->Wf;
+        d.lam1 = lam1;
+        d.lam2 = lam2;
+        const double h = dirn == 0 ? c->g.dx : c->g.dy;
+        d.cF1 = cF1 / h;
+        d.cD1 = cD1 / h;
+        d.cF2 = cF2 / h;
+        d.cD2 = cD2 / h;
+        d.lines = A->lines;
+        d.contrib = A->contrib;
+        d.dcell = A->dcell;
+        d.gW = A->gacc;
+        d.dirn = dirn;
+        if (dirn == 0) {
+            d.nn = c->desc.nx; d.nt = c->desc.ny; d.sn = 1; d.st = c->g.pitch;
+            d.ihn = 1.0 / c->g.dx; d.iht = 1.0 / c->g.dy;
+        } else {
+            d.nn = c->desc.ny; d.nt = c->desc.nx; d.sn = c->g.pitch; d.st = 1;
+            d.ihn = 1.0 / c->g.dy; d.iht = 1.0 / c->g.dx;
+        }
+        gks_status s = f32 ? sweep_vjp_t<float>(A, d) : sweep_vjp_t<double>(A, d);
+        if (s) return s;
+    }
+    const GridDev& g = c->g;
+    k_fold_y<<<(g.nx + 2 * NG + 127) / 128, 128, 0, c->stream>>>(g, A->gacc);
+    k_fold_x<<<(g.ny + 127) / 128, 128, 0, c->stream>>>(g, A->gacc);
+    CK(cudaGetLastError());
+    A->launches += 2;
+    return GKS_OK;
+}
+
+// A->lam <- (dW^{n+1}/dW^n)^T A->lam at the ghosted state Wn
+gks_status adjoint_step(gks_adjoint* A, const double* Wn, double dt)
+{
+    gks_ctx* c = A->c;
+    gks_status s;
+    if ((s = load_state(A, Wn))) return s;
+    // W* of this step (also fills the ghosts of W), then the ghosts of W*
+    if ((s = gks_stage(c, 1, dt))) return s;
+    if ((s = rt::enqueue_ghosts(c, c->Ws, c->stream))) return s;
+    // lam* = [d dF/dW*]^T (dt^2/(3h) Delta lam)
+    CK(cudaMemsetAsync(A->gacc, 0, c->arr_bytes, c->stream));
+    if ((s = stage_vjp(A, true, A->lam, nullptr, 0.0, dt * dt / 3.0, 0.0, 0.0))) return s;
+    std::swap(A->lams, A->gacc);
+    // stage 1 at W^n with the cotangents of A (lam) and of W* (lam*)
+    CK(cudaMemsetAsync(A->gacc, 0, c->arr_bytes, c->stream));
+    if ((s = stage_vjp(A, false, A->lam, A->lams, dt, dt * dt / 6.0, 0.5 * dt, dt * dt / 8.0))) return s;
+    const long long n = (long long)c->nv * c->g.plane;
+    k_sum3<<<blocks_for(n), 256, 0, c->stream>>>(A->lam, A->lams, A->gacc, A->nxt, n);
+    CK(cudaGetLastError());
+    ++A->launches;
+    std::swap(A->lam, A->nxt);
+    return GKS_OK;
+}
+
+gks_status check_supported(gks_ctx* c)
+{
+    if (c->desc.dim != 2) return rt::fail(c, GKS_EUNSUPPORTED, "the adjoint is built for 2-D grids");
+    if (c->sch.tau_mode != GKS_TAU_ZERO)
+        return rt::fail(c, GKS_EUNSUPPORTED, "the adjoint is built for the collision-free flux (tau_mode = zero)");
+    return GKS_OK;
+}
+
+gks_status sync_check(gks_ctx* c)
+{
+    gks_diag d;
+    return gks_get_diagnostics(c, &d);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+gks_status gks_adjoint_create(gks_ctx* c, int checkpoint_every, gks_adjoint** out)
+{
+    if (!c || !out || checkpoint_every < 1) return GKS_EINVAL;
+    *out = nullptr;
+    gks_status s = check_supported(c);
+    if (s) return s;
+    gks_adjoint* A = new (std::nothrow) gks_adjoint();
+    if (!A) return GKS_ENOMEM;
+    A->c = c;
+    A->k = checkpoint_every;
+    if ((s = adj_scratch(A)) || (s = adj_alloc(A, &A->WN))) {
+        gks_adjoint_destroy(A);
+        cudaGetLastError();
+        return s == GKS_ECUDA ? GKS_ENOMEM : s;
+    }
+    *out = A;
+    return GKS_OK;
+}
+
+void gks_adjoint_destroy(gks_adjoint* A)
+{
+    if (!A) return;
+    for (double* p : A->ckpt) cudaFree(p);
+    for (double* p : A->seg) cudaFree(p);
+    cudaFree(A->WN);
+    cudaFree(A->lam);
+    cudaFree(A->lams);
+    cudaFree(A->gacc);
+    cudaFree(A->nxt);
+    cudaFree(A->lines);
+    cudaFree(A->contrib);
+    cudaFree(A->dcell);
+    delete A;
+}
+
+gks_status gks_adjoint_forward(gks_adjoint* A, int nsteps, double dt)
+{
+    if (!A || nsteps < 1 || !(dt > 0.0) || !std::isfinite(dt)) return GKS_EINVAL;
+    gks_ctx* c = A->c;
+    gks_status s = check_supported(c);
+    if (s) return s;
+    const int ncp = (nsteps + A->k - 1) / A->k;
+    while ((int)A->ckpt.size() < ncp) {
+        double* p = nullptr;
+        if (cudaMalloc(&p, c->arr_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return rt::fail(c, GKS_ENOMEM, "no device memory for %d checkpoints", ncp);
+        }
+        A->ckpt.push_back(p);
+    }
+    A->have_forward = false;
+    for (int n = 0; n < nsteps; ++n) {
+        if (n % A->k == 0) CK(cudaMemcpyAsync(A->ckpt[n / A->k], c->W, c->arr_bytes, cudaMemcpyDeviceToDevice, c->stream));
+        if ((s = gks_step(c, dt))) return s;
+    }
+    CK(cudaMemcpyAsync(A->WN, c->W, c->arr_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if ((s = sync_check(c))) return s;
+    A->nsteps = nsteps;
+    A->dt = dt;
+    A->have_forward = true;
+    return GKS_OK;
+}
+
+gks_status gks_adjoint_backward(gks_adjoint* A, const double* gWN, double* gW0, int on_device)
+{
+    if (!A || !gWN || !gW0) return GKS_EINVAL;
+    gks_ctx* c = A->c;
+    if (!A->have_forward) return rt::fail(c, GKS_EINVAL, "gks_adjoint_backward needs a completed forward pass");
+    gks_status s;
+    while ((int)A->seg.size() < std::min(A->k, A->nsteps)) {
+        double* p = nullptr;
+        if (cudaMalloc(&p, c->arr_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return rt::fail(c, GKS_ENOMEM, "no device memory for a %d-step segment", A->k);
+        }
+        A->seg.push_back(p);
+    }
+    CK(cudaMemsetAsync(A->lam, 0, c->arr_bytes, c->stream));
+    if ((s = rt::copy_interior(c, A->lam, gWN, on_device, true))) return s;
+    const int ncp = (A->nsteps + A->k - 1) / A->k;
+    for (int sgi = ncp - 1; sgi >= 0; --sgi) {
+        const int n0 = sgi * A->k, n1 = std::min(n0 + A->k, A->nsteps);
+        if ((s = load_state(A, A->ckpt[sgi]))) return s;
+        for (int n = n0; n < n1; ++n) {
+            CK(cudaMemcpyAsync(A->seg[n - n0], c->W, c->arr_bytes, cudaMemcpyDeviceToDevice, c->stream));
+            if (n + 1 < n1 && (s = gks_step(c, A->dt))) return s;
+        }
+        for (int n = n1 - 1; n >= n0; --n)
+            if ((s = adjoint_step(A, A->seg[n - n0], A->dt))) return s;
+    }
+    if ((s = rt::copy_interior(c, A->lam, gW0, on_device, false))) return s;
+    // leave the context at the forward pass's final state
+    if ((s = load_state(A, A->WN))) return s;
+    return sync_check(c);
+}
+
+long long gks_adjoint_launches(const gks_adjoint* A) { return A ? A->launches : 0; }
+
+gks_status gks_vjp_step(gks_ctx* c, const double* W, const double* gout, double* gin, double dt, int on_device)
+{
+    if (!c || !W || !gout || !gin || !(dt > 0.0) || !std::isfinite(dt)) return GKS_EINVAL;
+    gks_adjoint* A = nullptr;
+    gks_status s = gks_adjoint_create(c, 1, &A);
+    if (s) return s;
+    if (!(s = gks_set_state(c, W, on_device)) && !(s = gks_adjoint_forward(A, 1, dt)))
+        s = gks_adjoint_backward(A, gout, gin, on_device);
+    gks_adjoint_destroy(A);
+    return s;
+}
+
+}  // extern "C"

@@ -19,6 +19,7 @@
 
 #include "../../include/gks.h"
 #include "gks_aux.cuh"
+#include "gks_ctx.h"
 #include "gks_launch.h"
 
 using namespace gks;
@@ -27,41 +28,9 @@ namespace {
 constexpr int GRAPH_STEPS = 8;
 }
 
-struct gks_ctx {
-    gks_grid_desc desc{};
-    GridDev g{};
-    gks_gas gas{};
-    gks_scheme sch{};
-    int nv = 0;
-    double *W = nullptr, *Ws = nullptr, *Ac = nullptr;
-    void *inc0 = nullptr, *inc1 = nullptr;  // x-sweep increments (2-D), working precision
-    float *Wf = nullptr, *Wsf = nullptr;     // float32 shadows of W, W* (2-D float32 path)
-    size_t arr_bytes = 0;
-    DevState* ds = nullptr;      // device
-    DevState* hs = nullptr;      // pinned host mirror
-    cudaStream_t stream = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    long long graph_nodes = 0;
-    unsigned long long param_version = 1, graph_version = 0;
-    long long launches = 0;
-    // the device already holds the CFL time step of the current state (set by
-    // a CFL step's commit, cleared by anything else that changes W or dt)
-    bool cfl_dt_ready = false;
-    std::string err;
-    // per-kernel event timing (gks_profile_enable)
-    bool prof = false, capturing = false;
-    struct EvPair {
-        cudaEvent_t a, b;
-        int kind;
-    };
-    std::vector<EvPair> ev;
-    size_t ev_used = 0;
-    long long prof_n[3] = {0, 0, 0};
-    double prof_ms[3] = {0, 0, 0};
-};
 
-namespace {
+namespace gks {
+namespace rt {
 
 gks_status fail(gks_ctx* c, gks_status s, const char* fmt, ...)
 {
@@ -76,17 +45,23 @@ gks_status fail(gks_ctx* c, gks_status s, const char* fmt, ...)
     return s;
 }
 
-#define CK(call)                                                                                    \
-    do {                                                                                            \
-        cudaError_t e_ = (call);                                                                    \
-        if (e_ != cudaSuccess) return fail(c, GKS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-    } while (0)
+}  // namespace rt
+}  // namespace gks
+
+using gks::rt::fail;
+
+namespace {
 
 double internal_dof(int dim, double gamma)
 {
     // 2-D: K = (5 - 3 gamma)/(gamma - 1) + 1 (Sec. 2.1); 1-D: K = (3 - gamma)/(gamma - 1)
     return dim == 2 ? (5.0 - 3.0 * gamma) / (gamma - 1.0) + 1.0 : (3.0 - gamma) / (gamma - 1.0);
 }
+
+}  // namespace
+
+namespace gks {
+namespace rt {
 
 HostFlux host_flux(const gks_ctx* c)
 {
@@ -102,6 +77,17 @@ HostFlux host_flux(const gks_ctx* c)
     return h;
 }
 
+}  // namespace rt
+}  // namespace gks
+using gks::rt::host_flux;
+
+namespace {
+
+}  // namespace
+
+namespace gks {
+namespace rt {
+
 TenoParams teno_params(const gks_ctx* c, bool tangential)
 {
     TenoParams t;
@@ -111,6 +97,12 @@ TenoParams teno_params(const gks_ctx* c, bool tangential)
     t.ct2 = tangential ? c->sch.ct2_t : c->sch.ct2;
     return t;
 }
+
+}  // namespace rt
+}  // namespace gks
+using gks::rt::teno_params;
+
+namespace {
 
 bool prepared_f32 = false, prepared_f64 = false;
 
@@ -156,6 +148,11 @@ cudaError_t prof_harvest(gks_ctx* c)
 // ---------------------------------------------------------------- launches
 // Ghost layers of W or W*.  On the 2-D float32 path the sweeps read only the
 // float32 shadow, so its ghosts are filled instead of the float64 ones.
+}  // namespace
+
+namespace gks {
+namespace rt {
+
 gks_status enqueue_ghosts(gks_ctx* c, double* arr, cudaStream_t st)
 {
     const int gx = c->desc.nx + 2 * NG;
@@ -172,6 +169,12 @@ gks_status enqueue_ghosts(gks_ctx* c, double* arr, cudaStream_t st)
     ++c->launches;
     return GKS_OK;
 }
+
+}  // namespace rt
+}  // namespace gks
+using gks::rt::enqueue_ghosts;
+
+namespace {
 
 gks_status enqueue_stage(gks_ctx* c, int stage, int with_sigma, cudaStream_t st)
 {
@@ -302,6 +305,11 @@ gks_status check_err(gks_ctx* c)
     return GKS_OK;
 }
 
+}  // namespace
+
+namespace gks {
+namespace rt {
+
 gks_status copy_interior(gks_ctx* c, double* arr, const double* W, int on_device, bool in)
 {
     const int nx = c->desc.nx, ny = (c->desc.dim == 2) ? c->desc.ny : 1;
@@ -321,6 +329,12 @@ gks_status copy_interior(gks_ctx* c, double* arr, const double* W, int on_device
     CK(cudaStreamSynchronize(c->stream));
     return GKS_OK;
 }
+
+}  // namespace rt
+}  // namespace gks
+using gks::rt::copy_interior;
+
+namespace {
 
 gks_status build_graph(gks_ctx* c)
 {

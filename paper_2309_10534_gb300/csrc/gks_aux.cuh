@@ -8,27 +8,6 @@
 namespace gks {
 
 // ------------------------------------------------------------------ ghosts
-// source index of ghost position g (ghosted coordinate) along a line of n
-// interior cells, and the velocity flips the rule implies
-__device__ __forceinline__ int ghost_src(int bc, int n, int g, bool& flip_n, bool& flip_all)
-{
-    flip_n = flip_all = false;
-    if (g >= NG && g < NG + n) return g;
-    const bool low = g < NG;
-    switch (bc) {
-    case 0:  // periodic
-        return NG + (((g - NG) % n) + n) % n;
-    case 1:  // zero gradient
-        return low ? NG : NG + n - 1;
-    case 3:  // no-slip adiabatic wall
-        flip_all = true;
-        return low ? 2 * NG - 1 - g : 2 * (NG + n) - 1 - g;
-    default:  // symmetry / reflect
-        flip_n = true;
-        return low ? 2 * NG - 1 - g : 2 * (NG + n) - 1 - g;
-    }
-}
-
 // One thread per ghost cell.  x ghosts of interior rows use the x rule; rows
 // of y ghosts use the y rule to pick an interior row, then the x rule for
 // x-ghost columns (the same values as filling x first, then y over the full

@@ -1,6 +1,7 @@
 // gks_host_replica.cu -- host compilations of the per-point device arithmetic
 // (include/gks_host_replica.h), used by unit tests without a GPU.
 #include "../../include/gks_host_replica.h"
+#include "gks_adjoint.cuh"
 #include "gks_device.cuh"
 
 namespace {
@@ -74,7 +75,68 @@ int flux_dispatch(int tau_mode, double gamma, double mu, double Pr, double c1, d
     return flux_t<T, DIM, true, false>(tau_mode, gamma, mu, Pr, c1, c2, dt, Wl, Wln, Wlt, Wr, Wrn, Wrt, F, dF);
 }
 
+template <typename T>
+int teno_vjp_t(const double* q, double eps, int qpow, double ct1, double ct2, const double* gfaces,
+               const double* ggauss, double* gq)
+{
+    T qq[5], g[5] = {T(0), T(0), T(0), T(0), T(0)};
+    for (int k = 0; k < 5; ++k) qq[k] = (T)q[k];
+    const gks::TenoParams P{eps, qpow, ct1, ct2};
+    gks::TenoSel<T> S;
+    gks::teno_select(qq, gks::teno_t<T>(P), S);
+    gks::teno_faces_T(S, (T)gfaces[0], (T)gfaces[1], (T)gfaces[2], (T)gfaces[3], g);
+    gks::teno_gauss_T(S, T(-0.28867513459481288), (T)ggauss[0], (T)ggauss[1], g);
+    gks::teno_gauss_T(S, T(0.28867513459481288), (T)ggauss[2], (T)ggauss[3], g);
+    for (int k = 0; k < 5; ++k) gq[k] = (double)g[k];
+    return S.large ? 1 : 0;
+}
+
+template <typename T>
+int flux_vjp_t(double gamma, const double* Wl, const double* Wln, const double* Wlt, const double* Wr,
+               const double* Wrn, const double* Wrt, const double* gF, const double* gdF, double* gl, double* gr)
+{
+    const double K = (5.0 - 3.0 * gamma) / (gamma - 1.0) + 1.0;
+    gks::FluxParams<T> p{};
+    p.gm1 = (T)(gamma - 1.0);
+    p.K = (T)K;
+    p.ntot = (T)(K + 2.0);
+    p.inv_ntot = (T)(1.0 / (K + 2.0));
+    p.tau_mode = 0;
+    gks::Side<T> L, R, gL, gR;
+    T f[4], d[4];
+    for (int k = 0; k < 4; ++k) {
+        L.W[k] = (T)Wl[k]; L.Wn[k] = (T)Wln[k]; L.Wt[k] = (T)Wlt[k];
+        R.W[k] = (T)Wr[k]; R.Wn[k] = (T)Wrn[k]; R.Wt[k] = (T)Wrt[k];
+        gL.W[k] = gL.Wn[k] = gL.Wt[k] = gR.W[k] = gR.Wn[k] = gR.Wt[k] = T(0);
+        f[k] = (T)gF[k];
+        d[k] = (T)gdF[k];
+    }
+    gks::point_flux_vjp(L, R, p, f, d, gL, gR);
+    for (int k = 0; k < 4; ++k) {
+        gl[k] = gL.W[k]; gl[4 + k] = gL.Wn[k]; gl[8 + k] = gL.Wt[k];
+        gr[k] = gR.W[k]; gr[4 + k] = gR.Wn[k]; gr[8 + k] = gR.Wt[k];
+    }
+    return 0;
+}
+
 }  // namespace
+
+extern "C" int gks_host_teno_vjp(int precision, const double* q, double eps, int qpow, double ct1, double ct2,
+                                 const double* gfaces, const double* ggauss, double* gq)
+{
+    if (!q || !gfaces || !ggauss || !gq || qpow < 1) return -1;
+    return precision == 1 ? teno_vjp_t<float>(q, eps, qpow, ct1, ct2, gfaces, ggauss, gq)
+                          : teno_vjp_t<double>(q, eps, qpow, ct1, ct2, gfaces, ggauss, gq);
+}
+
+extern "C" int gks_host_point_flux_vjp(int precision, double gamma, const double* Wl, const double* Wln,
+                                       const double* Wlt, const double* Wr, const double* Wrn, const double* Wrt,
+                                       const double* gF, const double* gdF, double* gl, double* gr)
+{
+    if (!Wl || !Wln || !Wlt || !Wr || !Wrn || !Wrt || !gF || !gdF || !gl || !gr) return -1;
+    return precision == 1 ? flux_vjp_t<float>(gamma, Wl, Wln, Wlt, Wr, Wrn, Wrt, gF, gdF, gl, gr)
+                          : flux_vjp_t<double>(gamma, Wl, Wln, Wlt, Wr, Wrn, Wrt, gF, gdF, gl, gr);
+}
 
 extern "C" int gks_host_time_coeffs(int precision, double s, double* cF, double* cD)
 {

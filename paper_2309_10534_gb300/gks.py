@@ -280,7 +280,10 @@ def _replica():
         L.gks_host_time_coeffs.argtypes = [C.c_int, C.c_double, _dp, _dp]
         L.gks_host_teno.argtypes = [C.c_int, _dp, C.c_double, C.c_int, C.c_double, C.c_double, _dp, _dp]
         L.gks_host_point_flux.argtypes = [C.c_int, C.c_int, C.c_int] + [C.c_double] * 6 + [_dp] * 8
-        for f in (L.gks_host_time_coeffs, L.gks_host_teno, L.gks_host_point_flux):
+        L.gks_host_teno_vjp.argtypes = [C.c_int, _dp] + [C.c_double, C.c_int, C.c_double, C.c_double] + [_dp] * 3
+        L.gks_host_point_flux_vjp.argtypes = [C.c_int, C.c_double] + [_dp] * 10
+        for f in (L.gks_host_time_coeffs, L.gks_host_teno, L.gks_host_point_flux, L.gks_host_teno_vjp,
+                  L.gks_host_point_flux_vjp):
             f.restype = C.c_int
         L._replica_declared = True
     return L
@@ -322,6 +325,29 @@ def host_point_flux(dim, Wl, Wln, Wlt, Wr, Wrn, Wrt, dt, precision="fp64", tau="
     if r:
         raise ValueError("bad argument")
     return F, dF
+
+
+def host_teno_vjp(q, gfaces, ggauss, precision="fp64", eps=1e-40, q_pow=7, ct1=1e-7, ct2=1e-5):
+    """Transpose of TENO-D at q with its selection held fixed: (gq[5], large)."""
+    qq, pq = _arr(q, 5)
+    gf, pgf = _arr(gfaces, 4)
+    gg, pgg = _arr(ggauss, 4)
+    gq, pgq = _arr(None, 5)
+    r = _replica().gks_host_teno_vjp(PRECISION[precision], pq, eps, q_pow, ct1, ct2, pgf, pgg, pgq)
+    if r < 0:
+        raise ValueError("bad argument")
+    return gq, bool(r)
+
+
+def host_point_flux_vjp(Wl, Wln, Wlt, Wr, Wrn, Wrt, gF, gdF, precision="fp64", gamma=1.4):
+    """Cotangents (gl[12], gr[12]) of the two sides' (W, Wn, Wt) from those of
+    (F, dF/dt) of the 2-D tau = 0 point flux (host build of the device code)."""
+    keep = [_arr(a, 4) for a in (Wl, Wln, Wlt, Wr, Wrn, Wrt, gF, gdF)]
+    gl, pl = _arr(None, 12)
+    gr, pr = _arr(None, 12)
+    if _replica().gks_host_point_flux_vjp(PRECISION[precision], gamma, *[k[1] for k in keep], pl, pr):
+        raise ValueError("bad argument")
+    return gl, gr
 
 
 def step1d_noalloc(W_in, W_out, dx, dt, bc=("zerograd", "zerograd"), precision="fp64", gamma=1.4, mu=0.0,
@@ -454,3 +480,129 @@ class Batch:
 
     def launches(self):
         return lib().gks_batch_launches(self.h)
+
+
+# ---------------------------------------------------------------- adjoint
+def _adj_lib():
+    L = lib()
+    if not getattr(L, "_adjoint_declared", False):
+        sig = {
+            "gks_adjoint_create": ([_vp, C.c_int, C.POINTER(_vp)], C.c_int),
+            "gks_adjoint_destroy": ([_vp], None),
+            "gks_adjoint_forward": ([_vp, C.c_int, C.c_double], C.c_int),
+            "gks_adjoint_backward": ([_vp, _vp, _vp, C.c_int], C.c_int),
+            "gks_adjoint_launches": ([_vp], C.c_longlong),
+            "gks_vjp_step": ([_vp, _vp, _vp, _vp, C.c_double, C.c_int], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        L._adjoint_declared = True
+    return L
+
+
+def _ptr(a, shape):
+    """(pointer, on_device, keep-alive) of a float64 state-shaped array."""
+    if hasattr(a, "data_ptr"):
+        if not (a.is_cuda and a.dtype.itemsize == 8 and a.is_contiguous() and a.numel() == int(np.prod(shape))):
+            raise ValueError("need a contiguous float64 CUDA tensor of shape %s" % (shape,))
+        return _vp(a.data_ptr()), 1, a
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != int(np.prod(shape)):
+        raise ValueError("need %d values" % int(np.prod(shape)))
+    return a.ctypes.data_as(_vp), 0, a
+
+
+class Adjoint:
+    """Checkpointed hand-written adjoint of a 2-D Solver with tau='zero'
+    (gks_adjoint_*): forward(nsteps, dt) advances the solver keeping a
+    checkpoint every k steps; backward(gWN) returns dJ/dW0 for the given
+    dJ/dWN (numpy in -> numpy out; CUDA tensor in -> CUDA tensor out)."""
+
+    def __init__(self, solver: Solver, checkpoint_every: int):
+        L = _adj_lib()
+        self.solver = solver
+        h = _vp()
+        solver._check(L.gks_adjoint_create(solver.h, int(checkpoint_every), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _adj_lib().gks_adjoint_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, nsteps, dt):
+        self.solver._check(_adj_lib().gks_adjoint_forward(self.h, int(nsteps), float(dt)))
+
+    def backward(self, gWN, out=None):
+        shape = self.solver.shape
+        p_in, dev, keep = _ptr(gWN, shape)
+        if out is None:
+            out = gWN.new_empty(gWN.shape) if dev else np.empty(shape)
+        p_out, dev2, _ = _ptr(out, shape)
+        if dev2 != dev:
+            raise ValueError("gWN and out must both be host arrays or both CUDA tensors")
+        self.solver._check(_adj_lib().gks_adjoint_backward(self.h, p_in, p_out, dev))
+        return out
+
+    def launches(self):
+        return int(_adj_lib().gks_adjoint_launches(self.h))
+
+
+def vjp_step(solver: Solver, W, gout, dt):
+    """(dS/dW)^T gout for one S2O4 step S of fixed dt at state W (host arrays).
+    The solver is left at S(W)."""
+    shape = solver.shape
+    pW, d1, kW = _ptr(W, shape)
+    pg, d2, kg = _ptr(gout, shape)
+    gin = np.empty(shape)
+    if d1 or d2:
+        raise ValueError("vjp_step takes host arrays")
+    solver._check(_adj_lib().gks_vjp_step(solver.h, pW, pg, gin.ctypes.data_as(_vp), float(dt), 0))
+    return gin
+
+
+_flow_cls = None
+
+
+def _flow():
+    global _flow_cls
+    if _flow_cls is None:
+        import torch
+
+        class GKSFlow(torch.autograd.Function):
+            """W_N = S^n(W_0) on a Solver; backward = the hand-written adjoint."""
+
+            @staticmethod
+            def forward(ctx, W0, solver, nsteps, dt, checkpoint_every):
+                W0c = W0.detach().contiguous()
+                solver.set_state(W0c)
+                adj = Adjoint(solver, checkpoint_every)
+                adj.forward(nsteps, dt)
+                WN = torch.empty_like(W0c)
+                solver.get_state(WN)
+                ctx.adj = adj
+                return WN
+
+            @staticmethod
+            def backward(ctx, gWN):
+                g = gWN.detach().to(torch.float64).contiguous()
+                gW0 = ctx.adj.backward(g)
+                return gW0, None, None, None, None
+
+        _flow_cls = GKSFlow
+    return _flow_cls
+
+
+def flow(W0, solver: Solver, nsteps: int, dt: float, checkpoint_every: int = 20):
+    """Differentiable map W_0 -> W_N (nsteps S2O4 steps of fixed dt) for a
+    float64 CUDA tensor W_0 of the solver's state shape, as a
+    torch.autograd.Function whose backward is the library's adjoint."""
+    return _flow().apply(W0, solver, nsteps, dt, checkpoint_every)

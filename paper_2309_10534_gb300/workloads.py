@@ -207,18 +207,32 @@ def ensemble_1d(count=4096, seed=2309, nmin=200, nmax=4000, gamma=1.4, t_end=0.1
 
 
 def isentropic_vortex(n=512, strength=5.0, center=(5.0, 5.0), length=10.0, gamma=1.4,
-                      seed=None, amplitude=1e-3, quad=4):
+                      seed=None, amplitude=1e-3, quad=4, kmax=4):
     """Isentropic vortex on a periodic [0, L]^2 in a (1, 1) mean flow
     (standard smooth Euler test; not from the paper).  Cell averages by
     quad x quad Gauss-Legendre points per cell.  With ``seed`` the initial
-    density gets a Gaussian-random perturbation of the given amplitude at
-    fixed (u, v, p), returned in ``extra['delta_rho']``."""
+    density gets a Gaussian-random perturbation at fixed (u, v, p): a
+    periodic Gaussian random field whose Fourier coefficients for wave
+    numbers 0 < max(|kx|, |ky|) <= kmax are independent standard normals,
+    scaled to an RMS of ``amplitude`` over the cell averages.  It stays
+    smooth on the grid (a white-noise field would make TENO-D's stencil
+    choice, and so the discrete flow map, non-smooth at the noise level).
+    The perturbation is returned in ``extra['delta_rho']``."""
     h = length / n
     gx, gw = np.polynomial.legendre.leggauss(quad)
     gx = 0.5 * gx
     gw = 0.5 * gw
     c = (np.arange(n) + 0.5) * h
     W = np.zeros((4, n, n))
+    modes = []
+    if seed is not None:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        for kx in range(-kmax, kmax + 1):
+            for ky in range(0, kmax + 1):
+                if (ky == 0 and kx <= 0) or max(abs(kx), ky) == 0:
+                    continue
+                modes.append((kx, ky, rng.standard_normal(), rng.standard_normal()))
+    drho = np.zeros((n, n))
     for a in range(quad):
         for b in range(quad):
             X, Y = np.meshgrid(c + gx[a] * h, c + gx[b] * h)
@@ -232,10 +246,12 @@ def isentropic_vortex(n=512, strength=5.0, center=(5.0, 5.0), length=10.0, gamma
             rho = T ** (1.0 / (gamma - 1.0))
             p = rho * T
             W += gw[a] * gw[b] * conserved_2d(rho, u, v, p, gamma)
+            for kx, ky, ca, cb in modes:
+                ph = 2 * math.pi * (kx * X + ky * Y) / length
+                drho += gw[a] * gw[b] * (ca * np.cos(ph) + cb * np.sin(ph))
     extra = {}
     if seed is not None:
-        rng = np.random.Generator(np.random.PCG64(seed))
-        drho = amplitude * rng.standard_normal((n, n))
+        drho *= amplitude / math.sqrt(np.mean(drho * drho))
         rho = W[0]
         u = W[1] / rho
         v = W[2] / rho
@@ -246,9 +262,9 @@ def isentropic_vortex(n=512, strength=5.0, center=(5.0, 5.0), length=10.0, gamma
                  t_end=2.0, name="isentropic_vortex", extra=extra)
 
 
-def random_smooth_2d(nx, ny, seed, gamma=1.4, amp=0.1, modes=3):
-    """Seeded smooth periodic state (few Fourier modes per field) for parity
-    tests of the smooth branch."""
+def random_smooth_2d(nx, ny, seed, gamma=1.4, amp=0.1, modes=3, kmax=3):
+    """Seeded smooth periodic state (few Fourier modes per field, wave
+    numbers 1..kmax per direction) for parity tests of the smooth branch."""
     rng = np.random.Generator(np.random.PCG64(seed))
     x = (np.arange(nx) + 0.5) / nx
     y = (np.arange(ny) + 0.5) / ny
@@ -257,7 +273,7 @@ def random_smooth_2d(nx, ny, seed, gamma=1.4, amp=0.1, modes=3):
     def field_(base):
         f = np.full_like(X, base)
         for _ in range(modes):
-            kx, ky = rng.integers(1, 4, size=2)
+            kx, ky = rng.integers(1, kmax + 1, size=2)
             ph = rng.uniform(0, 2 * np.pi)
             f += amp * rng.uniform(-1, 1) * np.sin(2 * np.pi * (kx * X + ky * Y) + ph)
         return f

@@ -1,0 +1,196 @@
+"""The hand-written adjoint (gks_adjoint_*, gks_vjp_step, gks.flow) against
+central finite differences of the oracle (FP64 CPU reference gradient) and of
+the GPU forward path, on smooth flows with the collision-free flux."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2309_10534_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+GAMMA = 1.4
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "adjoint_smooth24.txt")
+
+
+@pytest.fixture(scope="module")
+def gks():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_10534_gb300 import build, gks as G
+    build.build()
+    return G
+
+
+def _prims(W):
+    rho = W[0]
+    u, v = W[1] / rho, W[2] / rho
+    p = (GAMMA - 1.0) * (W[3] - 0.5 * rho * (u * u + v * v))
+    return rho, u, v, p
+
+
+def _drho_grad(gW0, u, v):
+    """dJ/d(delta rho) at fixed (u, v, p) from dJ/dW0 (chain rule through
+    W = (rho, rho u, rho v, p/(gamma-1) + rho (u^2 + v^2)/2))."""
+    return gW0[0] + u * gW0[1] + v * gW0[2] + 0.5 * (u * u + v * v) * gW0[3]
+
+
+def _smooth24_gradient(G, precision, k):
+    # the problem of tests/golden/make_adjoint_golden.py
+    n = 24
+    rho, u, v, p = _prims(WL.random_smooth_2d(n, n, seed=5, kmax=2))
+    W0 = WL.conserved_2d(rho, u, v, p, GAMMA)
+    S = G.Solver(2, n, n, bc=("periodic",) * 4, precision=precision, tau="zero")
+    S.set_state(W0)
+    A = G.Adjoint(S, k)
+    A.forward(6, 0.01)
+    WN = S.get_state()
+    gWN = np.zeros_like(WN)
+    gWN[0] = 2.0 * WN[0] / (n * n)
+    gW0 = A.backward(gWN)
+    J = float((WN[0] ** 2).sum() / (n * n))
+    return _drho_grad(gW0, u, v).ravel(), J, A
+
+
+def _golden():
+    d = np.loadtxt(GOLDEN)
+    with open(GOLDEN) as f:
+        f.readline()
+        head = f.readline()
+    J = float(head.split("J=")[1])
+    return d[:, 1], d[:, 2], J
+
+
+def test_adjoint_matches_oracle_reference_gradient(gks):
+    """Full-field gradient on 24 x 24 (576 parameters, 6 steps) against the
+    oracle's central differences.  Where the two FD step sizes agree (no
+    TENO-D choice flipped inside the probe; at least 85 % of the cells) the
+    adjoint agrees to 2e-6 of the largest component; the forward J agrees
+    with the oracle's to 1e-12."""
+    g1, g2, J_or = _golden()
+    g, J, _ = _smooth24_gradient(gks, "fp64", 3)
+    assert J == pytest.approx(J_or, rel=1e-12)
+    m = np.abs(g1).max()
+    ok = np.abs(g1 - g2) <= 1e-6 * m
+    assert ok.mean() >= 0.85, ok.mean()
+    err = np.abs(g - g1)[ok].max() / m
+    print(f"adjoint vs oracle FD: {ok.sum()} consistent components, max rel err {err:.3e}")
+    assert err <= 2e-6
+
+
+def test_adjoint_fp32_close_to_fp64(gks):
+    """float32 reconstruction/flux in forward and adjoint (float64 state and
+    cotangent accumulation): within 1e-4 of the float64 gradient."""
+    g64, _, _ = _smooth24_gradient(gks, "fp64", 3)
+    g32, _, _ = _smooth24_gradient(gks, "fp32", 3)
+    err = np.abs(g32 - g64).max() / np.abs(g64).max()
+    print(f"fp32 vs fp64 adjoint: {err:.3e}")
+    assert err <= 1e-4
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(gks):
+    """Recomputed segments repeat the forward pass exactly: the gradient is
+    the same bits for every checkpoint interval."""
+    ref, _, _ = _smooth24_gradient(gks, "fp64", 1)
+    for k in (2, 4, 6, 10):
+        g, _, _ = _smooth24_gradient(gks, "fp64", k)
+        assert np.array_equal(g, ref), k
+
+
+@pytest.mark.parametrize("bc", [("periodic",) * 4, ("reflect", "zerograd", "noslip", "symmetry")])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-7), ("fp32", 2e-5)])
+def test_vjp_step_matches_oracle_directional_derivative(gks, bc, precision, tol):
+    """One step's VJP on a non-square grid (x and y sweeps differ):
+    <(dS/dW)^T g, d> equals <g, (S(W + h d) - S(W - h d)) / 2h> with S the
+    oracle's step, for smooth directions d; every boundary rule's ghost fold
+    is exercised by the second case."""
+    nx, ny = 20, 16
+    W = WL.random_smooth_2d(nx, ny, seed=21, kmax=2)
+    P = O.make_problem(2, nx, ny, lx=1.25, ly=1.0, bc=bc, tau="zero")
+    dt = 0.4 * O.dt(P, W)
+    S = gks.Solver(2, nx, ny, lx=1.25, ly=1.0, bc=bc, precision=precision, tau="zero")
+    rng = np.random.default_rng(4)
+    for trial in range(3):
+        g = rng.standard_normal(W.shape)
+        d = WL.random_smooth_2d(nx, ny, seed=100 + trial, kmax=2) - WL.random_smooth_2d(nx, ny, seed=200 + trial,
+                                                                                       kmax=2)
+        gin = gks.vjp_step(S, W, g, dt)
+        h = 1e-6
+        fd = (O.step(P, W + h * d, dt) - O.step(P, W - h * d, dt)) / (2 * h)
+        lhs, rhs = float((gin * d).sum()), float((g * fd).sum())
+        scale = float(np.abs(g * fd).sum())
+        assert abs(lhs - rhs) <= tol * scale, (trial, lhs, rhs, scale)
+
+
+def test_torch_autograd_function(gks):
+    """gks.flow as a torch.autograd.Function: the gradient of J through the
+    differentiable initial-condition map (written in torch) equals the
+    adjoint's, and matches the oracle reference where it is consistent."""
+    import torch
+    n = 24
+    rho, u, v, p = _prims(WL.random_smooth_2d(n, n, seed=5, kmax=2))
+    dev = torch.device("cuda")
+    t = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    rho_t, u_t, v_t, p_t = t(rho), t(u), t(v), t(p)
+    delta = torch.zeros((n, n), dtype=torch.float64, device=dev, requires_grad=True)
+    r = rho_t + delta
+    W0 = torch.stack([r, r * u_t, r * v_t, p_t / (GAMMA - 1) + 0.5 * r * (u_t ** 2 + v_t ** 2)])
+    S = gks.Solver(2, n, n, bc=("periodic",) * 4, precision="fp64", tau="zero")
+    WN = gks.flow(W0, S, 6, 0.01, checkpoint_every=2)
+    J = (WN[0] ** 2).sum() / (n * n)
+    J.backward()
+    g = delta.grad.cpu().numpy().ravel()
+    ref, _, _ = _smooth24_gradient(gks, "fp64", 3)
+    assert np.abs(g - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def vortex_steps(n=512, t_end=2.0, length=10.0, cfl=0.5, smax=3.4):
+    """Fixed time step of the adjoint workload: t_end in equal steps at
+    CFL <= 0.5 (max signal speed of the vortex in its (1, 1) mean flow is
+    below 3.4): 700 steps of 2/700 on 512 x 512."""
+    dx = length / n
+    steps = int(np.ceil(t_end / (cfl * dx / smax)))
+    return steps, t_end / steps
+
+
+def test_full_size_vortex_directional_derivative(gks):
+    """The full adjoint workload: isentropic vortex (strength 5, periodic
+    [0, 10]^2) on 512 x 512 with a seeded smooth Gaussian-random density
+    perturbation of RMS 1e-3, J = integral of rho^2 at t = 2 (fixed dt at
+    CFL 0.5), checkpoint every 20 steps.  dJ/d(eps) along the perturbation
+    from the adjoint equals central differences of the float64 GPU forward
+    pass within 1e-4 (float64 and float32 adjoints)."""
+    n = 512
+    steps, dt = vortex_steps(n)
+    s = WL.isentropic_vortex(n=n, seed=2309, amplitude=1e-3)
+    rho1, u, v, p = _prims(s.W)
+    drho = s.extra["delta_rho"]
+    rho_b = rho1 - drho
+    area = s.dx * s.dy
+
+    def J_of(eps):
+        S = gks.Solver(2, n, n, lx=10.0, ly=10.0, bc=("periodic",) * 4, precision="fp64", tau="zero")
+        S.set_state(WL.conserved_2d(rho_b + eps * drho, u, v, p, GAMMA))
+        for _ in range(steps):
+            S.step(dt)
+        S.diagnostics()  # raises on a non-physical state
+        WN = S.get_state()
+        return float((WN[0] ** 2).sum() * area)
+
+    fds = [(J_of(1.0 + h) - J_of(1.0 - h)) / (2 * h) for h in (0.1, 0.05)]
+    print(f"FD at h = 0.1, 0.05: {fds[0]:.12e} {fds[1]:.12e}")
+    fd = fds[1]
+    for precision in ("fp64", "fp32"):
+        S = gks.Solver(2, n, n, lx=10.0, ly=10.0, bc=("periodic",) * 4, precision=precision, tau="zero")
+        S.set_state(s.W)
+        A = gks.Adjoint(S, 20)
+        A.forward(steps, dt)
+        WN = S.get_state()
+        gWN = np.zeros_like(WN)
+        gWN[0] = 2.0 * WN[0] * area
+        gW0 = A.backward(gWN)
+        adj = float((_drho_grad(gW0, u, v) * drho).sum())
+        print(f"{precision}: dJ/deps adjoint {adj:.12e}  FD {fd:.12e}  rel {abs(adj - fd) / abs(fd):.3e}")
+        assert abs(adj - fd) <= 1e-4 * abs(fd)
