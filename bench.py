@@ -14,6 +14,12 @@ events on the library's stream with a 256 MB L2 flush between steps (outside
 the events).  The sweep kernels are also timed individually by the
 library's event profiler for the roofline.
 
+Further legs on the same GPU, reported as objects of the same JSON line:
+"ensemble" (4096 independent 1-D Riemann problems of 200..4000 cells to
+t = 0.15 in one persistent launch, cell-updates/s) and "adjoint" (the
+hand-written adjoint on a 512 x 512 isentropic vortex, 700 steps to t = 2,
+checkpoint every 20 steps: backward ms per step, float32 and float64).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
 from __future__ import annotations
@@ -50,6 +56,8 @@ def parse():
     p.add_argument("--skip-cpu", action="store_true", help="omit the CPU-oracle baseline (profiling runs)")
     p.add_argument("--no-ensemble", dest="ensemble", action="store_false",
                    help="omit the batched 1-D ensemble leg")
+    p.add_argument("--no-adjoint", dest="adjoint", action="store_false",
+                   help="omit the adjoint leg")
     return p.parse_args()
 
 
@@ -217,6 +225,57 @@ def ensemble_leg(gks, WL, stream, peak32):
                          "basis": "whole launch vs measured FP32 FMA peak"}}
 
 
+def adjoint_leg(gks, WL, stream, precision):
+    """Hand-written adjoint on the isentropic vortex (strength 5, periodic
+    [0, 10]^2, 512 x 512, smooth seeded density perturbation of RMS 1e-3):
+    J = integral of rho^2 at t = 2 in 700 fixed steps (CFL 0.5), checkpoint
+    every 20 steps.  Forward (with checkpoints) and backward (segment
+    recomputation + adjoint steps) timed with CUDA events on the solver's
+    stream; ms per step of each."""
+    import numpy as np
+    import torch
+    n, steps, k = 512, 700, 20
+    dt = 2.0 / steps
+    s = WL.isentropic_vortex(n=n, seed=2309, amplitude=1e-3)
+    S = gks.Solver(2, n, n, lx=10.0, ly=10.0, bc=("periodic",) * 4, precision=precision, tau="zero")
+    S.set_stream(stream.cuda_stream)
+    A = gks.Adjoint(S, k)
+    dev = stream.device
+    W0 = torch.from_numpy(s.W).to(dev)
+    # warm-up: one short forward/backward (kernel loading, allocations)
+    S.set_state(W0)
+    A.forward(2, dt)
+    A.backward(torch.zeros_like(W0))
+    S.set_state(W0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    L0, A0 = S.kernel_launches(), A.launches()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    A.forward(steps, dt)
+    ev[1].record(stream)
+    WN = torch.empty_like(W0)
+    S.get_state(WN)
+    gWN = torch.zeros_like(W0)
+    gWN[0] = 2.0 * WN[0] * (s.dx * s.dy)
+    gW0 = A.backward(gWN)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    launches = (S.kernel_launches() - L0) + (A.launches() - A0)
+    drho = torch.from_numpy(s.extra["delta_rho"]).to(dev)
+    u, v = W0[1] / W0[0], W0[2] / W0[0]
+    g = gW0[0] + u * gW0[1] + v * gW0[2] + 0.5 * (u * u + v * v) * gW0[3]
+    dJ = float((g * drho).sum())
+    A.close()
+    S.close()
+    return {"value": bwd / steps, "unit": "ms/step", "workload": "isentropic_vortex_adjoint",
+            "grid": "%dx%d" % (n, n), "steps": steps, "dt": dt, "checkpoint_every": k,
+            "forward_ms_per_step": fwd / steps, "backward_ms": bwd, "forward_ms": fwd,
+            "gpu_launches": launches, "dJ_deps": dJ,
+            "precision": ("fp32 reconstruction+flux, fp64 state and cotangents" if precision == "fp32"
+                          else "fp64")}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -288,6 +347,10 @@ def main():
     k64 = max(1, args.fp64_steps)
     ms64, launches64, sn64, sms64 = timed(S64, k64, min(args.warmup, 3))
     ens = ensemble_leg(gks, WL, stream, peak32) if args.ensemble else None
+    adj = None
+    if args.adjoint:
+        adj = adjoint_leg(gks, WL, stream, "fp32")
+        adj["fp64"] = adjoint_leg(gks, WL, stream, "fp64")
     clk = clocks.stop()
 
     # same number of steps on both paths from the same state: relative L1 of fp32 vs fp64
@@ -368,6 +431,8 @@ def main():
     }
     if ens:
         line["ensemble"] = ens
+    if adj:
+        line["adjoint"] = adj
     if world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(n=args.cpu_sample)
     print(json.dumps(line))
