@@ -16,7 +16,10 @@ library's event profiler for the roofline.
 
 Further legs on the same GPU, reported as objects of the same JSON line:
 "ensemble" (4096 independent 1-D Riemann problems of 200..4000 cells to
-t = 0.15 in one persistent launch, cell-updates/s) and "adjoint" (the
+t = 0.15 in one persistent launch, cell-updates/s), "viscous" (Navier-Stokes
+viscous shock tube on 2048 x 1024, 200 steps from t = 0), "errors_vs_oracle"
+(both GPU paths against the FP64 oracle on the CPU baseline's sample) and
+"adjoint" (the
 hand-written adjoint on a 512 x 512 isentropic vortex, 700 steps to t = 2,
 checkpoint every 20 steps: backward ms per step, float32 and float64).
 
@@ -58,6 +61,8 @@ def parse():
                    help="omit the batched 1-D ensemble leg")
     p.add_argument("--no-adjoint", dest="adjoint", action="store_false",
                    help="omit the adjoint leg")
+    p.add_argument("--no-viscous", dest="viscous", action="store_false",
+                   help="omit the viscous shock tube leg")
     return p.parse_args()
 
 
@@ -151,7 +156,28 @@ def cpu_baseline(steps_budget_s=15.0, n=96):
             break
     el = time.perf_counter() - t0
     return {"value": n * n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%dx%d grid of the same problem, %d CFL steps, single thread" % (n, n, steps)}
+            "sample": "%dx%d grid of the same problem, %d CFL steps, single thread" % (n, n, steps)}, (s, W, steps)
+
+
+def oracle_errors(gks, sample):
+    """Stated errors of both GPU paths against the FP64 oracle on the CPU
+    baseline's sample (same grid, same initial state, same number of CFL
+    steps): relative L1 (sum |e| / sum |W|) and relative Linf (max |e| /
+    max |W|) over all conserved variables."""
+    import numpy as np
+    s, W_or, steps = sample
+    out = {"sample": "%dx%d riemann2d_config3, %d CFL steps" % (s.nx, s.ny, steps)}
+    for precision in ("fp64", "fp32"):
+        S = gks.solver_for(s, precision)
+        for _ in range(steps):
+            S.step(0.0)
+        W = S.get_state()
+        S.diagnostics()
+        e = np.abs(W - W_or)
+        out[precision] = {"l1_rel": float(e.sum() / np.abs(W_or).sum()),
+                          "linf_rel": float(e.max() / np.abs(W_or).max())}
+        S.close()
+    return out
 
 
 def run_reference(args):
@@ -223,6 +249,35 @@ def ensemble_leg(gks, WL, stream, peak32):
             "roofline": {"bound": "alu", "kernel": "k_batch<float>", "achieved": tf, "peak": peak32,
                          "unit": "TFLOP/s", "frac": tf / peak32,
                          "basis": "whole launch vs measured FP32 FMA peak"}}
+
+
+def viscous_leg(gks, WL, stream, precision, steps):
+    """Navier-Stokes viscous shock tube (Re = 200, Pr = 0.73, no-slip walls,
+    symmetric top) on 2048 x 1024: `steps` CFL steps from t = 0 (the full run
+    to t = 1 takes ~1e5 viscous-limited steps), CUDA events around each step,
+    256 MB L2 flush between steps."""
+    import torch
+    s = WL.viscous_shock_tube(2048, 1024, Re=200.0, Pr=0.73)
+    S = gks.solver_for(s, precision)
+    S.set_stream(stream.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=stream.device)
+    for _ in range(2):
+        S.step(0.0)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        S.step(0.0)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    S.diagnostics()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    cells = 2048 * 1024
+    S.close()
+    return {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "workload": "viscous_shock_tube",
+            "grid": "2048x1024", "steps": steps, "ms_per_step": ms / steps, "tau": "ns", "Re": 200.0,
+            "Pr": 0.73, "precision": precision}
 
 
 def adjoint_leg(gks, WL, stream, precision):
@@ -347,6 +402,10 @@ def main():
     k64 = max(1, args.fp64_steps)
     ms64, launches64, sn64, sms64 = timed(S64, k64, min(args.warmup, 3))
     ens = ensemble_leg(gks, WL, stream, peak32) if args.ensemble else None
+    visc = None
+    if args.viscous:
+        visc = viscous_leg(gks, WL, stream, "fp32", 200)
+        visc["fp64"] = viscous_leg(gks, WL, stream, "fp64", 10)
     adj = None
     if args.adjoint:
         adj = adjoint_leg(gks, WL, stream, "fp32")
@@ -431,10 +490,13 @@ def main():
     }
     if ens:
         line["ensemble"] = ens
+    if visc:
+        line["viscous"] = visc
     if adj:
         line["adjoint"] = adj
     if world == 1 and not args.skip_cpu:
-        line["cpu_baseline"] = cpu_baseline(n=args.cpu_sample)
+        line["cpu_baseline"], sample = cpu_baseline(n=args.cpu_sample)
+        line["errors_vs_oracle"] = oracle_errors(gks, sample)
     print(json.dumps(line))
     if dist:
         dist.barrier()

@@ -266,11 +266,11 @@ __device__ __forceinline__ int gvar(int v, bool swap) { return (swap && (v == 1 
 template <typename T, int TN, int TT> struct SweepSmem {
     T w[4][TT + 4][TN + 6];           // cells: tangential rows t0-2.., normal n0-3..
     T rec[4][4][TT + 4][TN + 1];      // [vL, sL, vR, sR][var][row][face]
-    T gp[24][TT * (TN + 1)][2];       // Gauss-point states [quantity][pair][gp]
+    T flux[8 * (TN + 1) * (TT + 1)];  // face fluxes for the update (layout: sfi)
 };
 
 template <typename T, bool NONEQ, bool PRFIX, int TN, int TT>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4) ? 2 : 1)
+__global__ void __launch_bounds__(256, (sizeof(T) == 4) ? 4 : 1)
 k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, DevState* ds)
 {
     if (ds->done) return;
@@ -280,7 +280,12 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
     static_assert(NP == NT, "one (face,row) pair per thread");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SweepSmem<T, TN, TT>& sm = *reinterpret_cast<SweepSmem<T, TN, TT>*>(smem_raw);
-    T* sF = &sm.rec[0][0][0][0];         // reused after the Gauss-point phase: [k][row][face]
+    // face fluxes for the update: [k][row][face] for x faces; [k][face][row]
+    // (rows padded) for y faces, so that phase 3 runs along the unit-stride x
+    // direction in both sweeps
+    T* sF = sm.flux;
+    const bool fy = a.dirn != 0;
+    auto sfi = [&](int k, int r, int f) { return fy ? (k * NF + f) * (TT + 1) + r : (k * TT + r) * NF + f; };
 
     const double dt = ds->dt;
     fp.dt = (T)dt;
@@ -330,44 +335,16 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
     }
     __syncthreads();
 
-    // phase 2a: tangential TENO-D of the line averages to the two Gauss points
-    {
-        const int r = tid / NF, f = tid % NF;  // pair = tid
-        const T ih = (T)a.iht;
-        const T g0 = T(-0.28867513459481288), g1 = T(0.28867513459481288);  // -+1/(2 sqrt 3)
-#pragma unroll1
-        for (int side = 0; side < 2; ++side) {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                T q[5];
-                TenoSel<T> S;
-                T va, da, vb, db;
-#pragma unroll
-                for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * side][v][r + s][f];
-                teno_select(q, tnt, S);
-                teno_gauss(S, g0, va, da);
-                teno_gauss(S, g1, vb, db);
-                sm.gp[12 * side + v][tid][0] = va;
-                sm.gp[12 * side + v][tid][1] = vb;
-                sm.gp[12 * side + 8 + v][tid][0] = da * ih;
-                sm.gp[12 * side + 8 + v][tid][1] = db * ih;
-#pragma unroll
-                for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * side + 1][v][r + s][f];
-                teno_select(q, tnt, S);
-                teno_gauss(S, g0, va, da);
-                teno_gauss(S, g1, vb, db);
-                sm.gp[12 * side + 4 + v][tid][0] = va;
-                sm.gp[12 * side + 4 + v][tid][1] = vb;
-            }
-        }
-    }
-    __syncthreads();
-
-    // phase 2b: merge + flux at each Gauss point; thread pairs hold the two
-    // Gauss points of one face segment and average them (weights 1/2)
+    // phase 2: per (face segment, Gauss point): tangential TENO-D of the line
+    // averages to the Gauss point, then merge + flux.  The two lanes of a face
+    // segment split the work: lane gpi reconstructs side gpi (0: left, 1:
+    // right) at both Gauss points, keeps its own point and hands the other
+    // point's values to its partner; after the flux they average (weights 1/2).
     unsigned int nfb = 0, err = 0;
     const T tdt = (T)dt;
-#pragma unroll1
+    const T iht = (T)a.iht;
+    const T gA = T(-0.28867513459481288), gB = T(0.28867513459481288);  // -+1/(2 sqrt 3)
+#pragma unroll 1
     for (int task = tid; task < 2 * NP; task += NT) {
         const int pair = task >> 1, gpi = task & 1;
         const int r = pair / NF, f = pair % NF;
@@ -376,12 +353,31 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
         Side<T> L, R;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            L.W[v] = sm.gp[v][pair][gpi];
-            L.Wn[v] = sm.gp[4 + v][pair][gpi];
-            L.Wt[v] = sm.gp[8 + v][pair][gpi];
-            R.W[v] = sm.gp[12 + v][pair][gpi];
-            R.Wn[v] = sm.gp[16 + v][pair][gpi];
-            R.Wt[v] = sm.gp[20 + v][pair][gpi];
+            T q[5];
+            TenoSel<T> S;
+            T va, da, vb, db;
+#pragma unroll
+            for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * gpi][v][r + s][f];
+            teno_select(q, tnt, S);
+            teno_gauss(S, gA, va, da);
+            teno_gauss(S, gB, vb, db);
+            // own side at own point; the partner's point goes to the partner
+            T own = gpi ? vb : va, got = __shfl_xor_sync(0xffffffffu, gpi ? va : vb, 1);
+            L.W[v] = gpi ? got : own;
+            R.W[v] = gpi ? own : got;
+            own = (gpi ? db : da) * iht;
+            got = __shfl_xor_sync(0xffffffffu, (gpi ? da : db) * iht, 1);
+            L.Wt[v] = gpi ? got : own;
+            R.Wt[v] = gpi ? own : got;
+#pragma unroll
+            for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * gpi + 1][v][r + s][f];
+            teno_select(q, tnt, S);
+            teno_gauss(S, gA, va, da);
+            teno_gauss(S, gB, vb, db);
+            own = gpi ? vb : va;
+            got = __shfl_xor_sync(0xffffffffu, gpi ? va : vb, 1);
+            L.Wn[v] = gpi ? got : own;
+            R.Wn[v] = gpi ? own : got;
         }
         T F[4] = {T(0), T(0), T(0), T(0)}, dF[4] = {T(0), T(0), T(0), T(0)};
         if (valid) {
@@ -404,14 +400,14 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
             F[v] = T(0.5) * (F[v] + __shfl_xor_sync(0xffffffffu, F[v], 1));
             dF[v] = T(0.5) * (dF[v] + __shfl_xor_sync(0xffffffffu, dF[v], 1));
         }
-        if (gpi == 0) {  // rec was last read before the barrier ending phase 2a
+        if (gpi == 0) {
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 if (a.stage == 1) {
-                    sF[(v * TT + r) * NF + f] = T(0.5) * F[v] + T(0.125) * tdt * dF[v];
-                    sF[((4 + v) * TT + r) * NF + f] = F[v] + tdt * T(1.0 / 6.0) * dF[v];
+                    sF[sfi(v, r, f)] = T(0.5) * F[v] + T(0.125) * tdt * dF[v];
+                    sF[sfi(4 + v, r, f)] = F[v] + tdt * T(1.0 / 6.0) * dF[v];
                 } else {
-                    sF[(v * TT + r) * NF + f] = tdt * T(1.0 / 3.0) * dF[v];
+                    sF[sfi(v, r, f)] = tdt * T(1.0 / 3.0) * dF[v];
                 }
             }
         }
@@ -422,7 +418,8 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
     T sig = T(0);
     const T cn = (T)(dt * a.ihn);
     if (tid < TN * TT) {
-        const int r = tid / TN, c = tid % TN;
+        // x faces: the normal (x) index fastest; y faces: the tangential (x) index
+        const int r = fy ? tid % TT : tid / TN, c = fy ? tid / TT : tid % TN;
         const int in = n0 + c, it = t0 + r;
         if (in < a.nn && it < a.nt) {
             const long long o = org + in * a.sn + it * a.st;
@@ -432,9 +429,9 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 const long long go = (long long)gvar(v, swap) * g.plane + o;
-                const T d0 = cn * (sF[(v * TT + r) * NF + c + 1] - sF[(v * TT + r) * NF + c]);
+                const T d0 = cn * (sF[sfi(v, r, c + 1)] - sF[sfi(v, r, c)]);
                 const T d1 = (a.stage == 1)
-                           ? cn * (sF[((4 + v) * TT + r) * NF + c + 1] - sF[((4 + v) * TT + r) * NF + c])
+                           ? cn * (sF[sfi(4 + v, r, c + 1)] - sF[sfi(4 + v, r, c)])
                            : T(0);
                 if (a.pass == 0) {
                     inc0[go] = d0;
