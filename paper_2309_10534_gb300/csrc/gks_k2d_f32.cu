@@ -8,19 +8,19 @@ template <bool NONEQ, bool PRFIX>
 cudaError_t launch_one(const GridDev& g, const SweepArgs& a, const FluxParams<float>& fp, const TenoParams& tn,
                        const TenoParams& tt, DevState* ds, cudaStream_t st)
 {
-    constexpr int TN = SWEEP_TN, TT = SWEEP_TT;
+    constexpr int TN = SWEEP_TN, TT = SWEEP_TT32;
     auto kern = k2d_sweep<float, NONEQ, PRFIX, TN, TT>;
     const size_t smem = sizeof(SweepSmem<float, TN, TT>);
     dim3 grid((a.nn + TN - 1) / TN, (a.nt + TT - 1) / TT);
-    kern<<<grid, SWEEP_THREADS, smem, st>>>(g, a, fp, teno_t<float>(tn), teno_t<float>(tt), ds);
+    kern<<<grid, TT * (TN + 1), smem, st>>>(g, a, fp, teno_t<float>(tn), teno_t<float>(tt), ds);
     return cudaGetLastError();
 }
 template <bool NONEQ, bool PRFIX>
 cudaError_t set_smem()
 {
-    return cudaFuncSetAttribute(k2d_sweep<float, NONEQ, PRFIX, SWEEP_TN, SWEEP_TT>,
+    return cudaFuncSetAttribute(k2d_sweep<float, NONEQ, PRFIX, SWEEP_TN, SWEEP_TT32>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(SweepSmem<float, SWEEP_TN, SWEEP_TT>));
+                                (int)sizeof(SweepSmem<float, SWEEP_TN, SWEEP_TT32>));
 }
 }  // namespace
 

@@ -270,11 +270,11 @@ template <typename T, int TN, int TT> struct SweepSmem {
 };
 
 template <typename T, bool NONEQ, bool PRFIX, int TN, int TT>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4) ? 4 : 1)
+__global__ void __launch_bounds__(TT * (TN + 1), (sizeof(T) == 4) ? 1024 / (TT * (TN + 1)) : 1)
 k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, DevState* ds)
 {
     if (ds->done) return;
-    constexpr int NT = 256;
+    constexpr int NT = TT * (TN + 1);    // one thread per (face, row) pair
     constexpr int NF = TN + 1;           // faces per tile row
     constexpr int NP = TT * NF;          // (face, row) pairs
     static_assert(NP == NT, "one (face,row) pair per thread");

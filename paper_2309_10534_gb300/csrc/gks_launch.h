@@ -8,10 +8,12 @@
 
 namespace gks {
 
-// tile of the 2-D sweep: TN cells along the face normal (TN + 1 faces) x TT rows
+// tile of the 2-D sweep: TN cells along the face normal (TN + 1 faces) x TT
+// rows, one thread per (face, row) pair; float32 blocks hold 64 registers per
+// thread (1024 / threads blocks per SM)
 constexpr int SWEEP_TN = 31;
-constexpr int SWEEP_TT = 8;
-constexpr int SWEEP_THREADS = 256;
+constexpr int SWEEP_TT32 = 16;
+constexpr int SWEEP_TT64 = 8;
 // cells per block of the 1-D stage (TN + 1 threads, one per face)
 constexpr int STAGE1D_TN = 127;
 
