@@ -61,6 +61,10 @@ def parse():
                    help="omit the batched 1-D ensemble leg")
     p.add_argument("--no-adjoint", dest="adjoint", action="store_false",
                    help="omit the adjoint leg")
+    p.add_argument("--ensemble-max-steps", type=int, default=0,
+                   help="cap the ensemble leg at this many steps per problem (profiling runs)")
+    p.add_argument("--ensemble-launch", default="",
+                   help="THREADS,BLOCKS_PER_SM for the ensemble leg instead of the autotuner")
     p.add_argument("--no-viscous", dest="viscous", action="store_false",
                    help="omit the viscous shock tube leg")
     return p.parse_args()
@@ -209,7 +213,7 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def ensemble_leg(gks, WL, stream, peak32):
+def ensemble_leg(gks, WL, stream, peak32, max_steps=0, launch=None):
     """4096 independent 1-D Riemann problems (200..4000 cells, seeded) to
     t = 0.15 in one persistent launch, float32 flux / float64 state, launch
     shape from the autotuner.  One untimed run captures the graph; the timed
@@ -222,14 +226,18 @@ def ensemble_leg(gks, WL, stream, peak32):
     B = gks.Batch(E.ncells, np.ones(E.ncells.size), precision="fp32")
     B.set_stream(stream.cuda_stream)
     B.set_state(E.W)
-    th, bp, _ = B.tune(0.005, use_cache=False)
-    B.advance_to(E.t_end, allow_failed=True)
+    if launch:
+        th, bp = launch
+        B.set_launch(th, bp)
+    else:
+        th, bp, _ = B.tune(0.005, use_cache=False)
+    B.advance_to(E.t_end, max_steps=max_steps, allow_failed=True)
     B.set_state(E.W)
     L0 = B.launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    nbad = B.advance_to(E.t_end, allow_failed=True)
+    nbad = B.advance_to(E.t_end, max_steps=max_steps, allow_failed=True)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -401,7 +409,10 @@ def main():
     S64 = solver("fp64")
     k64 = max(1, args.fp64_steps)
     ms64, launches64, sn64, sms64 = timed(S64, k64, min(args.warmup, 3))
-    ens = ensemble_leg(gks, WL, stream, peak32) if args.ensemble else None
+    ens = None
+    if args.ensemble:
+        launch = tuple(int(x) for x in args.ensemble_launch.split(",")) if args.ensemble_launch else None
+        ens = ensemble_leg(gks, WL, stream, peak32, args.ensemble_max_steps, launch)
     visc = None
     if args.viscous:
         visc = viscous_leg(gks, WL, stream, "fp32", 200)

@@ -146,8 +146,9 @@ cudaError_t prof_harvest(gks_ctx* c)
 }
 
 // ---------------------------------------------------------------- launches
-// Ghost layers of W or W*.  On the 2-D float32 path the sweeps read only the
-// float32 shadow, so its ghosts are filled instead of the float64 ones.
+// Ghost layers of W or W*.  On the float32 path the stage kernels read W* in
+// float32 (and, in 2-D, W through its float32 shadow), so those ghosts are
+// filled instead of the float64 ones.
 }  // namespace
 
 namespace gks {
@@ -158,12 +159,9 @@ gks_status enqueue_ghosts(gks_ctx* c, double* arr, cudaStream_t st)
     const int gx = c->desc.nx + 2 * NG;
     const int n = (c->desc.dim == 1) ? 2 * NG : 2 * NG * gx + 2 * NG * c->desc.ny;
     const int pi = prof_begin(c, st, 1);
-    if (c->Wf) {
-        float* shadow = (arr == c->W) ? c->Wf : c->Wsf;
-        k_fill_ghosts<float><<<(n + 127) / 128, 128, 0, st>>>(c->g, shadow, c->ds);
-    } else {
-        k_fill_ghosts<double><<<(n + 127) / 128, 128, 0, st>>>(c->g, arr, c->ds);
-    }
+    float* shadow = (arr == c->Ws) ? c->Wsf : (arr == c->W ? c->Wf : nullptr);
+    if (shadow) k_fill_ghosts<float><<<(n + 127) / 128, 128, 0, st>>>(c->g, shadow, c->ds);
+    else k_fill_ghosts<double><<<(n + 127) / 128, 128, 0, st>>>(c->g, arr, c->ds);
     CK(cudaGetLastError());
     prof_end(c, st, pi);
     ++c->launches;
@@ -186,8 +184,16 @@ gks_status enqueue_stage(gks_ctx* c, int stage, int with_sigma, cudaStream_t st)
         a.stage = stage;
         a.with_sigma = with_sigma;
         a.idx = 1.0 / c->g.dx;
-        if (stage == 1) { a.src = c->W; a.out0 = c->Ws; a.out1 = c->Ac; }
-        else { a.src = c->Ws; a.out0 = c->W; a.acc = c->Ac; }
+        if (f32) {
+            // float32 W* (Wsf) and accumulator increment (inc1)
+            float* inc = static_cast<float*>(c->inc1);
+            if (stage == 1) { a.src = c->W; a.out0f = c->Wsf; a.out1f = inc; }
+            else { a.srcf = c->Wsf; a.base = c->W; a.out0 = c->W; a.accf = inc; }
+        } else if (stage == 1) {
+            a.src = c->W; a.out0 = c->Ws; a.out1 = c->Ac;
+        } else {
+            a.src = c->Ws; a.out0 = c->W; a.acc = c->Ac;
+        }
         const int pi = prof_begin(c, st, 0);
         CK(launch_stage1d(f32, c->g, a, hf, tn, c->ds, st));
         prof_end(c, st, pi);
@@ -463,6 +469,11 @@ gks_status gks_create(const gks_grid_desc* d, gks_ctx** out)
             e6 = cudaMalloc(&c->Wf, fb);
             if (e6 == cudaSuccess) e6 = cudaMalloc(&c->Wsf, fb);
         }
+    } else if (d->precision == GKS_FP32_FLUX) {
+        // 1-D float32 path: W* and the accumulator increment in float32
+        const size_t fb = (size_t)c->nv * g.plane * sizeof(float);
+        e6 = cudaMalloc(&c->Wsf, fb);
+        e7 = cudaMalloc(&c->inc1, fb);
     }
     if (e1 || e2 || e3 || e4 || e5 || e6 || e7) {
         gks_destroy(c);
@@ -571,7 +582,7 @@ gks_status gks_get_buffer(gks_ctx* c, int which, double* W, int on_device)
 {
     if (!c || !W || which < 0 || which > 2) return GKS_EINVAL;
     double* arr = which == 0 ? c->W : (which == 1 ? c->Ws : c->Ac);
-    if (c->Wf && which > 0) {
+    if (c->Wsf && which > 0) {
         // float32 path: W* lives in float32, the accumulator as an increment
         const long long n = (long long)c->nv * c->g.plane;
         const int blocks = (int)((n + 255) / 256 > 4096 ? 4096 : (n + 255) / 256);

@@ -18,8 +18,10 @@ struct gks_ctx {
     gks_scheme sch{};
     int nv = 0;
     double *W = nullptr, *Ws = nullptr, *Ac = nullptr;
-    void *inc0 = nullptr, *inc1 = nullptr;  // x-sweep increments (2-D), working precision
-    float *Wf = nullptr, *Wsf = nullptr;     // float32 shadows of W, W* (2-D float32 path)
+    void *inc0 = nullptr, *inc1 = nullptr;  // 2-D: x-sweep increments, working precision;
+                                             // 1-D float32: inc1 = accumulator increment
+    float* Wf = nullptr;                     // float32 shadow of W (2-D float32 path)
+    float* Wsf = nullptr;                    // W* in float32 (float32 path)
     size_t arr_bytes = 0;
     gks::DevState* ds = nullptr;      // device
     gks::DevState* hs = nullptr;      // pinned host mirror

@@ -6,7 +6,7 @@
 // advances it to t_end with its own CFL steps, writes it back and pops the
 // next.  The whole problem stays with one block, so the stage barrier is a
 // __syncthreads and blocks never wait on each other.  A stage sweeps the
-// problem in chunks of NT-1 cells with the same per-cell and per-face
+// problem in chunks of NT-6 cells with the same per-cell and per-face
 // arithmetic as the single-grid 1-D kernel (zero-gradient ends by clamped
 // indices).  The launch (queue reset + kernel) is captured once as a CUDA
 // graph per (t_end, max_steps, launch shape); a small autotuner times the
@@ -35,7 +35,10 @@ using namespace gks;
 namespace {
 
 struct BatchDev {
-    double *W, *Ws, *A;           // packed [3][total]
+    double* W;                    // packed [3][total] state
+    void *Ws, *A;                 // W* and the accumulator: float64 arrays on the
+                                  // float64 path; on the float32 path W* in float32
+                                  // and the accumulator increment in float32
     long long total;              // cells of all problems
     const long long* off;         // first cell of each problem
     const int* n;                 // cells per problem
@@ -78,21 +81,25 @@ __device__ __forceinline__ unsigned int block_or(unsigned int v, unsigned int* r
     return r;
 }
 
+// A chunk holds TN = NT - 6 cells, so that its TN + 6 stencil cells, TN + 2
+// reconstructed cells and TN + 1 faces each take one pass of the block.
 template <typename T, int NT> struct ChunkSmem {
-    T q[3][NT + 5];             // cells c0-3 .. c0+TN+2 (TN = NT-1)
+    T q[3][NT];                 // cells c0-3 .. c0+TN+2
     T L[3][2][NT], R[3][2][NT]; // face states [var][value, slope][face]
     T G[2][3][NT];              // face fluxes for the update
 };
 
 // One stage over cells [c0, c0+TN) of a problem: load (clamped indices =
-// zero-gradient ghosts), TENO-D per cell, flux per face, update.
+// zero-gradient ghosts), TENO-D per cell, flux per face, update.  The update
+// follows the single-grid 1-D kernel: float64 W* and accumulator on the
+// float64 path; on the float32 path W* and the accumulator increment in
+// float32 and one float64 update of W per value and step.
 template <typename T, int NT, bool NONEQ, bool PRFIX>
-__device__ void stage_chunk(ChunkSmem<T, NT>& sm, const double* src, double* out0, double* out1, const double* acc,
-                            long long vstride, int n, int c0, int stage, double dt, double idx,
-                            const FluxParams<T>& fp, const TenoT<T>& tn, T& sig, unsigned int& err,
-                            unsigned int& nfb, T gamma, T mu, T hcell)
+__device__ void stage_chunk(ChunkSmem<T, NT>& sm, double* W, T* Ws, T* A, long long vstride, int n, int c0,
+                            int stage, double dt, double idx, const FluxParams<T>& fp, const TenoT<T>& tn, T& sig,
+                            unsigned int& err, unsigned int& nfb, T gamma, T mu, T hcell)
 {
-    constexpr int TN = NT - 1;
+    constexpr int TN = NT - 6;
     const int tid = threadIdx.x;
     const int slot[3] = {0, 1, 3};
     __syncthreads();  // shared memory of the previous chunk is free
@@ -100,7 +107,8 @@ __device__ void stage_chunk(ChunkSmem<T, NT>& sm, const double* src, double* out
         const int v = k / (TN + 6), c = k % (TN + 6);
         int i = c0 - 3 + c;
         i = i < 0 ? 0 : (i >= n ? n - 1 : i);
-        sm.q[v][c] = (T)src[(long long)v * vstride + i];
+        const long long gi = (long long)v * vstride + i;
+        sm.q[v][c] = stage == 1 ? (T)W[gi] : Ws[gi];
     }
     __syncthreads();
     const T ih = (T)idx;
@@ -147,34 +155,48 @@ __device__ void stage_chunk(ChunkSmem<T, NT>& sm, const double* src, double* out
         T F[4], dF[4];
         point_flux<T, 1, NONEQ, PRFIX>(L, R, fp, F, dF);
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-            const int s = slot[v];
-            if (stage == 1) {
-                sm.G[0][v][f] = T(0.5) * F[s] + T(0.125) * tdt * dF[s];
-                sm.G[1][v][f] = F[s] + tdt * T(1.0 / 6.0) * dF[s];
-            } else {
-                sm.G[0][v][f] = tdt * T(1.0 / 3.0) * dF[s];
-            }
-        }
+        for (int v = 0; v < 3; ++v) stage_comb<T>(stage, F[slot[v]], dF[slot[v]], tdt, sm.G[0][v][f], sm.G[1][v][f]);
     }
     __syncthreads();
     const double cx = dt * idx;
+    const T cxt = (T)cx;
     for (int c = tid; c < TN; c += NT) {
         const int i = c0 + c;
         if (i >= n) continue;
-        if (stage == 1) {
+        if constexpr (sizeof(T) == 4) {
+            if (stage == 1) {
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    const long long gi = (long long)v * vstride + i;
+                    Ws[gi] = wstar32(sm.q[v][c + 3], cxt, sm.G[0][v][c + 1] - sm.G[0][v][c]);
+                    A[gi] = cxt * (sm.G[1][v][c + 1] - sm.G[1][v][c]);
+                }
+            } else {
+                T w[3];
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    const long long gi = (long long)v * vstride + i;
+                    const double r = wnew32(W[gi], A[gi], cxt, sm.G[0][v][c + 1] - sm.G[0][v][c]);
+                    W[gi] = r;
+                    w[v] = (T)r;
+                }
+                sig = fmax(sig, cell_sigma1<T>(w[0], w[1], w[2], gamma, mu, hcell, err));
+            }
+        } else if (stage == 1) {
 #pragma unroll
             for (int v = 0; v < 3; ++v) {
-                const double w = src[(long long)v * vstride + i];
-                out0[(long long)v * vstride + i] = w - cx * (double)(sm.G[0][v][c + 1] - sm.G[0][v][c]);
-                out1[(long long)v * vstride + i] = w - cx * (double)(sm.G[1][v][c + 1] - sm.G[1][v][c]);
+                const long long gi = (long long)v * vstride + i;
+                const double w = W[gi];
+                Ws[gi] = upd64(w, cx, (double)(sm.G[0][v][c + 1] - sm.G[0][v][c]));
+                A[gi] = upd64(w, cx, (double)(sm.G[1][v][c + 1] - sm.G[1][v][c]));
             }
         } else {
             double w[3];
 #pragma unroll
             for (int v = 0; v < 3; ++v) {
-                w[v] = acc[(long long)v * vstride + i] - cx * (double)(sm.G[0][v][c + 1] - sm.G[0][v][c]);
-                out0[(long long)v * vstride + i] = w[v];
+                const long long gi = (long long)v * vstride + i;
+                w[v] = upd64(A[gi], cx, (double)(sm.G[0][v][c + 1] - sm.G[0][v][c]));
+                W[gi] = w[v];
             }
             sig = fmax(sig, cell_sigma<T>(w, 1, gamma, mu, hcell, err));
         }
@@ -188,7 +210,7 @@ __global__ void __launch_bounds__(NT) k_batch(BatchDev b, FluxParams<T> fp, Teno
     __shared__ T red[NT / 32];
     __shared__ unsigned int redu[NT / 32];
     __shared__ int s_prob;
-    constexpr int TN = NT - 1;
+    constexpr int TN = NT - 6;
     const int tid = threadIdx.x;
     const T gamma = (T)b.gamma, mu = (T)b.mu;
     for (;;) {
@@ -203,18 +225,15 @@ __global__ void __launch_bounds__(NT) k_batch(BatchDev b, FluxParams<T> fp, Teno
         const double dx = b.dx[p], idx = 1.0 / dx;
         const T hcell = (T)dx;
         double* W = b.W + off;
-        double* Ws = b.Ws + off;
-        double* A = b.A + off;
+        T* Ws = static_cast<T*>(b.Ws) + off;
+        T* A = static_cast<T*>(b.A) + off;
         double t = b.t[p];
         long long steps = 0;
         unsigned int err = 0, nfb = 0;
         // CFL rate of the starting state
         T sig = T(0);
-        for (int i = tid; i < n; i += NT) {
-            double w[3];
-            for (int v = 0; v < 3; ++v) w[v] = W[(long long)v * b.total + i];
-            sig = fmax(sig, cell_sigma<T>(w, 1, gamma, mu, hcell, err));
-        }
+        for (int i = tid; i < n; i += NT)
+            sig = fmax(sig, cell_sigma1<T>((T)W[i], (T)W[b.total + i], (T)W[2 * b.total + i], gamma, mu, hcell, err));
         sig = block_max<T, NT>(sig, red);
         err = block_or(err, redu);
         while (t < b.t_end && (b.max_steps <= 0 || steps < b.max_steps) && !err) {
@@ -223,12 +242,12 @@ __global__ void __launch_bounds__(NT) k_batch(BatchDev b, FluxParams<T> fp, Teno
             FluxParams<T> f = fp;
             f.dt = (T)dt;
             for (int c0 = 0; c0 < n; c0 += TN)
-                stage_chunk<T, NT, NONEQ, PRFIX>(sm, W, Ws, A, nullptr, b.total, n, c0, 1, dt, idx, f, tn, sig, err,
-                                                 nfb, gamma, mu, hcell);
+                stage_chunk<T, NT, NONEQ, PRFIX>(sm, W, Ws, A, b.total, n, c0, 1, dt, idx, f, tn, sig, err, nfb, gamma,
+                                                 mu, hcell);
             T s2 = T(0);
             for (int c0 = 0; c0 < n; c0 += TN)
-                stage_chunk<T, NT, NONEQ, PRFIX>(sm, Ws, W, nullptr, A, b.total, n, c0, 2, dt, idx, f, tn, s2, err,
-                                                 nfb, gamma, mu, hcell);
+                stage_chunk<T, NT, NONEQ, PRFIX>(sm, W, Ws, A, b.total, n, c0, 2, dt, idx, f, tn, s2, err, nfb, gamma,
+                                                 mu, hcell);
             sig = block_max<T, NT>(s2, red);
             err = block_or(err, redu);
             t += dt;
@@ -295,7 +314,8 @@ struct gks_batch {
     std::vector<int> n;
     std::vector<double> len;
     std::vector<long long> off;
-    double *W = nullptr, *Ws = nullptr, *A = nullptr;
+    double* W = nullptr;
+    void *Ws = nullptr, *A = nullptr;
     long long* d_off = nullptr;
     int *d_n = nullptr, *d_order = nullptr, *d_queue = nullptr;
     double *d_dx = nullptr, *d_t = nullptr, *d_speed = nullptr;
@@ -506,10 +526,11 @@ gks_status gks_batch_create(int count, const int* ncells, const double* lengths,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t arr = sizeof(double) * 3 * (size_t)tot;
+    const size_t warr = (precision == GKS_FP32_FLUX ? sizeof(float) : sizeof(double)) * 3 * (size_t)tot;
     std::vector<double> dx(count);
     for (int k = 0; k < count; ++k) dx[k] = b->len[k] / b->n[k];
-    bool ok = cudaMalloc(&b->W, arr) == cudaSuccess && cudaMalloc(&b->Ws, arr) == cudaSuccess &&
-              cudaMalloc(&b->A, arr) == cudaSuccess && cudaMalloc(&b->d_off, sizeof(long long) * count) == cudaSuccess &&
+    bool ok = cudaMalloc(&b->W, arr) == cudaSuccess && cudaMalloc(&b->Ws, warr) == cudaSuccess &&
+              cudaMalloc(&b->A, warr) == cudaSuccess && cudaMalloc(&b->d_off, sizeof(long long) * count) == cudaSuccess &&
               cudaMalloc(&b->d_n, sizeof(int) * count) == cudaSuccess &&
               cudaMalloc(&b->d_order, sizeof(int) * count) == cudaSuccess &&
               cudaMalloc(&b->d_queue, sizeof(int)) == cudaSuccess &&

@@ -110,16 +110,69 @@ __device__ __forceinline__ void block_commit(T s, bool with_sigma, unsigned int 
     }
 }
 
+// ------------------------------------------------------------------ stage arithmetic
+// Stage combinations of the face flux F and its time derivative dF
+// (Sec. 2.2): stage 1: g0 = F/2 + dt/8 dF (for W*), g1 = F + dt/6 dF (for the
+// accumulator); stage 2: g0 = dt/3 dF.  Explicit fused multiply-adds, here
+// and in the updates below, give every kernel the same rounding.
+template <typename T>
+__device__ __forceinline__ void stage_comb(int stage, T F, T dF, T dt, T& g0, T& g1)
+{
+    if (stage == 1) {
+        g0 = fma(T(0.125) * dt, dF, T(0.5) * F);
+        g1 = fma(dt * T(1.0 / 6.0), dF, F);
+    } else {
+        g0 = (dt * T(1.0 / 3.0)) * dF;
+        g1 = T(0);
+    }
+}
+// float64 path: W* = W - cx dG0, A = W - cx dG1; stage 2: W = A - cx dG0
+__device__ __forceinline__ double upd64(double w, double cx, double dG) { return fma(-cx, dG, w); }
+// float32 path: W* = W - cx dG0 and the increment cx dG1 in float32; stage 2:
+// W = W - (increment + cx dG0), the sum in float32, the update in float64
+__device__ __forceinline__ float wstar32(float w, float cx, float dG) { return fmaf(-cx, dG, w); }
+__device__ __forceinline__ double wnew32(double w, float inc, float cx, float dG)
+{
+    return w - (double)fmaf(cx, dG, inc);
+}
+
 // ------------------------------------------------------------------ 1-D stage
+// float64 path: W* and the accumulator A are float64 arrays.
+// float32 path (as the 2-D one): W* is only the stage-2 reconstruction input,
+// so it is formed and kept in float32, and the accumulator is kept as the
+// float32 increment dt/dx d(F + dt/6 dF); the only float64 arithmetic is the
+// final update W^{n+1} = W^n - (increment + dt/dx d(dt/3 dF*)).
 struct Stage1DArgs {
-    const double* src;   // reconstruction input (W for stage 1, W* for stage 2), ghosts filled
-    double* out0;        // stage 1: W*; stage 2: W (new state)
-    double* out1;        // stage 1: accumulator A; stage 2: unused
-    const double* acc;   // stage 2: accumulator A; stage 1: unused
+    const double* src;   // float64 reconstruction input (W; float64 path stage 2: W*), ghosts filled
+    const float* srcf;   // float32 path, stage 2: W* (float32, ghosts filled)
+    double* out0;        // float64 path stage 1: W*; stage 2: the new state
+    double* out1;        // float64 path stage 1: accumulator A
+    const double* acc;   // float64 path stage 2: accumulator A
+    float* out0f;        // float32 path stage 1: W*
+    float* out1f;        // float32 path stage 1: accumulator increment
+    const float* accf;   // float32 path stage 2: accumulator increment
+    const double* base;  // float32 path stage 2: W^n
     int stage;
     int with_sigma;      // stage 2: reduce the CFL rate of the new state
     double idx;          // 1 / dx
 };
+
+// CFL rate of one 1-D cell from its working-precision values (the same
+// expression as cell_sigma with V = 0, so both give the same bits)
+template <typename T>
+__device__ __forceinline__ T cell_sigma1(T w0, T w1, T w2, T gamma, T mu, T h, unsigned int& err)
+{
+    const T r = w0, ir = T(1) / r;
+    const T U = w1 * ir, V = T(0);
+    const T E = w2;
+    const T p = (gamma - T(1)) * (E - T(0.5) * r * (U * U + V * V));
+    if (!(r > T(0) && p > T(0) && isfinite(p))) err |= 1u;
+    const T a = sqrt(gamma * p * ir);
+    const T ih = T(1) / h;
+    T s = (sqrt(U * U + V * V) + a) * ih;
+    if (mu > T(0)) s = fmax(s, T(4) * mu * ir * ih * ih);
+    return s;
+}
 
 template <typename T, bool NONEQ, bool PRFIX, int TN>
 __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, FluxParams<T> fp, TenoT<T> tn,
@@ -140,7 +193,16 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
     for (int k = tid; k < 3 * (TN + 6); k += NT) {
         const int v = k / (TN + 6), c = k % (TN + 6);
         const int gi = i0 + c;  // ghosted index of cell i0 - 3 + c
-        sq[v][c] = gi < gx ? (T)a.src[(long long)v * g.plane + gi] : T(0);
+        T val = T(0);
+        if (gi < gx) {
+            if constexpr (sizeof(T) == 4) {
+                if (a.stage == 2) val = a.srcf[(long long)v * g.plane + gi];
+                else val = (T)a.src[(long long)v * g.plane + gi];
+            } else {
+                val = a.src[(long long)v * g.plane + gi];
+            }
+        }
+        sq[v][c] = val;
     }
     __syncthreads();
     const T idx_ = (T)a.idx;
@@ -190,36 +252,48 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
         point_flux<T, 1, NONEQ, PRFIX>(L, R, fp, F, dF);
         const T tdt = (T)dt;
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-            const int s = slot[v];
-            if (a.stage == 1) {
-                sG[0][v][f] = T(0.5) * F[s] + T(0.125) * tdt * dF[s];
-                sG[1][v][f] = F[s] + tdt * T(1.0 / 6.0) * dF[s];
-            } else {
-                sG[0][v][f] = tdt * T(1.0 / 3.0) * dF[s];
-            }
-        }
+        for (int v = 0; v < 3; ++v) stage_comb<T>(a.stage, F[slot[v]], dF[slot[v]], tdt, sG[0][v][f], sG[1][v][f]);
     }
     __syncthreads();
     // phase 3: update
     T sig = T(0);
     const double cx = dt * a.idx;
+    const T cxt = (T)cx;
     for (int c = tid; c < TN; c += NT) {
         const int i = i0 + c;
         if (i >= g.nx) continue;
         const long long o = i + NG;
-        if (a.stage == 1) {
+        if constexpr (sizeof(T) == 4) {
+            if (a.stage == 1) {
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    a.out0f[(long long)v * g.plane + o] = wstar32(sq[v][c + 3], cxt, sG[0][v][c + 1] - sG[0][v][c]);
+                    a.out1f[(long long)v * g.plane + o] = cxt * (sG[1][v][c + 1] - sG[1][v][c]);
+                }
+            } else {
+                T w[3];
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    const long long gi = (long long)v * g.plane + o;
+                    const double r = wnew32(a.base[gi], a.accf[gi], cxt, sG[0][v][c + 1] - sG[0][v][c]);
+                    a.out0[gi] = r;
+                    w[v] = (T)r;
+                }
+                if (a.with_sigma)
+                    sig = fmax(sig, cell_sigma1<T>(w[0], w[1], w[2], (T)g.gamma, (T)g.mu, (T)g.dx, err));
+            }
+        } else if (a.stage == 1) {
 #pragma unroll
             for (int v = 0; v < 3; ++v) {
                 const double w = a.src[(long long)v * g.plane + o];
-                a.out0[(long long)v * g.plane + o] = w - cx * (double)(sG[0][v][c + 1] - sG[0][v][c]);
-                a.out1[(long long)v * g.plane + o] = w - cx * (double)(sG[1][v][c + 1] - sG[1][v][c]);
+                a.out0[(long long)v * g.plane + o] = upd64(w, cx, (double)(sG[0][v][c + 1] - sG[0][v][c]));
+                a.out1[(long long)v * g.plane + o] = upd64(w, cx, (double)(sG[1][v][c + 1] - sG[1][v][c]));
             }
         } else {
             double w[4];
 #pragma unroll
             for (int v = 0; v < 3; ++v) {
-                const double r = a.acc[(long long)v * g.plane + o] - cx * (double)(sG[0][v][c + 1] - sG[0][v][c]);
+                const double r = upd64(a.acc[(long long)v * g.plane + o], cx, (double)(sG[0][v][c + 1] - sG[0][v][c]));
                 a.out0[(long long)v * g.plane + o] = r;
                 w[v] = r;
             }
@@ -403,12 +477,10 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
         if (gpi == 0) {
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                if (a.stage == 1) {
-                    sF[sfi(v, r, f)] = T(0.5) * F[v] + T(0.125) * tdt * dF[v];
-                    sF[sfi(4 + v, r, f)] = F[v] + tdt * T(1.0 / 6.0) * dF[v];
-                } else {
-                    sF[sfi(v, r, f)] = tdt * T(1.0 / 3.0) * dF[v];
-                }
+                T g0, g1;
+                stage_comb<T>(a.stage, F[v], dF[v], tdt, g0, g1);
+                sF[sfi(v, r, f)] = g0;
+                if (a.stage == 1) sF[sfi(4 + v, r, f)] = g1;
             }
         }
     }

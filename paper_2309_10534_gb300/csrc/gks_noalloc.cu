@@ -94,7 +94,8 @@ __global__ void k_load(const double* __restrict__ Win, double* __restrict__ W, i
     }
 }
 
-__global__ void k_ghosts(double* __restrict__ W, int nx, int bc0, int bc1)
+template <typename E>
+__global__ void k_ghosts(E* __restrict__ W, int nx, int bc0, int bc1)
 {
     const int k = threadIdx.x;
     if (k >= 2 * NG) return;
@@ -102,7 +103,7 @@ __global__ void k_ghosts(double* __restrict__ W, int nx, int bc0, int bc1)
     bool flip;
     const int src = ghost_source(k < NG ? bc0 : bc1, nx, i, flip);
     for (int v = 0; v < 3; ++v) {
-        const double val = W[(long long)v * PITCH + src];
+        const E val = W[(long long)v * PITCH + src];
         W[(long long)v * PITCH + i] = (flip && v == 1) ? -val : val;
     }
 }
@@ -167,20 +168,25 @@ extern "C" gks_status gks_step1d_noalloc(const double* W_in, double* W_out, int 
     TenoParams tn{sch->eps, sch->q, sch->ct1, sch->ct2};
     const int f32 = precision == GKS_FP32_FLUX;
 
+    // the float32 path keeps W* and the accumulator increment in float32, in
+    // the same scratch regions
+    float* Wsf = reinterpret_cast<float*>(Ws);
+    float* incf = reinterpret_cast<float*>(Ac);
     k_load<<<(nx + 2 * NG + 127) / 128, 128, 0, st>>>(W_in, W, nx, bc[0], bc[1], ds, dt);
     Stage1DArgs a1{};
     a1.idx = 1.0 / dx;
     a1.src = W;
-    a1.out0 = Ws;
-    a1.out1 = Ac;
+    if (f32) { a1.out0f = Wsf; a1.out1f = incf; }
+    else { a1.out0 = Ws; a1.out1 = Ac; }
     a1.stage = 1;
     if (launch_stage1d(f32, g, a1, hf, tn, ds, st) != cudaSuccess) return GKS_ECUDA;
-    k_ghosts<<<1, 32, 0, st>>>(Ws, nx, bc[0], bc[1]);
+    if (f32) k_ghosts<float><<<1, 32, 0, st>>>(Wsf, nx, bc[0], bc[1]);
+    else k_ghosts<double><<<1, 32, 0, st>>>(Ws, nx, bc[0], bc[1]);
     Stage1DArgs a2{};
     a2.idx = 1.0 / dx;
-    a2.src = Ws;
+    if (f32) { a2.srcf = Wsf; a2.base = W; a2.accf = incf; }
+    else { a2.src = Ws; a2.acc = Ac; }
     a2.out0 = Wn;
-    a2.acc = Ac;
     a2.stage = 2;
     a2.with_sigma = 1;  // checks the new state for rho, p > 0 and finiteness
     if (launch_stage1d(f32, g, a2, hf, tn, ds, st) != cudaSuccess) return GKS_ECUDA;

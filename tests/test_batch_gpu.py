@@ -86,23 +86,26 @@ def test_batch_fp32_against_oracle_and_exact(gks, small, threads):
     assert e_gpu == pytest.approx(e_ora, rel=5e-2)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-6)])
-def test_batch_equals_single_grid_path(gks, small, precision, tol):
-    """Same device arithmetic as gks_advance_to on each problem alone (the
-    float32 bound allows for contraction differences between the two
-    compilations, amplified by TENO-D switches)."""
+@pytest.mark.parametrize("precision,tol,max_steps", [("fp64", 1e-13, 0), ("fp32", 1e-6, 3)])
+def test_batch_equals_single_grid_path(gks, small, precision, tol, max_steps):
+    """Same device arithmetic as gks_advance_to on each problem alone.  In
+    float64 the whole run to t = 0.03 agrees to 1e-13.  In float32 the two
+    kernels (compiled separately, so free to contract a multiply-add
+    differently) agree to the last bit or one float32 ulp per step; through
+    shocks TENO-D switches amplify an ulp over tens of steps, so the float32
+    comparison is taken over the first 3 steps."""
     E, _ = small
     B = gks.Batch(E.ncells, np.ones(E.ncells.size), precision=precision)
     B.set_state(E.W)
-    B.advance_to(0.03)
+    B.advance_to(0.03, max_steps=max_steps)
     out = B.get_state()
     _, steps_b, _, _ = B.progress()
     worst = 0.0
-    for k in (0, 4, 5, 11, 23):
+    for k in range(E.ncells.size):
         n, W = _problem(E, k)
         S = gks.Solver(1, n, precision=precision, tau="euler")
         S.set_state(W[:, None, :])
-        steps, t = S.advance_to(0.03)
+        steps, t = S.advance_to(0.03, max_steps=max_steps)
         assert steps == steps_b[k]
         worst = max(worst, _rel(out[:, E.offsets[k]:E.offsets[k] + n], S.get_state()[:, 0, :]))
     print(f"{precision} batch vs single grid: worst rel L1 {worst:.3e}")
