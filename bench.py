@@ -61,6 +61,10 @@ def parse():
                    help="omit the batched 1-D ensemble leg")
     p.add_argument("--no-adjoint", dest="adjoint", action="store_false",
                    help="omit the adjoint leg")
+    p.add_argument("--adjoint-steps", type=int, default=700,
+                   help="steps of the adjoint leg (700 = t = 2; fewer for profiling runs)")
+    p.add_argument("--no-adjoint-fp64", dest="adjoint_fp64", action="store_false",
+                   help="omit the float64 run of the adjoint leg")
     p.add_argument("--ensemble-max-steps", type=int, default=0,
                    help="cap the ensemble leg at this many steps per problem (profiling runs)")
     p.add_argument("--ensemble-launch", default="",
@@ -288,7 +292,7 @@ def viscous_leg(gks, WL, stream, precision, steps):
             "Pr": 0.73, "precision": precision}
 
 
-def adjoint_leg(gks, WL, stream, precision):
+def adjoint_leg(gks, WL, stream, precision, steps=700):
     """Hand-written adjoint on the isentropic vortex (strength 5, periodic
     [0, 10]^2, 512 x 512, smooth seeded density perturbation of RMS 1e-3):
     J = integral of rho^2 at t = 2 in 700 fixed steps (CFL 0.5), checkpoint
@@ -297,8 +301,8 @@ def adjoint_leg(gks, WL, stream, precision):
     stream; ms per step of each."""
     import numpy as np
     import torch
-    n, steps, k = 512, 700, 20
-    dt = 2.0 / steps
+    n, k = 512, 20
+    dt = 2.0 / 700
     s = WL.isentropic_vortex(n=n, seed=2309, amplitude=1e-3)
     S = gks.Solver(2, n, n, lx=10.0, ly=10.0, bc=("periodic",) * 4, precision=precision, tau="zero")
     S.set_stream(stream.cuda_stream)
@@ -419,8 +423,9 @@ def main():
         visc["fp64"] = viscous_leg(gks, WL, stream, "fp64", 10)
     adj = None
     if args.adjoint:
-        adj = adjoint_leg(gks, WL, stream, "fp32")
-        adj["fp64"] = adjoint_leg(gks, WL, stream, "fp64")
+        adj = adjoint_leg(gks, WL, stream, "fp32", args.adjoint_steps)
+        if args.adjoint_fp64:
+            adj["fp64"] = adjoint_leg(gks, WL, stream, "fp64", args.adjoint_steps)
     clk = clocks.stop()
 
     # same number of steps on both paths from the same state: relative L1 of fp32 vs fp64

@@ -159,7 +159,7 @@ __device__ __forceinline__ void sel_decode(unsigned c, TenoSel<T>& S)
 // tangential TENO-D.  Two adjacent lanes hold the two Gauss points of one face
 // segment; lane 0 finishes the left side's quantities, lane 1 the right's.
 template <typename T>
-__global__ void __launch_bounds__(128) k_adj_gauss(GridDev g, AdjDir a, FluxParams<T> fp, TenoT<T> tt)
+__global__ void __launch_bounds__(128, (sizeof(T) == 4) ? 4 : 1) k_adj_gauss(GridDev g, AdjDir a, FluxParams<T> fp, TenoT<T> tt)
 {
     const int gp = threadIdx.x & 1;
     const int x = (blockIdx.x * blockDim.x + threadIdx.x) >> 1, y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -176,25 +176,40 @@ __global__ void __launch_bounds__(128) k_adj_gauss(GridDev g, AdjDir a, FluxPara
     const T gpos = gp ? T(0.28867513459481288) : T(-0.28867513459481288);
     const T iht = (T)a.iht;
 
-    // forward: the Gauss-point states of both sides at this lane's point
+    // forward, as the forward sweep: lane gp reconstructs side gp (0: left,
+    // 1: right) at both Gauss points, keeps its own point and hands the other
+    // point's values to its partner
     Side<T> L, R;
-    unsigned long long codes = 0;  // 4 bits per quantity q = 4 k + v
-#pragma unroll 1
-    for (int k = 0; k < 4; ++k) {
+    unsigned codes = 0;  // selections of the own side: 4 bits per quantity kk * 4 + v
+    const T gA = T(-0.28867513459481288), gB = T(0.28867513459481288);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            T q[5];
+    for (int v = 0; v < 4; ++v) {
+        T q[5];
+        TenoSel<T> S;
+        T va, da, vb, db;
 #pragma unroll
-            for (int s = 0; s < 5; ++s) q[s] = Lq[(k * 4 + v) * LP + lidx(a, fc, rc - 2 + s)];
-            TenoSel<T> S;
-            teno_select(q, tt, S);
-            T val, der;
-            teno_gauss(S, gpos, val, der);
-            codes |= (unsigned long long)sel_code(S) << (4 * (k * 4 + v));
-            Side<T>& X = (k < 2) ? L : R;
-            if ((k & 1) == 0) { X.W[v] = val; X.Wt[v] = der * iht; }
-            else X.Wn[v] = val;
-        }
+        for (int s = 0; s < 5; ++s) q[s] = Lq[((2 * gp) * 4 + v) * LP + lidx(a, fc, rc - 2 + s)];
+        teno_select(q, tt, S);
+        codes |= sel_code(S) << (4 * v);
+        teno_gauss(S, gA, va, da);
+        teno_gauss(S, gB, vb, db);
+        T own = gp ? vb : va, got = __shfl_xor_sync(0xffffffffu, gp ? va : vb, 1);
+        L.W[v] = gp ? got : own;
+        R.W[v] = gp ? own : got;
+        own = (gp ? db : da) * iht;
+        got = __shfl_xor_sync(0xffffffffu, (gp ? da : db) * iht, 1);
+        L.Wt[v] = gp ? got : own;
+        R.Wt[v] = gp ? own : got;
+#pragma unroll
+        for (int s = 0; s < 5; ++s) q[s] = Lq[((2 * gp + 1) * 4 + v) * LP + lidx(a, fc, rc - 2 + s)];
+        teno_select(q, tt, S);
+        codes |= sel_code(S) << (4 * (4 + v));
+        teno_gauss(S, gA, va, da);
+        teno_gauss(S, gB, vb, db);
+        own = gp ? vb : va;
+        got = __shfl_xor_sync(0xffffffffu, gp ? va : vb, 1);
+        L.Wn[v] = gp ? got : own;
+        R.Wn[v] = gp ? own : got;
     }
     // positivity fallback, as the forward: the adjacent cell average, zero slopes
     const bool fbL = valid && !physical<T, 2>(L.W, fp.gm1);
@@ -221,8 +236,10 @@ __global__ void __launch_bounds__(128) k_adj_gauss(GridDev g, AdjDir a, FluxPara
             d1 -= a.lam1[b + (fc - 1) * a.sn];
             if (a.lam2) d2 -= a.lam2[b + (fc - 1) * a.sn];
         }
-        gF[v] = (T)(0.5 * (a.cF1 * d1 + a.cF2 * d2));
-        gdF[v] = (T)(0.5 * (a.cD1 * d1 + a.cD2 * d2));
+        // the differences in float64, the rest in the working precision
+        const T e1 = (T)d1, e2 = (T)d2;
+        gF[v] = T(0.5) * ((T)a.cF1 * e1 + (T)a.cF2 * e2);
+        gdF[v] = T(0.5) * ((T)a.cD1 * e1 + (T)a.cD2 * e2);
     }
     Side<T> gL, gR;
 #pragma unroll
@@ -253,8 +270,7 @@ __global__ void __launch_bounds__(128) k_adj_gauss(GridDev g, AdjDir a, FluxPara
         oWt[v] = __shfl_xor_sync(0xffffffffu, other.Wt[v], 1);
     }
     if (!valid) return;
-    const unsigned long long pcodes = codes;  // both lanes computed the same selections
-    const T gm = T(-0.28867513459481288), gpl = T(0.28867513459481288);
+    const T gm = gA, gpl = gB;
     T* C = static_cast<T*>(a.contrib);
 #pragma unroll 1
     for (int kk = 0; kk < 2; ++kk) {
@@ -263,7 +279,7 @@ __global__ void __launch_bounds__(128) k_adj_gauss(GridDev g, AdjDir a, FluxPara
         for (int v = 0; v < 4; ++v) {
             const int qi = k * 4 + v;
             TenoSel<T> S;
-            sel_decode((unsigned)(pcodes >> (4 * qi)) & 15u, S);
+            sel_decode((codes >> (4 * (kk * 4 + v))) & 15u, S);
             // cotangents at the - point and the + point
             T gvm, gdm, gvp, gdp;
             if (kk == 0) {
@@ -357,39 +373,39 @@ __global__ void __launch_bounds__(256) k_adj_gather(GridDev g, AdjDir a)
 
 // ---- transpose of the ghost fill: y ghost rows first (over the full ghosted
 // width), then the x ghost columns of the interior rows.  One thread per
-// column (row) walks its six ghost cells in a fixed order.
+// (column or row, variable) walks its six ghost cells in a fixed order.
 __global__ void k_fold_y(GridDev g, double* gW)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int gx = g.nx + 2 * NG;
-    if (i >= gx) return;
+    if (idx >= 4 * gx) return;
+    const int v = idx / gx, i = idx % gx;
+    double* P = gW + (long long)v * g.plane + i;
     for (int k = 0; k < 2 * NG; ++k) {
         const int j = k < NG ? k : g.ny + k;
         bool fn, fa;
         const int sj = ghost_src(g.bc[2 + (j >= NG + g.ny)], g.ny, j, fn, fa);
-        for (int v = 0; v < 4; ++v) {
-            const bool neg = (v == 2 && (fn || fa)) || (v == 1 && fa);
-            double* p = gW + (long long)v * g.plane + (long long)j * g.pitch + i;
-            gW[(long long)v * g.plane + (long long)sj * g.pitch + i] += neg ? -*p : *p;
-            *p = 0.0;
-        }
+        const bool neg = (v == 2 && (fn || fa)) || (v == 1 && fa);
+        const double x = P[(long long)j * g.pitch];
+        P[(long long)sj * g.pitch] += neg ? -x : x;
+        P[(long long)j * g.pitch] = 0.0;
     }
 }
 
 __global__ void k_fold_x(GridDev g, double* gW)
 {
-    const int j = NG + blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= NG + g.ny) return;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 4 * g.ny) return;
+    const int v = idx / g.ny, j = NG + idx % g.ny;
+    double* P = gW + (long long)v * g.plane + (long long)j * g.pitch;
     for (int k = 0; k < 2 * NG; ++k) {
         const int i = k < NG ? k : g.nx + k;
         bool fn, fa;
         const int si = ghost_src(g.bc[(i >= NG + g.nx)], g.nx, i, fn, fa);
-        for (int v = 0; v < 4; ++v) {
-            const bool neg = (v == 1 && (fn || fa)) || (v == 2 && fa);
-            double* p = gW + (long long)v * g.plane + (long long)j * g.pitch + i;
-            gW[(long long)v * g.plane + (long long)j * g.pitch + si] += neg ? -*p : *p;
-            *p = 0.0;
-        }
+        const bool neg = (v == 1 && (fn || fa)) || (v == 2 && fa);
+        const double x = P[i];
+        P[si] += neg ? -x : x;
+        P[i] = 0.0;
     }
 }
 
@@ -523,8 +539,8 @@ gks_status stage_vjp(gks_adjoint* A, bool stage2_input, const double* lam1, cons
         if (s) return s;
     }
     const GridDev& g = c->g;
-    k_fold_y<<<(g.nx + 2 * NG + 127) / 128, 128, 0, c->stream>>>(g, A->gacc);
-    k_fold_x<<<(g.ny + 127) / 128, 128, 0, c->stream>>>(g, A->gacc);
+    k_fold_y<<<(4 * (g.nx + 2 * NG) + 127) / 128, 128, 0, c->stream>>>(g, A->gacc);
+    k_fold_x<<<(4 * g.ny + 127) / 128, 128, 0, c->stream>>>(g, A->gacc);
     CK(cudaGetLastError());
     A->launches += 2;
     return GKS_OK;
