@@ -194,10 +194,11 @@ long long  gks_batch_launches(const gks_batch *b);
  * stencil selection of the forward pass held fixed, and of the ghost fill.
  * An adjoint object belongs to one context (2-D, tau_mode zero; otherwise
  * GKS_EUNSUPPORTED) and uses that context's state and stream.
- * checkpoint_every = k >= 1: the forward pass keeps W every k steps (device
- * memory: ceil(nsteps/k) + k + 8 state-sized arrays plus scratch of about
- * 116 x nx x ny values of the working precision); the backward pass
- * recomputes one k-step segment at a time. */
+ * checkpoint_every = k >= 1: the forward pass keeps W every k steps; the
+ * backward pass recomputes one k-step segment at a time, keeping W and W* of
+ * each of its steps (device memory: ceil(nsteps/k) + 2k + 6 state-sized
+ * arrays plus scratch of about 116 x nx x ny values of the working
+ * precision). */
 typedef struct gks_adjoint gks_adjoint;
 gks_status gks_adjoint_create(gks_ctx *ctx, int checkpoint_every, gks_adjoint **out);
 void       gks_adjoint_destroy(gks_adjoint *adj);

@@ -33,8 +33,8 @@
 // do not take, adds with atomics).
 //
 // Checkpointing: gks_adjoint_forward keeps W every k steps; the backward pass
-// recomputes each k-step segment from its checkpoint, keeping its states, and
-// runs the segment's adjoint steps in reverse.
+// recomputes each k-step segment from its checkpoint, stage by stage, keeping
+// W and W* of every step, and runs the segment's adjoint steps in reverse.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -433,6 +433,7 @@ struct gks_adjoint {
     bool have_forward = false;
     std::vector<double*> ckpt;   // W at steps 0, k, 2k, ... (ghosted)
     std::vector<double*> seg;    // W of the segment being reversed
+    std::vector<void*> segs;     // its W* (float32 on the float32 path), from the recomputation
     double* WN = nullptr;        // final state of the forward pass
     double *lam = nullptr, *lams = nullptr, *gacc = nullptr, *nxt = nullptr;
     void *lines = nullptr, *contrib = nullptr, *dcell = nullptr;
@@ -546,14 +547,22 @@ gks_status stage_vjp(gks_adjoint* A, bool stage2_input, const double* lam1, cons
     return GKS_OK;
 }
 
-// A->lam <- (dW^{n+1}/dW^n)^T A->lam at the ghosted state Wn
-gks_status adjoint_step(gks_adjoint* A, const double* Wn, double dt)
+size_t wstar_bytes(const gks_ctx* c)
+{
+    return (size_t)c->nv * c->g.plane * (c->Wsf ? sizeof(float) : sizeof(double));
+}
+
+// A->lam <- (dW^{n+1}/dW^n)^T A->lam at the ghosted state Wn with its stage
+// state Ws (as the forward pass computed it)
+gks_status adjoint_step(gks_adjoint* A, const double* Wn, const void* Ws)
 {
     gks_ctx* c = A->c;
+    const double dt = A->dt;
     gks_status s;
     if ((s = load_state(A, Wn))) return s;
-    // W* of this step (also fills the ghosts of W), then the ghosts of W*
-    if ((s = gks_stage(c, 1, dt))) return s;
+    void* ws = c->Wsf ? static_cast<void*>(c->Wsf) : static_cast<void*>(c->Ws);
+    CK(cudaMemcpyAsync(ws, Ws, wstar_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+    if ((s = rt::enqueue_ghosts(c, c->W, c->stream))) return s;
     if ((s = rt::enqueue_ghosts(c, c->Ws, c->stream))) return s;
     // lam* = [d dF/dW*]^T (dt^2/(3h) Delta lam)
     CK(cudaMemsetAsync(A->gacc, 0, c->arr_bytes, c->stream));
@@ -613,6 +622,7 @@ void gks_adjoint_destroy(gks_adjoint* A)
     if (!A) return;
     for (double* p : A->ckpt) cudaFree(p);
     for (double* p : A->seg) cudaFree(p);
+    for (void* p : A->segs) cudaFree(p);
     cudaFree(A->WN);
     cudaFree(A->lam);
     cudaFree(A->lams);
@@ -660,11 +670,14 @@ gks_status gks_adjoint_backward(gks_adjoint* A, const double* gWN, double* gW0, 
     gks_status s;
     while ((int)A->seg.size() < std::min(A->k, A->nsteps)) {
         double* p = nullptr;
-        if (cudaMalloc(&p, c->arr_bytes) != cudaSuccess) {
+        void* q = nullptr;
+        if (cudaMalloc(&p, c->arr_bytes) != cudaSuccess || cudaMalloc(&q, wstar_bytes(c)) != cudaSuccess) {
+            cudaFree(p);
             cudaGetLastError();
             return rt::fail(c, GKS_ENOMEM, "no device memory for a %d-step segment", A->k);
         }
         A->seg.push_back(p);
+        A->segs.push_back(q);
     }
     CK(cudaMemsetAsync(A->lam, 0, c->arr_bytes, c->stream));
     if ((s = rt::copy_interior(c, A->lam, gWN, on_device, true))) return s;
@@ -672,12 +685,17 @@ gks_status gks_adjoint_backward(gks_adjoint* A, const double* gWN, double* gW0, 
     for (int sgi = ncp - 1; sgi >= 0; --sgi) {
         const int n0 = sgi * A->k, n1 = std::min(n0 + A->k, A->nsteps);
         if ((s = load_state(A, A->ckpt[sgi]))) return s;
+        // recompute the segment stage by stage (the same kernels and W as the
+        // forward pass's steps), keeping W and W* of every step
+        const void* ws = c->Wsf ? static_cast<const void*>(c->Wsf) : static_cast<const void*>(c->Ws);
         for (int n = n0; n < n1; ++n) {
             CK(cudaMemcpyAsync(A->seg[n - n0], c->W, c->arr_bytes, cudaMemcpyDeviceToDevice, c->stream));
-            if (n + 1 < n1 && (s = gks_step(c, A->dt))) return s;
+            if ((s = gks_stage(c, 1, A->dt))) return s;
+            CK(cudaMemcpyAsync(A->segs[n - n0], ws, wstar_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+            if (n + 1 < n1 && (s = gks_stage(c, 2, A->dt))) return s;
         }
         for (int n = n1 - 1; n >= n0; --n)
-            if ((s = adjoint_step(A, A->seg[n - n0], A->dt))) return s;
+            if ((s = adjoint_step(A, A->seg[n - n0], A->segs[n - n0]))) return s;
     }
     if ((s = rt::copy_interior(c, A->lam, gW0, on_device, false))) return s;
     // leave the context at the forward pass's final state

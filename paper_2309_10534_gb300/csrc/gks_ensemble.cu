@@ -103,12 +103,16 @@ __device__ void stage_chunk(ChunkSmem<T, NT>& sm, double* W, T* Ws, T* A, long l
     const int tid = threadIdx.x;
     const int slot[3] = {0, 1, 3};
     __syncthreads();  // shared memory of the previous chunk is free
+    // each variable's array through its own base pointer; cell offsets in 32 bits
+    double* Wv[3] = {W, W + vstride, W + 2 * vstride};
+    T* Wsv[3] = {Ws, Ws + vstride, Ws + 2 * vstride};
+    T* Av[3] = {A, A + vstride, A + 2 * vstride};
     for (int k = tid; k < 3 * (TN + 6); k += NT) {
         const int v = k / (TN + 6), c = k % (TN + 6);
         int i = c0 - 3 + c;
         i = i < 0 ? 0 : (i >= n ? n - 1 : i);
-        const long long gi = (long long)v * vstride + i;
-        sm.q[v][c] = stage == 1 ? (T)W[gi] : Ws[gi];
+        if (stage == 1) sm.q[v][c] = (T)(v == 0 ? W : (v == 1 ? Wv[1] : Wv[2]))[i];
+        else sm.q[v][c] = (v == 0 ? Ws : (v == 1 ? Wsv[1] : Wsv[2]))[i];
     }
     __syncthreads();
     const T ih = (T)idx;
@@ -167,36 +171,32 @@ __device__ void stage_chunk(ChunkSmem<T, NT>& sm, double* W, T* Ws, T* A, long l
             if (stage == 1) {
 #pragma unroll
                 for (int v = 0; v < 3; ++v) {
-                    const long long gi = (long long)v * vstride + i;
-                    Ws[gi] = wstar32(sm.q[v][c + 3], cxt, sm.G[0][v][c + 1] - sm.G[0][v][c]);
-                    A[gi] = cxt * (sm.G[1][v][c + 1] - sm.G[1][v][c]);
+                    Wsv[v][i] = wstar32(sm.q[v][c + 3], cxt, sm.G[0][v][c + 1] - sm.G[0][v][c]);
+                    Av[v][i] = cxt * (sm.G[1][v][c + 1] - sm.G[1][v][c]);
                 }
             } else {
                 T w[3];
 #pragma unroll
                 for (int v = 0; v < 3; ++v) {
-                    const long long gi = (long long)v * vstride + i;
-                    const double r = wnew32(W[gi], A[gi], cxt, sm.G[0][v][c + 1] - sm.G[0][v][c]);
-                    W[gi] = r;
+                    const double r = wnew32(Wv[v][i], Av[v][i], cxt, sm.G[0][v][c + 1] - sm.G[0][v][c]);
+                    Wv[v][i] = r;
                     w[v] = (T)r;
                 }
-                sig = fmax(sig, cell_sigma1<T>(w[0], w[1], w[2], gamma, mu, hcell, err));
+                sig = fmax(sig, cell_sigma<T, T>(w, 1, gamma, mu, hcell, err));
             }
         } else if (stage == 1) {
 #pragma unroll
             for (int v = 0; v < 3; ++v) {
-                const long long gi = (long long)v * vstride + i;
-                const double w = W[gi];
-                Ws[gi] = upd64(w, cx, (double)(sm.G[0][v][c + 1] - sm.G[0][v][c]));
-                A[gi] = upd64(w, cx, (double)(sm.G[1][v][c + 1] - sm.G[1][v][c]));
+                const double w = Wv[v][i];
+                Wsv[v][i] = upd64(w, cx, (double)(sm.G[0][v][c + 1] - sm.G[0][v][c]));
+                Av[v][i] = upd64(w, cx, (double)(sm.G[1][v][c + 1] - sm.G[1][v][c]));
             }
         } else {
             double w[3];
 #pragma unroll
             for (int v = 0; v < 3; ++v) {
-                const long long gi = (long long)v * vstride + i;
-                w[v] = upd64(A[gi], cx, (double)(sm.G[0][v][c + 1] - sm.G[0][v][c]));
-                W[gi] = w[v];
+                w[v] = upd64(Av[v][i], cx, (double)(sm.G[0][v][c + 1] - sm.G[0][v][c]));
+                Wv[v][i] = w[v];
             }
             sig = fmax(sig, cell_sigma<T>(w, 1, gamma, mu, hcell, err));
         }
@@ -232,8 +232,10 @@ __global__ void __launch_bounds__(NT) k_batch(BatchDev b, FluxParams<T> fp, Teno
         unsigned int err = 0, nfb = 0;
         // CFL rate of the starting state
         T sig = T(0);
-        for (int i = tid; i < n; i += NT)
-            sig = fmax(sig, cell_sigma1<T>((T)W[i], (T)W[b.total + i], (T)W[2 * b.total + i], gamma, mu, hcell, err));
+        for (int i = tid; i < n; i += NT) {
+            const T w0[3] = {(T)W[i], (T)W[b.total + i], (T)W[2 * b.total + i]};
+            sig = fmax(sig, cell_sigma<T, T>(w0, 1, gamma, mu, hcell, err));
+        }
         sig = block_max<T, NT>(sig, red);
         err = block_or(err, redu);
         while (t < b.t_end && (b.max_steps <= 0 || steps < b.max_steps) && !err) {

@@ -65,8 +65,8 @@ __device__ __forceinline__ int ghost_src(int bc, int n, int g, bool& flip_n, boo
 // sigma = max((|U| + a)/h, 4 nu / h^2), dt = cfl / sigma  (Sec. 5), in the
 // kernel's arithmetic type (the float32 path takes its time step in float32;
 // only the state and its accumulation are float64)
-template <typename T>
-__device__ __forceinline__ T cell_sigma(const double* w, int dim, T gamma, T mu, T h, unsigned int& err)
+template <typename T, typename WT = double>
+__device__ __forceinline__ T cell_sigma(const WT* w, int dim, T gamma, T mu, T h, unsigned int& err)
 {
     const T r = (T)w[0], ir = T(1) / r;
     const T U = (T)w[1] * ir, V = (dim == 2) ? (T)w[2] * ir : T(0);
@@ -157,23 +157,6 @@ struct Stage1DArgs {
     double idx;          // 1 / dx
 };
 
-// CFL rate of one 1-D cell from its working-precision values (the same
-// expression as cell_sigma with V = 0, so both give the same bits)
-template <typename T>
-__device__ __forceinline__ T cell_sigma1(T w0, T w1, T w2, T gamma, T mu, T h, unsigned int& err)
-{
-    const T r = w0, ir = T(1) / r;
-    const T U = w1 * ir, V = T(0);
-    const T E = w2;
-    const T p = (gamma - T(1)) * (E - T(0.5) * r * (U * U + V * V));
-    if (!(r > T(0) && p > T(0) && isfinite(p))) err |= 1u;
-    const T a = sqrt(gamma * p * ir);
-    const T ih = T(1) / h;
-    T s = (sqrt(U * U + V * V) + a) * ih;
-    if (mu > T(0)) s = fmax(s, T(4) * mu * ir * ih * ih);
-    return s;
-}
-
 template <typename T, bool NONEQ, bool PRFIX, int TN>
 __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, FluxParams<T> fp, TenoT<T> tn,
                                                     DevState* ds)
@@ -190,16 +173,17 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
     const int gx = g.nx + 2 * NG;
     const int slot[3] = {0, 1, 3};
 
+    const int pl = (int)g.plane;  // a 1-D plane is one ghosted row
     for (int k = tid; k < 3 * (TN + 6); k += NT) {
         const int v = k / (TN + 6), c = k % (TN + 6);
         const int gi = i0 + c;  // ghosted index of cell i0 - 3 + c
         T val = T(0);
         if (gi < gx) {
             if constexpr (sizeof(T) == 4) {
-                if (a.stage == 2) val = a.srcf[(long long)v * g.plane + gi];
-                else val = (T)a.src[(long long)v * g.plane + gi];
+                if (a.stage == 2) val = a.srcf[v * pl + gi];
+                else val = (T)a.src[v * pl + gi];
             } else {
-                val = a.src[(long long)v * g.plane + gi];
+                val = a.src[v * pl + gi];
             }
         }
         sq[v][c] = val;
@@ -262,39 +246,38 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
     for (int c = tid; c < TN; c += NT) {
         const int i = i0 + c;
         if (i >= g.nx) continue;
-        const long long o = i + NG;
+        const int o = i + NG;
         if constexpr (sizeof(T) == 4) {
             if (a.stage == 1) {
 #pragma unroll
                 for (int v = 0; v < 3; ++v) {
-                    a.out0f[(long long)v * g.plane + o] = wstar32(sq[v][c + 3], cxt, sG[0][v][c + 1] - sG[0][v][c]);
-                    a.out1f[(long long)v * g.plane + o] = cxt * (sG[1][v][c + 1] - sG[1][v][c]);
+                    a.out0f[v * pl + o] = wstar32(sq[v][c + 3], cxt, sG[0][v][c + 1] - sG[0][v][c]);
+                    a.out1f[v * pl + o] = cxt * (sG[1][v][c + 1] - sG[1][v][c]);
                 }
             } else {
                 T w[3];
 #pragma unroll
                 for (int v = 0; v < 3; ++v) {
-                    const long long gi = (long long)v * g.plane + o;
+                    const int gi = v * pl + o;
                     const double r = wnew32(a.base[gi], a.accf[gi], cxt, sG[0][v][c + 1] - sG[0][v][c]);
                     a.out0[gi] = r;
                     w[v] = (T)r;
                 }
-                if (a.with_sigma)
-                    sig = fmax(sig, cell_sigma1<T>(w[0], w[1], w[2], (T)g.gamma, (T)g.mu, (T)g.dx, err));
+                if (a.with_sigma) sig = fmax(sig, cell_sigma<T, T>(w, 1, (T)g.gamma, (T)g.mu, (T)g.dx, err));
             }
         } else if (a.stage == 1) {
 #pragma unroll
             for (int v = 0; v < 3; ++v) {
-                const double w = a.src[(long long)v * g.plane + o];
-                a.out0[(long long)v * g.plane + o] = upd64(w, cx, (double)(sG[0][v][c + 1] - sG[0][v][c]));
-                a.out1[(long long)v * g.plane + o] = upd64(w, cx, (double)(sG[1][v][c + 1] - sG[1][v][c]));
+                const double w = a.src[v * pl + o];
+                a.out0[v * pl + o] = upd64(w, cx, (double)(sG[0][v][c + 1] - sG[0][v][c]));
+                a.out1[v * pl + o] = upd64(w, cx, (double)(sG[1][v][c + 1] - sG[1][v][c]));
             }
         } else {
             double w[4];
 #pragma unroll
             for (int v = 0; v < 3; ++v) {
-                const double r = upd64(a.acc[(long long)v * g.plane + o], cx, (double)(sG[0][v][c + 1] - sG[0][v][c]));
-                a.out0[(long long)v * g.plane + o] = r;
+                const double r = upd64(a.acc[v * pl + o], cx, (double)(sG[0][v][c + 1] - sG[0][v][c]));
+                a.out0[v * pl + o] = r;
                 w[v] = r;
             }
             if (a.with_sigma) sig = fmax(sig, cell_sigma<T>(w, 1, (T)g.gamma, (T)g.mu, (T)g.dx, err));
@@ -367,7 +350,12 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
     const int n0 = blockIdx.x * TN, t0 = blockIdx.y * TT;
     // local frame: normal momentum first; y faces swap the two momentum components
     const bool swap = a.dirn != 0;
-    const long long org = (long long)NG * g.pitch + NG;  // interior (0,0)
+    // offsets within one variable plane fit in 32 bits; each variable's plane
+    // is reached through its own base pointer
+    const int org = NG * g.pitch + NG;  // interior (0,0)
+    const int sn = (int)a.sn, st = (int)a.st;
+    const long long pv1 = (long long)gvar(1, swap) * g.plane, pv2 = (long long)gvar(2, swap) * g.plane;
+    const long long pv3 = 3 * g.plane;
 
     // load cells (normal n0-3 .. n0+TN+2, tangential t0-2 .. t0+TT+1); the
     // thread index runs fastest along the unit-stride direction
@@ -380,9 +368,10 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
             const int in = n0 - 3 + cn, it = t0 - 2 + ct;
             T val = T(0);
             if (in < a.nn + 3 && it < a.nt + 2) {  // ghosted extent (negative side is covered by ghosts)
-                const long long gi = (long long)gvar(v, swap) * g.plane + org + in * a.sn + it * a.st;
-                if constexpr (sizeof(T) == 4) val = a.srcf[gi];
-                else val = a.src[gi];
+                const long long pv = v == 0 ? 0 : (v == 1 ? pv1 : (v == 2 ? pv2 : pv3));
+                const int off = org + in * sn + it * st;
+                if constexpr (sizeof(T) == 4) val = (a.srcf + pv)[off];
+                else val = (a.src + pv)[off];
             }
             sm.w[v][ct][cn] = val;
         }
@@ -494,13 +483,14 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
         const int r = fy ? tid % TT : tid / TN, c = fy ? tid / TT : tid % TN;
         const int in = n0 + c, it = t0 + r;
         if (in < a.nn && it < a.nt) {
-            const long long o = org + in * a.sn + it * a.st;
+            const int o = org + in * sn + it * st;
             T* inc0 = static_cast<T*>(a.inc0);
             T* inc1 = static_cast<T*>(a.inc1);
             double wn[4];
+            T wf[4];
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                const long long go = (long long)gvar(v, swap) * g.plane + o;
+                const long long go = (v == 0 ? 0 : (v == 1 ? pv1 : (v == 2 ? pv2 : pv3))) + o;
                 const T d0 = cn * (sF[sfi(v, r, c + 1)] - sF[sfi(v, r, c)]);
                 const T d1 = (a.stage == 1)
                            ? cn * (sF[sfi(4 + v, r, c + 1)] - sF[sfi(4 + v, r, c)])
@@ -515,8 +505,8 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
                     } else {
                         const double res = a.base[go] - (double)(inc1[go] + inc0[go] + d0);
                         a.out0[go] = res;
-                        a.out0f[go] = (float)res;
-                        wn[v] = res;  // local order; the CFL rate only needs |U|
+                        wf[v] = (float)res;  // local order; the CFL rate only needs |U|
+                        a.out0f[go] = wf[v];
                     }
                 } else if (a.stage == 1) {
                     const double w = a.base[go];
@@ -528,7 +518,10 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
                     wn[v] = res;  // local order; the CFL rate only needs |U|
                 }
             }
-            if (a.with_sigma) sig = cell_sigma<T>(wn, 2, (T)g.gamma, (T)g.mu, (T)a.hmin, err);
+            if (a.with_sigma) {
+                if constexpr (sizeof(T) == 4) sig = cell_sigma<T, T>(wf, 2, (T)g.gamma, (T)g.mu, (T)a.hmin, err);
+                else sig = cell_sigma<T>(wn, 2, (T)g.gamma, (T)g.mu, (T)a.hmin, err);
+            }
         }
     }
     block_commit<NT, T>(sig, a.with_sigma != 0, err, nfb, ds);
