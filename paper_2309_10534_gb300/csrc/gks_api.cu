@@ -9,6 +9,7 @@
 // the host reads the completion flag once per replay.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -26,7 +27,26 @@ using namespace gks;
 
 namespace {
 constexpr int GRAPH_STEPS = 8;
+
+// interior [nv][ny][nx] <-> ghosted layout (1-D: ny = 1, no ghost rows)
+__device__ __forceinline__ long long ghosted_index(const GridDev& g, long long k)
+{
+    const int ny = (g.dim == 2) ? g.ny : 1;
+    const long long per_v = (long long)g.nx * ny;
+    const int v = (int)(k / per_v);
+    const long long r = k - v * per_v;
+    const int j = (int)(r / g.nx), i = (int)(r - (long long)j * g.nx);
+    return (long long)v * g.plane + (long long)((g.dim == 2 ? NG : 0) + j) * g.pitch + NG + i;
 }
+__global__ void k_unpack(GridDev g, const double* __restrict__ src, double* __restrict__ arr, long long n)
+{
+    for (long long k = blockIdx.x * 256ll + threadIdx.x; k < n; k += 256ll * gridDim.x) arr[ghosted_index(g, k)] = src[k];
+}
+__global__ void k_pack(GridDev g, const double* __restrict__ arr, double* __restrict__ dst, long long n)
+{
+    for (long long k = blockIdx.x * 256ll + threadIdx.x; k < n; k += 256ll * gridDim.x) dst[k] = arr[ghosted_index(g, k)];
+}
+}  // namespace
 
 
 namespace gks {
@@ -318,20 +338,26 @@ namespace rt {
 
 gks_status copy_interior(gks_ctx* c, double* arr, const double* W, int on_device, bool in)
 {
-    const int nx = c->desc.nx, ny = (c->desc.dim == 2) ? c->desc.ny : 1;
-    const size_t spitch = (size_t)nx * sizeof(double), dpitch = (size_t)c->g.pitch * sizeof(double);
-    const long long row0 = (c->desc.dim == 2) ? NG : 0;
-    for (int v = 0; v < c->nv; ++v) {
-        double* dev = arr + (long long)v * c->g.plane + row0 * c->g.pitch + NG;
-        const double* hostv = W + (size_t)v * nx * ny;
-        if (in) {
-            CK(cudaMemcpy2DAsync(dev, dpitch, hostv, spitch, spitch, ny,
-                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-        } else {
-            CK(cudaMemcpy2DAsync((double*)hostv, spitch, dev, dpitch, spitch, ny,
-                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
-        }
+    // A caller's array [nv][ny][nx] is moved in one contiguous copy (host
+    // arrays through a device staging buffer) and scattered into / gathered
+    // from the ghosted layout by a kernel: one large transfer runs at the
+    // link's rate, where a pitched copy of short rows does not.
+    const long long n = (long long)c->nv * c->desc.nx * ((c->desc.dim == 2) ? c->desc.ny : 1);
+    const double* src = W;
+    double* dst = const_cast<double*>(W);
+    if (!on_device) {
+        if (!c->stage) CK(cudaMalloc(&c->stage, sizeof(double) * (size_t)n));
+        src = dst = c->stage;
+        if (in) CK(cudaMemcpyAsync(c->stage, W, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
     }
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 8192);
+    if (in) k_unpack<<<blocks, 256, 0, c->stream>>>(c->g, src, arr, n);
+    else k_pack<<<blocks, 256, 0, c->stream>>>(c->g, arr, dst, n);
+    CK(cudaGetLastError());
+    ++c->launches;
+    if (!on_device && !in)
+        CK(cudaMemcpyAsync(const_cast<double*>(W), c->stage, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost,
+                           c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return GKS_OK;
 }
@@ -511,6 +537,7 @@ void gks_destroy(gks_ctx* c)
     cudaFree(c->inc1);
     cudaFree(c->Wf);
     cudaFree(c->Wsf);
+    cudaFree(c->stage);
     cudaFree(c->ds);
     if (c->hs) cudaFreeHost(c->hs);
     delete c;

@@ -22,6 +22,7 @@ struct gks_ctx {
                                              // 1-D float32: inc1 = accumulator increment
     float* Wf = nullptr;                     // float32 shadow of W (2-D float32 path)
     float* Wsf = nullptr;                    // W* in float32 (float32 path)
+    double* stage = nullptr;                 // device staging of host arrays (allocated on first use)
     size_t arr_bytes = 0;
     gks::DevState* ds = nullptr;      // device
     gks::DevState* hs = nullptr;      // pinned host mirror
