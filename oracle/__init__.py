@@ -38,16 +38,19 @@ class Problem(C.Structure):
         ("eps", C.c_double), ("qpow", C.c_double),
         ("ct1", C.c_double), ("ct2", C.c_double), ("ct1_t", C.c_double), ("ct2_t", C.c_double),
         ("positivity_fallback", C.c_int),
+        ("recon", C.c_int), ("d_hi", C.c_double), ("d_lo", C.c_double), ("eps_ao", C.c_double),
     ]
 
 
 BC = {"periodic": 0, "zerograd": 1, "symmetry": 2, "noslip": 3, "reflect": 4}
 TAU = {"zero": 0, "euler": 1, "ns": 2}
+RECON = {"teno_d": 0, "weno_ao": 1}
 
 
 def make_problem(dim, nx, ny=1, *, lx=1.0, ly=1.0, bc=("zerograd",) * 4, gamma=1.4, mu=0.0, Pr=1.0,
                  tau="euler", c1=0.01, c2=1.0, cfl=0.5, eps=1e-40, q=7.0, ct1=1e-7, ct2=1e-5,
-                 ct1_t=None, ct2_t=None, positivity_fallback=1) -> Problem:
+                 ct1_t=None, ct2_t=None, positivity_fallback=1, recon="teno_d", d_hi=0.85, d_lo=0.85,
+                 eps_ao=1e-8) -> Problem:
     p = Problem()
     p.dim, p.nx, p.ny = dim, nx, (ny if dim == 2 else 1)
     p.dx = lx / nx
@@ -62,6 +65,8 @@ def make_problem(dim, nx, ny=1, *, lx=1.0, ly=1.0, bc=("zerograd",) * 4, gamma=1
     p.ct1_t = ct1 if ct1_t is None else ct1_t
     p.ct2_t = ct2 if ct2_t is None else ct2_t
     p.positivity_fallback = positivity_fallback
+    p.recon = RECON[recon] if isinstance(recon, str) else int(recon)
+    p.d_hi, p.d_lo, p.eps_ao = d_hi, d_lo, eps_ao
     return p
 
 
@@ -82,6 +87,8 @@ def _declare(L):
     L.or_teno_d.argtypes = [_dp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, _dp, _dp,
                             _dp, _ip]
     L.or_teno_d.restype = C.c_int
+    L.or_weno_ao.argtypes = [_dp, C.c_double, C.c_double, C.c_double, C.c_int, _dp, _dp, _dp, _dp]
+    L.or_weno_ao.restype = None
     L.or_moments_u.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int, _dp]
     L.or_moments_u.restype = None
     L.or_micro_slope.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, _dp, _dp]
@@ -145,6 +152,17 @@ def teno_d(q5, xs, eps=1e-40, q=7.0, ct1=1e-7, ct2=1e-5):
     large = lib().or_teno_d(_d(q5), eps, q, ct1, ct2, len(xs), _d(xs), _d(val), _d(dval),
                             sel.ctypes.data_as(_ip))
     return val, dval, bool(large), sel
+
+
+def weno_ao(q5, xs, eps=1e-8, d_hi=0.85, d_lo=0.85):
+    """WENO5-AO of Sec. 3.2 on five cell averages; returns (val, dval, wbar[4])."""
+    q5 = _f64(q5)
+    xs = _f64(np.atleast_1d(xs))
+    val = np.zeros(len(xs))
+    dval = np.zeros(len(xs))
+    wbar = np.zeros(4)
+    lib().or_weno_ao(_d(q5), eps, d_hi, d_lo, len(xs), _d(xs), _d(val), _d(dval), _d(wbar))
+    return val, dval, wbar
 
 
 def moments_u(U, lam, half=0, nmax=6):

@@ -52,6 +52,11 @@
  *   R14 positivity fallback (not in the paper): a reconstructed point state
  *       with rho <= 0 or p <= 0 is replaced by the adjacent cell average with
  *       zero slopes on that side.  Counted.
+ *   R23 WENO5-AO linear weights gamma_3 = d_Hi, gamma_1 = (1-d_Hi) d_Lo,
+ *       gamma_0 = gamma_2 = (1-d_Hi)(1-d_Lo)/2 (the printed indices are
+ *       garbled), d_Hi = d_Lo = 0.85, tau's third term with beta_2.
+ *   R24 WENO5-AO weights with the squared ratio (tau/(beta_k+eps))^2; the
+ *       2-D WENO-AO accuracy table is reproduced only with it.
  */
 #include "gks_oracle.h"
 
@@ -238,6 +243,70 @@ int or_teno_d(const double *q5, double eps, double qpow, double ct1, double ct2,
         dval[e] = dv;
     }
     return 0;
+}
+
+/* WENO5-AO, Sec. 3.2.  The sub-stencil quadratics and the large-stencil
+ * quartic are the same fitted polynomials as for TENO-D; beta by Eq. (3.7).
+ * Linear weights: gamma_3 = d_Hi, gamma_1 = (1 - d_Hi) d_Lo,
+ * gamma_0 = gamma_2 = (1 - d_Hi)(1 - d_Lo)/2 (reading R23); global indicator
+ * tau = (|beta_3 - beta_0| + |beta_3 - beta_1| + |beta_3 - beta_2|)/3;
+ * omega_k = gamma_k (1 + (tau/(beta_k + eps))^2) (reading R24: the squared
+ * ratio of the adaptive-order weights; with it the 2-D WENO-AO accuracy table
+ * is reproduced to 4e-6, with the first power of Eq. (3.5) only to 3 %),
+ * normalised over the four stencils; the AO(5,3) polynomial is
+ *   P = wbar_3 (p_3/gamma_3 - sum_k gamma_k/gamma_3 p_k) + sum_k wbar_k p_k. */
+void or_weno_ao(const double *q5, double eps, double d_hi, double d_lo, int n, const double *xs,
+                double *val, double *dval, double *wbar)
+{
+    init_fits();
+    double c3[3][3], c5[5], beta[4], d5[5];
+    const double qc = q5[2];
+    for (int s = 0; s < 5; ++s) d5[s] = q5[s] - qc;
+    for (int k = 0; k < 3; ++k) {
+        apply_fit(3, FIT3[k], d5 + k, c3[k]);
+        beta[k] = or_beta(2, c3[k]);
+        c3[k][0] += qc;
+    }
+    apply_fit(5, FIT5, d5, c5);
+    beta[3] = or_beta(4, c5);
+    c5[0] += qc;
+    double g[4];
+    g[3] = d_hi;
+    g[1] = (1.0 - d_hi) * d_lo;
+    g[0] = g[2] = 0.5 * (1.0 - d_hi) * (1.0 - d_lo);
+    const double tau = (fabs(beta[3] - beta[0]) + fabs(beta[3] - beta[1]) + fabs(beta[3] - beta[2])) / 3.0;
+    double w[4], sum = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        const double r = tau / (beta[k] + eps);
+        w[k] = g[k] * (1.0 + r * r);
+        sum += w[k];
+    }
+    for (int k = 0; k < 4; ++k) w[k] /= sum;
+    if (wbar)
+        for (int k = 0; k < 4; ++k) wbar[k] = w[k];
+    for (int e = 0; e < n; ++e) {
+        double v = w[3] / g[3] * or_poly_eval(4, c5, xs[e]);
+        double dv = w[3] / g[3] * or_poly_deriv(4, c5, xs[e]);
+        for (int k = 0; k < 3; ++k) {
+            const double a = w[k] - w[3] * g[k] / g[3];
+            v += a * or_poly_eval(2, c3[k], xs[e]);
+            dv += a * or_poly_deriv(2, c3[k], xs[e]);
+        }
+        val[e] = v;
+        dval[e] = dv;
+    }
+}
+
+/* the scheme's 5-cell reconstruction (TENO-D or WENO5-AO) at the points xs */
+static void recon5(const or_problem *P, const double *q5, int tangential, int n, const double *xs, double *val,
+                   double *dval)
+{
+    if (P->recon == OR_RECON_WENO_AO) {
+        or_weno_ao(q5, P->eps_ao, P->d_hi, P->d_lo, n, xs, val, dval, NULL);
+        return;
+    }
+    or_teno_d(q5, P->eps, P->qpow, tangential ? P->ct1_t : P->ct1, tangential ? P->ct2_t : P->ct2, n, xs, val, dval,
+              NULL);
 }
 
 /* ------------------------------------------------------------------ */
@@ -721,9 +790,9 @@ static int face_flux(const or_problem *P, const grid_t *g, const double *Wg, int
                 }
             }
             double val, dval;
-            or_teno_d(ql, P->eps, P->qpow, P->ct1, P->ct2, 1, &xl, &val, &dval, NULL);
+            recon5(P, ql, 0, 1, &xl, &val, &dval);
             lv[r][v] = val; lx[r][v] = dval / hn;
-            or_teno_d(qr, P->eps, P->qpow, P->ct1, P->ct2, 1, &xr, &val, &dval, NULL);
+            recon5(P, qr, 0, 1, &xr, &val, &dval);
             rv[r][v] = val; rx[r][v] = dval / hn;
         }
     }
@@ -751,16 +820,16 @@ static int face_flux(const or_problem *P, const grid_t *g, const double *Wg, int
     for (int v = 0; v < nv; ++v) {
         double q[5], val[2], dval[2];
         for (int r = 0; r < 5; ++r) q[r] = lv[r][v];
-        or_teno_d(q, P->eps, P->qpow, P->ct1_t, P->ct2_t, 2, xg, val, dval, NULL);
+        recon5(P, q, 1, 2, xg, val, dval);
         for (int m = 0; m < 2; ++m) { Wl[m][v] = val[m]; Wlt[m][v] = dval[m] / ht; }
         for (int r = 0; r < 5; ++r) q[r] = lx[r][v];
-        or_teno_d(q, P->eps, P->qpow, P->ct1_t, P->ct2_t, 2, xg, val, dval, NULL);
+        recon5(P, q, 1, 2, xg, val, dval);
         for (int m = 0; m < 2; ++m) Wln[m][v] = val[m];
         for (int r = 0; r < 5; ++r) q[r] = rv[r][v];
-        or_teno_d(q, P->eps, P->qpow, P->ct1_t, P->ct2_t, 2, xg, val, dval, NULL);
+        recon5(P, q, 1, 2, xg, val, dval);
         for (int m = 0; m < 2; ++m) { Wr[m][v] = val[m]; Wrt[m][v] = dval[m] / ht; }
         for (int r = 0; r < 5; ++r) q[r] = rx[r][v];
-        or_teno_d(q, P->eps, P->qpow, P->ct1_t, P->ct2_t, 2, xg, val, dval, NULL);
+        recon5(P, q, 1, 2, xg, val, dval);
         for (int m = 0; m < 2; ++m) Wrn[m][v] = val[m];
     }
     /* step 3: merge + flux at each Gauss point, average with weights 1/2 */

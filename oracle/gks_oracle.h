@@ -13,6 +13,8 @@
  *   Sec. 3.2  derivatives on the stencils, kinetic merge Eqs. (3.25)-(3.26),
  *             2-D dimension-by-dimension steps
  *   Sec. 4.2  TENO-D selection Eqs. (4.5)-(4.14)
+ *   Sec. 3.2  WENO5-AO weights and AO(5,3) polynomial (the alternative
+ *             reconstruction the paper compares against)
  *   Sec. 5    collision time, CFL time step
  * Readings of garbled or silent passages are listed in the .c file header.
  */
@@ -44,7 +46,12 @@ typedef struct {
     double ct1, ct2;      /* thresholds C_T1, C_T2, normal direction */
     double ct1_t, ct2_t;  /* thresholds used in the tangential direction */
     int positivity_fallback; /* 1: first-order state when rho<=0 or p<=0 at a point */
+    int recon;            /* OR_RECON_*: TENO-D (Sec. 4.2) or WENO5-AO (Sec. 3.2) */
+    double d_hi, d_lo;    /* WENO5-AO linear-weight parameters d_Hi, d_Lo */
+    double eps_ao;        /* WENO5-AO epsilon of Eq. (3.5) */
 } or_problem;
+
+enum { OR_RECON_TENO_D = 0, OR_RECON_WENO_AO = 1 };
 
 /* ---- reconstruction primitives (Sec. 3.1, 3.2, 4.2) ---- */
 /* n x n matrix (row-major) mapping cell averages at integer offsets to the
@@ -57,6 +64,13 @@ double or_beta(int deg, const double *c);
 /* TENO-D on the 5 cell averages q[0..4] = Qbar_{i-2..i+2}; evaluates the
  * selected reconstruction and its xi-derivative at the points xs[0..n-1].
  * Returns delta_{3,1}; sel[0..2] receives delta_{k,2} (0 when large). */
+/* WENO5-AO (Sec. 3.2) on the 5 cell averages: WENO-Z-type weights of Eq.
+ * (3.5) on the large stencil and the three sub-stencils with the linear
+ * weights of d_Hi, d_Lo, evaluated with the AO(5,3) polynomial and its
+ * xi-derivative at xs[0..n-1]; wbar[0..3] (may be NULL) receives the
+ * normalised weights of S0, S1, S2, S3. */
+void   or_weno_ao(const double *q5, double eps, double d_hi, double d_lo, int n, const double *xs,
+                  double *val, double *dval, double *wbar);
 int    or_teno_d(const double *q5, double eps, double qpow, double ct1, double ct2,
                  int n, const double *xs, double *val, double *dval, int *sel);
 

@@ -215,3 +215,41 @@ def test_full_size_ensemble_to_t_end_fp32(gks, full):
         e_ora += np.abs(Wo[0] - ex[0]).mean()
     print(f"distance to exact over {len(picked)} problems: {e_gpu:.6e} (oracle {e_ora:.6e})")
     assert e_gpu == pytest.approx(e_ora, rel=1e-1)
+
+
+@pytest.mark.parametrize("threads", [128, 256])
+def test_batch_ragged_sizes_and_chunk_edges(gks, threads):
+    """Problem sizes at the chunk boundaries of both block sizes (a chunk is
+    threads - 6 cells: 122 and 250), the 3-cell minimum and one problem
+    larger than any in the workload, each equal to the single-grid path
+    (float64, 1e-13) after 5 steps in one launch."""
+    sizes = [3, 4, 121, 122, 123, 244, 245, 249, 250, 251, 500, 501, 5003]
+    rng = np.random.default_rng(17)
+    Ws = []
+    for n in sizes:
+        left = (float(np.exp(rng.uniform(-1, 1))), float(rng.uniform(-0.5, 0.5)), float(np.exp(rng.uniform(-1, 1))))
+        right = (float(np.exp(rng.uniform(-1, 1))), float(rng.uniform(-0.5, 0.5)), float(np.exp(rng.uniform(-1, 1))))
+        Ws.append(WL._riemann_1d(n, left, right, 0.5, 1.4))
+    B = gks.Batch(np.array(sizes), np.ones(len(sizes)), precision="fp64")
+    B.set_launch(threads, 2)
+    B.set_state(np.concatenate(Ws, axis=1))
+    B.advance_to(1.0, max_steps=5)
+    out = B.get_state()
+    _, steps, err, _ = B.progress()
+    assert np.all(steps == 5) and np.all(err == 0)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for k, n in enumerate(sizes):
+        S = gks.Solver(1, n, precision="fp64", tau="euler")
+        S.set_state(Ws[k][:, None, :])
+        S.advance_to(1.0, max_steps=5)
+        assert _rel(out[:, off[k]:off[k + 1]], S.get_state()[:, 0, :]) < 1e-13, n
+
+
+def test_batch_rejects_bad_descriptors(gks):
+    with pytest.raises(gks.GKSError):
+        gks.Batch(np.array([2]), np.ones(1))          # fewer than 3 cells
+    with pytest.raises(gks.GKSError):
+        gks.Batch(np.array([10]), np.zeros(1))        # zero length
+    B = gks.Batch(np.array([10, 20]), np.ones(2))
+    with pytest.raises(gks.GKSError):
+        B.set_launch(96, 2)                           # unsupported block size

@@ -488,3 +488,87 @@ def test_ns_heat_flux_is_fourier_law_with_prandtl_fix(dim, Pr):
     q = mu * 3.5 * p * rx / rho ** 2
     assert Fd[-1] == pytest.approx(q * dt / Pr, rel=1e-11)
     assert Fh[-1] == pytest.approx(q * dt / 2 / Pr, rel=1e-11)
+
+
+# ---------------------------------------------------------------- WENO5-AO (Sec. 3.2)
+def test_weno_ao_exact_on_quadratics():
+    """Every candidate polynomial reproduces quadratic data, so the AO(5,3)
+    polynomial does too, whatever the weights: exact values and derivatives
+    at the faces and Gauss points."""
+    xs = np.array([-0.5, 0.5, -0.5 / np.sqrt(3), 0.5 / np.sqrt(3)])
+    a, b, c = 0.7, -1.3, 2.1
+    # cell averages of a + b x + c x^2 over [j - 1/2, j + 1/2]
+    q = np.array([a + b * j + c * (j * j + 1.0 / 12.0) for j in range(-2, 3)])
+    val, dval, wbar = O.weno_ao(q, xs)
+    assert np.allclose(val, a + b * xs + c * xs * xs, rtol=0, atol=1e-13)
+    assert np.allclose(dval, b + 2 * c * xs, rtol=0, atol=1e-13)
+    assert wbar.sum() == pytest.approx(1.0, abs=1e-15)
+
+
+def test_weno_ao_large_weight_one_is_the_linear_quartic():
+    """d_Hi = 1 leaves only the large stencil: the fifth-order linear
+    reconstruction, i.e. TENO-D's large-stencil branch on smooth data."""
+    q = np.array([1.0, 1.1, 1.25, 1.45, 1.7])
+    xs = np.array([-0.5, 0.5, -0.3, 0.2])
+    v_ao, d_ao, w = O.weno_ao(q, xs, d_hi=1.0)
+    v_t, d_t, large, _ = O.teno_d(q, xs)
+    assert large and np.allclose(w, [0, 0, 0, 1])
+    assert np.allclose(v_ao, v_t, rtol=1e-14) and np.allclose(d_ao, d_t, rtol=1e-13)
+
+
+def test_weno_ao_weights_tend_to_linear_on_smooth_data():
+    """On smooth data tau / beta = O(h^2): the normalised weights approach
+    the linear weights (d_Hi, d_Lo = 0.85) as the grid is refined."""
+    g = np.array([0.5 * 0.15 * 0.15, 0.15 * 0.85, 0.5 * 0.15 * 0.15, 0.85])
+    dev = []
+    for h in (0.2, 0.1, 0.05):
+        x = np.arange(-2, 3) * h
+        q = (np.cos(x - h / 2) - np.cos(x + h / 2)) / h + 0.3  # cell averages of sin x + 0.3
+        _, _, w = O.weno_ao(q, [0.5])
+        dev.append(np.abs(w - g).max())
+    assert dev[0] > dev[1] > dev[2] and dev[2] < 0.2 * dev[1]
+
+
+def test_weno_ao_picks_the_smooth_substencil_at_a_jump():
+    """At a jump between cells i and i+1 the weight of the large stencil and of
+    the stencils crossing the jump collapse; the left sub-stencil (constant
+    data) carries the reconstruction, which stays within the data range."""
+    q = np.array([1.0, 1.0, 1.0, 0.125, 0.125])
+    val, _, w = O.weno_ao(q, [0.5, -0.5])
+    assert w[0] > 0.99 and w[3] < 1e-3
+    assert 0.125 - 1e-12 <= val[0] <= 1.0 + 1e-12 and val[1] == pytest.approx(1.0, abs=1e-3)
+
+
+def test_weno_ao_accuracy_2d_matches_paper_table():
+    """Sec. 5.5 WENO-AO table, N = 10 and 20 rows to 1e-5 relative (readings:
+    d_Hi = d_Lo = 0.85, squared weight ratio; the first power of Eq. (3.5) is
+    3 % off at N = 10)."""
+    tab = _acc_table("accuracy_2d_wenoao.txt")
+    for n in (10, 20):
+        s = WL.advection_2d(n)
+        P = O.make_problem(2, n, n, recon="weno_ao", **s.problem_kwargs())
+        W, steps, t, _ = O.run(P, s.W, 2.0)
+        e = W[0] - WL.advection_2d_exact_rho(n, t)
+        got = [np.mean(abs(e)), np.sqrt(np.mean(e * e)), abs(e).max()]
+        assert np.allclose(got, tab[n], rtol=1e-5), (n, got, tab[n])
+
+
+def test_weno_ao_accuracy_1d_matches_paper_table_and_order():
+    """Sec. 5.1 WENO-AO table: within 1 % (the same constant factor as the
+    TENO-D table), orders within 0.02."""
+    tab = _acc_table("accuracy_1d_wenoao.txt")
+    got = {}
+    for n in (10, 20, 40):
+        s = WL.advection_1d(n)
+        P = O.make_problem(1, n, recon="weno_ao", **s.problem_kwargs())
+        W = s.W.copy()
+        dt = 0.2 * s.dx
+        for _ in range(int(round(2.0 / dt))):
+            W = O.step(P, W, dt)
+        e = W[0, 0] - WL.advection_1d_exact_rho(n, 2.0)
+        got[n] = np.array([np.mean(abs(e)), np.sqrt(np.mean(e * e)), abs(e).max()])
+        assert np.allclose(got[n], tab[n], rtol=1e-2), (n, got[n], tab[n])
+    for a, b in ((10, 20), (20, 40)):
+        o_got = np.log2(got[a] / got[b])
+        o_tab = np.log2(np.array(tab[a]) / np.array(tab[b]))
+        assert np.all(abs(o_got - o_tab) < 0.02)
