@@ -16,7 +16,8 @@ library's event profiler for the roofline.
 
 Further legs on the same GPU, reported as objects of the same JSON line:
 "ensemble" (4096 independent 1-D Riemann problems of 200..4000 cells to
-t = 0.15 in one persistent launch, cell-updates/s), "viscous" (Navier-Stokes
+t = 0.15 in one persistent launch, cell-updates/s), "weno_ao" (the main
+workload with the WENO5-AO reconstruction), "viscous" (Navier-Stokes
 viscous shock tube on 2048 x 1024, 200 steps from t = 0), "errors_vs_oracle"
 (both GPU paths against the FP64 oracle on the CPU baseline's sample) and
 "adjoint" (the
@@ -71,6 +72,8 @@ def parse():
                    help="THREADS,BLOCKS_PER_SM for the ensemble leg instead of the autotuner")
     p.add_argument("--no-viscous", dest="viscous", action="store_false",
                    help="omit the viscous shock tube leg")
+    p.add_argument("--no-weno-ao", dest="weno_ao", action="store_false",
+                   help="omit the WENO5-AO leg")
     return p.parse_args()
 
 
@@ -263,6 +266,44 @@ def ensemble_leg(gks, WL, stream, peak32, max_steps=0, launch=None):
                          "basis": "whole launch vs measured FP32 FMA peak"}}
 
 
+def weno_ao_leg(gks, WL, stream, peak32, steps, warmup):
+    """The same 1024^2 Riemann workload with the WENO5-AO reconstruction
+    (Sec. 3.2, the scheme the paper compares against): float32 flux, CUDA
+    events around each step, 256 MB L2 flush between steps, sweep kernels
+    timed by the library's event profiler for the roofline."""
+    import torch
+    s = WL.riemann2d(N_GRID, split=0.8, t_end=0.8)
+    S = gks.solver_for(s, "fp32", recon="weno_ao")
+    S.set_stream(stream.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=stream.device)
+    for _ in range(warmup):
+        S.step(0.0)
+    torch.cuda.synchronize()
+    S.profile(True)
+    S.profile_read(0)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        S.step(0.0)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    S.diagnostics()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    sn, sms = S.profile_read(0)
+    S.profile(False)
+    S.close()
+    cells = N_GRID * N_GRID
+    fm = gks.count_flops(2, "fp32", "euler", 1.0, recon="weno_ao")
+    launch_ms = sms / max(sn, 1)
+    tf = fm["flops_per_cell_sweep"] * cells / (launch_ms * 1e-3) / 1e12
+    return {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "workload": "riemann2d_config3_weno_ao",
+            "grid": "%dx%d" % (N_GRID, N_GRID), "steps": steps, "ms_per_step": ms / steps,
+            "flops_per_cell_update": fm["flops_per_cell_update"],
+            "roofline": {"bound": "alu", "kernel": "k2d_sweep<float, WENO5-AO>", "achieved": tf, "peak": peak32,
+                         "unit": "TFLOP/s", "frac": tf / peak32, "launch_ms": launch_ms}}
+
+
 def viscous_leg(gks, WL, stream, precision, steps):
     """Navier-Stokes viscous shock tube (Re = 200, Pr = 0.73, no-slip walls,
     symmetric top) on 2048 x 1024: `steps` CFL steps from t = 0 (the full run
@@ -417,6 +458,7 @@ def main():
     if args.ensemble:
         launch = tuple(int(x) for x in args.ensemble_launch.split(",")) if args.ensemble_launch else None
         ens = ensemble_leg(gks, WL, stream, peak32, args.ensemble_max_steps, launch)
+    ao = weno_ao_leg(gks, WL, stream, peak32, args.steps, args.warmup) if args.weno_ao else None
     visc = None
     if args.viscous:
         visc = viscous_leg(gks, WL, stream, "fp32", 200)
@@ -506,6 +548,8 @@ def main():
     }
     if ens:
         line["ensemble"] = ens
+    if ao:
+        line["weno_ao"] = ao
     if visc:
         line["viscous"] = visc
     if adj:

@@ -90,7 +90,19 @@ typedef struct {
     int tau_mode;            /* gks_tau_mode */
     int positivity_fallback; /* 1: a reconstructed point state with rho<=0 or p<=0 is replaced
                                 by the adjacent cell average with zero slopes (not in the paper) */
+    int recon;               /* gks_recon: TENO-D (default) or WENO5-AO */
+    double d_hi, d_lo;       /* WENO5-AO linear-weight parameters (Sec. 3.2; default 0.85, 0.85) */
+    double eps_ao;           /* WENO5-AO epsilon (default 1e-8) */
 } gks_scheme;
+
+/* Reconstruction of the non-equilibrium states (values and slopes at the
+ * faces, values at the Gauss points): TENO-D (Sec. 4.2, the paper's scheme)
+ * or WENO5-AO (Sec. 3.2, the scheme it is compared with): adaptive-order
+ * weights gamma_k (1 + (tau/(beta_k+eps))^2) on the quartic and the three
+ * quadratics, gamma_3 = d_hi, gamma_1 = (1-d_hi) d_lo, gamma_0 = gamma_2 =
+ * (1-d_hi)(1-d_lo)/2.  Batches and the adjoint take TENO-D only
+ * (GKS_EUNSUPPORTED otherwise). */
+typedef enum { GKS_RECON_TENO_D = 0, GKS_RECON_WENO_AO = 1 } gks_recon;
 
 typedef struct {
     unsigned int error_word; /* bit 0: non-physical state after an update; bit 1: fallback failed */
@@ -242,6 +254,9 @@ typedef struct {
     double fp64_flops_per_cell_update;       /* float64 share (all flops on the float64 path) */
 } gks_flop_model;
 gks_status gks_count_flops(int dim, int precision, int tau_mode, double Pr, gks_flop_model *out);
+/* the same for either reconstruction (gks_recon) */
+gks_status gks_count_flops_recon(int dim, int precision, int tau_mode, double Pr, int recon,
+                                 gks_flop_model *out);
 
 /* Measured arithmetic peak of the current device: fused multiply-adds in 16
  * independent chains per thread on 8 blocks of 256 threads per SM, one launch

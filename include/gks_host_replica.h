@@ -40,6 +40,10 @@ int gks_host_point_flux(int dim, int precision, int tau_mode, double gamma, doub
                         const double *Wr, const double *Wrn, const double *Wrt,
                         double *F, double *dF);
 
+/* WENO5-AO (Sec. 3.2) on five cell averages, outputs as gks_host_teno. */
+int gks_host_weno_ao(int precision, const double *q, double eps_ao, double d_hi, double d_lo,
+                     double *faces, double *gauss);
+
 /* Transpose of TENO-D with the selection of q held fixed (the adjoint's
  * frozen selection; with it the reconstruction is linear in q): the
  * cotangents gfaces[0..3] of faces[] and ggauss[0..3] of gauss[] as in

@@ -115,6 +115,10 @@ TenoParams teno_params(const gks_ctx* c, bool tangential)
     t.q = c->sch.q;
     t.ct1 = tangential ? c->sch.ct1_t : c->sch.ct1;
     t.ct2 = tangential ? c->sch.ct2_t : c->sch.ct2;
+    t.recon = c->sch.recon;
+    t.d_hi = c->sch.d_hi;
+    t.d_lo = c->sch.d_lo;
+    t.eps_ao = c->sch.eps_ao;
     return t;
 }
 
@@ -465,6 +469,9 @@ gks_status gks_create(const gks_grid_desc* d, gks_ctx** out)
     c->sch.q = 7;
     c->sch.tau_mode = GKS_TAU_EULER;
     c->sch.positivity_fallback = 1;
+    c->sch.recon = GKS_RECON_TENO_D;
+    c->sch.d_hi = c->sch.d_lo = 0.85;
+    c->sch.eps_ao = 1e-8;
 
     GridDev& g = c->g;
     g.dim = d->dim;
@@ -562,6 +569,10 @@ gks_status gks_set_scheme(gks_ctx* c, const gks_scheme* s)
     if (!(s->cfl > 0.0) || s->q < 1 || s->q > 32 || !(s->eps >= 0.0) || !(s->ct1 >= 0.0) || !(s->ct2 >= 0.0) ||
         !(s->ct1_t >= 0.0) || !(s->ct2_t >= 0.0) || s->tau_mode < 0 || s->tau_mode > 2)
         return fail(c, GKS_EINVAL, "scheme parameters out of range");
+    if ((s->recon != GKS_RECON_TENO_D && s->recon != GKS_RECON_WENO_AO) ||
+        (s->recon == GKS_RECON_WENO_AO && (!(s->d_hi > 0.0 && s->d_hi <= 1.0) || !(s->d_lo >= 0.0 && s->d_lo <= 1.0) ||
+                                           !(s->eps_ao > 0.0))))
+        return fail(c, GKS_EINVAL, "reconstruction parameters out of range");
     if (!s->positivity_fallback)
         return fail(c, GKS_EUNSUPPORTED, "the kernels always apply the positivity fallback");
     c->sch = *s;

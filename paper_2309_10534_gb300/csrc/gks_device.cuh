@@ -53,19 +53,25 @@ GKS_HD T ipow(T x, int q)
     return r;
 }
 
-// ------------------------------------------------------------------ TENO-D
+// ------------------------------------------------------------------ reconstruction parameters
+// recon 0: TENO-D (Sec. 4.2); 1: WENO5-AO (Sec. 3.2), the reconstruction the
+// paper compares against.
 struct TenoParams {
     double eps;
     int q;
     double ct1, ct2;  // thresholds of the first / second selection
+    int recon = 0;
+    double d_hi = 0.85, d_lo = 0.85, eps_ao = 1e-8;  // WENO5-AO
 };
 
 // the same parameters in the arithmetic type of the kernel (no conversions
 // from double inside the hot loop); eps is clamped to the smallest normal
-// float in float32
+// float in float32.  WENO5-AO: linear weights g[0..3] of the three
+// sub-stencils and the large stencil, gr[k] = g[k]/g[3], and 1/g[3].
 template <typename T> struct TenoT {
     T eps, ct1, ct2;
     int q;
+    T g[4], gr[3], ig3, eps_ao;
 };
 
 template <typename T>
@@ -77,6 +83,16 @@ inline TenoT<T> teno_t(const TenoParams& P)
     t.ct1 = (T)P.ct1;
     t.ct2 = (T)P.ct2;
     t.q = P.q;
+    const double g3 = P.d_hi, g1 = (1.0 - P.d_hi) * P.d_lo, g0 = 0.5 * (1.0 - P.d_hi) * (1.0 - P.d_lo);
+    t.g[0] = (T)g0;
+    t.g[1] = (T)g1;
+    t.g[2] = (T)g0;
+    t.g[3] = (T)g3;
+    t.gr[0] = (T)(g0 / g3);
+    t.gr[1] = (T)(g1 / g3);
+    t.gr[2] = (T)(g0 / g3);
+    t.ig3 = (T)(1.0 / g3);
+    t.eps_ao = (T)P.eps_ao;
     return t;
 }
 
@@ -87,6 +103,7 @@ template <typename T> struct TenoSel {
     T b[3], c[3];       // quadratic k: p = q2 - c/12 + b xi + c xi^2
     T u1, u2, u3, u4;   // quartic in the Legendre-type basis
     T w[3];             // sub-stencil weights (0 when the large stencil is used)
+    T w3;               // WENO5-AO: weight of the quartic (TENO-D: unused)
     bool large;
 };
 
@@ -94,6 +111,57 @@ template <typename T> struct TenoSel {
 // Legendre form.  Selection of Eqs. (4.5)-(4.7) and (4.11)-(4.12) on powers
 // normalised by the smallest beta + eps (below), without divisions and
 // without (beta+eps)^-q, which would overflow in float32.
+// the sub-stencil quadratics and the large-stencil quartic (Sec. 3.1)
+template <typename T>
+GKS_HD void stencil_coeffs(const T q[5], TenoSel<T>& S)
+{
+    const T q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3], q4 = q[4];
+    S.q2 = q2;
+    S.b[0] = T(0.5) * (q0 - T(4) * q1 + T(3) * q2);
+    S.c[0] = T(0.5) * (q0 - T(2) * q1 + q2);
+    S.b[1] = T(0.5) * (q3 - q1);
+    S.c[1] = T(0.5) * (q1 - T(2) * q2 + q3);
+    S.b[2] = T(0.5) * (T(-3) * q2 + T(4) * q3 - q4);
+    S.c[2] = T(0.5) * (q2 - T(2) * q3 + q4);
+    S.u1 = (T(11) * q0 - T(82) * q1 + T(82) * q3 - T(11) * q4) * T(1.0 / 120.0);
+    S.u2 = (T(-3) * q0 + T(40) * q1 - T(74) * q2 + T(40) * q3 - T(3) * q4) * T(1.0 / 56.0);
+    S.u3 = (-q0 + T(2) * q1 - T(2) * q3 + q4) * T(1.0 / 12.0);
+    S.u4 = (q0 - T(4) * q1 + T(6) * q2 - T(4) * q3 + q4) * T(1.0 / 24.0);
+}
+
+// WENO5-AO (Sec. 3.2): beta by Eq. (3.7), global indicator
+// tau = mean |beta_3 - beta_k|, weights gamma_k (1 + (tau/(beta_k + eps))^2)
+// normalised over the four stencils, and the AO(5,3) polynomial
+//   P = wbar_3/gamma_3 p_3 + sum_k (wbar_k - wbar_3 gamma_k/gamma_3) p_k,
+// stored as the evaluation weights w3 (quartic) and w[k] (quadratics).
+template <typename T>
+GKS_HD void ao_select(const T q[5], const TenoT<T>& P, TenoSel<T>& S)
+{
+    stencil_coeffs(q, S);
+    T beta[4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) beta[k] = S.b[k] * S.b[k] + T(13.0 / 3.0) * S.c[k] * S.c[k];
+    {
+        const T a = S.u1 + T(0.1) * S.u3, bq = S.u2 + T(123.0 / 455.0) * S.u4;
+        beta[3] = a * a + T(13.0 / 3.0) * bq * bq + T(781.0 / 20.0) * S.u3 * S.u3
+                + T(1421461.0 / 2275.0) * S.u4 * S.u4;
+    }
+    const T tau = (fabs(beta[3] - beta[0]) + fabs(beta[3] - beta[1]) + fabs(beta[3] - beta[2])) * T(1.0 / 3.0);
+    T om[4], sum = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T r = tau / (beta[k] + P.eps_ao);
+        om[k] = P.g[k] * (T(1) + r * r);
+        sum += om[k];
+    }
+    const T is = T(1) / sum;
+    const T w3 = om[3] * is;
+    S.w3 = w3 * P.ig3;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) S.w[k] = om[k] * is - w3 * P.gr[k];
+    S.large = false;
+}
+
 template <typename T>
 GKS_HD void teno_select(const T q[5], const TenoT<T>& P, TenoSel<T>& S)
 {
@@ -182,6 +250,48 @@ GKS_HD void teno_faces(const T q[5], const TenoSel<T>& S, T& vp, T& dp, T& vm, T
     vm += S.q2;
 }
 
+// WENO5-AO values and xi-derivatives at the faces: the quartic's (Eqs. 4.8,
+// 4.9 and mirror) and the quadratics' (Eqs. 4.13, 4.14) blended by S.w3, S.w
+template <typename T>
+GKS_HD void ao_faces(const T q[5], const TenoSel<T>& S, T& vp, T& dp, T& vm, T& dm)
+{
+    const T lvp = (T(2) * q[0] - T(13) * q[1] + T(47) * q[2] + T(27) * q[3] - T(3) * q[4]) * T(1.0 / 60.0);
+    const T ldp = (q[1] - T(15) * q[2] + T(15) * q[3] - q[4]) * T(1.0 / 12.0);
+    const T lvm = (T(-3) * q[0] + T(27) * q[1] + T(47) * q[2] - T(13) * q[3] + T(2) * q[4]) * T(1.0 / 60.0);
+    const T ldm = (q[0] - T(15) * q[1] + T(15) * q[2] - q[3]) * T(1.0 / 12.0);
+    T svp = T(0), sdp = T(0), svm = T(0), sdm = T(0), ws = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T w = S.w[k], bh = T(0.5) * S.b[k], c6 = S.c[k] * T(1.0 / 6.0);
+        svp += w * (bh + c6);
+        svm += w * (c6 - bh);
+        sdp += w * (S.b[k] + S.c[k]);
+        sdm += w * (S.b[k] - S.c[k]);
+        ws += w;
+    }
+    vp = S.w3 * lvp + ws * S.q2 + svp;
+    vm = S.w3 * lvm + ws * S.q2 + svm;
+    dp = S.w3 * ldp + sdp;
+    dm = S.w3 * ldm + sdm;
+}
+
+// WENO5-AO value and xi-derivative at the Gauss point xi = g (xi^2 = 1/12)
+template <typename T>
+GKS_HD void ao_gauss(const TenoSel<T>& S, T g, T& v, T& d)
+{
+    T sv = T(0), sd = T(0), ws = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        sv += S.w[k] * S.b[k] * g;
+        sd += S.w[k] * (S.b[k] + T(2) * S.c[k] * g);
+        ws += S.w[k];
+    }
+    const T lv = S.q2 + S.u1 * g - S.u3 * g * T(1.0 / 15.0) - S.u4 * T(1.0 / 180.0);
+    const T ld = S.u1 + T(2) * S.u2 * g + T(0.1) * S.u3 - T(2.0 / 21.0) * S.u4 * g;
+    v = S.w3 * lv + ws * S.q2 + sv;
+    d = S.w3 * ld + sd;
+}
+
 // value and xi-derivative at the Gauss point xi = g (g = +-1/(2 sqrt 3), xi^2 = 1/12)
 template <typename T>
 GKS_HD void teno_gauss(const TenoSel<T>& S, T g, T& v, T& d)
@@ -199,6 +309,26 @@ GKS_HD void teno_gauss(const TenoSel<T>& S, T g, T& v, T& d)
         v += S.w[k] * S.b[k] * g;
         d += S.w[k] * (S.b[k] + T(2) * S.c[k] * g);
     }
+}
+
+// the scheme's reconstruction: REC 0 = TENO-D, 1 = WENO5-AO
+template <int REC, typename T>
+GKS_HD void rec_select(const T q[5], const TenoT<T>& P, TenoSel<T>& S)
+{
+    if constexpr (REC == 0) teno_select(q, P, S);
+    else ao_select(q, P, S);
+}
+template <int REC, typename T>
+GKS_HD void rec_faces(const T q[5], const TenoSel<T>& S, T& vp, T& dp, T& vm, T& dm)
+{
+    if constexpr (REC == 0) teno_faces(q, S, vp, dp, vm, dm);
+    else ao_faces(q, S, vp, dp, vm, dm);
+}
+template <int REC, typename T>
+GKS_HD void rec_gauss(const TenoSel<T>& S, T g, T& v, T& d)
+{
+    if constexpr (REC == 0) teno_gauss(S, g, v, d);
+    else ao_gauss(S, g, v, d);
 }
 
 // ------------------------------------------------------------------ kinetic layer

@@ -523,7 +523,7 @@ gks_status gks_batch_create(int count, const int* ncells, const double* lengths,
         tot += b->n[k];
     }
     b->total = tot;
-    b->sch = {0.5, 0.01, 1.0, 1e-7, 1e-5, 1e-7, 1e-5, 1e-40, 7, GKS_TAU_EULER, 1};
+    b->sch = {0.5, 0.01, 1.0, 1e-7, 1e-5, 1e-7, 1e-5, 1e-40, 7, GKS_TAU_EULER, 1, GKS_RECON_TENO_D, 0.85, 0.85, 1e-8};
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -602,6 +602,7 @@ gks_status gks_batch_set_scheme(gks_batch* b, const gks_scheme* s)
     if (!(s->cfl > 0.0) || s->q < 1 || s->q > 32 || !(s->eps >= 0.0) || s->tau_mode < 0 || s->tau_mode > 2)
         return bfail(b, GKS_EINVAL, "scheme parameters out of range");
     if (!s->positivity_fallback) return bfail(b, GKS_EUNSUPPORTED, "the kernels always apply the positivity fallback");
+    if (s->recon != GKS_RECON_TENO_D) return bfail(b, GKS_EUNSUPPORTED, "batches reconstruct with TENO-D only");
     b->sch = *s;
     ++b->version;
     return GKS_OK;

@@ -119,7 +119,38 @@ int flux_vjp_t(double gamma, const double* Wl, const double* Wln, const double* 
     return 0;
 }
 
+template <typename T>
+int weno_ao_t(const double* q, double eps_ao, double d_hi, double d_lo, double* faces, double* gauss)
+{
+    T qq[5];
+    for (int k = 0; k < 5; ++k) qq[k] = (T)q[k];
+    gks::TenoParams P{1e-40, 7, 1e-7, 1e-5};
+    P.recon = 1;
+    P.d_hi = d_hi;
+    P.d_lo = d_lo;
+    P.eps_ao = eps_ao;
+    gks::TenoSel<T> S;
+    gks::ao_select(qq, gks::teno_t<T>(P), S);
+    T vp, dp, vm, dm;
+    gks::ao_faces(qq, S, vp, dp, vm, dm);
+    faces[0] = vp; faces[1] = dp; faces[2] = vm; faces[3] = dm;
+    T v, d;
+    gks::ao_gauss(S, T(-0.28867513459481288), v, d);
+    gauss[0] = v; gauss[1] = d;
+    gks::ao_gauss(S, T(0.28867513459481288), v, d);
+    gauss[2] = v; gauss[3] = d;
+    return 0;
+}
+
 }  // namespace
+
+extern "C" int gks_host_weno_ao(int precision, const double* q, double eps_ao, double d_hi, double d_lo,
+                                double* faces, double* gauss)
+{
+    if (!q || !faces || !gauss || !(d_hi > 0.0)) return -1;
+    return precision == 1 ? weno_ao_t<float>(q, eps_ao, d_hi, d_lo, faces, gauss)
+                          : weno_ao_t<double>(q, eps_ao, d_hi, d_lo, faces, gauss);
+}
 
 extern "C" int gks_host_teno_vjp(int precision, const double* q, double eps, int qpow, double ct1, double ct2,
                                  const double* gfaces, const double* ggauss, double* gq)

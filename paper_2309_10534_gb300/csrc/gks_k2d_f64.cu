@@ -4,41 +4,54 @@
 namespace gks {
 
 namespace {
-template <bool NONEQ, bool PRFIX>
+template <bool NONEQ, bool PRFIX, int REC>
 cudaError_t launch_one(const GridDev& g, const SweepArgs& a, const FluxParams<double>& fp, const TenoParams& tn,
                        const TenoParams& tt, DevState* ds, cudaStream_t st)
 {
     constexpr int TN = SWEEP_TN, TT = SWEEP_TT64;
-    auto kern = k2d_sweep<double, NONEQ, PRFIX, TN, TT>;
+    auto kern = k2d_sweep<double, NONEQ, PRFIX, TN, TT, REC>;
     const size_t smem = sizeof(SweepSmem<double, TN, TT>);
     dim3 grid((a.nn + TN - 1) / TN, (a.nt + TT - 1) / TT);
     kern<<<grid, TT * (TN + 1), smem, st>>>(g, a, fp, teno_t<double>(tn), teno_t<double>(tt), ds);
     return cudaGetLastError();
 }
-template <bool NONEQ, bool PRFIX>
+template <bool NONEQ, bool PRFIX, int REC>
 cudaError_t set_smem()
 {
-    return cudaFuncSetAttribute(k2d_sweep<double, NONEQ, PRFIX, SWEEP_TN, SWEEP_TT64>,
+    return cudaFuncSetAttribute(k2d_sweep<double, NONEQ, PRFIX, SWEEP_TN, SWEEP_TT64, REC>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(SweepSmem<double, SWEEP_TN, SWEEP_TT64>));
+}
+template <int REC>
+cudaError_t set_smem_all()
+{
+    cudaError_t e = set_smem<false, false, REC>();
+    if (e == cudaSuccess) e = set_smem<true, false, REC>();
+    if (e == cudaSuccess) e = set_smem<true, true, REC>();
+    return e;
+}
+template <int REC>
+cudaError_t launch_rec(const GridDev& g, const SweepArgs& a, const HostFlux& hf, const TenoParams& tn,
+                       const TenoParams& tt, DevState* ds, cudaStream_t st)
+{
+    const FluxParams<double> fp = make_flux_params<double>(hf);
+    if (hf.tau_mode == 0) return launch_one<false, false, REC>(g, a, fp, tn, tt, ds, st);
+    if (hf.prfac != 0.0 && hf.tau_mode == 2) return launch_one<true, true, REC>(g, a, fp, tn, tt, ds, st);
+    return launch_one<true, false, REC>(g, a, fp, tn, tt, ds, st);
 }
 }  // namespace
 
 cudaError_t prepare_sweep_f64()
 {
-    cudaError_t e = set_smem<false, false>();
-    if (e == cudaSuccess) e = set_smem<true, false>();
-    if (e == cudaSuccess) e = set_smem<true, true>();
+    cudaError_t e = set_smem_all<0>();
+    if (e == cudaSuccess) e = set_smem_all<1>();
     return e;
 }
 
 cudaError_t launch_sweep_f64(const GridDev& g, const SweepArgs& a, const HostFlux& hf, const TenoParams& tn,
                              const TenoParams& tt, DevState* ds, cudaStream_t st)
 {
-    const FluxParams<double> fp = make_flux_params<double>(hf);
-    if (hf.tau_mode == 0) return launch_one<false, false>(g, a, fp, tn, tt, ds, st);
-    if (hf.prfac != 0.0 && hf.tau_mode == 2) return launch_one<true, true>(g, a, fp, tn, tt, ds, st);
-    return launch_one<true, false>(g, a, fp, tn, tt, ds, st);
+    return tn.recon == 1 ? launch_rec<1>(g, a, hf, tn, tt, ds, st) : launch_rec<0>(g, a, hf, tn, tt, ds, st);
 }
 
 }  // namespace gks

@@ -157,7 +157,7 @@ struct Stage1DArgs {
     double idx;          // 1 / dx
 };
 
-template <typename T, bool NONEQ, bool PRFIX, int TN>
+template <typename T, bool NONEQ, bool PRFIX, int TN, int REC = 0>
 __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, FluxParams<T> fp, TenoT<T> tn,
                                                     DevState* ds)
 {
@@ -198,9 +198,9 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
 #pragma unroll
             for (int s = 0; s < 5; ++s) q[s] = sq[v][c + s];
             TenoSel<T> S;
-            teno_select(q, tn, S);
+            rec_select<REC>(q, tn, S);
             T vp, dp, vm, dm;
-            teno_faces(q, S, vp, dp, vm, dm);
+            rec_faces<REC>(q, S, vp, dp, vm, dm);
             if (c <= TN) { sL[v][0][c] = vp; sL[v][1][c] = dp * idx_; }
             if (c >= 1) { sR[v][0][c - 1] = vm; sR[v][1][c - 1] = dm * idx_; }
         }
@@ -326,7 +326,7 @@ template <typename T, int TN, int TT> struct SweepSmem {
     T flux[8 * (TN + 1) * (TT + 1)];  // face fluxes for the update (layout: sfi)
 };
 
-template <typename T, bool NONEQ, bool PRFIX, int TN, int TT>
+template <typename T, bool NONEQ, bool PRFIX, int TN, int TT, int REC = 0>
 __global__ void __launch_bounds__(TT * (TN + 1), (sizeof(T) == 4) ? 1024 / (TT * (TN + 1)) : 1)
 k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, DevState* ds)
 {
@@ -389,9 +389,9 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
 #pragma unroll
             for (int s = 0; s < 5; ++s) q[s] = sm.w[v][r][c + s];
             TenoSel<T> S;
-            teno_select(q, tnn, S);
+            rec_select<REC>(q, tnn, S);
             T vp, dp, vm, dm;
-            teno_faces(q, S, vp, dp, vm, dm);
+            rec_faces<REC>(q, S, vp, dp, vm, dm);
             if (c <= TN) { sm.rec[0][v][r][c] = vp; sm.rec[1][v][r][c] = dp * ih; }
             if (c >= 1) { sm.rec[2][v][r][c - 1] = vm; sm.rec[3][v][r][c - 1] = dm * ih; }
         }
@@ -421,9 +421,9 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
             T va, da, vb, db;
 #pragma unroll
             for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * gpi][v][r + s][f];
-            teno_select(q, tnt, S);
-            teno_gauss(S, gA, va, da);
-            teno_gauss(S, gB, vb, db);
+            rec_select<REC>(q, tnt, S);
+            rec_gauss<REC>(S, gA, va, da);
+            rec_gauss<REC>(S, gB, vb, db);
             // own side at own point; the partner's point goes to the partner
             T own = gpi ? vb : va, got = __shfl_xor_sync(0xffffffffu, gpi ? va : vb, 1);
             L.W[v] = gpi ? got : own;
@@ -434,9 +434,9 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
             R.Wt[v] = gpi ? own : got;
 #pragma unroll
             for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * gpi + 1][v][r + s][f];
-            teno_select(q, tnt, S);
-            teno_gauss(S, gA, va, da);
-            teno_gauss(S, gB, vb, db);
+            rec_select<REC>(q, tnt, S);
+            rec_gauss<REC>(S, gA, va, da);
+            rec_gauss<REC>(S, gB, vb, db);
             own = gpi ? vb : va;
             got = __shfl_xor_sync(0xffffffffu, gpi ? va : vb, 1);
             L.Wn[v] = gpi ? got : own;

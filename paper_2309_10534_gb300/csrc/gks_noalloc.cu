@@ -130,6 +130,7 @@ extern "C" gks_status gks_step1d_noalloc(const double* W_in, double* W_out, int 
     if ((bc[0] == GKS_BC_PERIODIC) != (bc[1] == GKS_BC_PERIODIC)) return GKS_EINVAL;
     if (!(gas->gamma > 1.0 && gas->gamma < 3.0) || !(gas->mu >= 0.0) || !(gas->Pr > 0.0)) return GKS_EINVAL;
     if (sch->q < 1 || sch->q > 32 || sch->tau_mode < 0 || sch->tau_mode > 2) return GKS_EINVAL;
+    if (sch->recon != GKS_RECON_TENO_D && sch->recon != GKS_RECON_WENO_AO) return GKS_EINVAL;
     if (!sch->positivity_fallback) return GKS_EUNSUPPORTED;
 
     double* base = nullptr;
@@ -165,7 +166,7 @@ extern "C" gks_status gks_step1d_noalloc(const double* W_in, double* W_out, int 
     hf.mu = gas->mu;
     hf.prfac = (sch->tau_mode == GKS_TAU_NS) ? 1.0 / gas->Pr - 1.0 : 0.0;
     hf.tau_mode = sch->tau_mode;
-    TenoParams tn{sch->eps, sch->q, sch->ct1, sch->ct2};
+    TenoParams tn{sch->eps, sch->q, sch->ct1, sch->ct2, sch->recon, sch->d_hi, sch->d_lo, sch->eps_ao};
     const int f32 = precision == GKS_FP32_FLUX;
 
     // the float32 path keeps W* and the accumulator increment in float32, in

@@ -88,7 +88,7 @@ void sample_side(Side<T>& S, double rho, double U, double V, double p, double ga
     if (DIM == 1) { S.W[2] = S.Wn[2] = S.Wt[2] = T(0); }
 }
 
-template <typename B, int DIM, bool NONEQ, bool PRFIX>
+template <typename B, int DIM, bool NONEQ, bool PRFIX, int REC>
 void count(int tau_mode, double Pr, gks_flop_model* out)
 {
     using T = Cnt<B>;
@@ -111,20 +111,27 @@ void count(int tau_mode, double Pr, gks_flop_model* out)
     tp.ct1 = T(1e-7);
     tp.ct2 = T(1e-5);
     tp.q = tp0.q;
+    {
+        const TenoT<double> td = teno_t<double>(tp0);
+        for (int k = 0; k < 4; ++k) tp.g[k] = T(td.g[k]);
+        for (int k = 0; k < 3; ++k) tp.gr[k] = T(td.gr[k]);
+        tp.ig3 = T(td.ig3);
+        tp.eps_ao = T(td.eps_ao);
+    }
 
     const T q[5] = {T(1.00), T(1.011), T(1.023), T(1.036), T(1.050)};
     const Counts recon = measure([&] {
         TenoSel<T> S;
-        teno_select(q, tp, S);
+        rec_select<REC>(q, tp, S);
         T a, b, c, d;
-        teno_faces(q, S, a, b, c, d);
+        rec_faces<REC>(q, S, a, b, c, d);
     });
     const Counts tang = measure([&] {
         TenoSel<T> S;
-        teno_select(q, tp, S);
+        rec_select<REC>(q, tp, S);
         T a, b;
-        teno_gauss(S, T(0.28867513459481288), a, b);
-        teno_gauss(S, T(-0.28867513459481288), a, b);
+        rec_gauss<REC>(S, T(0.28867513459481288), a, b);
+        rec_gauss<REC>(S, T(-0.28867513459481288), a, b);
     });
     Side<T> L, R;
     sample_side<T, DIM>(L, 1.0, 0.3, 0.2, 1.0, gamma, 0.0);
@@ -172,22 +179,38 @@ void count(int tau_mode, double Pr, gks_flop_model* out)
 }  // namespace opc
 }  // namespace gks
 
-extern "C" gks_status gks_count_flops(int dim, int precision, int tau_mode, double Pr, gks_flop_model* out)
+namespace {
+template <int REC>
+void count_rec(int dim, bool f32, int tau_mode, double Pr, gks_flop_model* out)
 {
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!out || (dim != 1 && dim != 2) || tau_mode < 0 || tau_mode > 2 || !(Pr > 0.0)) return GKS_EINVAL;
     using namespace gks::opc;
     const bool pr = tau_mode == 2 && Pr != 1.0;
-    const bool f32 = precision == GKS_FP32_FLUX;
 #define GKS_COUNT(B, D)                                                     \
-    if (tau_mode == 0) count<B, D, false, false>(tau_mode, Pr, out);        \
-    else if (pr) count<B, D, true, true>(tau_mode, Pr, out);                \
-    else count<B, D, true, false>(tau_mode, Pr, out);
+    if (tau_mode == 0) count<B, D, false, false, REC>(tau_mode, Pr, out);   \
+    else if (pr) count<B, D, true, true, REC>(tau_mode, Pr, out);           \
+    else count<B, D, true, false, REC>(tau_mode, Pr, out);
     if (f32 && dim == 2) { GKS_COUNT(float, 2) }
     else if (f32) { GKS_COUNT(float, 1) }
     else if (dim == 2) { GKS_COUNT(double, 2) }
     else { GKS_COUNT(double, 1) }
 #undef GKS_COUNT
+}
+}  // namespace
+
+extern "C" gks_status gks_count_flops_recon(int dim, int precision, int tau_mode, double Pr, int recon,
+                                            gks_flop_model* out)
+{
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!out || (dim != 1 && dim != 2) || tau_mode < 0 || tau_mode > 2 || !(Pr > 0.0) || recon < 0 || recon > 1)
+        return GKS_EINVAL;
+    const bool f32 = precision == GKS_FP32_FLUX;
+    if (recon == 1) count_rec<1>(dim, f32, tau_mode, Pr, out);
+    else count_rec<0>(dim, f32, tau_mode, Pr, out);
     return GKS_OK;
+}
+
+extern "C" gks_status gks_count_flops(int dim, int precision, int tau_mode, double Pr, gks_flop_model* out)
+{
+    return gks_count_flops_recon(dim, precision, tau_mode, Pr, GKS_RECON_TENO_D, out);
 }

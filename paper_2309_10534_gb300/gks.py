@@ -18,6 +18,7 @@ GKS_OK, GKS_EINVAL, GKS_ENOMEM, GKS_ECUDA, GKS_ENONPHYSICAL, GKS_ETIMEOUT, GKS_E
 BC = {"periodic": 0, "zerograd": 1, "symmetry": 2, "noslip": 3, "reflect": 4}
 PRECISION = {"fp64": 0, "fp32": 1}
 TAU = {"zero": 0, "euler": 1, "ns": 2}
+RECON = {"teno_d": 0, "weno_ao": 1}
 
 
 class GridDesc(C.Structure):
@@ -34,7 +35,8 @@ class Scheme(C.Structure):
     _fields_ = [("cfl", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
                 ("ct1", C.c_double), ("ct2", C.c_double), ("ct1_t", C.c_double), ("ct2_t", C.c_double),
                 ("eps", C.c_double), ("q", C.c_int), ("tau_mode", C.c_int),
-                ("positivity_fallback", C.c_int)]
+                ("positivity_fallback", C.c_int), ("recon", C.c_int), ("d_hi", C.c_double),
+                ("d_lo", C.c_double), ("eps_ao", C.c_double)]
 
 
 class Diag(C.Structure):
@@ -104,11 +106,13 @@ def _status_string(s):
 
 def default_scheme(**kw) -> Scheme:
     s = Scheme(cfl=0.5, c1=0.01, c2=1.0, ct1=1e-7, ct2=1e-5, ct1_t=1e-7, ct2_t=1e-5, eps=1e-40, q=7,
-               tau_mode=TAU["euler"], positivity_fallback=1)
+               tau_mode=TAU["euler"], positivity_fallback=1, recon=0, d_hi=0.85, d_lo=0.85, eps_ao=1e-8)
     for k, v in kw.items():
         if k == "tau" or k == "tau_mode":
             v = TAU[v] if isinstance(v, str) else int(v)
             k = "tau_mode"
+        if k == "recon":
+            v = RECON[v] if isinstance(v, str) else int(v)
         setattr(s, k, v)
     if "ct1" in kw and "ct1_t" not in kw:
         s.ct1_t = kw["ct1"]
@@ -253,11 +257,15 @@ def alu_peak(precision="fp32", target_ms=200.0):
     return v.value
 
 
-def count_flops(dim, precision="fp32", tau="euler", Pr=1.0):
+def count_flops(dim, precision="fp32", tau="euler", Pr=1.0, recon="teno_d"):
     """Algorithmic operation count of the library's stage arithmetic per cell."""
     m = FlopModel()
-    st = lib().gks_count_flops(int(dim), PRECISION[precision] if isinstance(precision, str) else int(precision),
-                               TAU[tau] if isinstance(tau, str) else int(tau), float(Pr), C.byref(m))
+    L = lib()
+    L.gks_count_flops_recon.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(FlopModel)]
+    L.gks_count_flops_recon.restype = C.c_int
+    st = L.gks_count_flops_recon(int(dim), PRECISION[precision] if isinstance(precision, str) else int(precision),
+                                 TAU[tau] if isinstance(tau, str) else int(tau), float(Pr),
+                                 RECON[recon] if isinstance(recon, str) else int(recon), C.byref(m))
     if st != GKS_OK:
         raise GKSError(st, "gks_count_flops")
     return {k: getattr(m, k) for k, _ in FlopModel._fields_}
@@ -281,9 +289,10 @@ def _replica():
         L.gks_host_teno.argtypes = [C.c_int, _dp, C.c_double, C.c_int, C.c_double, C.c_double, _dp, _dp]
         L.gks_host_point_flux.argtypes = [C.c_int, C.c_int, C.c_int] + [C.c_double] * 6 + [_dp] * 8
         L.gks_host_teno_vjp.argtypes = [C.c_int, _dp] + [C.c_double, C.c_int, C.c_double, C.c_double] + [_dp] * 3
+        L.gks_host_weno_ao.argtypes = [C.c_int, _dp, C.c_double, C.c_double, C.c_double, _dp, _dp]
         L.gks_host_point_flux_vjp.argtypes = [C.c_int, C.c_double] + [_dp] * 10
         for f in (L.gks_host_time_coeffs, L.gks_host_teno, L.gks_host_point_flux, L.gks_host_teno_vjp,
-                  L.gks_host_point_flux_vjp):
+                  L.gks_host_point_flux_vjp, L.gks_host_weno_ao):
             f.restype = C.c_int
         L._replica_declared = True
     return L
@@ -325,6 +334,16 @@ def host_point_flux(dim, Wl, Wln, Wlt, Wr, Wrn, Wrt, dt, precision="fp64", tau="
     if r:
         raise ValueError("bad argument")
     return F, dF
+
+
+def host_weno_ao(q, precision="fp64", eps_ao=1e-8, d_hi=0.85, d_lo=0.85):
+    """(faces[vp, dp, vm, dm], gauss[v-, d-, v+, d+]) of WENO5-AO for one stencil."""
+    qq, pq = _arr(q, 5)
+    f, pf = _arr(None, 4)
+    g, pg = _arr(None, 4)
+    if _replica().gks_host_weno_ao(PRECISION[precision], pq, eps_ao, d_hi, d_lo, pf, pg):
+        raise ValueError("bad argument")
+    return f, g
 
 
 def host_teno_vjp(q, gfaces, ggauss, precision="fp64", eps=1e-40, q_pow=7, ct1=1e-7, ct2=1e-5):

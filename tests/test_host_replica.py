@@ -101,3 +101,23 @@ def test_point_flux_matches_oracle(G, dim, tau, Pr):
         F32, dF32 = G.host_point_flux(dim, Wl, Wln, Wlt, Wr, Wrn, Wrt, dt, precision="fp32", tau=tau,
                                       mu=0.02, Pr=Pr)
         assert np.allclose(F32[sl], Fo, rtol=0, atol=3e-6 * scale)
+
+
+def test_weno_ao_matches_oracle(G):
+    """WENO5-AO (Sec. 3.2), host build of the device code vs the oracle:
+    faces and Gauss points, values and xi-derivatives, float64 to 1e-14."""
+    rng = np.random.default_rng(42)
+    stencils = [np.array([1.0, 1.1, 1.25, 1.45, 1.7]), np.array([1.0, 1.0, 1.0, 0.125, 0.125]),
+                np.array([0.1, 1.0, 1.02, 1.03, 1.05]), np.ones(5)] + [rng.normal(size=5) for _ in range(20)]
+    g = 0.5 / np.sqrt(3.0)
+    for q in stencils:
+        f, gp = G.host_weno_ao(q)
+        v, d, _ = O.weno_ao(q, [0.5, -0.5])
+        vg, dg, _ = O.weno_ao(q, [-g, g])
+        want_f = np.array([v[0], d[0], v[1], d[1]])
+        want_g = np.array([vg[0], dg[0], vg[1], dg[1]])
+        scale = max(1.0, np.abs(q).max())
+        assert np.abs(f - want_f).max() <= 1e-14 * scale
+        assert np.abs(gp - want_g).max() <= 1e-14 * scale
+        f32, _ = G.host_weno_ao(q, precision="fp32")
+        assert np.abs(f32 - want_f).max() <= 2e-6 * scale
