@@ -220,16 +220,23 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def ensemble_leg(gks, WL, stream, peak32, max_steps=0, launch=None):
+def ensemble_leg(gks, WL, stream, peak32, max_steps=0, launch=None, rank=0, world=1, dist=None):
     """4096 independent 1-D Riemann problems (200..4000 cells, seeded) to
     t = 0.15 in one persistent launch, float32 flux / float64 state, launch
     shape from the autotuner.  One untimed run captures the graph; the timed
     run replays it from the same initial state.  Cell-updates = sum over
     problems of cells x steps taken (a problem flagged non-physical stops
-    early and counts only its own steps)."""
+    early and counts only its own steps).  With N ranks the problems are
+    split longest-first over the ranks (no collective on the data path);
+    value = all ranks' cell-updates / the slowest rank's time."""
     import numpy as np
     import torch
     E = WL.ensemble_1d()
+    shard = gks.partition_lpt(E.ncells.astype(np.float64) ** 2, world)[rank]
+    ncells = E.ncells[shard]
+    W = np.concatenate([E.W[:, E.offsets[k]:E.offsets[k] + E.ncells[k]] for k in shard], axis=1)
+    E = WL.Ensemble(ncells, np.concatenate([[0], np.cumsum(ncells)[:-1]]), W, E.left[shard], E.right[shard],
+                    E.gamma, E.t_end)
     B = gks.Batch(E.ncells, np.ones(E.ncells.size), precision="fp32")
     B.set_stream(stream.cuda_stream)
     B.set_state(E.W)
@@ -250,12 +257,16 @@ def ensemble_leg(gks, WL, stream, peak32, max_steps=0, launch=None):
     ms = e0.elapsed_time(e1)
     t, steps, err, _ = B.progress()
     cu = float((E.ncells.astype(np.float64) * steps).sum())
+    dev = stream.device if dist is not None and dist.get_backend() == "nccl" else None
+    ms = gks.reduce_scalars([ms], "max", dist, dev)[0]
+    cu, nbad = gks.reduce_scalars([cu, nbad], "sum", dist, dev)
     fpc = gks.count_flops(1, "fp32", "euler", 1.0)["flops_per_cell_update"]
     tf = fpc * cu / (ms * 1e-3) / 1e12
     launches = B.launches() - L0   # graph replays, one kernel each
     B.close()
     return {"value": cu / (ms * 1e-3), "unit": UNIT, "workload": "ensemble_1d_riemann",
-            "problems": int(E.ncells.size), "cells": int(E.ncells.sum()), "t_end": E.t_end,
+            "problems_per_rank": int(E.ncells.size), "cells_per_rank": int(E.ncells.sum()), "t_end": E.t_end,
+            "scaling": "strong", "n_gpus": world,
             "ms": ms, "cell_updates": cu, "max_steps_per_problem": int(steps.max()),
             "flagged_nonphysical": int(nbad), "launch": {"threads": th, "blocks_per_sm": bp},
             "gpu_launches": launches,
@@ -457,7 +468,7 @@ def main():
     ens = None
     if args.ensemble:
         launch = tuple(int(x) for x in args.ensemble_launch.split(",")) if args.ensemble_launch else None
-        ens = ensemble_leg(gks, WL, stream, peak32, args.ensemble_max_steps, launch)
+        ens = ensemble_leg(gks, WL, stream, peak32, args.ensemble_max_steps, launch, rank, world, dist)
     ao = weno_ao_leg(gks, WL, stream, peak32, args.steps, args.warmup) if args.weno_ao else None
     visc = None
     if args.viscous:

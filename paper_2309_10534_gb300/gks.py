@@ -501,6 +501,34 @@ class Batch:
         return lib().gks_batch_launches(self.h)
 
 
+# ---------------------------------------------------------------- multi-GPU helpers
+def partition_lpt(costs, parts):
+    """Split independent problems over `parts` ranks, longest processing time
+    first (each problem, in decreasing cost, goes to the least-loaded rank;
+    ties by rank).  Returns one sorted index array per rank."""
+    costs = np.asarray(costs, dtype=np.float64)
+    order = np.argsort(-costs, kind="stable")
+    load = np.zeros(parts)
+    owner = np.empty(costs.size, dtype=np.int64)
+    for k in order:
+        r = int(np.argmin(load))
+        owner[k] = r
+        load[r] += costs[k]
+    return [np.flatnonzero(owner == r) for r in range(parts)]
+
+
+def reduce_scalars(values, op="max", dist=None, device=None):
+    """Max or sum of per-rank scalars over all ranks (identity without a
+    process group).  `device`: where the collective's tensor lives (a CUDA
+    device for NCCL, None for the CPU / gloo)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return t.cpu().tolist()
+
+
 # ---------------------------------------------------------------- adjoint
 def _adj_lib():
     L = lib()
