@@ -361,7 +361,8 @@ def adjoint_leg(gks, WL, stream, precision, steps=700):
     A = gks.Adjoint(S, k)
     dev = stream.device
     W0 = torch.from_numpy(s.W).to(dev)
-    # warm-up: one short forward/backward (kernel loading, allocations)
+    # warm-up: every buffer of the timed passes, one short forward/backward
+    A.reserve(steps)
     S.set_state(W0)
     A.forward(2, dt)
     A.backward(torch.zeros_like(W0))

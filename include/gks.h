@@ -222,6 +222,9 @@ gks_status gks_adjoint_forward(gks_adjoint *adj, int nsteps, double dt);
  * [nv][ny][nx] float64 (host, or device with on_device = 1).  Leaves the
  * context at W_N.  Synchronises. */
 gks_status gks_adjoint_backward(gks_adjoint *adj, const double *gWN, double *gW0, int on_device);
+/* Allocate up front what forward/backward passes of up to nsteps steps
+ * need (checkpoints and segment states), so that they allocate nothing. */
+gks_status gks_adjoint_reserve(gks_adjoint *adj, int nsteps);
 /* kernel launches issued by the adjoint's own kernels (forward steps not counted) */
 long long  gks_adjoint_launches(const gks_adjoint *adj);
 /* One step's vector-Jacobian product: gin = (dS/dW)^T gout for the S2O4 step

@@ -579,6 +579,34 @@ gks_status adjoint_step(gks_adjoint* A, const double* Wn, const void* Ws)
     return GKS_OK;
 }
 
+// checkpoints for nsteps steps and the k segment states (W and W*), kept
+// for the adjoint's lifetime
+gks_status reserve(gks_adjoint* A, int nsteps)
+{
+    gks_ctx* c = A->c;
+    const int ncp = (nsteps + A->k - 1) / A->k;
+    while ((int)A->ckpt.size() < ncp) {
+        double* p = nullptr;
+        if (cudaMalloc(&p, c->arr_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return rt::fail(c, GKS_ENOMEM, "no device memory for %d checkpoints", ncp);
+        }
+        A->ckpt.push_back(p);
+    }
+    while ((int)A->seg.size() < A->k) {
+        double* p = nullptr;
+        void* q = nullptr;
+        if (cudaMalloc(&p, c->arr_bytes) != cudaSuccess || cudaMalloc(&q, wstar_bytes(c)) != cudaSuccess) {
+            cudaFree(p);
+            cudaGetLastError();
+            return rt::fail(c, GKS_ENOMEM, "no device memory for a %d-step segment", A->k);
+        }
+        A->seg.push_back(p);
+        A->segs.push_back(q);
+    }
+    return GKS_OK;
+}
+
 gks_status check_supported(gks_ctx* c)
 {
     if (c->desc.dim != 2) return rt::fail(c, GKS_EUNSUPPORTED, "the adjoint is built for 2-D grids");
@@ -642,15 +670,7 @@ gks_status gks_adjoint_forward(gks_adjoint* A, int nsteps, double dt)
     gks_ctx* c = A->c;
     gks_status s = check_supported(c);
     if (s) return s;
-    const int ncp = (nsteps + A->k - 1) / A->k;
-    while ((int)A->ckpt.size() < ncp) {
-        double* p = nullptr;
-        if (cudaMalloc(&p, c->arr_bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return rt::fail(c, GKS_ENOMEM, "no device memory for %d checkpoints", ncp);
-        }
-        A->ckpt.push_back(p);
-    }
+    if ((s = reserve(A, nsteps))) return s;
     A->have_forward = false;
     for (int n = 0; n < nsteps; ++n) {
         if (n % A->k == 0) CK(cudaMemcpyAsync(A->ckpt[n / A->k], c->W, c->arr_bytes, cudaMemcpyDeviceToDevice, c->stream));
@@ -670,17 +690,7 @@ gks_status gks_adjoint_backward(gks_adjoint* A, const double* gWN, double* gW0, 
     gks_ctx* c = A->c;
     if (!A->have_forward) return rt::fail(c, GKS_EINVAL, "gks_adjoint_backward needs a completed forward pass");
     gks_status s;
-    while ((int)A->seg.size() < std::min(A->k, A->nsteps)) {
-        double* p = nullptr;
-        void* q = nullptr;
-        if (cudaMalloc(&p, c->arr_bytes) != cudaSuccess || cudaMalloc(&q, wstar_bytes(c)) != cudaSuccess) {
-            cudaFree(p);
-            cudaGetLastError();
-            return rt::fail(c, GKS_ENOMEM, "no device memory for a %d-step segment", A->k);
-        }
-        A->seg.push_back(p);
-        A->segs.push_back(q);
-    }
+    if ((s = reserve(A, A->nsteps))) return s;
     CK(cudaMemsetAsync(A->lam, 0, c->arr_bytes, c->stream));
     if ((s = rt::copy_interior(c, A->lam, gWN, on_device, true))) return s;
     const int ncp = (A->nsteps + A->k - 1) / A->k;
@@ -706,6 +716,12 @@ gks_status gks_adjoint_backward(gks_adjoint* A, const double* gWN, double* gW0, 
 }
 
 long long gks_adjoint_launches(const gks_adjoint* A) { return A ? A->launches : 0; }
+
+gks_status gks_adjoint_reserve(gks_adjoint* A, int nsteps)
+{
+    if (!A || nsteps < 1) return GKS_EINVAL;
+    return reserve(A, nsteps);
+}
 
 gks_status gks_vjp_step(gks_ctx* c, const double* W, const double* gout, double* gin, double dt, int on_device)
 {

@@ -539,6 +539,7 @@ def _adj_lib():
             "gks_adjoint_forward": ([_vp, C.c_int, C.c_double], C.c_int),
             "gks_adjoint_backward": ([_vp, _vp, _vp, C.c_int], C.c_int),
             "gks_adjoint_launches": ([_vp], C.c_longlong),
+            "gks_adjoint_reserve": ([_vp, C.c_int], C.c_int),
             "gks_vjp_step": ([_vp, _vp, _vp, _vp, C.c_double, C.c_int], C.c_int),
         }
         for name, (args, res) in sig.items():
@@ -584,6 +585,10 @@ class Adjoint:
             self.close()
         except Exception:
             pass
+
+    def reserve(self, nsteps):
+        """Allocate the checkpoints and segment states of nsteps-step passes."""
+        self.solver._check(_adj_lib().gks_adjoint_reserve(self.h, int(nsteps)))
 
     def forward(self, nsteps, dt):
         self.solver._check(_adj_lib().gks_adjoint_forward(self.h, int(nsteps), float(dt)))
