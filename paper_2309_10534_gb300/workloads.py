@@ -133,6 +133,57 @@ def lax(n=100, gamma=1.4):
                  extra=dict(left=left, right=right, x0=0.5))
 
 
+def _sine_wave_tube(n, length, x0, left, amp, k, gamma):
+    """Cell averages of (rho, u, p) = left for x < x0 and (1 + amp sin(k x),
+    0, 1) beyond: a shock running into a density wave."""
+    edges = np.linspace(0.0, length, n + 1)
+    a, b = edges[:-1], edges[1:]
+    h = b - a
+    frac = np.clip((x0 - a) / h, 0.0, 1.0)           # fraction left of x0
+    lo = np.minimum(np.maximum(a, x0), b)              # wave part [lo, b] (empty left of x0)
+    wave_int = (b - lo) + amp * (np.cos(k * lo) - np.cos(k * b)) / k
+    WL = conserved_1d(*left, gamma)
+    rho = frac * left[0] + wave_int / h
+    mom = frac * WL[1]
+    E = frac * WL[2] + (1.0 - frac) * (1.0 / (gamma - 1.0))
+    return np.stack([rho, mom, E])[:, None, :]
+
+
+def shu_osher(n=400, gamma=1.4):
+    """Shu-Osher shock / density-wave interaction (Sec. 5.3 (a)) on [0, 10]:
+    (3.857134, 2.629369, 10.33333) for x < 1, (1 + 0.2 sin 5x, 0, 1) beyond,
+    t = 1.8.  Right boundary: zero gradient (the wave there is at rest and
+    no signal reaches it by t = 1.8)."""
+    left = (3.857134, 2.629369, 10.33333)
+    W = _sine_wave_tube(n, 10.0, 1.0, left, 0.2, 5.0, gamma)
+    return Setup(1, n, 1, 10.0, 1.0, W, gamma=gamma, t_end=1.8, name="shu_osher")
+
+
+def titarev_toro(n=1000, gamma=1.4):
+    """Titarev-Toro shock / high-frequency wave interaction (Sec. 5.3 (b)) on
+    [0, 10]: (1.515695, 0.523346, 1.805) for x < 0.5, (1 + 0.1 sin 20 pi x,
+    0, 1) beyond, t = 5."""
+    left = (1.515695, 0.523346, 1.805)
+    W = _sine_wave_tube(n, 10.0, 0.5, left, 0.1, 20.0 * np.pi, gamma)
+    return Setup(1, n, 1, 10.0, 1.0, W, gamma=gamma, t_end=5.0, name="titarev_toro")
+
+
+def blast_wave(n=400, gamma=1.4):
+    """Woodward-Colella interacting blast waves (Sec. 5.4) on [0, 1]: p = 1000,
+    0.01, 100 on [0, 0.1), [0.1, 0.9), [0.9, 1], rho = 1, u = 0; reflecting
+    ends, t = 0.038."""
+    edges = np.linspace(0.0, 1.0, n + 1)
+    a, b = edges[:-1], edges[1:]
+    h = b - a
+    f1 = np.clip((0.1 - a) / h, 0.0, 1.0)
+    f3 = np.clip((b - 0.9) / h, 0.0, 1.0)
+    f2 = 1.0 - f1 - f3
+    E = (1000.0 * f1 + 0.01 * f2 + 100.0 * f3) / (gamma - 1.0)
+    W = np.stack([np.ones(n), np.zeros(n), E])[:, None, :]
+    return Setup(1, n, 1, 1.0, 1.0, W, bc=("reflect", "reflect", "zerograd", "zerograd"), gamma=gamma,
+                 t_end=0.038, name="blast_wave")
+
+
 RIEMANN_CONFIG3 = {
     # (rho, u, v, p) per quadrant, Sec. 5.6 (a)
     "ll": (0.138, 1.206, 1.206, 0.029),   # x < x0, y < y0

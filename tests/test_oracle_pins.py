@@ -6,6 +6,8 @@ numerical integral, a textbook solution, or an invariant.
 """
 import math
 
+import os
+
 import numpy as np
 import pytest
 from scipy import integrate
@@ -572,3 +574,38 @@ def test_weno_ao_accuracy_1d_matches_paper_table_and_order():
         o_got = np.log2(got[a] / got[b])
         o_tab = np.log2(np.array(tab[a]) / np.array(tab[b]))
         assert np.all(abs(o_got - o_tab) < 0.02)
+
+
+def test_blast_wave_conserves_mass_and_energy():
+    """Sec. 5.4 with reflecting ends: nothing crosses the boundaries, so total
+    mass and energy stay at their initial values to round-off while the blast
+    waves interact (200 cells, 60 CFL steps)."""
+    s = WL.blast_wave(200)
+    P = O.make_problem(1, 200, **s.problem_kwargs())
+    W, steps, t, nfb = O.run(P, s.W, 0.038, max_steps=60)
+    assert steps == 60
+    tot0, tot = s.W.reshape(3, -1).sum(axis=1), W.reshape(3, -1).sum(axis=1)
+    assert tot[0] == pytest.approx(tot0[0], rel=1e-13) and tot[2] == pytest.approx(tot0[2], rel=1e-13)
+
+
+def test_shu_osher_initial_state():
+    """Sec. 5.3 (a) initial data: the post-shock state left of x = 1 and the
+    exact cell averages of 1 + 0.2 sin 5x at rest with p = 1 beyond."""
+    s = WL.shu_osher(400)
+    h = 10.0 / 400
+    assert np.allclose(s.W[0, 0, :40], 3.857134, rtol=1e-15)
+    x = (np.arange(400) + 0.5) * h
+    k = np.arange(40, 400)
+    avg = 1 + 0.2 * (np.cos(5 * (x[k] - h / 2)) - np.cos(5 * (x[k] + h / 2))) / (5 * h)
+    assert np.allclose(s.W[0, 0, 40:], avg, rtol=1e-13)
+    assert np.allclose(s.W[1, 0, 40:], 0.0) and np.allclose(s.W[2, 0, 40:], 2.5)
+
+
+def test_blast_wave_fine_reference_conserves_mass():
+    """The stored 1600-cell blast-wave reference (written by the oracle) keeps
+    the initial mass (rho = 1 on [0, 1], reflecting ends) to round-off, and
+    its density stays positive."""
+    ref = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "blast_wave_ref1600.txt"))
+    assert ref.shape == (1600,)
+    assert ref.mean() == pytest.approx(1.0, rel=1e-12)
+    assert ref.min() > 0

@@ -1,0 +1,134 @@
+"""The paper's remaining 1-D workloads (Sec. 5.2-5.4) and the Re = 1000
+viscous shock tube (Sec. 5.8) through the GPU path against the FP64 oracle.
+
+Shock runs switch TENO-D stencils discontinuously, so the float64 GPU run is
+compared with the oracle's own round-off envelope (the spread of oracle runs
+whose initial data differ by 1e-15); float32 runs with the stated bound of
+the mixed path on shock runs (1e-3 relative L1)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2309_10534_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gks():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_10534_gb300 import build, gks as G
+    build.build()
+    return G
+
+
+def rel_l1(a, b):
+    a = np.asarray(a).reshape(a.shape[0], -1)
+    b = np.asarray(b).reshape(b.shape[0], -1)
+    return float(np.abs(a - b).sum() / np.abs(b).sum())
+
+
+def envelope(P, W0, t_end, seeds=(0,)):
+    Wa = O.run(P, W0, t_end)[0]
+    spread = 0.0
+    for sd in seeds:
+        rng = np.random.default_rng(sd)
+        Wb = O.run(P, W0 * (1 + 1e-15 * rng.standard_normal(W0.shape)), t_end)[0]
+        spread = max(spread, rel_l1(Wb, Wa))
+    return Wa, spread
+
+
+GOLDEN_BW = os.path.join(os.path.dirname(__file__), "golden", "blast_wave_ref1600.txt")
+
+# (name, setup, t_end, float32 bound or None for the grid-scaled default)
+CASES = [
+    ("lax", lambda: WL.lax(100), 0.14, None),
+    ("shu_osher", lambda: WL.shu_osher(400), 1.8, None),
+    ("titarev_toro", lambda: WL.titarev_toro(1000), 1.0, None),
+    # pressure ratio 1e5 and positivity fallbacks: float32 moves the switches
+    # in more cells (measured 6.5e-3); judged on the physical scale below
+    ("blast_wave", lambda: WL.blast_wave(400), 0.038, 1e-2),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_1d_paper_workload(gks, case):
+    """Lax (Sec. 5.2 a), Shu-Osher (5.3 a), Titarev-Toro (5.3 b, to t = 1),
+    blast waves with reflecting ends (5.4): float64 within 10x the oracle's
+    envelope (and 1e-10).  float32 rounding moves TENO-D switches in the few
+    cells at each discontinuity, so its relative L1 distance scales like
+    1/n: the bound is 1e-3 at 400 cells (the Sod bound), 1e-3 * 400/n on
+    coarser grids, or 10x the oracle's envelope where that is wider (on
+    Shu-Osher a 1e-15 change of the initial data already moves the oracle's
+    own result by 6e-4).  The blast waves take 1e-2 in float32 and are
+    judged against a fine-grid reference below."""
+    name, make, t_end, tol32 = case
+    s = make()
+    P = O.make_problem(1, s.nx, **s.problem_kwargs())
+    Wo, spread = envelope(P, s.W, t_end)
+    if tol32 is None:
+        tol32 = max(1e-3 * max(1.0, 400 / s.nx), 10 * spread)
+    for precision, tol in (("fp64", max(1e-10, 10 * spread)), ("fp32", tol32)):
+        S = gks.solver_for(s, precision)
+        steps, t = S.advance_to(t_end)
+        assert t == pytest.approx(t_end, abs=1e-14)
+        err = rel_l1(S.get_state(), Wo)
+        print(f"{name} {precision}: rel L1 {err:.3e} (oracle envelope {spread:.2e})")
+        assert err < tol, (name, precision, err, spread)
+        S.diagnostics()
+
+
+def test_lax_against_exact_solution(gks):
+    """Lax tube at t = 0.14 on 100 cells: distance to the exact Riemann
+    solution equals the oracle's to 1e-3 in float64 and 5 % in float32."""
+    import exact_riemann as ER
+    s = WL.lax(100)
+    P = O.make_problem(1, 100, **s.problem_kwargs())
+    Wo = O.run(P, s.W, 0.14)[0]
+    ex = ER.cell_averages(s.extra["left"], s.extra["right"], 100, 0.14)
+    e_ora = np.mean(abs(Wo[0, 0] - ex[0]))
+    for precision, rel in (("fp64", 1e-3), ("fp32", 5e-2)):
+        S = gks.solver_for(s, precision)
+        S.advance_to(0.14)
+        e_gpu = np.mean(abs(S.get_state()[0, 0] - ex[0]))
+        print(f"lax {precision}: distance to exact {e_gpu:.6e} (oracle {e_ora:.6e})")
+        assert e_gpu == pytest.approx(e_ora, rel=rel), precision
+        assert S.diagnostics().error_word == 0
+
+
+def test_blast_wave_against_fine_grid_reference(gks):
+    """Blast waves (Sec. 5.4) on 400 cells at t = 0.038 against the oracle's
+    1600-cell solution averaged over groups of 4 cells: the float64 GPU run's
+    density distance equals the 400-cell oracle's (6.3 % relative L1, the
+    discretisation error), and float32 rounding leaves it within 10 % of
+    that: float32 costs nothing measurable next to the grid's own error."""
+    ref = np.loadtxt(GOLDEN_BW).reshape(400, 4).mean(axis=1)
+    s = WL.blast_wave(400)
+    P = O.make_problem(1, 400, **s.problem_kwargs())
+    Wo = O.run(P, s.W, s.t_end)[0]
+    e_ora = np.abs(Wo[0, 0] - ref).sum() / np.abs(ref).sum()
+    for precision, rel in (("fp64", 1e-6), ("fp32", 1e-1)):
+        S = gks.solver_for(s, precision)
+        S.advance_to(s.t_end)
+        e = np.abs(S.get_state()[0, 0] - ref).sum() / np.abs(ref).sum()
+        print(f"blast wave {precision}: density distance to the 1600-cell reference {e:.5f} (oracle {e_ora:.5f})")
+        assert e <= e_ora * (1 + rel), precision
+
+
+def test_viscous_shock_tube_re1000_steps(gks):
+    """Sec. 5.8 with Re = 1000 (the paper's second viscous case) on 64 x 32,
+    3 CFL steps, float64 to 1e-12 relative L1, float32 to 1e-5."""
+    s = WL.viscous_shock_tube(64, 32, Re=1000.0, Pr=0.73)
+    P = O.make_problem(2, 64, 32, **s.problem_kwargs())
+    W = s.W
+    for _ in range(3):
+        W = O.step(P, W, O.dt(P, W))
+    for precision, tol in (("fp64", 1e-12), ("fp32", 1e-5)):
+        S = gks.solver_for(s, precision)
+        for _ in range(3):
+            S.step(0.0)
+        assert rel_l1(S.get_state(), W) < tol, precision
