@@ -3,6 +3,7 @@
 #include "../../include/gks_host_replica.h"
 #include "gks_adjoint.cuh"
 #include "gks_device.cuh"
+#include "gks_pair.cuh"
 
 namespace {
 
@@ -32,6 +33,29 @@ int teno_t(const double* q, double eps, int qpow, double ct1, double ct2, double
     gks::teno_gauss(S, T(0.28867513459481288), v, d);
     gauss[2] = v; gauss[3] = d;
     return S.large ? 1 : 0;
+}
+
+// packed TENO-D of the float32 2-D sweep: lane x holds q, lane y -q (the
+// selection is sign-symmetric, so lane y must give exactly the negated
+// values: a check that the lanes stay independent); faces from the scalar
+// float32 code, Gauss points from lane x; -2 if the lanes disagree
+int teno_packed(const double* q, double eps, int qpow, double ct1, double ct2, double* faces, double* gauss)
+{
+    const int large = teno_t<float>(q, eps, qpow, ct1, ct2, faces, gauss);
+    gks::f2 qq[5];
+    for (int k = 0; k < 5; ++k) qq[k] = gks::f2((float)q[k], -(float)q[k]);
+    const gks::TenoParams P{eps, qpow, ct1, ct2};
+    gks::TenoSel2 S;
+    gks::teno_select_x2(qq, gks::teno_t<float>(P), S);
+    const float gp[2] = {-0.28867513459481288f, 0.28867513459481288f};
+    for (int i = 0; i < 2; ++i) {
+        gks::f2 v, d;
+        gks::teno_gauss_x2(S, gp[i], v, d);
+        if (v.y() != -v.x() || d.y() != -d.x()) return -2;
+        gauss[2 * i] = v.x();
+        gauss[2 * i + 1] = d.x();
+    }
+    return large;
 }
 
 template <typename T, int DIM, bool NONEQ, bool PRFIX>
@@ -179,6 +203,7 @@ extern "C" int gks_host_teno(int precision, const double* q, double eps, int qpo
                              double* faces, double* gauss)
 {
     if (!q || !faces || !gauss || qpow < 1) return -1;
+    if (precision == 2) return teno_packed(q, eps, qpow, ct1, ct2, faces, gauss);
     return precision == 1 ? teno_t<float>(q, eps, qpow, ct1, ct2, faces, gauss)
                           : teno_t<double>(q, eps, qpow, ct1, ct2, faces, gauss);
 }

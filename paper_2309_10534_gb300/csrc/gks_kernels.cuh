@@ -15,6 +15,7 @@
 #pragma once
 
 #include "gks_device.cuh"
+#include "gks_pair.cuh"
 
 namespace gks {
 
@@ -416,29 +417,46 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
         Side<T> L, R;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            T q[5];
-            TenoSel<T> S;
-            T va, da, vb, db;
+            // line averages of the side's value (W) and normal slope (Wn) at
+            // the two Gauss points: value and tangential derivative of W,
+            // value of Wn
+            T wa, wda, wb, wdb, na, nb;
+            if constexpr (sizeof(T) == 4 && REC == 0) {
+                // both streams as one packed pair (x: W, y: Wn)
+                f2 q[5];
 #pragma unroll
-            for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * gpi][v][r + s][f];
-            rec_select<REC>(q, tnt, S);
-            rec_gauss<REC>(S, gA, va, da);
-            rec_gauss<REC>(S, gB, vb, db);
+                for (int s = 0; s < 5; ++s) q[s] = f2(sm.rec[2 * gpi][v][r + s][f], sm.rec[2 * gpi + 1][v][r + s][f]);
+                TenoSel2 S;
+                teno_select_x2(q, tnt, S);
+                f2 va, da, vb, db;
+                teno_gauss_x2(S, gA, va, da);
+                teno_gauss_x2(S, gB, vb, db);
+                wa = va.x(), wda = da.x(), wb = vb.x(), wdb = db.x(), na = va.y(), nb = vb.y();
+            } else {
+                T q[5];
+                TenoSel<T> S;
+                T dn;
+#pragma unroll
+                for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * gpi][v][r + s][f];
+                rec_select<REC>(q, tnt, S);
+                rec_gauss<REC>(S, gA, wa, wda);
+                rec_gauss<REC>(S, gB, wb, wdb);
+#pragma unroll
+                for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * gpi + 1][v][r + s][f];
+                rec_select<REC>(q, tnt, S);
+                rec_gauss<REC>(S, gA, na, dn);
+                rec_gauss<REC>(S, gB, nb, dn);
+            }
             // own side at own point; the partner's point goes to the partner
-            T own = gpi ? vb : va, got = __shfl_xor_sync(0xffffffffu, gpi ? va : vb, 1);
+            T own = gpi ? wb : wa, got = __shfl_xor_sync(0xffffffffu, gpi ? wa : wb, 1);
             L.W[v] = gpi ? got : own;
             R.W[v] = gpi ? own : got;
-            own = (gpi ? db : da) * iht;
-            got = __shfl_xor_sync(0xffffffffu, (gpi ? da : db) * iht, 1);
+            own = (gpi ? wdb : wda) * iht;
+            got = __shfl_xor_sync(0xffffffffu, (gpi ? wda : wdb) * iht, 1);
             L.Wt[v] = gpi ? got : own;
             R.Wt[v] = gpi ? own : got;
-#pragma unroll
-            for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * gpi + 1][v][r + s][f];
-            rec_select<REC>(q, tnt, S);
-            rec_gauss<REC>(S, gA, va, da);
-            rec_gauss<REC>(S, gB, vb, db);
-            own = gpi ? vb : va;
-            got = __shfl_xor_sync(0xffffffffu, gpi ? va : vb, 1);
+            own = gpi ? nb : na;
+            got = __shfl_xor_sync(0xffffffffu, gpi ? na : nb, 1);
             L.Wn[v] = gpi ? got : own;
             R.Wn[v] = gpi ? own : got;
         }

@@ -1,0 +1,172 @@
+// gks_pair.cuh -- packed float32 pairs for the tangential reconstruction of
+// the float32 2-D sweep.
+//
+// GB300's FP32 units execute two-lane packed instructions (FFMA2, FADD2,
+// FMUL2: one issue slot, two IEEE round-to-nearest results).  The 2-D sweep
+// is issue-bound, so the tangential TENO-D of a face side, which runs the
+// same arithmetic on two independent line-average streams (the value W and
+// the normal slope W_n), runs them as one packed stream (W in .x, W_n in .y).
+// `f2` is a drop-in arithmetic type for the templated kernel arithmetic: a
+// product stays unevaluated (`Prod`) until it is added, so `a * b + c`
+// becomes one fused multiply-add, as the compiler's contraction does for
+// scalar code.  Divisions and comparisons run per lane.
+#pragma once
+
+#include "gks_device.cuh"
+
+namespace gks {
+
+struct __align__(8) f2 {
+    float2 v;
+    f2() = default;
+    GKS_HD f2(float s) : v(make_float2(s, s)) {}
+    GKS_HD f2(double s) : v(make_float2((float)s, (float)s)) {}
+    GKS_HD f2(int s) : v(make_float2((float)s, (float)s)) {}
+    GKS_HD f2(float a, float b) : v(make_float2(a, b)) {}
+    GKS_HD explicit f2(float2 p) : v(p) {}
+    GKS_HD float x() const { return v.x; }
+    GKS_HD float y() const { return v.y; }
+};
+
+GKS_HD f2 pmul(f2 a, f2 b)
+{
+#ifdef __CUDA_ARCH__
+    return f2(__fmul2_rn(a.v, b.v));
+#else
+    return f2(a.v.x * b.v.x, a.v.y * b.v.y);
+#endif
+}
+GKS_HD f2 padd(f2 a, f2 b)
+{
+#ifdef __CUDA_ARCH__
+    return f2(__fadd2_rn(a.v, b.v));
+#else
+    return f2(a.v.x + b.v.x, a.v.y + b.v.y);
+#endif
+}
+GKS_HD f2 pfma(f2 a, f2 b, f2 c)
+{
+#ifdef __CUDA_ARCH__
+    return f2(__ffma2_rn(a.v, b.v, c.v));
+#else
+    return f2(fmaf(a.v.x, b.v.x, c.v.x), fmaf(a.v.y, b.v.y, c.v.y));
+#endif
+}
+GKS_HD f2 pneg(f2 a) { return f2(-a.v.x, -a.v.y); }
+
+// an unevaluated product a * b
+struct Prod {
+    f2 a, b;
+    GKS_HD operator f2() const { return pmul(a, b); }
+};
+
+GKS_HD Prod operator*(f2 a, f2 b) { return Prod{a, b}; }
+GKS_HD Prod operator*(Prod p, f2 b) { return Prod{f2(p), b}; }
+GKS_HD Prod operator*(f2 a, Prod p) { return Prod{a, f2(p)}; }
+GKS_HD Prod operator*(Prod p, Prod q) { return Prod{f2(p), f2(q)}; }
+
+GKS_HD f2 operator+(f2 a, f2 b) { return padd(a, b); }
+GKS_HD f2 operator+(Prod p, f2 c) { return pfma(p.a, p.b, c); }
+GKS_HD f2 operator+(f2 c, Prod p) { return pfma(p.a, p.b, c); }
+GKS_HD f2 operator+(Prod p, Prod q) { return pfma(p.a, p.b, f2(q)); }
+
+GKS_HD f2 operator-(f2 a) { return pneg(a); }
+GKS_HD Prod operator-(Prod p) { return Prod{pneg(p.a), p.b}; }
+GKS_HD f2 operator-(f2 a, f2 b) { return padd(a, pneg(b)); }
+GKS_HD f2 operator-(Prod p, f2 c) { return pfma(p.a, p.b, pneg(c)); }
+GKS_HD f2 operator-(f2 c, Prod p) { return pfma(pneg(p.a), p.b, c); }
+GKS_HD f2 operator-(Prod p, Prod q) { return pfma(p.a, p.b, pneg(f2(q))); }
+
+// per-lane division (the build's float division, as in scalar code)
+GKS_HD f2 operator/(f2 a, f2 b) { return f2(a.v.x / b.v.x, a.v.y / b.v.y); }
+GKS_HD f2 operator/(Prod p, f2 b) { return f2(p) / b; }
+
+GKS_HD f2& operator+=(f2& a, f2 b) { return a = a + b; }
+GKS_HD f2& operator+=(f2& a, Prod p) { return a = p + a; }
+GKS_HD f2& operator-=(f2& a, f2 b) { return a = a - b; }
+GKS_HD f2& operator*=(f2& a, f2 b) { return a = pmul(a, b); }
+
+// TENO-D selection (Sec. 4.2, Eqs. 4.5-4.7 and 4.11-4.12) of two 5-cell
+// stencils at once, one per lane, with the selection folded into the
+// coefficients: a lane that keeps the large stencil has zero sub-stencil
+// weights, a lane that keeps sub-stencils has zero quartic coefficients, so
+// one formula evaluates either choice.  Same powers-of-ratios form as
+// teno_select (no division by beta, nothing overflows).
+struct TenoSel2 {
+    f2 q2, b[3], c[3], u1, u2, u3, u4, w[3];
+};
+
+GKS_HD float lane_min4(float a, float b, float c, float d)
+{
+    float m = a < b ? a : b;
+    m = m < c ? m : c;
+    return m < d ? m : d;
+}
+
+GKS_HD void teno_select_x2(const f2 q[5], const TenoT<float>& P, TenoSel2& S)
+{
+    TenoSel<f2> C;
+    stencil_coeffs(q, C);
+    const f2 eps(P.eps);
+    f2 t[4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t[k] = C.b[k] * C.b[k] + f2(13.0 / 3.0) * C.c[k] * C.c[k] + eps;
+    {
+        const f2 a = C.u1 + f2(0.1) * C.u3, bq = C.u2 + f2(123.0 / 455.0) * C.u4;
+        t[3] = a * a + f2(13.0 / 3.0) * bq * bq + f2(781.0 / 20.0) * C.u3 * C.u3
+             + f2(1421461.0 / 2275.0) * C.u4 * C.u4 + eps;
+    }
+    const f2 m(lane_min4(t[0].x(), t[1].x(), t[2].x(), t[3].x()), lane_min4(t[0].y(), t[1].y(), t[2].y(), t[3].y()));
+    f2 p[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const f2 r = m * f2(1.0f / t[j].x(), 1.0f / t[j].y());
+        if (P.q == 7) {
+            const f2 r2 = r * r, r3 = r2 * r;
+            p[j] = r3 * r3 * r;
+        } else {
+            p[j] = f2(ipow(r.x(), P.q), ipow(r.y(), P.q));
+        }
+    }
+    const f2 s012 = p[0] + p[1] + p[2];
+    const f2 lim = f2(P.ct1) * (s012 + p[3]);
+    const float lx = (p[3].x() >= lim.x()) ? 1.0f : 0.0f, ly = (p[3].y() >= lim.y()) ? 1.0f : 0.0f;
+    const f2 thr = f2(P.ct2) * s012;
+    f2 d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        d[k] = f2(p[k].x() >= thr.x() ? 1.0f : 0.0f, p[k].y() >= thr.y() ? 1.0f : 0.0f);
+    // at least one sub-stencil passes the second cut (its ratio is the
+    // largest, >= s012 / 3 > C_T2 s012), so dsum >= 1
+    const f2 dsum = d[0] + d[1] + d[2];
+    const f2 inv = f2((1.0f - lx) / dsum.x(), (1.0f - ly) / dsum.y());  // 0 on large-stencil lanes
+    const f2 lm(lx, ly);
+    S.q2 = C.q2;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        S.b[k] = C.b[k];
+        S.c[k] = C.c[k];
+        S.w[k] = d[k] * inv;
+    }
+    S.u1 = C.u1 * lm;
+    S.u2 = C.u2 * lm;
+    S.u3 = C.u3 * lm;
+    S.u4 = C.u4 * lm;
+}
+
+// value and xi-derivative at the Gauss point xi = g of both lanes' selection
+// (quartic: P2(g) = 0, P3(g) = -g/15, P4(g) = -1/180, P3'(g) = 1/10,
+// P4'(g) = -2g/21; quadratics: q2 + b g + c (g^2 - 1/12) = q2 + b g)
+GKS_HD void teno_gauss_x2(const TenoSel2& S, float g, f2& v, f2& d)
+{
+    const f2 G(g);
+    v = S.q2 + S.u1 * G - S.u3 * f2(g * (1.0f / 15.0f)) - S.u4 * f2(1.0f / 180.0f);
+    d = S.u1 + f2(2.0f * g) * S.u2 + f2(0.1f) * S.u3 - f2(g * (2.0f / 21.0f)) * S.u4;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        v += S.w[k] * S.b[k] * G;
+        d += S.w[k] * (S.b[k] + f2(2.0f * g) * S.c[k]);
+    }
+}
+
+}  // namespace gks

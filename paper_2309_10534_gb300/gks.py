@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libgks.so")
 
 GKS_OK, GKS_EINVAL, GKS_ENOMEM, GKS_ECUDA, GKS_ENONPHYSICAL, GKS_ETIMEOUT, GKS_EUNSUPPORTED = range(7)
 BC = {"periodic": 0, "zerograd": 1, "symmetry": 2, "noslip": 3, "reflect": 4}
-PRECISION = {"fp64": 0, "fp32": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "fp32x2": 2}
 TAU = {"zero": 0, "euler": 1, "ns": 2}
 RECON = {"teno_d": 0, "weno_ao": 1}
 
@@ -318,6 +318,8 @@ def host_teno(q, precision="fp64", eps=1e-40, q_pow=7, ct1=1e-7, ct2=1e-5):
     f, pf = _arr(None, 4)
     g, pg = _arr(None, 4)
     r = _replica().gks_host_teno(PRECISION[precision], pq, eps, q_pow, ct1, ct2, pf, pg)
+    if r == -2:
+        raise AssertionError("packed TENO-D lanes disagree")
     if r < 0:
         raise ValueError("bad argument")
     return f, g, bool(r)

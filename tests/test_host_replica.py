@@ -59,6 +59,12 @@ def test_teno_matches_oracle(G):
         f32, g32, l32 = G.host_teno(q, "fp32")
         if l32 == large:
             assert np.allclose(f32, faces, rtol=0, atol=2e-5 * (1 + abs(q).max()))
+            # packed-pair selection of the float32 2-D sweep (lanes checked
+            # against each other inside): the same choice, float32 values
+            _, gp2, lp2 = G.host_teno(q, "fp32x2")
+            assert lp2 == l32, q
+            assert np.allclose(gp2, g32, rtol=0, atol=2e-5 * (1 + abs(q).max())), q
+            assert np.allclose(gp2, gauss, rtol=0, atol=2e-5 * (1 + abs(q).max())), q
 
 
 def _state(dim, rng, rho=None):
@@ -74,7 +80,8 @@ def _state(dim, rng, rho=None):
 def test_point_flux_matches_oracle(G, dim, tau, Pr):
     """F and dF/dt of one point: the device arithmetic (closed-form slopes,
     folded time coefficients) against the oracle (moment-matrix solves,
-    F(dt) and F(dt/2) combined as Sec. 2.2 prints)."""
+    F(dt) and F(dt/2) combined as Sec. 2.2 prints); float32 within float32
+    bounds."""
     rng = np.random.default_rng(7 + dim)
     P = O.make_problem(dim, 8, 8, tau=tau, mu=0.02, Pr=Pr)
     sl = [0, 1, 2, 3] if dim == 2 else [0, 1, 3]
@@ -101,6 +108,9 @@ def test_point_flux_matches_oracle(G, dim, tau, Pr):
         F32, dF32 = G.host_point_flux(dim, Wl, Wln, Wlt, Wr, Wrn, Wrt, dt, precision="fp32", tau=tau,
                                       mu=0.02, Pr=Pr)
         assert np.allclose(F32[sl], Fo, rtol=0, atol=3e-6 * scale)
+        # dF/dt in float32 within 2e-5 of the largest float64 component
+        # (measured up to 8e-6)
+        assert np.abs(dF32 - dF).max() <= 2e-5 * np.abs(dF).max()
 
 
 def test_weno_ao_matches_oracle(G):
