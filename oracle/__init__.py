@@ -39,18 +39,20 @@ class Problem(C.Structure):
         ("ct1", C.c_double), ("ct2", C.c_double), ("ct1_t", C.c_double), ("ct2_t", C.c_double),
         ("positivity_fallback", C.c_int),
         ("recon", C.c_int), ("d_hi", C.c_double), ("d_lo", C.c_double), ("eps_ao", C.c_double),
+        ("merge", C.c_int),
     ]
 
 
 BC = {"periodic": 0, "zerograd": 1, "symmetry": 2, "noslip": 3, "reflect": 4}
 TAU = {"zero": 0, "euler": 1, "ns": 2}
 RECON = {"teno_d": 0, "weno_ao": 1}
+MERGE = {"kinetic": 0, "average": 1}
 
 
 def make_problem(dim, nx, ny=1, *, lx=1.0, ly=1.0, bc=("zerograd",) * 4, gamma=1.4, mu=0.0, Pr=1.0,
                  tau="euler", c1=0.01, c2=1.0, cfl=0.5, eps=1e-40, q=7.0, ct1=1e-7, ct2=1e-5,
                  ct1_t=None, ct2_t=None, positivity_fallback=1, recon="teno_d", d_hi=0.85, d_lo=0.85,
-                 eps_ao=1e-8) -> Problem:
+                 eps_ao=1e-8, merge="kinetic") -> Problem:
     p = Problem()
     p.dim, p.nx, p.ny = dim, nx, (ny if dim == 2 else 1)
     p.dx = lx / nx
@@ -67,6 +69,7 @@ def make_problem(dim, nx, ny=1, *, lx=1.0, ly=1.0, bc=("zerograd",) * 4, gamma=1
     p.positivity_fallback = positivity_fallback
     p.recon = RECON[recon] if isinstance(recon, str) else int(recon)
     p.d_hi, p.d_lo, p.eps_ao = d_hi, d_lo, eps_ao
+    p.merge = MERGE[merge] if isinstance(merge, str) else int(merge)
     return p
 
 

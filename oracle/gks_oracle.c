@@ -602,6 +602,14 @@ int or_flux_point(const or_problem *P,
     moment_apsi(dim, &mlp, 0, 0, al_t, tl);
     moment_apsi(dim, &mrm, 0, 0, ar_t, tr);
     for (int k = 0; k < nv; ++k) W0t[k] = rl * tl[k] + rr * tr[k];
+    if (P->merge == OR_MERGE_AVERAGE) {
+        /* Sec. 3.2: arithmetic averaging of the two sides, for smooth flow */
+        for (int k = 0; k < nv; ++k) {
+            W0[k] = 0.5 * (Wl[k] + Wr[k]);
+            W0n[k] = 0.5 * (Wln[k] + Wrn[k]);
+            W0t[k] = 0.5 * (Wlt[k] + Wrt[k]);
+        }
+    }
 
     double r0, U0, V0, lam0, p0;
     if (primitives(dim, gamma, W0, &r0, &U0, &V0, &lam0, &p0)) return -1;

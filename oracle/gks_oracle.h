@@ -49,9 +49,13 @@ typedef struct {
     int recon;            /* OR_RECON_*: TENO-D (Sec. 4.2) or WENO5-AO (Sec. 3.2) */
     double d_hi, d_lo;    /* WENO5-AO linear-weight parameters d_Hi, d_Lo */
     double eps_ao;        /* WENO5-AO epsilon of Eq. (3.5) */
+    int merge;            /* OR_MERGE_*: equilibrium state at the interface */
 } or_problem;
 
 enum { OR_RECON_TENO_D = 0, OR_RECON_WENO_AO = 1 };
+/* kinetic weighting of Eqs. (3.25)-(3.26), or the arithmetic average of the
+ * two sides that Sec. 3.2 allows for smooth flow */
+enum { OR_MERGE_KINETIC = 0, OR_MERGE_AVERAGE = 1 };
 
 /* ---- reconstruction primitives (Sec. 3.1, 3.2, 4.2) ---- */
 /* n x n matrix (row-major) mapping cell averages at integer offsets to the

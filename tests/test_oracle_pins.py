@@ -609,3 +609,74 @@ def test_blast_wave_fine_reference_conserves_mass():
     assert ref.shape == (1600,)
     assert ref.mean() == pytest.approx(1.0, rel=1e-12)
     assert ref.min() > 0
+
+
+# ---------------------------------------------------------------- arithmetic-average merge
+def _euler_flux(W, gamma, dim):
+    r, mu = W[0], W[1]
+    mv = W[2] if dim == 2 else 0.0
+    E = W[-1]
+    p = (gamma - 1.0) * (E - 0.5 * (mu * mu + mv * mv) / r)
+    U = mu / r
+    F = [mu, mu * U + p] + ([mv * U] if dim == 2 else []) + [U * (E + p)]
+    return np.array(F)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_average_merge_collision_free_flux_is_euler_flux_of_the_mean(dim):
+    """Sec. 3.2's arithmetic-average merge with tau = 0 and zero slopes: g is
+    the Maxwellian of W0 = (W_l + W_r)/2 at all times, so the time-integrated
+    flux over dt is dt times the Euler flux of the mean state (closed form)."""
+    rng = np.random.default_rng(31 + dim)
+    P = O.make_problem(dim, 8, 8, tau="zero", merge="average")
+    nv = dim + 2
+    for _ in range(10):
+        Wl, Wr = (_uniform(dim, np.exp(rng.uniform(-0.5, 0.5)), rng.uniform(-0.7, 0.7),
+                           rng.uniform(-0.7, 0.7) if dim == 2 else 0.0, np.exp(rng.uniform(-0.5, 0.5)))
+                  for _ in range(2))
+        z = np.zeros(nv)
+        dt = 1e-3
+        Fd, Fh, rc = O.flux_point(P, Wl, z, z if dim == 2 else None, Wr, z, z if dim == 2 else None, dt)
+        assert rc == 0
+        want = _euler_flux(0.5 * (Wl + Wr), 1.4, dim)
+        assert np.allclose(Fd / dt, want, rtol=1e-13, atol=1e-13 * abs(want).max())
+        assert np.allclose(Fh / (dt / 2), want, rtol=1e-13, atol=1e-13 * abs(want).max())
+
+
+@pytest.mark.parametrize("tau", ["zero", "euler", "ns"])
+def test_average_merge_equals_kinetic_merge_for_equal_sides(tau):
+    """With identical left and right states and slopes the kinetic weighting
+    of Eqs. (3.25)-(3.26) returns that state (the two half spaces add up to
+    the full space), so both merges give the same flux."""
+    rng = np.random.default_rng(5)
+    Pk = O.make_problem(2, 8, 8, tau=tau, mu=0.01)
+    Pa = O.make_problem(2, 8, 8, tau=tau, mu=0.01, merge="average")
+    for _ in range(8):
+        W = _uniform(2, np.exp(rng.uniform(-0.5, 0.5)), *rng.uniform(-0.7, 0.7, 2), np.exp(rng.uniform(-0.5, 0.5)))
+        Wn, Wt = 0.2 * rng.normal(size=4), 0.2 * rng.normal(size=4)
+        Fk, Hk, rk = O.flux_point(Pk, W, Wn, Wt, W, Wn, Wt, 1e-3)
+        Fa, Ha, ra = O.flux_point(Pa, W, Wn, Wt, W, Wn, Wt, 1e-3)
+        assert rk == ra == 0
+        assert np.allclose(Fa, Fk, rtol=1e-12, atol=1e-14)
+        assert np.allclose(Ha, Hk, rtol=1e-12, atol=1e-14)
+
+
+def test_average_merge_fifth_order_on_smooth_advection():
+    """Sec. 5.1 advection with the arithmetic-average merge: the scheme stays
+    fifth order (measured orders 5.8, 5.6, 5.3 from 10 to 80 cells, each
+    refinement at least 4.8) and more accurate than the kinetic merge at
+    every grid (measured 2.6-9x smaller L1 error)."""
+    got = {}
+    for merge in ("kinetic", "average"):
+        for n in (10, 20, 40, 80):
+            s = WL.advection_1d(n)
+            P = O.make_problem(1, n, merge=merge, **s.problem_kwargs())
+            W = s.W.copy()
+            dt = 0.2 * s.dx
+            for _ in range(int(round(2.0 / dt))):
+                W = O.step(P, W, dt)
+            got[merge, n] = np.mean(abs(W[0, 0] - WL.advection_1d_exact_rho(n, 2.0)))
+    for a, b in ((10, 20), (20, 40), (40, 80)):
+        assert np.log2(got["average", a] / got["average", b]) >= 4.8
+    for n in (10, 20, 40, 80):
+        assert got["average", n] < got["kinetic", n]
