@@ -93,6 +93,7 @@ typedef struct {
     int recon;               /* gks_recon: TENO-D (default) or WENO5-AO */
     double d_hi, d_lo;       /* WENO5-AO linear-weight parameters (Sec. 3.2; default 0.85, 0.85) */
     double eps_ao;           /* WENO5-AO epsilon (default 1e-8) */
+    int merge;               /* gks_merge: equilibrium state at the interface (default kinetic) */
 } gks_scheme;
 
 /* Reconstruction of the non-equilibrium states (values and slopes at the
@@ -103,6 +104,16 @@ typedef struct {
  * (1-d_hi)(1-d_lo)/2.  Batches and the adjoint take TENO-D only
  * (GKS_EUNSUPPORTED otherwise). */
 typedef enum { GKS_RECON_TENO_D = 0, GKS_RECON_WENO_AO = 1 } gks_recon;
+
+/* Equilibrium state W0 and its slopes at an interface point (Sec. 3.2):
+ * the kinetic weighting of Eqs. (3.25)-(3.26) (W0 = rho_l <psi>_{u>0} +
+ * rho_r <psi>_{u<0}, likewise for the slopes; the paper's scheme), or the
+ * arithmetic average of the two reconstructed sides, W0 = (W_l + W_r)/2,
+ * W0_n = (W_l,n + W_r,n)/2, W0_t = (W_l,t + W_r,t)/2, which the paper allows
+ * for smooth flow.  The non-equilibrium terms are the same either way.  The
+ * adjoint takes the kinetic merge only (GKS_EUNSUPPORTED otherwise);
+ * gks_step1d_noalloc always uses the kinetic merge. */
+typedef enum { GKS_MERGE_KINETIC = 0, GKS_MERGE_AVERAGE = 1 } gks_merge;
 
 typedef struct {
     unsigned int error_word; /* bit 0: non-physical state after an update; bit 1: fallback failed */

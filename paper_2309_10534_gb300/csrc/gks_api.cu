@@ -94,6 +94,7 @@ HostFlux host_flux(const gks_ctx* c)
     h.mu = c->gas.mu;
     h.prfac = (c->sch.tau_mode == GKS_TAU_NS) ? 1.0 / c->gas.Pr - 1.0 : 0.0;
     h.tau_mode = c->sch.tau_mode;
+    h.merge = c->sch.merge;
     return h;
 }
 
@@ -472,6 +473,7 @@ gks_status gks_create(const gks_grid_desc* d, gks_ctx** out)
     c->sch.recon = GKS_RECON_TENO_D;
     c->sch.d_hi = c->sch.d_lo = 0.85;
     c->sch.eps_ao = 1e-8;
+    c->sch.merge = GKS_MERGE_KINETIC;
 
     GridDev& g = c->g;
     g.dim = d->dim;
@@ -573,6 +575,8 @@ gks_status gks_set_scheme(gks_ctx* c, const gks_scheme* s)
         (s->recon == GKS_RECON_WENO_AO && (!(s->d_hi > 0.0 && s->d_hi <= 1.0) || !(s->d_lo >= 0.0 && s->d_lo <= 1.0) ||
                                            !(s->eps_ao > 0.0))))
         return fail(c, GKS_EINVAL, "reconstruction parameters out of range");
+    if (s->merge != GKS_MERGE_KINETIC && s->merge != GKS_MERGE_AVERAGE)
+        return fail(c, GKS_EINVAL, "merge must be GKS_MERGE_KINETIC or GKS_MERGE_AVERAGE");
     if (!s->positivity_fallback)
         return fail(c, GKS_EUNSUPPORTED, "the kernels always apply the positivity fallback");
     c->sch = *s;

@@ -629,6 +629,7 @@ template <typename T> struct FluxParams {
     T c1, c2, mu; // collision time (Sec. 5)
     T prfac;      // 1/Pr - 1
     int tau_mode; // 0 zero, 1 Euler, 2 NS
+    int merge = 0; // 0 kinetic weighting (Eqs. 3.25, 3.26), 1 arithmetic average of the sides
 };
 
 template <typename T> struct Side {  // one reconstructed side (local frame, 4 slots; 1-D slot 2 = 0)
@@ -754,6 +755,16 @@ GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& 
     T pl, pr;
     side_terms<T, DIM, NONEQ, PRFIX>(L, true, P, W0, W0n, W0t, S3, S4, S5, N4, N5, pl);
     side_terms<T, DIM, NONEQ, PRFIX>(R, false, P, W0, W0n, W0t, S3, S4, S5, N4, N5, pr);
+    if (P.merge == 1) {
+        // arithmetic average of the two sides in place of the kinetic
+        // weighting (Sec. 3.2, for smooth flow); the side terms stay
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            W0[i] = T(0.5) * (L.W[i] + R.W[i]);
+            W0n[i] = T(0.5) * (L.Wn[i] + R.Wn[i]);
+            W0t[i] = T(0.5) * (L.Wt[i] + R.Wt[i]);
+        }
+    }
 
     // equilibrium state g0: rho0 <u psi>_0 is the Euler flux of W0 and
     // rho0 <u A0 psi>_0 = (dF/dW) W0_time with W0_time = rho0 <A0 psi>_0 from

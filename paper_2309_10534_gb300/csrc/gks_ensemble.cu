@@ -401,6 +401,7 @@ HostFlux host_flux_1d(const gks_batch* b)
     h.mu = b->gas.mu;
     h.prfac = (b->sch.tau_mode == GKS_TAU_NS) ? 1.0 / b->gas.Pr - 1.0 : 0.0;
     h.tau_mode = b->sch.tau_mode;
+    h.merge = b->sch.merge;
     return h;
 }
 
@@ -603,6 +604,8 @@ gks_status gks_batch_set_scheme(gks_batch* b, const gks_scheme* s)
         return bfail(b, GKS_EINVAL, "scheme parameters out of range");
     if (!s->positivity_fallback) return bfail(b, GKS_EUNSUPPORTED, "the kernels always apply the positivity fallback");
     if (s->recon != GKS_RECON_TENO_D) return bfail(b, GKS_EUNSUPPORTED, "batches reconstruct with TENO-D only");
+    if (s->merge != GKS_MERGE_KINETIC && s->merge != GKS_MERGE_AVERAGE)
+        return bfail(b, GKS_EINVAL, "merge must be GKS_MERGE_KINETIC or GKS_MERGE_AVERAGE");
     b->sch = *s;
     ++b->version;
     return GKS_OK;

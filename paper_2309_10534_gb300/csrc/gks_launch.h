@@ -20,6 +20,7 @@ constexpr int STAGE1D_TN = 127;
 struct HostFlux {
     double gamma, K, ntot, c1, c2, mu, prfac;
     int tau_mode;
+    int merge = 0;
 };
 
 cudaError_t launch_sweep_f32(const GridDev& g, const SweepArgs& a, const HostFlux& hf, const TenoParams& tn,
@@ -47,6 +48,7 @@ inline FluxParams<T> make_flux_params(const HostFlux& h)
     p.mu = (T)h.mu;
     p.prfac = (T)h.prfac;
     p.tau_mode = h.tau_mode;
+    p.merge = h.merge;
     return p;
 }
 

@@ -19,6 +19,7 @@ BC = {"periodic": 0, "zerograd": 1, "symmetry": 2, "noslip": 3, "reflect": 4}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32x2": 2}
 TAU = {"zero": 0, "euler": 1, "ns": 2}
 RECON = {"teno_d": 0, "weno_ao": 1}
+MERGE = {"kinetic": 0, "average": 1}
 
 
 class GridDesc(C.Structure):
@@ -36,7 +37,7 @@ class Scheme(C.Structure):
                 ("ct1", C.c_double), ("ct2", C.c_double), ("ct1_t", C.c_double), ("ct2_t", C.c_double),
                 ("eps", C.c_double), ("q", C.c_int), ("tau_mode", C.c_int),
                 ("positivity_fallback", C.c_int), ("recon", C.c_int), ("d_hi", C.c_double),
-                ("d_lo", C.c_double), ("eps_ao", C.c_double)]
+                ("d_lo", C.c_double), ("eps_ao", C.c_double), ("merge", C.c_int)]
 
 
 class Diag(C.Structure):
@@ -106,13 +107,16 @@ def _status_string(s):
 
 def default_scheme(**kw) -> Scheme:
     s = Scheme(cfl=0.5, c1=0.01, c2=1.0, ct1=1e-7, ct2=1e-5, ct1_t=1e-7, ct2_t=1e-5, eps=1e-40, q=7,
-               tau_mode=TAU["euler"], positivity_fallback=1, recon=0, d_hi=0.85, d_lo=0.85, eps_ao=1e-8)
+               tau_mode=TAU["euler"], positivity_fallback=1, recon=0, d_hi=0.85, d_lo=0.85, eps_ao=1e-8,
+               merge=0)
     for k, v in kw.items():
         if k == "tau" or k == "tau_mode":
             v = TAU[v] if isinstance(v, str) else int(v)
             k = "tau_mode"
         if k == "recon":
             v = RECON[v] if isinstance(v, str) else int(v)
+        if k == "merge":
+            v = MERGE[v] if isinstance(v, str) else int(v)
         setattr(s, k, v)
     if "ct1" in kw and "ct1_t" not in kw:
         s.ct1_t = kw["ct1"]
