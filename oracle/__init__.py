@@ -39,20 +39,20 @@ class Problem(C.Structure):
         ("ct1", C.c_double), ("ct2", C.c_double), ("ct1_t", C.c_double), ("ct2_t", C.c_double),
         ("positivity_fallback", C.c_int),
         ("recon", C.c_int), ("d_hi", C.c_double), ("d_lo", C.c_double), ("eps_ao", C.c_double),
-        ("merge", C.c_int),
+        ("merge", C.c_int), ("zpow", C.c_double),
     ]
 
 
 BC = {"periodic": 0, "zerograd": 1, "symmetry": 2, "noslip": 3, "reflect": 4}
 TAU = {"zero": 0, "euler": 1, "ns": 2}
-RECON = {"teno_d": 0, "weno_ao": 1}
+RECON = {"teno_d": 0, "weno_ao": 1, "weno_z": 2, "teno5": 3}
 MERGE = {"kinetic": 0, "average": 1}
 
 
 def make_problem(dim, nx, ny=1, *, lx=1.0, ly=1.0, bc=("zerograd",) * 4, gamma=1.4, mu=0.0, Pr=1.0,
-                 tau="euler", c1=0.01, c2=1.0, cfl=0.5, eps=1e-40, q=7.0, ct1=1e-7, ct2=1e-5,
+                 tau="euler", c1=0.01, c2=1.0, cfl=0.5, eps=1e-40, q=None, ct1=1e-7, ct2=1e-5,
                  ct1_t=None, ct2_t=None, positivity_fallback=1, recon="teno_d", d_hi=0.85, d_lo=0.85,
-                 eps_ao=1e-8, merge="kinetic") -> Problem:
+                 eps_ao=1e-8, merge="kinetic", zpow=1.0) -> Problem:
     p = Problem()
     p.dim, p.nx, p.ny = dim, nx, (ny if dim == 2 else 1)
     p.dx = lx / nx
@@ -63,6 +63,8 @@ def make_problem(dim, nx, ny=1, *, lx=1.0, ly=1.0, bc=("zerograd",) * 4, gamma=1
     p.gamma, p.mu, p.Pr = gamma, mu, Pr
     p.tau_mode = TAU[tau] if isinstance(tau, str) else int(tau)
     p.c1, p.c2, p.cfl = c1, c2, cfl
+    if q is None:  # TENO-D: q = 7 (Eq. 4.5); TENO5: q = 6 (Eq. 4.1)
+        q = 6.0 if recon in ("teno5", 3) else 7.0
     p.eps, p.qpow, p.ct1, p.ct2 = eps, q, ct1, ct2
     p.ct1_t = ct1 if ct1_t is None else ct1_t
     p.ct2_t = ct2 if ct2_t is None else ct2_t
@@ -70,6 +72,7 @@ def make_problem(dim, nx, ny=1, *, lx=1.0, ly=1.0, bc=("zerograd",) * 4, gamma=1
     p.recon = RECON[recon] if isinstance(recon, str) else int(recon)
     p.d_hi, p.d_lo, p.eps_ao = d_hi, d_lo, eps_ao
     p.merge = MERGE[merge] if isinstance(merge, str) else int(merge)
+    p.zpow = zpow
     return p
 
 
@@ -92,6 +95,10 @@ def _declare(L):
     L.or_teno_d.restype = C.c_int
     L.or_weno_ao.argtypes = [_dp, C.c_double, C.c_double, C.c_double, C.c_int, _dp, _dp, _dp, _dp]
     L.or_weno_ao.restype = None
+    L.or_weno3.argtypes = [_dp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, _dp, _dp, _dp]
+    L.or_weno3.restype = C.c_int
+    L.or_recon_faces.argtypes = [C.POINTER(Problem), _dp, _dp]
+    L.or_recon_faces.restype = C.c_int
     L.or_moments_u.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int, _dp]
     L.or_moments_u.restype = None
     L.or_micro_slope.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, _dp, _dp]
@@ -166,6 +173,29 @@ def weno_ao(q5, xs, eps=1e-8, d_hi=0.85, d_lo=0.85):
     wbar = np.zeros(4)
     lib().or_weno_ao(_d(q5), eps, d_hi, d_lo, len(xs), _d(xs), _d(val), _d(dval), _d(wbar))
     return val, dval, wbar
+
+
+def weno3(q5, xs, teno5=False, eps=None, zpow=1.0, q=6.0, ct=1e-7):
+    """WENO5-Z (Sec. 3.1) or TENO5 (Sec. 4.1) values of five cell averages at
+    the points xs; returns (val, wbar[3] at the last point)."""
+    q5 = _f64(q5)
+    xs = _f64(np.atleast_1d(xs))
+    if eps is None:
+        eps = 1e-40 if teno5 else 1e-8
+    val = np.zeros(len(xs))
+    wbar = np.zeros(3)
+    if lib().or_weno3(_d(q5), int(bool(teno5)), eps, zpow, q, ct, len(xs), _d(xs), _d(val), _d(wbar)):
+        raise ValueError("no linear weights at these points")
+    return val, wbar
+
+
+def recon_faces(P: Problem, q5):
+    """The problem's normal reconstruction of one cell: (v(+1/2), dv/dxi(+1/2),
+    v(-1/2), dv/dxi(-1/2))."""
+    q5 = _f64(q5)
+    out = np.zeros(4)
+    lib().or_recon_faces(C.byref(P), _d(q5), _d(out))
+    return out
 
 
 def moments_u(U, lam, half=0, nmax=6):

@@ -297,6 +297,77 @@ void or_weno_ao(const double *q5, double eps, double d_hi, double d_lo, int n, c
     }
 }
 
+/* WENO5-Z (Sec. 3.1) and TENO5 (Sec. 4.1) values.  The linear weights at xi
+ * follow from their definition, sum_k d_k p_k(xi) = p_3(xi) for all data:
+ * Qbar_{i-2} enters only p_0 and Qbar_{i+2} only p_2, which fixes d_0 and
+ * d_2, and d_1 = 1 - d_0 - d_2 (every p_k reproduces constants); the other
+ * coefficients are checked.  At xi = 1/2 this gives (0.1, 0.6, 0.3). */
+int or_weno3(const double *q5, int teno5, double eps, double zpow, double q, double ct, int n,
+             const double *xs, double *val, double *wbar)
+{
+    init_fits();
+    double c3[3][3], beta[3], d5[5];
+    const double qc = q5[2];
+    for (int s = 0; s < 5; ++s) d5[s] = q5[s] - qc;
+    for (int k = 0; k < 3; ++k) {
+        apply_fit(3, FIT3[k], d5 + k, c3[k]);
+        beta[k] = or_beta(2, c3[k]);
+        c3[k][0] += qc;
+    }
+    const double tau = fabs(beta[0] - beta[2]);
+    for (int e = 0; e < n; ++e) {
+        const double xi = xs[e];
+        /* a[k][j]: weight of Qbar_{i-2+k+j} in p_k(xi); A[s]: of Qbar_{i-2+s} in p_3(xi) */
+        double a[3][3], A[5], pw[5];
+        pw[0] = 1.0;
+        for (int m = 1; m < 5; ++m) pw[m] = pw[m - 1] * xi;
+        for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < 3; ++j) {
+                a[k][j] = 0.0;
+                for (int m = 0; m < 3; ++m) a[k][j] += FIT3[k][m * 3 + j] * pw[m];
+            }
+        for (int s = 0; s < 5; ++s) {
+            A[s] = 0.0;
+            for (int m = 0; m < 5; ++m) A[s] += FIT5[m * 5 + s] * pw[m];
+        }
+        double d[3];
+        d[0] = A[0] / a[0][0];
+        d[2] = A[4] / a[2][2];
+        d[1] = 1.0 - d[0] - d[2];
+        for (int s = 0; s < 5; ++s) {  /* the identity must hold for every Qbar */
+            double lhs = 0.0;
+            for (int k = 0; k < 3; ++k)
+                if (s - k >= 0 && s - k < 3) lhs += d[k] * a[k][s - k];
+            if (fabs(lhs - A[s]) > 1e-12) return -1;
+        }
+        double w[3], sum = 0.0;
+        if (!teno5) {
+            for (int k = 0; k < 3; ++k) {
+                w[k] = d[k] * (1.0 + pow(tau / (beta[k] + eps), zpow));
+                sum += w[k];
+            }
+            for (int k = 0; k < 3; ++k) w[k] /= sum;
+        } else {
+            double g[3], gs = 0.0, ds = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                g[k] = pow(1.0 + tau / (beta[k] + eps), q);
+                gs += g[k];
+            }
+            for (int k = 0; k < 3; ++k) {
+                w[k] = (g[k] / gs < ct) ? 0.0 : d[k];
+                ds += w[k];
+            }
+            for (int k = 0; k < 3; ++k) w[k] /= ds;
+        }
+        double v = 0.0;
+        for (int k = 0; k < 3; ++k) v += w[k] * or_poly_eval(2, c3[k], xi);
+        val[e] = v;
+        if (wbar)
+            for (int k = 0; k < 3; ++k) wbar[k] = w[k];
+    }
+    return 0;
+}
+
 /* the scheme's 5-cell reconstruction (TENO-D or WENO5-AO) at the points xs */
 static void recon5(const or_problem *P, const double *q5, int tangential, int n, const double *xs, double *val,
                    double *dval)
@@ -305,8 +376,32 @@ static void recon5(const or_problem *P, const double *q5, int tangential, int n,
         or_weno_ao(q5, P->eps_ao, P->d_hi, P->d_lo, n, xs, val, dval, NULL);
         return;
     }
+    if (P->recon == OR_RECON_WENO_Z || P->recon == OR_RECON_TENO5) {
+        /* face values of the cell (xi = +1/2: left state of its right face;
+         * -1/2: right state of its left face) and the slopes of the quadratic
+         * with the cell's average and these two values, Eq. (3.11) */
+        const double faces[2] = {0.5, -0.5};
+        double fv[2];
+        const int t5 = P->recon == OR_RECON_TENO5;
+        or_weno3(q5, t5, t5 ? P->eps : P->eps_ao, P->zpow, P->qpow, P->ct1, 2, faces, fv, NULL);
+        const double vp = fv[0], vm = fv[1];
+        for (int e = 0; e < n; ++e) {
+            if (xs[e] > 0.0) { val[e] = vp; dval[e] = 2.0 * (vm + 2.0 * vp - 3.0 * q5[2]); }
+            else { val[e] = vm; dval[e] = -2.0 * (2.0 * vm + vp - 3.0 * q5[2]); }
+        }
+        (void)tangential;
+        return;
+    }
     or_teno_d(q5, P->eps, P->qpow, tangential ? P->ct1_t : P->ct1, tangential ? P->ct2_t : P->ct2, n, xs, val, dval,
               NULL);
+}
+
+int or_recon_faces(const or_problem *P, const double *q5, double *out)
+{
+    const double xp = 0.5, xm = -0.5;
+    recon5(P, q5, 0, 1, &xp, &out[0], &out[1]);
+    recon5(P, q5, 0, 1, &xm, &out[2], &out[3]);
+    return 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -551,6 +646,15 @@ int or_flux_point(const or_problem *P,
                   const double *Wcl, const double *Wcr,
                   double dt, double *Fdt, double *Fhalf)
 {
+    return or_flux_point_eq(P, Wl_in, Wln_in, Wlt_in, Wr_in, Wrn_in, Wrt_in, Wcl, Wcr, NULL, dt, Fdt, Fhalf);
+}
+
+int or_flux_point_eq(const or_problem *P,
+                     const double *Wl_in, const double *Wln_in, const double *Wlt_in,
+                     const double *Wr_in, const double *Wrn_in, const double *Wrt_in,
+                     const double *Wcl, const double *Wcr, const double *W0n_lin,
+                     double dt, double *Fdt, double *Fhalf)
+{
     const int dim = P->dim, nv = dim + 2;
     const double gamma = P->gamma, K = internal_dof(dim, gamma);
     double Wl[4], Wln[4], Wlt[4], Wr[4], Wrn[4], Wrt[4];
@@ -610,6 +714,8 @@ int or_flux_point(const or_problem *P,
             W0t[k] = 0.5 * (Wlt[k] + Wrt[k]);
         }
     }
+    if (W0n_lin) /* conventional path: the equilibrium slope by Eq. (3.12) */
+        for (int k = 0; k < nv; ++k) W0n[k] = W0n_lin[k];
 
     double r0, U0, V0, lam0, p0;
     if (primitives(dim, gamma, W0, &r0, &U0, &V0, &lam0, &p0)) return -1;
@@ -814,13 +920,24 @@ static int face_flux(const or_problem *P, const grid_t *g, const double *Wg, int
 
     for (int k = 0; k < nv; ++k) { Fdt[k] = 0.0; Fhalf[k] = 0.0; }
     if (dim == 1) {
-        double fd[4], fh[4];
-        int rc = or_flux_point(P, lv[0], lx[0], NULL, rv[0], rx[0], NULL, Wcl, Wcr, dt, fd, fh);
+        double fd[4], fh[4], w0n[4];
+        const int conv = P->recon == OR_RECON_WENO_Z || P->recon == OR_RECON_TENO5;
+        if (conv) /* Eq. (3.12) from the cell averages i-1 .. i+2 around the face */
+            for (int v = 0; v < nv; ++v) {
+                const double qm1 = Wg[GIDX(*g, v, jc, ic - 1)], q0 = Wg[GIDX(*g, v, jc, ic)];
+                const double q1 = Wg[GIDX(*g, v, jc, ic + 1)], q2 = Wg[GIDX(*g, v, jc, ic + 2)];
+                w0n[v] = (-(q2 - qm1) / 12.0 + 1.25 * (q1 - q0)) / hn;
+            }
+        int rc = or_flux_point_eq(P, lv[0], lx[0], NULL, rv[0], rx[0], NULL, Wcl, Wcr, conv ? w0n : NULL, dt, fd,
+                                  fh);
         if (rc < 0) return -1;
         if (rc > 0 && nfb) ++*nfb;
         for (int k = 0; k < nv; ++k) { Fdt[k] = fd[k]; Fhalf[k] = fh[k]; }
         return 0;
     }
+
+    /* the conventional path (WENO5-Z / TENO5 GKS) is built in 1-D only */
+    if (P->recon == OR_RECON_WENO_Z || P->recon == OR_RECON_TENO5) return -1;
 
     /* step 2: tangential TENO-D to the two Gauss points */
     const double xg[2] = {-0.5 / sqrt(3.0), 0.5 / sqrt(3.0)};

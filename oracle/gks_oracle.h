@@ -50,9 +50,13 @@ typedef struct {
     double d_hi, d_lo;    /* WENO5-AO linear-weight parameters d_Hi, d_Lo */
     double eps_ao;        /* WENO5-AO epsilon of Eq. (3.5) */
     int merge;            /* OR_MERGE_*: equilibrium state at the interface */
+    double zpow;          /* WENO5-Z exponent of tau/(beta+eps) in Eq. (3.5) */
 } or_problem;
 
-enum { OR_RECON_TENO_D = 0, OR_RECON_WENO_AO = 1 };
+/* TENO-D (Sec. 4.2), WENO5-AO (Sec. 3.2), and the conventional path
+ * (Sec. 3.1, 4.1; 1-D only): WENO5-Z or TENO5 face values, slopes from the
+ * quadratic of Eq. (3.11), equilibrium slope from the linear Eq. (3.12) */
+enum { OR_RECON_TENO_D = 0, OR_RECON_WENO_AO = 1, OR_RECON_WENO_Z = 2, OR_RECON_TENO5 = 3 };
 /* kinetic weighting of Eqs. (3.25)-(3.26), or the arithmetic average of the
  * two sides that Sec. 3.2 allows for smooth flow */
 enum { OR_MERGE_KINETIC = 0, OR_MERGE_AVERAGE = 1 };
@@ -92,11 +96,33 @@ void   or_time_coeffs(double delta, double tau, double *q);
  * variables and their normal / tangential derivatives on both sides.
  * Returns 1 when the positivity fallback replaced a side, else 0;
  * -1 on a non-physical state that the fallback could not fix. */
+/* WENO5-Z (Sec. 3.1, Eqs. 3.5-3.9) or TENO5 (Sec. 4.1, Eqs. 4.1-4.4) value of
+ * the five cell averages q5 = Qbar_{i-2..i+2} at the points xs[0..n-1]
+ * (xi = (x - x_i)/dx): the three quadratics p_k blended with weights built
+ * on the linear weights d_k(xi) that combine them into the quartic at xi.
+ * teno5 = 0: WENO-Z, omega_k = d_k (1 + (tau/(beta_k+eps))^zpow) normalised,
+ * tau = |beta_0 - beta_2|; teno5 = 1: gamma_k = (1 + tau/(beta_k+eps))^q,
+ * chi_k = gamma_k / sum gamma, delta_k = [chi_k >= ct], omega_k = d_k delta_k
+ * normalised.  wbar (optional) receives the weights at the last point.
+ * Returns 0, or -1 if xs admits no linear weights. */
+int    or_weno3(const double *q5, int teno5, double eps, double zpow, double q, double ct, int n,
+                const double *xs, double *val, double *wbar);
+/* the problem's normal reconstruction of one cell's five averages q5:
+ * out = (value, xi-derivative at xi = +1/2, value, xi-derivative at -1/2) */
+int    or_recon_faces(const or_problem *P, const double *q5, double *out);
 int    or_flux_point(const or_problem *P,
                      const double *Wl, const double *Wln, const double *Wlt,
                      const double *Wr, const double *Wrn, const double *Wrt,
                      const double *Wcl, const double *Wcr,
                      double dt, double *Fdt, double *Fhalf);
+/* the same with the equilibrium normal slope W0_n given (the conventional
+ * path's Eq. 3.12) instead of the kinetic merge of the side slopes; NULL:
+ * or_flux_point */
+int    or_flux_point_eq(const or_problem *P,
+                        const double *Wl, const double *Wln, const double *Wlt,
+                        const double *Wr, const double *Wrn, const double *Wrt,
+                        const double *Wcl, const double *Wcr, const double *W0n_lin,
+                        double dt, double *Fdt, double *Fhalf);
 
 /* ---- solver (Sec. 2.2, 3.2, 5) ---- */
 /* W and Wout: interior SoA [nvar][ny][nx]; nvar = dim + 2 */
