@@ -17,7 +17,8 @@ library's event profiler for the roofline.
 Further legs on the same GPU, reported as objects of the same JSON line:
 "ensemble" (4096 independent 1-D Riemann problems of 200..4000 cells to
 t = 0.15 in one persistent launch, cell-updates/s), "weno_ao" (the main
-workload with the WENO5-AO reconstruction), "viscous" (Navier-Stokes
+workload with the WENO5-AO reconstruction), "recon_1d" (Sod's tube on 2^22
+cells with the TENO-D, WENO5-Z and TENO5 face reconstructions), "viscous" (Navier-Stokes
 viscous shock tube on 2048 x 1024, 200 steps from t = 0), "errors_vs_oracle"
 (both GPU paths against the FP64 oracle on the CPU baseline's sample) and
 "adjoint" (the
@@ -74,6 +75,8 @@ def parse():
                    help="omit the viscous shock tube leg")
     p.add_argument("--no-weno-ao", dest="weno_ao", action="store_false",
                    help="omit the WENO5-AO leg")
+    p.add_argument("--no-recon-1d", dest="recon_1d", action="store_false",
+                   help="omit the 1-D leg that times TENO-D, WENO5-Z and TENO5 face reconstructions")
     return p.parse_args()
 
 
@@ -315,6 +318,50 @@ def weno_ao_leg(gks, WL, stream, peak32, steps, warmup):
                          "unit": "TFLOP/s", "frac": tf / peak32, "launch_ms": launch_ms}}
 
 
+N_1D = 1 << 22
+
+
+def recon_1d_leg(gks, WL, stream, peak32, steps, warmup):
+    """The 1-D path with each face reconstruction: TENO-D (the paper's
+    scheme) and the conventional WENO5-Z and TENO5 GKS (Sec. 3.1, 4.1; face
+    values, slopes by Eq. 3.11, equilibrium slope by Eq. 3.12).  Workload:
+    Sod's tube on 2^22 cells (Euler tau), float32 flux, CFL steps, CUDA
+    events around each step, 256 MB L2 flush between steps; the stage
+    kernels timed by the library's event profiler for the roofline."""
+    import torch
+    s = WL.sod(N_1D)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=stream.device)
+    out = {}
+    for recon in ("teno_d", "weno_z", "teno5"):
+        S = gks.solver_for(s, "fp32", recon=recon)
+        S.set_stream(stream.cuda_stream)
+        for _ in range(warmup):
+            S.step(0.0)
+        torch.cuda.synchronize()
+        S.profile(True)
+        S.profile_read(0)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            S.step(0.0)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        S.diagnostics()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        sn, sms = S.profile_read(0)
+        S.profile(False)
+        S.close()
+        fm = gks.count_flops(1, "fp32", "euler", 1.0, recon=recon)
+        launch_ms = sms / max(sn, 1)
+        tf = fm["flops_per_cell_sweep"] * N_1D / (launch_ms * 1e-3) / 1e12
+        out[recon] = {"value": N_1D * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                      "flops_per_cell_update": fm["flops_per_cell_update"],
+                      "roofline": {"bound": "alu", "kernel": "k1d_stage<float, %s>" % recon, "achieved": tf,
+                                   "peak": peak32, "unit": "TFLOP/s", "frac": tf / peak32, "launch_ms": launch_ms}}
+    return {"workload": "sod_1d", "cells": N_1D, "steps": steps, "precision": "fp32", "by_recon": out}
+
+
 def viscous_leg(gks, WL, stream, precision, steps):
     """Navier-Stokes viscous shock tube (Re = 200, Pr = 0.73, no-slip walls,
     symmetric top) on 2048 x 1024: `steps` CFL steps from t = 0 (the full run
@@ -471,6 +518,7 @@ def main():
         launch = tuple(int(x) for x in args.ensemble_launch.split(",")) if args.ensemble_launch else None
         ens = ensemble_leg(gks, WL, stream, peak32, args.ensemble_max_steps, launch, rank, world, dist)
     ao = weno_ao_leg(gks, WL, stream, peak32, args.steps, args.warmup) if args.weno_ao else None
+    r1d = recon_1d_leg(gks, WL, stream, peak32, args.steps, args.warmup) if args.recon_1d else None
     visc = None
     if args.viscous:
         visc = viscous_leg(gks, WL, stream, "fp32", 200)
@@ -562,6 +610,8 @@ def main():
         line["ensemble"] = ens
     if ao:
         line["weno_ao"] = ao
+    if r1d:
+        line["recon_1d"] = r1d
     if visc:
         line["viscous"] = visc
     if adj:

@@ -86,13 +86,13 @@ typedef struct {
     double ct1, ct2;         /* TENO-D cut-offs C_T1, C_T2 normal to the face (Eqs. 4.7, 4.12) */
     double ct1_t, ct2_t;     /* cut-offs of the tangential (Gauss-point) reconstruction */
     double eps;              /* epsilon of Eq. (4.5) (default 1e-40; float32 path clamps to FLT_MIN) */
-    int q;                   /* power of Eq. (4.5), integer >= 1 (default 7) */
+    int q;                   /* power of Eq. (4.5), integer >= 1 (default 7); TENO5: of Eq. (4.1) */
     int tau_mode;            /* gks_tau_mode */
     int positivity_fallback; /* 1: a reconstructed point state with rho<=0 or p<=0 is replaced
                                 by the adjacent cell average with zero slopes (not in the paper) */
     int recon;               /* gks_recon: TENO-D (default) or WENO5-AO */
     double d_hi, d_lo;       /* WENO5-AO linear-weight parameters (Sec. 3.2; default 0.85, 0.85) */
-    double eps_ao;           /* WENO5-AO epsilon (default 1e-8) */
+    double eps_ao;           /* WENO5-AO and WENO5-Z epsilon (default 1e-8) */
     int merge;               /* gks_merge: equilibrium state at the interface (default kinetic) */
 } gks_scheme;
 
@@ -102,8 +102,16 @@ typedef struct {
  * weights gamma_k (1 + (tau/(beta_k+eps))^2) on the quartic and the three
  * quadratics, gamma_3 = d_hi, gamma_1 = (1-d_hi) d_lo, gamma_0 = gamma_2 =
  * (1-d_hi)(1-d_lo)/2.  Batches and the adjoint take TENO-D only
- * (GKS_EUNSUPPORTED otherwise). */
-typedef enum { GKS_RECON_TENO_D = 0, GKS_RECON_WENO_AO = 1 } gks_recon;
+ * (GKS_EUNSUPPORTED otherwise).
+ * WENO5-Z and TENO5 (Sec. 3.1, 4.1) are the paper's conventional path, on
+ * 1-D grids only (GKS_EUNSUPPORTED in 2-D): face values from the three
+ * quadratics with WENO-Z weights d_k (1 + tau/(beta_k + eps_ao)), tau =
+ * |beta_0 - beta_2| (Eq. 3.5), or TENO5 weights (Eqs. 4.1-4.4: power q, the
+ * paper's q = 6, cut-off ct1, epsilon eps); non-equilibrium slopes from the
+ * quadratic through the cell average and both face values (Eq. 3.11); the
+ * equilibrium state by the kinetic merge of the face values and its slope by
+ * the linear Eq. (3.12).  Set q = 6 for TENO5 (the default 7 is TENO-D's). */
+typedef enum { GKS_RECON_TENO_D = 0, GKS_RECON_WENO_AO = 1, GKS_RECON_WENO_Z = 2, GKS_RECON_TENO5 = 3 } gks_recon;
 
 /* Equilibrium state W0 and its slopes at an interface point (Sec. 3.2):
  * the kinetic weighting of Eqs. (3.25)-(3.26) (W0 = rho_l <psi>_{u>0} +

@@ -48,6 +48,12 @@ int gks_host_point_flux(int dim, int precision, int tau_mode, double gamma, doub
 int gks_host_weno_ao(int precision, const double *q, double eps_ao, double d_hi, double d_lo,
                      double *faces, double *gauss);
 
+/* The conventional path's face reconstruction (Sec. 3.1, 4.1) of five cell
+ * averages: WENO5-Z (teno5 = 0; eps the WENO epsilon of Eq. 3.5) or TENO5
+ * (teno5 = 1; eps, power qpow and cut-off ct of Eqs. 4.1-4.3); faces[0..3]
+ * = value and xi-slope (Eq. 3.11) at xi = +1/2, then at -1/2. */
+int gks_host_weno3(int precision, int teno5, const double *q, double eps, int qpow, double ct, double *faces);
+
 /* Transpose of TENO-D with the selection of q held fixed (the adjoint's
  * frozen selection; with it the reconstruction is linear in q): the
  * cotangents gfaces[0..3] of faces[] and ggauss[0..3] of gauss[] as in

@@ -571,10 +571,13 @@ gks_status gks_set_scheme(gks_ctx* c, const gks_scheme* s)
     if (!(s->cfl > 0.0) || s->q < 1 || s->q > 32 || !(s->eps >= 0.0) || !(s->ct1 >= 0.0) || !(s->ct2 >= 0.0) ||
         !(s->ct1_t >= 0.0) || !(s->ct2_t >= 0.0) || s->tau_mode < 0 || s->tau_mode > 2)
         return fail(c, GKS_EINVAL, "scheme parameters out of range");
-    if ((s->recon != GKS_RECON_TENO_D && s->recon != GKS_RECON_WENO_AO) ||
+    if (s->recon < GKS_RECON_TENO_D || s->recon > GKS_RECON_TENO5 ||
         (s->recon == GKS_RECON_WENO_AO && (!(s->d_hi > 0.0 && s->d_hi <= 1.0) || !(s->d_lo >= 0.0 && s->d_lo <= 1.0) ||
-                                           !(s->eps_ao > 0.0))))
+                                           !(s->eps_ao > 0.0))) ||
+        (s->recon == GKS_RECON_WENO_Z && !(s->eps_ao > 0.0)))
         return fail(c, GKS_EINVAL, "reconstruction parameters out of range");
+    if ((s->recon == GKS_RECON_WENO_Z || s->recon == GKS_RECON_TENO5) && c->desc.dim != 1)
+        return fail(c, GKS_EUNSUPPORTED, "WENO5-Z and TENO5 (the conventional path) are built for 1-D grids");
     if (s->merge != GKS_MERGE_KINETIC && s->merge != GKS_MERGE_AVERAGE)
         return fail(c, GKS_EINVAL, "merge must be GKS_MERGE_KINETIC or GKS_MERGE_AVERAGE");
     if (!s->positivity_fallback)

@@ -55,7 +55,8 @@ GKS_HD T ipow(T x, int q)
 
 // ------------------------------------------------------------------ reconstruction parameters
 // recon 0: TENO-D (Sec. 4.2); 1: WENO5-AO (Sec. 3.2), the reconstruction the
-// paper compares against.
+// paper compares against; 2: WENO5-Z and 3: TENO5, the conventional path
+// (Sec. 3.1, 4.1; 1-D grids).
 struct TenoParams {
     double eps;
     int q;
@@ -311,18 +312,93 @@ GKS_HD void teno_gauss(const TenoSel<T>& S, T g, T& v, T& d)
     }
 }
 
-// the scheme's reconstruction: REC 0 = TENO-D, 1 = WENO5-AO
+// The conventional path (Sec. 3.1, 4.1): WENO5-Z (REC 2) or TENO5 (REC 3)
+// face values from the three quadratics, slopes from the quadratic through
+// the cell average and the two face values (Eq. 3.11).  The selection keeps,
+// per sub-stencil, the part of the weight that does not depend on the point:
+// WENO-Z 1 + tau/(beta_k + eps) (Eq. 3.5, tau = |beta_0 - beta_2|), TENO5 the
+// cut-off delta_k of Eq. (4.3).  TENO5's chi_k = gamma_k / sum gamma with
+// gamma_k = (1 + tau/t_k)^q, t_k = beta_k + eps (Eqs. 4.1, 4.2), is formed
+// from gamma_k / gamma_max = ((t_m / t_k) (t_k + tau)/(t_m + tau))^q, t_m the
+// smallest t (the largest gamma), so nothing overflows in float32.
+template <int REC, typename T>
+GKS_HD void weno3_select(const T q[5], const TenoT<T>& P, TenoSel<T>& S)
+{
+    stencil_coeffs(q, S);
+    T beta[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) beta[k] = S.b[k] * S.b[k] + T(13.0 / 3.0) * S.c[k] * S.c[k];
+    const T tau = fabs(beta[0] - beta[2]);
+    if constexpr (REC == 2) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) S.w[k] = T(1) + tau / (beta[k] + P.eps_ao);
+    } else {
+        T t[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) t[k] = beta[k] + P.eps;
+        T m = t[0] < t[1] ? t[0] : t[1];
+        m = m < t[2] ? m : t[2];
+        const T imt = T(1) / (m + tau);
+        T p[3], sum = T(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const T r = (m / t[k]) * ((t[k] + tau) * imt);
+            if (P.q == 6) {
+                const T r3 = r * r * r;
+                p[k] = r3 * r3;
+            } else {
+                p[k] = ipow(r, P.q);
+            }
+            sum += p[k];
+        }
+        const T thr = P.ct1 * sum;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) S.w[k] = (p[k] >= thr) ? T(1) : T(0);
+    }
+    S.w3 = T(0);
+    S.large = false;
+}
+
+// values at xi = +-1/2 with the linear weights of each face (d = 0.1, 0.6,
+// 0.3 at +1/2, mirrored at -1/2), omega_k = d_k w_k / sum d_j w_j, and the
+// xi-slopes of Eq. (3.11)
+template <typename T>
+GKS_HD void weno3_faces(const T q[5], const TenoSel<T>& S, T& vp, T& dp, T& vm, T& dm)
+{
+    const T dP[3] = {T(0.1), T(0.6), T(0.3)};
+    T np = T(0), nm = T(0), sp = T(0), sm = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T bh = T(0.5) * S.b[k], c6 = S.c[k] * T(1.0 / 6.0);
+        const T ap = dP[k] * S.w[k], am = dP[2 - k] * S.w[k];
+        np += ap * (bh + c6);  // p_k(+1/2) - q2
+        nm += am * (c6 - bh);  // p_k(-1/2) - q2
+        sp += ap;
+        sm += am;
+    }
+    const T ep = np / sp, em = nm / sm;
+    vp = S.q2 + ep;
+    vm = S.q2 + em;
+    dp = T(2) * (em + T(2) * ep);
+    dm = T(-2) * (T(2) * em + ep);
+    (void)q;
+}
+
+// the scheme's reconstruction: REC 0 = TENO-D, 1 = WENO5-AO, 2 = WENO5-Z and
+// 3 = TENO5 (conventional path, faces only)
 template <int REC, typename T>
 GKS_HD void rec_select(const T q[5], const TenoT<T>& P, TenoSel<T>& S)
 {
     if constexpr (REC == 0) teno_select(q, P, S);
-    else ao_select(q, P, S);
+    else if constexpr (REC == 1) ao_select(q, P, S);
+    else weno3_select<REC>(q, P, S);
 }
 template <int REC, typename T>
 GKS_HD void rec_faces(const T q[5], const TenoSel<T>& S, T& vp, T& dp, T& vm, T& dm)
 {
     if constexpr (REC == 0) teno_faces(q, S, vp, dp, vm, dm);
-    else ao_faces(q, S, vp, dp, vm, dm);
+    else if constexpr (REC == 1) ao_faces(q, S, vp, dp, vm, dm);
+    else weno3_faces(q, S, vp, dp, vm, dm);
 }
 template <int REC, typename T>
 GKS_HD void rec_gauss(const TenoSel<T>& S, T g, T& v, T& d)
@@ -746,8 +822,11 @@ GKS_HD void side_terms(const Side<T>& S, bool upper, const FluxParams<T>& P,
 
 // F and dF/dt (per unit time; Sec. 2.2) at one interface point in the local
 // frame.  Both sides must be physical (the caller applies the fallback).
+// W0n_lin: the equilibrium normal slope of the conventional path (Eq. 3.12),
+// replacing the kinetic merge of the side slopes; nullptr otherwise
 template <typename T, int DIM, bool NONEQ, bool PRFIX>
-GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& P, T* F, T* dF)
+GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& P, T* F, T* dF,
+                       const T* W0n_lin = nullptr)
 {
     T W0[4] = {0, 0, 0, 0}, W0n[4] = {0, 0, 0, 0}, W0t[4] = {0, 0, 0, 0};
     T S3[4] = {0, 0, 0, 0}, S4[4] = {0, 0, 0, 0}, S5[4] = {0, 0, 0, 0};
@@ -764,6 +843,10 @@ GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& 
             W0n[i] = T(0.5) * (L.Wn[i] + R.Wn[i]);
             W0t[i] = T(0.5) * (L.Wt[i] + R.Wt[i]);
         }
+    }
+    if (W0n_lin) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) W0n[i] = W0n_lin[i];
     }
 
     // equilibrium state g0: rho0 <u psi>_0 is the Euler flux of W0 and

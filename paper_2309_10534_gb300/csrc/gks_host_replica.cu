@@ -176,6 +176,31 @@ extern "C" int gks_host_weno_ao(int precision, const double* q, double eps_ao, d
                           : weno_ao_t<double>(q, eps_ao, d_hi, d_lo, faces, gauss);
 }
 
+template <typename T, int REC>
+int weno3_t(const double* q, double eps, int qpow, double ct, double* faces)
+{
+    T qq[5];
+    for (int k = 0; k < 5; ++k) qq[k] = (T)q[k];
+    gks::TenoParams P{eps, qpow, ct, 0.0};
+    P.recon = REC;
+    P.eps_ao = eps;
+    gks::TenoSel<T> S;
+    gks::rec_select<REC>(qq, gks::teno_t<T>(P), S);
+    T vp, dp, vm, dm;
+    gks::rec_faces<REC>(qq, S, vp, dp, vm, dm);
+    faces[0] = vp; faces[1] = dp; faces[2] = vm; faces[3] = dm;
+    return 0;
+}
+
+extern "C" int gks_host_weno3(int precision, int teno5, const double* q, double eps, int qpow, double ct,
+                              double* faces)
+{
+    if (!q || !faces || qpow < 1 || !(eps > 0.0)) return -1;
+    if (teno5)
+        return precision == 1 ? weno3_t<float, 3>(q, eps, qpow, ct, faces) : weno3_t<double, 3>(q, eps, qpow, ct, faces);
+    return precision == 1 ? weno3_t<float, 2>(q, eps, qpow, ct, faces) : weno3_t<double, 2>(q, eps, qpow, ct, faces);
+}
+
 extern "C" int gks_host_teno_vjp(int precision, const double* q, double eps, int qpow, double ct1, double ct2,
                                  const double* gfaces, const double* ggauss, double* gq)
 {

@@ -234,7 +234,18 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
             if (!physical<T, 1>(R.W, fp.gm1)) err |= 2u;
         }
         T F[4], dF[4];
-        point_flux<T, 1, NONEQ, PRFIX>(L, R, fp, F, dF);
+        if constexpr (REC >= 2) {
+            // conventional path: equilibrium slope from the cell averages
+            // i-1 .. i+2 around the face by the linear Eq. (3.12)
+            T w0n[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+            for (int v = 0; v < 3; ++v)
+                w0n[slot[v]] = (T(1.25) * (sq[v][f + 3] - sq[v][f + 2]) - T(1.0 / 12.0) * (sq[v][f + 4] - sq[v][f + 1]))
+                             * idx_;
+            point_flux<T, 1, NONEQ, PRFIX>(L, R, fp, F, dF, w0n);
+        } else {
+            point_flux<T, 1, NONEQ, PRFIX>(L, R, fp, F, dF);
+        }
         const T tdt = (T)dt;
 #pragma unroll
         for (int v = 0; v < 3; ++v) stage_comb<T>(a.stage, F[slot[v]], dF[slot[v]], tdt, sG[0][v][f], sG[1][v][f]);

@@ -110,7 +110,7 @@ void count(int tau_mode, double Pr, gks_flop_model* out)
     tp.eps = T(1e-40);
     tp.ct1 = T(1e-7);
     tp.ct2 = T(1e-5);
-    tp.q = tp0.q;
+    tp.q = (REC == 3) ? 6 : tp0.q;
     {
         const TenoT<double> td = teno_t<double>(tp0);
         for (int k = 0; k < 4; ++k) tp.g[k] = T(td.g[k]);
@@ -126,13 +126,15 @@ void count(int tau_mode, double Pr, gks_flop_model* out)
         T a, b, c, d;
         rec_faces<REC>(q, S, a, b, c, d);
     });
-    const Counts tang = measure([&] {
-        TenoSel<T> S;
-        rec_select<REC>(q, tp, S);
-        T a, b;
-        rec_gauss<REC>(S, T(0.28867513459481288), a, b);
-        rec_gauss<REC>(S, T(-0.28867513459481288), a, b);
-    });
+    Counts tang;
+    if constexpr (REC < 2)
+        tang = measure([&] {
+            TenoSel<T> S;
+            rec_select<REC>(q, tp, S);
+            T a, b;
+            rec_gauss<REC>(S, T(0.28867513459481288), a, b);
+            rec_gauss<REC>(S, T(-0.28867513459481288), a, b);
+        });
     Side<T> L, R;
     sample_side<T, DIM>(L, 1.0, 0.3, 0.2, 1.0, gamma, 0.0);
     sample_side<T, DIM>(R, 1.0, 0.3, 0.2, 1.0, gamma, 1e-4);
@@ -154,6 +156,12 @@ void count(int tau_mode, double Pr, gks_flop_model* out)
         sweep += avg;
     } else {
         sweep += flux;
+        if (REC >= 2) {  // the equilibrium slope of Eq. (3.12) per face
+            Counts lin;
+            lin.add = 3 * nv;
+            lin.mul = 3 * nv;
+            sweep += lin;
+        }
     }
     Counts upd1, upd2;                              // stage combinations and update, per cell
     upd1.add = nv * (2 + 2 + 2);                   // G1, G2 sums, two differences, two updates
@@ -202,10 +210,13 @@ extern "C" gks_status gks_count_flops_recon(int dim, int precision, int tau_mode
 {
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
-    if (!out || (dim != 1 && dim != 2) || tau_mode < 0 || tau_mode > 2 || !(Pr > 0.0) || recon < 0 || recon > 1)
+    if (!out || (dim != 1 && dim != 2) || tau_mode < 0 || tau_mode > 2 || !(Pr > 0.0) || recon < 0 || recon > 3)
         return GKS_EINVAL;
+    if (recon >= 2 && dim != 1) return GKS_EUNSUPPORTED;
     const bool f32 = precision == GKS_FP32_FLUX;
     if (recon == 1) count_rec<1>(dim, f32, tau_mode, Pr, out);
+    else if (recon == 2) count_rec<2>(1, f32, tau_mode, Pr, out);
+    else if (recon == 3) count_rec<3>(1, f32, tau_mode, Pr, out);
     else count_rec<0>(dim, f32, tau_mode, Pr, out);
     return GKS_OK;
 }

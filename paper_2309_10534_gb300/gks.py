@@ -18,7 +18,7 @@ GKS_OK, GKS_EINVAL, GKS_ENOMEM, GKS_ECUDA, GKS_ENONPHYSICAL, GKS_ETIMEOUT, GKS_E
 BC = {"periodic": 0, "zerograd": 1, "symmetry": 2, "noslip": 3, "reflect": 4}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32x2": 2}
 TAU = {"zero": 0, "euler": 1, "ns": 2}
-RECON = {"teno_d": 0, "weno_ao": 1}
+RECON = {"teno_d": 0, "weno_ao": 1, "weno_z": 2, "teno5": 3}
 MERGE = {"kinetic": 0, "average": 1}
 
 
@@ -109,6 +109,8 @@ def default_scheme(**kw) -> Scheme:
     s = Scheme(cfl=0.5, c1=0.01, c2=1.0, ct1=1e-7, ct2=1e-5, ct1_t=1e-7, ct2_t=1e-5, eps=1e-40, q=7,
                tau_mode=TAU["euler"], positivity_fallback=1, recon=0, d_hi=0.85, d_lo=0.85, eps_ao=1e-8,
                merge=0)
+    if kw.get("recon") in ("teno5", 3) and "q" not in kw:
+        kw = dict(kw, q=6)  # TENO5's power (Eq. 4.1); TENO-D's default is 7
     for k, v in kw.items():
         if k == "tau" or k == "tau_mode":
             v = TAU[v] if isinstance(v, str) else int(v)
@@ -295,8 +297,9 @@ def _replica():
         L.gks_host_teno_vjp.argtypes = [C.c_int, _dp] + [C.c_double, C.c_int, C.c_double, C.c_double] + [_dp] * 3
         L.gks_host_weno_ao.argtypes = [C.c_int, _dp, C.c_double, C.c_double, C.c_double, _dp, _dp]
         L.gks_host_point_flux_vjp.argtypes = [C.c_int, C.c_double] + [_dp] * 10
+        L.gks_host_weno3.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_int, C.c_double, _dp]
         for f in (L.gks_host_time_coeffs, L.gks_host_teno, L.gks_host_point_flux, L.gks_host_teno_vjp,
-                  L.gks_host_point_flux_vjp, L.gks_host_weno_ao):
+                  L.gks_host_point_flux_vjp, L.gks_host_weno_ao, L.gks_host_weno3):
             f.restype = C.c_int
         L._replica_declared = True
     return L
@@ -340,6 +343,18 @@ def host_point_flux(dim, Wl, Wln, Wlt, Wr, Wrn, Wrt, dt, precision="fp64", tau="
     if r:
         raise ValueError("bad argument")
     return F, dF
+
+
+def host_weno3(q, teno5=False, precision="fp64", eps=None, q_pow=6, ct=1e-7):
+    """(vp, dp, vm, dm) of the conventional path's WENO5-Z / TENO5 face
+    reconstruction for one stencil."""
+    if eps is None:
+        eps = 1e-40 if teno5 else 1e-8
+    qq, pq = _arr(q, 5)
+    f, pf = _arr(None, 4)
+    if _replica().gks_host_weno3(PRECISION[precision], int(bool(teno5)), pq, eps, int(q_pow), ct, pf):
+        raise ValueError("bad argument")
+    return f
 
 
 def host_weno_ao(q, precision="fp64", eps_ao=1e-8, d_hi=0.85, d_lo=0.85):

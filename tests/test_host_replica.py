@@ -131,3 +131,21 @@ def test_weno_ao_matches_oracle(G):
         assert np.abs(gp - want_g).max() <= 1e-14 * scale
         f32, _ = G.host_weno_ao(q, precision="fp32")
         assert np.abs(f32 - want_f).max() <= 2e-6 * scale
+
+
+@pytest.mark.parametrize("teno5", [False, True])
+def test_weno3_matches_oracle(G, teno5):
+    """WENO5-Z and TENO5 face values with the slopes of Eq. (3.11), host build
+    of the device code vs the oracle: float64 to 1e-13, float32 to 2e-6."""
+    rng = np.random.default_rng(8)
+    recon = "teno5" if teno5 else "weno_z"
+    P = O.make_problem(1, 8, recon=recon)
+    stencils = [np.array([1.0, 1.1, 1.25, 1.45, 1.7]), np.array([1.0, 1.0, 1.0, 0.125, 0.125]),
+                np.array([0.1, 1.0, 1.02, 1.03, 1.05]), np.ones(5)] + [rng.normal(size=5) for _ in range(30)]
+    for q in stencils:
+        want = O.recon_faces(P, q)
+        scale = max(1.0, np.abs(q).max())
+        got = G.host_weno3(q, teno5)
+        assert np.abs(got - want).max() <= 1e-13 * scale, (q, got, want)
+        g32 = G.host_weno3(q, teno5, precision="fp32")
+        assert np.abs(g32 - want).max() <= 2e-6 * scale, (q, g32, want)  # measured 4.4e-7
