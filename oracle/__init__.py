@@ -40,10 +40,13 @@ class Problem(C.Structure):
         ("positivity_fallback", C.c_int),
         ("recon", C.c_int), ("d_hi", C.c_double), ("d_lo", C.c_double), ("eps_ao", C.c_double),
         ("merge", C.c_int), ("zpow", C.c_double),
+        ("t", C.c_double), ("bc_in", C.c_double * 4), ("bc_pre", C.c_double * 4),
+        ("shock_x0", C.c_double), ("shock_theta", C.c_double), ("shock_speed", C.c_double),
     ]
 
 
-BC = {"periodic": 0, "zerograd": 1, "symmetry": 2, "noslip": 3, "reflect": 4}
+BC = {"periodic": 0, "zerograd": 1, "symmetry": 2, "noslip": 3, "reflect": 4,
+      "inflow": 5, "wall_after_x0": 6, "moving_shock": 7}
 TAU = {"zero": 0, "euler": 1, "ns": 2}
 RECON = {"teno_d": 0, "weno_ao": 1, "weno_z": 2, "teno5": 3}
 MERGE = {"kinetic": 0, "average": 1}
@@ -52,7 +55,8 @@ MERGE = {"kinetic": 0, "average": 1}
 def make_problem(dim, nx, ny=1, *, lx=1.0, ly=1.0, bc=("zerograd",) * 4, gamma=1.4, mu=0.0, Pr=1.0,
                  tau="euler", c1=0.01, c2=1.0, cfl=0.5, eps=1e-40, q=None, ct1=1e-7, ct2=1e-5,
                  ct1_t=None, ct2_t=None, positivity_fallback=1, recon="teno_d", d_hi=0.85, d_lo=0.85,
-                 eps_ao=1e-8, merge="kinetic", zpow=1.0) -> Problem:
+                 eps_ao=1e-8, merge="kinetic", zpow=1.0, t=0.0, bc_in=None, bc_pre=None, shock_x0=0.0,
+                 shock_theta=np.pi / 3, shock_speed=0.0) -> Problem:
     p = Problem()
     p.dim, p.nx, p.ny = dim, nx, (ny if dim == 2 else 1)
     p.dx = lx / nx
@@ -73,6 +77,16 @@ def make_problem(dim, nx, ny=1, *, lx=1.0, ly=1.0, bc=("zerograd",) * 4, gamma=1
     p.d_hi, p.d_lo, p.eps_ao = d_hi, d_lo, eps_ao
     p.merge = MERGE[merge] if isinstance(merge, str) else int(merge)
     p.zpow = zpow
+    # state-setting boundary rules: conserved states (rho, rho u, [rho v,] E)
+    # stored as 4 slots with the energy last
+    for name, st in (("bc_in", bc_in), ("bc_pre", bc_pre)):
+        if st is not None:
+            st = list(st)
+            if len(st) == 3:
+                st = [st[0], st[1], 0.0, st[2]]
+            getattr(p, name)[:] = [float(x) for x in st]
+    p.t = t
+    p.shock_x0, p.shock_theta, p.shock_speed = shock_x0, shock_theta, shock_speed
     return p
 
 

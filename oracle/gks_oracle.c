@@ -821,14 +821,38 @@ static grid_t make_grid(const or_problem *P)
 
 #define GIDX(g, v, j, i) (((size_t)(v) * (g).gy + (size_t)(j)) * (g).gx + (size_t)(i))
 
+/* state of a state-setting rule at the ghost centre (x, y) at time t, or
+ * NULL when the rule copies from the interior there */
+static const double *ghost_state(const or_problem *P, int bc, double x, double y, double t)
+{
+    if (bc == OR_BC_INFLOW) return P->bc_in;
+    if (bc == OR_BC_WALL_AFTER_X0) return (x < P->shock_x0) ? P->bc_in : NULL;
+    if (bc == OR_BC_MOVING_SHOCK) {
+        const double xs = P->shock_x0 + y / tan(P->shock_theta) + P->shock_speed * t / sin(P->shock_theta);
+        return (x < xs) ? P->bc_in : P->bc_pre;
+    }
+    return NULL;
+}
+
 /* velocity component index normal to x (1) or y (2) */
 static void ghost_from(const or_problem *P, const grid_t *g, double *Wg, int bc, int dir, int side,
-                       int line)
+                       int line, double t)
 {
     /* dir 0: x ghosts on row `line` (ghosted row index); dir 1: y ghosts on column `line` */
     int n = (dir == 0) ? g->nx : g->ny;
     for (int k = 1; k <= NG; ++k) {
         int gidx = (side == 0) ? NG - k : NG + n - 1 + k;  /* ghost position */
+        /* ghost centre (the grid starts at the origin) */
+        const int gi = (dir == 0) ? gidx : line, gj = (dir == 0) ? line : gidx;
+        const double *st = ghost_state(P, bc, (gi - NG + 0.5) * P->dx, (gj - NG + 0.5) * P->dy, t);
+        if (st) {
+            const int ie = g->nv - 1; /* energy slot */
+            for (int v = 0; v < g->nv; ++v) {
+                size_t dst_i = (dir == 0) ? GIDX(*g, v, line, gidx) : GIDX(*g, v, gidx, line);
+                Wg[dst_i] = (v == ie) ? st[3] : st[v];
+            }
+            continue;
+        }
         int src;
         switch (bc) {
         case OR_BC_PERIODIC: src = (side == 0) ? NG + n - k : NG + k - 1; break;
@@ -840,7 +864,8 @@ static void ghost_from(const or_problem *P, const grid_t *g, double *Wg, int bc,
             size_t src_i = (dir == 0) ? GIDX(*g, v, line, src) : GIDX(*g, v, src, line);
             double val = Wg[src_i];
             int normal_v = (dir == 0) ? 1 : 2;
-            if ((bc == OR_BC_SYMMETRY || bc == OR_BC_REFLECT) && v == normal_v) val = -val;
+            if ((bc == OR_BC_SYMMETRY || bc == OR_BC_REFLECT || bc == OR_BC_WALL_AFTER_X0) && v == normal_v)
+                val = -val;
             if (bc == OR_BC_NOSLIP && (v == 1 || (g->dim == 2 && v == 2))) val = -val;
             Wg[dst_i] = val;
         }
@@ -848,19 +873,26 @@ static void ghost_from(const or_problem *P, const grid_t *g, double *Wg, int bc,
     (void)P;
 }
 
-void or_fill_ghosts(const or_problem *P, double *Wg)
+/* ghosts of the state at time t: x ghosts of the interior rows first, then y
+ * ghosts over the full ghosted width (reading R13) */
+static void fill_ghosts_t(const or_problem *P, double *Wg, double t)
 {
     grid_t g = make_grid(P);
     int j0 = (g.dim == 2) ? NG : 0, j1 = (g.dim == 2) ? NG + g.ny : 1;
     for (int j = j0; j < j1; ++j) {
-        ghost_from(P, &g, Wg, P->bc[0], 0, 0, j);
-        ghost_from(P, &g, Wg, P->bc[1], 0, 1, j);
+        ghost_from(P, &g, Wg, P->bc[0], 0, 0, j, t);
+        ghost_from(P, &g, Wg, P->bc[1], 0, 1, j, t);
     }
     if (g.dim == 2)
         for (int i = 0; i < g.gx; ++i) {
-            ghost_from(P, &g, Wg, P->bc[2], 1, 0, i);
-            ghost_from(P, &g, Wg, P->bc[3], 1, 1, i);
+            ghost_from(P, &g, Wg, P->bc[2], 1, 0, i, t);
+            ghost_from(P, &g, Wg, P->bc[3], 1, 1, i, t);
         }
+}
+
+void or_fill_ghosts(const or_problem *P, double *Wg)
+{
+    fill_ghosts_t(P, Wg, P->t);
 }
 
 static void to_ghosted(const grid_t *g, const double *W, double *Wg)
@@ -1092,9 +1124,9 @@ int or_step(const or_problem *P, const double *W, double dt, double *Wout, long 
                 Ws[c] = val;
             }
 
-    /* stage 2 on W*: only dF(W*, t*) is needed */
+    /* stage 2 on W* (time t + dt/2): only dF(W*, t*) is needed */
     to_ghosted(&g, Ws, w.Wg);
-    or_fill_ghosts(P, w.Wg);
+    fill_ghosts_t(P, w.Wg, P->t + 0.5 * dt);
     rc = all_fluxes(P, &g, w.Wg, dt, w.Fx_dt, w.Fx_h, w.Fy_dt, w.Fy_h, nfallback);
     if (rc) goto outw;
     flux_and_derivative(nfx, w.Fx_dt, w.Fx_h, dt, NULL, dFxs);
@@ -1157,10 +1189,12 @@ int or_run(const or_problem *P, double *W, double t_end, long max_steps, long *s
     double t = 0.0;
     long s = 0;
     int rc = 0;
+    or_problem Q = *P; /* the boundary time follows the run: P->t + t */
     while (t < t_end && (max_steps <= 0 || s < max_steps)) {
         double dt = or_dt(P, W);
         if (t + dt > t_end) dt = t_end - t;
-        rc = or_step(P, W, dt, Wn, nfallback);
+        Q.t = P->t + t;
+        rc = or_step(&Q, W, dt, Wn, nfallback);
         if (rc) break;
         memcpy(W, Wn, n * sizeof(double));
         t += dt;

@@ -26,7 +26,13 @@ extern "C" {
 #endif
 
 /* boundary kinds for ghost layers */
-enum { OR_BC_PERIODIC = 0, OR_BC_ZEROGRAD = 1, OR_BC_SYMMETRY = 2, OR_BC_NOSLIP = 3, OR_BC_REFLECT = 4 };
+enum { OR_BC_PERIODIC = 0, OR_BC_ZEROGRAD = 1, OR_BC_SYMMETRY = 2, OR_BC_NOSLIP = 3, OR_BC_REFLECT = 4,
+       /* state-setting rules (double Mach reflection, Sec. 5.7): INFLOW sets
+        * the ghosts to bc_in; WALL_AFTER_X0 (y sides) sets bc_in for ghost
+        * centres with x < shock_x0 and reflects beyond; MOVING_SHOCK (y sides)
+        * sets bc_in behind and bc_pre ahead of the oblique shock
+        * x_s(y, t) = shock_x0 + y cot(theta) + shock_speed t / sin(theta) */
+       OR_BC_INFLOW = 5, OR_BC_WALL_AFTER_X0 = 6, OR_BC_MOVING_SHOCK = 7 };
 /* collision-time models (Sec. 5) */
 enum { OR_TAU_ZERO = 0, OR_TAU_EULER = 1, OR_TAU_NS = 2 };
 
@@ -51,6 +57,11 @@ typedef struct {
     double eps_ao;        /* WENO5-AO epsilon of Eq. (3.5) */
     int merge;            /* OR_MERGE_*: equilibrium state at the interface */
     double zpow;          /* WENO5-Z exponent of tau/(beta+eps) in Eq. (3.5) */
+    double t;             /* time of the state passed in (time-dependent ghosts) */
+    double bc_in[4];      /* conserved state of the INFLOW rule / behind the shock */
+    double bc_pre[4];     /* conserved state ahead of the shock */
+    double shock_x0, shock_theta, shock_speed; /* shock foot on y = 0, angle to the
+                                                  x-axis (rad), normal speed */
 } or_problem;
 
 /* TENO-D (Sec. 4.2), WENO5-AO (Sec. 3.2), and the conventional path

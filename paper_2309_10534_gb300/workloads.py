@@ -42,6 +42,9 @@ class Setup:
     t_end: float = 0.0
     name: str = ""
     extra: dict = field(default_factory=dict)
+    # state-setting boundary data (bc_in, bc_pre: conserved (rho, rho u,
+    # rho v, E); shock_x0, shock_theta, shock_speed), passed to both sides
+    bcstate: dict = field(default_factory=dict)
 
     @property
     def dx(self):
@@ -53,7 +56,7 @@ class Setup:
 
     def problem_kwargs(self):
         return dict(lx=self.lx, ly=self.ly, bc=self.bc, gamma=self.gamma, mu=self.mu, Pr=self.Pr,
-                    tau=self.tau, cfl=self.cfl)
+                    tau=self.tau, cfl=self.cfl, **self.bcstate)
 
 
 def conserved_1d(rho, u, p, gamma):
@@ -193,21 +196,91 @@ RIEMANN_CONFIG3 = {
 }
 
 
-def riemann2d(n=1024, ny=None, split=0.8, t_end=0.8, gamma=1.4):
-    """Four-quadrant Riemann problem (configuration 3) on [0, 1]^2 with exact
-    cell averages (area fractions of each quadrant)."""
+RIEMANN_CONFIG6 = {
+    # (rho, u, v, p) per quadrant, Sec. 5.6 (b): four contact discontinuities
+    "ll": (1.0, -0.75, 0.5, 1.0),
+    "lr": (3.0, -0.75, -0.5, 1.0),
+    "ur": (1.0, -0.75, -0.5, 1.0),
+    "ul": (2.0, 0.75, 0.5, 1.0),
+}
+
+
+def riemann2d(n=1024, ny=None, split=0.8, t_end=0.8, gamma=1.4, config=3, cfl=0.5):
+    """Four-quadrant Riemann problem (configuration 3, or 6 with its split at
+    0.5) on [0, 1]^2 with exact cell averages (area fractions of each
+    quadrant)."""
     ny = n if ny is None else ny
     xe = np.linspace(0.0, 1.0, n + 1)
     ye = np.linspace(0.0, 1.0, ny + 1)
     fx = np.clip((split - xe[:-1]) / (xe[1:] - xe[:-1]), 0.0, 1.0)  # fraction with x < split
     fy = np.clip((split - ye[:-1]) / (ye[1:] - ye[:-1]), 0.0, 1.0)
     FX, FY = np.meshgrid(fx, fy)
+    table = RIEMANN_CONFIG3 if config == 3 else RIEMANN_CONFIG6
     W = np.zeros((4, ny, n))
     for key, wx, wy in (("ll", FX, FY), ("lr", 1 - FX, FY), ("ur", 1 - FX, 1 - FY),
                         ("ul", FX, 1 - FY)):
-        W += (wx * wy)[None] * conserved_2d(*RIEMANN_CONFIG3[key], gamma)[:, None, None]
-    return Setup(2, n, ny, 1.0, 1.0, W, bc=("zerograd",) * 4, gamma=gamma, t_end=t_end,
-                 name="riemann2d_config3", extra=dict(split=split))
+        W += (wx * wy)[None] * conserved_2d(*table[key], gamma)[:, None, None]
+    return Setup(2, n, ny, 1.0, 1.0, W, bc=("zerograd",) * 4, gamma=gamma, t_end=t_end, cfl=cfl,
+                 name="riemann2d_config%d" % config, extra=dict(split=split))
+
+
+def riemann2d_config6(n=400, t_end=0.6, cfl=0.8, gamma=1.4):
+    """Configuration 6 (Sec. 5.6 (b)): split at (0.5, 0.5), t = 0.6, CFL 0.8."""
+    return riemann2d(n, split=0.5, t_end=t_end, gamma=gamma, config=6, cfl=cfl)
+
+
+def _area_left_of_line(x0, x1, y0, y1, a, c, sub=64):
+    """Fraction of the cell [x0, x1] x [y0, y1] with x < a + c y: the exact
+    integral over y of the clipped linear fraction, by the midpoint rule on
+    sub-intervals split at the two kinks (exact: the integrand is linear
+    between kinks)."""
+    h = x1 - x0
+    f = lambda y: np.clip((a + c * y - x0) / h, 0.0, 1.0)
+    # kinks where the line crosses x0 and x1
+    ys = [y0, y1]
+    if c != 0.0:
+        for xk in (x0, x1):
+            yk = (xk - a) / c
+            if y0 < yk < y1:
+                ys.append(yk)
+    ys = sorted(ys)
+    tot = 0.0
+    for ya, yb in zip(ys[:-1], ys[1:]):
+        tot += 0.5 * (f(ya) + f(yb)) * (yb - ya)  # linear between kinks: trapezoid is exact
+    return tot / (y1 - y0)
+
+
+DMR_POST = (8.0, 4.125 * np.sqrt(3.0), -4.125, 116.5)  # (rho, u, v, p) behind the shock, Sec. 5.7
+DMR_PRE = (1.4, 0.0, 0.0, 1.0)
+
+
+def double_mach(nx=960, ny=240, t_end=0.2, cfl=0.5, gamma=1.4):
+    """Double Mach reflection (Sec. 5.7) on [0, 4] x [0, 1]: a Mach 10 shock
+    at 60 degrees to the x-axis through (1/6, 0), post-shock state behind
+    it; inflow of the post-shock state on the left, zero gradient on the
+    right, the post-shock state on the bottom for x < 1/6 and a reflecting
+    wall beyond, the exact moving shock on the top.  Exact cell averages of
+    the initial discontinuity."""
+    x0, theta, us = 1.0 / 6.0, np.pi / 3.0, 10.0
+    c = 1.0 / np.tan(theta)
+    dx, dy = 4.0 / nx, 1.0 / ny
+    frac = np.empty((ny, nx))
+    for j in range(ny):
+        for i in range(nx):
+            xa, xb, ya, yb = i * dx, (i + 1) * dx, j * dy, (j + 1) * dy
+            if xb <= x0 + c * ya:
+                frac[j, i] = 1.0
+            elif xa >= x0 + c * yb:
+                frac[j, i] = 0.0
+            else:
+                frac[j, i] = _area_left_of_line(xa, xb, ya, yb, x0, c)
+    Wpost = conserved_2d(*DMR_POST, gamma)
+    Wpre = conserved_2d(*DMR_PRE, gamma)
+    W = frac[None] * Wpost[:, None, None] + (1.0 - frac[None]) * Wpre[:, None, None]
+    bcstate = dict(bc_in=tuple(float(x) for x in Wpost), bc_pre=tuple(float(x) for x in Wpre),
+                   shock_x0=x0, shock_theta=theta, shock_speed=us)
+    return Setup(2, nx, ny, 4.0, 1.0, W, bc=("inflow", "zerograd", "wall_after_x0", "moving_shock"),
+                 gamma=gamma, cfl=cfl, t_end=t_end, name="double_mach", bcstate=bcstate)
 
 
 def viscous_shock_tube(nx=2048, ny=1024, Re=200.0, Pr=0.73, gamma=1.4, t_end=1.0, cfl=0.2):

@@ -751,3 +751,71 @@ def test_conventional_path_is_one_dimensional():
     P = O.make_problem(2, 8, 8, bc=("periodic",) * 4, recon="weno_z")
     with pytest.raises(Exception):
         O.step(P, W, 1e-3)
+
+
+# ---------------------------------------------------------------- double Mach reflection
+def test_double_mach_states_are_a_mach_10_shock():
+    """Sec. 5.7's post- and pre-shock states satisfy the Rankine-Hugoniot
+    conditions across a shock inclined at 60 degrees moving with normal
+    speed 10 into gas at rest with sound speed 1 (Mach 10): mass, normal
+    momentum and total enthalpy fluxes in the shock frame agree, and the
+    tangential velocity is continuous."""
+    g = 1.4
+    th = np.pi / 3
+    n = np.array([np.sin(th), -np.cos(th)])   # normal to the shock line, towards the pre-shock gas
+    tvec = np.array([np.cos(th), np.sin(th)])
+    s = 10.0
+    post, pre = WL.DMR_POST, WL.DMR_PRE
+    assert np.sqrt(g * pre[3] / pre[0]) == pytest.approx(1.0, rel=1e-15)
+
+    def fluxes(st):
+        r, u, v, p = st
+        w = np.dot([u, v], n) - s
+        return r * w, r * w * w + p, g / (g - 1) * p / r + 0.5 * w * w, np.dot([u, v], tvec)
+    for a, b in zip(fluxes(post), fluxes(pre)):
+        assert a == pytest.approx(b, rel=1e-12, abs=1e-12)
+
+
+def test_double_mach_initial_cell_averages():
+    """Exact cell averages of the initial shock: the post-shock area is
+    1/6 + 1/(2 sqrt 3) (the region x < 1/6 + y/sqrt 3 of the unit strip)."""
+    s = WL.double_mach(96, 24)
+    Wpost = WL.conserved_2d(*WL.DMR_POST, 1.4)
+    Wpre = WL.conserved_2d(*WL.DMR_PRE, 1.4)
+    frac = (s.W[0] - Wpre[0]) / (Wpost[0] - Wpre[0])
+    assert frac.sum() * s.dx * s.dy == pytest.approx(1.0 / 6.0 + 0.5 / np.sqrt(3.0), rel=1e-13)
+    assert np.allclose(s.W, frac[None] * Wpost[:, None, None] + (1 - frac[None]) * Wpre[:, None, None], atol=1e-12)
+
+
+def test_double_mach_ghost_rules():
+    """The state-setting ghosts at t = 0.05 (ghost centres, grid from the
+    origin): left inflow = post-shock state; bottom post-shock for
+    x < 1/6, reflecting wall (v negated mirror) beyond; top post-shock
+    behind x_s = 1/6 + y/sqrt 3 + 20 t/sqrt 3, pre-shock ahead."""
+    nx, ny = 48, 12
+    s = WL.double_mach(nx, ny)
+    kw = s.problem_kwargs()
+    P = O.make_problem(2, nx, ny, t=0.05, **kw)
+    gx, gy = nx + 6, ny + 6
+    rng = np.random.default_rng(3)
+    Wg = np.zeros((4, gy, gx))
+    Wg[:, 3:3 + ny, 3:3 + nx] = s.W + 0.01 * rng.normal(size=s.W.shape)
+    O.fill_ghosts(P, Wg)
+    Wpost = np.array(WL.conserved_2d(*WL.DMR_POST, 1.4))
+    Wpre = np.array(WL.conserved_2d(*WL.DMR_PRE, 1.4))
+    dx, dy = 4.0 / nx, 1.0 / ny
+    for j in range(3, 3 + ny):
+        for i in range(3):
+            assert np.array_equal(Wg[:, j, i], Wpost)
+    for i in range(gx):
+        x = (i - 3 + 0.5) * dx
+        for k in range(3):
+            jb, src = 2 - k, 3 + k                     # bottom ghost row, its mirror row
+            if x < 1.0 / 6.0:
+                assert np.array_equal(Wg[:, jb, i], Wpost), (i, jb)
+            else:
+                assert np.array_equal(Wg[:, jb, i], Wg[:, src, i] * np.array([1, 1, -1, 1])), (i, jb)
+            jt = 3 + ny + k
+            y = (jt - 3 + 0.5) * dy
+            xs = 1.0 / 6.0 + (y + 20 * 0.05) / np.sqrt(3.0)
+            assert np.array_equal(Wg[:, jt, i], Wpost if x < xs else Wpre), (i, jt)
