@@ -54,8 +54,27 @@ typedef enum {
     GKS_BC_ZEROGRAD = 1,     /* "non-reflecting": copy of the edge cell */
     GKS_BC_SYMMETRY = 2,     /* mirror, normal velocity negated */
     GKS_BC_NOSLIP = 3,       /* mirror, both velocity components negated (adiabatic wall) */
-    GKS_BC_REFLECT = 4       /* same ghost rule as GKS_BC_SYMMETRY */
+    GKS_BC_REFLECT = 4,      /* same ghost rule as GKS_BC_SYMMETRY */
+    /* State-setting rules (the double Mach reflection, Sec. 5.7), with the
+     * states of gks_set_boundary_states; ghost cells are judged by their
+     * centres, W* ghosts at t + dt/2. */
+    GKS_BC_INFLOW = 5,        /* every ghost = the inflow state */
+    GKS_BC_WALL_AFTER_X0 = 6, /* y sides: the inflow state where x < shock_x0, reflecting wall beyond */
+    GKS_BC_MOVING_SHOCK = 7   /* y sides: the inflow state behind the moving oblique shock
+                                 x_s(y, t) = shock_x0 + (y - y0) cot(theta) + speed t / sin(theta),
+                                 the pre-shock state ahead of it */
 } gks_bc;
+
+/* States and shock of the state-setting boundary rules: conserved
+ * (rho, rho u, rho v, E); 1-D grids use (rho, rho u, -, E) of the same four
+ * slots. */
+typedef struct {
+    double inflow[4];        /* GKS_BC_INFLOW ghosts; behind the shock */
+    double pre[4];           /* ahead of the shock */
+    double shock_x0;         /* where the shock meets y = y0 at t = 0 */
+    double shock_theta;      /* angle of the shock line to the x-axis, radians, in (0, pi) */
+    double shock_speed;      /* normal speed of the shock */
+} gks_boundary_states;
 
 typedef enum {
     GKS_FP64 = 0,            /* every step in float64 */
@@ -138,6 +157,8 @@ gks_status gks_create(const gks_grid_desc *desc, gks_ctx **out);
 void       gks_destroy(gks_ctx *ctx);
 gks_status gks_set_gas(gks_ctx *ctx, const gks_gas *gas);
 gks_status gks_set_scheme(gks_ctx *ctx, const gks_scheme *scheme);
+/* Data of the state-setting boundary rules (default: all zero).  Copied. */
+gks_status gks_set_boundary_states(gks_ctx *ctx, const gks_boundary_states *states);
 /* cudaStream_t passed as void*; NULL = legacy default stream */
 gks_status gks_set_stream(gks_ctx *ctx, void *stream);
 

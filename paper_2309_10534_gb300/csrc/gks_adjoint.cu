@@ -614,6 +614,9 @@ gks_status check_supported(gks_ctx* c)
         return rt::fail(c, GKS_EUNSUPPORTED, "the adjoint is built for the collision-free flux (tau_mode = zero)");
     if (c->sch.recon != GKS_RECON_TENO_D)
         return rt::fail(c, GKS_EUNSUPPORTED, "the adjoint is built for TENO-D (frozen stencil selection)");
+    for (int k = 0; k < 4; ++k)
+        if (c->desc.bc[k] > GKS_BC_REFLECT)
+            return rt::fail(c, GKS_EUNSUPPORTED, "the adjoint is built for the copying boundary rules");
     if (c->sch.merge != GKS_MERGE_KINETIC)
         return rt::fail(c, GKS_EUNSUPPORTED, "the adjoint is built for the kinetic merge");
     return GKS_OK;

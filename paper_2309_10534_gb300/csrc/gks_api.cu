@@ -185,8 +185,9 @@ gks_status enqueue_ghosts(gks_ctx* c, double* arr, cudaStream_t st)
     const int n = (c->desc.dim == 1) ? 2 * NG : 2 * NG * gx + 2 * NG * c->desc.ny;
     const int pi = prof_begin(c, st, 1);
     float* shadow = (arr == c->Ws) ? c->Wsf : (arr == c->W ? c->Wf : nullptr);
-    if (shadow) k_fill_ghosts<float><<<(n + 127) / 128, 128, 0, st>>>(c->g, shadow, c->ds);
-    else k_fill_ghosts<double><<<(n + 127) / 128, 128, 0, st>>>(c->g, arr, c->ds);
+    const double toff = (arr == c->Ws) ? 0.5 : 0.0;  // W* belongs to t + dt/2
+    if (shadow) k_fill_ghosts<float><<<(n + 127) / 128, 128, 0, st>>>(c->g, shadow, c->ds, toff);
+    else k_fill_ghosts<double><<<(n + 127) / 128, 128, 0, st>>>(c->g, arr, c->ds, toff);
     CK(cudaGetLastError());
     prof_end(c, st, pi);
     ++c->launches;
@@ -449,8 +450,12 @@ gks_status gks_create(const gks_grid_desc* d, gks_ctx** out)
     if (d->nx < 3 || (d->dim == 2 && d->ny < 3)) return GKS_EINVAL;
     if (!(d->x1 > d->x0) || (d->dim == 2 && !(d->y1 > d->y0))) return GKS_EINVAL;
     if (d->precision != GKS_FP64 && d->precision != GKS_FP32_FLUX) return GKS_EINVAL;
-    for (int k = 0; k < 4; ++k)
-        if (d->bc[k] < GKS_BC_PERIODIC || d->bc[k] > GKS_BC_REFLECT) return GKS_EINVAL;
+    for (int k = 0; k < 4; ++k) {
+        if (d->bc[k] < GKS_BC_PERIODIC || d->bc[k] > GKS_BC_MOVING_SHOCK) return GKS_EINVAL;
+        // the wall-after-x0 and moving-shock rules are rules of the y sides
+        if ((d->bc[k] == GKS_BC_WALL_AFTER_X0 || d->bc[k] == GKS_BC_MOVING_SHOCK) && (k < 2 || d->dim != 2))
+            return GKS_EINVAL;
+    }
     if ((d->bc[0] == GKS_BC_PERIODIC) != (d->bc[1] == GKS_BC_PERIODIC)) return GKS_EINVAL;
     if (d->dim == 2 && (d->bc[2] == GKS_BC_PERIODIC) != (d->bc[3] == GKS_BC_PERIODIC)) return GKS_EINVAL;
     if ((long long)d->nx * (d->dim == 2 ? d->ny : 1) > (1ll << 31)) return GKS_EINVAL;
@@ -487,6 +492,9 @@ gks_status gks_create(const gks_grid_desc* d, gks_ctx** out)
     for (int k = 0; k < 4; ++k) g.bc[k] = d->bc[k];
     g.gamma = c->gas.gamma;
     g.mu = c->gas.mu;
+    g.ox = d->x0;
+    g.oy = (d->dim == 2) ? d->y0 : 0.0;
+    g.bs = BcStates{};
 
     c->arr_bytes = (size_t)c->nv * g.plane * sizeof(double);
     cudaError_t e1 = cudaMalloc(&c->W, c->arr_bytes);
@@ -561,6 +569,24 @@ gks_status gks_set_gas(gks_ctx* c, const gks_gas* gas)
     c->cfl_dt_ready = false;
     c->g.gamma = gas->gamma;
     c->g.mu = gas->mu;
+    ++c->param_version;
+    return GKS_OK;
+}
+
+gks_status gks_set_boundary_states(gks_ctx* c, const gks_boundary_states* b)
+{
+    if (!c || !b) return GKS_EINVAL;
+    for (int k = 0; k < 4; ++k)
+        if (!std::isfinite(b->inflow[k]) || !std::isfinite(b->pre[k]))
+            return fail(c, GKS_EINVAL, "boundary states must be finite");
+    if (!(b->shock_theta > 0.0 && b->shock_theta < 3.14159265358979323846) || !std::isfinite(b->shock_x0) ||
+        !std::isfinite(b->shock_speed))
+        return fail(c, GKS_EINVAL, "shock angle must lie in (0, pi); shock data finite");
+    BcStates& s = c->g.bs;
+    for (int k = 0; k < 4; ++k) { s.in[k] = b->inflow[k]; s.pre[k] = b->pre[k]; }
+    s.x0 = b->shock_x0;
+    s.cot = std::cos(b->shock_theta) / std::sin(b->shock_theta);
+    s.vx = b->shock_speed / std::sin(b->shock_theta);
     ++c->param_version;
     return GKS_OK;
 }

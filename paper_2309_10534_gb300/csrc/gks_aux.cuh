@@ -12,8 +12,10 @@ namespace gks {
 // of y ghosts use the y rule to pick an interior row, then the x rule for
 // x-ghost columns (the same values as filling x first, then y over the full
 // ghosted width).
+// State-setting rules (inflow, wall after x0, moving shock) write their state;
+// toff: the array's time is t + toff dt (0 for W, 1/2 for W*).
 template <typename E>
-__global__ void k_fill_ghosts(GridDev g, E* __restrict__ W, const DevState* ds)
+__global__ void k_fill_ghosts(GridDev g, E* __restrict__ W, const DevState* ds, double toff)
 {
     if (ds && ds->done) return;
     const int gx = g.nx + 2 * NG;
@@ -38,12 +40,29 @@ __global__ void k_fill_ghosts(GridDev g, E* __restrict__ W, const DevState* ds)
             i = k < NG ? k : g.nx + k;
         }
     }
-    bool fxn, fxa, fyn = false, fya = false;
+    bool fxn = false, fxa = false, fyn = false, fya = false;
+    const double t = ds ? ds->t + toff * ds->dt : 0.0;
+    const double xc = g.ox + (i - NG + 0.5) * g.dx, yc = g.oy + (j - NG + 0.5) * g.dy;
     int sj = j;
-    if (g.dim == 2) sj = ghost_src(g.bc[2 + (j >= NG + g.ny)], g.ny, j, fyn, fya);
-    int si = ghost_src(g.bc[(i >= NG + g.nx)], g.nx, i, fxn, fxa);
+    if (g.dim == 2 && (j < NG || j >= NG + g.ny)) {
+        const int by = g.bc[2 + (j >= NG + g.ny)];
+        const double* st = ghost_state(g, by, xc, yc, t);
+        if (st) {
+            for (int v = 0; v < nv; ++v)
+                W[(long long)v * g.plane + (long long)j * g.pitch + i] = (E)st[v == nv - 1 ? 3 : v];
+            return;
+        }
+        sj = ghost_src(by, g.ny, j, fyn, fya);
+    }
+    int si = i;
+    const double* sx = nullptr;  // x ghost column under an inflow rule
+    if (i < NG || i >= NG + g.nx) {
+        const int bx = g.bc[(i >= NG + g.nx)];
+        sx = ghost_state(g, bx, xc, yc, t);
+        if (!sx) si = ghost_src(bx, g.nx, i, fxn, fxa);
+    }
     for (int v = 0; v < nv; ++v) {
-        E val = W[(long long)v * g.plane + (long long)sj * g.pitch + si];
+        E val = sx ? (E)sx[v == nv - 1 ? 3 : v] : W[(long long)v * g.plane + (long long)sj * g.pitch + si];
         // x rule flips the x velocity (v=1) for symmetry, both for no-slip
         const int vx = 1, vy = (g.dim == 2) ? 2 : -1;
         bool neg = false;

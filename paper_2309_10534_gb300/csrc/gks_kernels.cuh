@@ -32,13 +32,34 @@ struct DevState {
     unsigned int pad;
 };
 
+// state-setting boundary rules: conserved states (energy in slot 3) and the
+// moving oblique shock x_s(y, t) = x0 + (y - oy) cot + vx t
+struct BcStates {
+    double in[4], pre[4];
+    double x0, cot, vx;
+};
+
 struct GridDev {
     int dim, nx, ny, pitch, gy;
     long long plane;   // elements per variable plane = gy * pitch
     double dx, dy;
     int bc[4];
     double gamma, mu;
+    double ox, oy;     // domain origin (cell centres at ox + (i + 1/2) dx)
+    BcStates bs;
 };
+
+constexpr int BC_INFLOW = 5, BC_WALL_AFTER_X0 = 6, BC_MOVING_SHOCK = 7;
+
+// the state a state-setting rule gives the ghost centred at (x, y) at time t,
+// or nullptr where the rule copies from the interior
+__device__ __forceinline__ const double* ghost_state(const GridDev& g, int bc, double x, double y, double t)
+{
+    if (bc == BC_INFLOW) return g.bs.in;
+    if (bc == BC_WALL_AFTER_X0) return (x < g.bs.x0) ? g.bs.in : nullptr;
+    if (bc == BC_MOVING_SHOCK) return (x < g.bs.x0 + (y - g.oy) * g.bs.cot + g.bs.vx * t) ? g.bs.in : g.bs.pre;
+    return nullptr;
+}
 
 // ------------------------------------------------------------------ ghosts
 // source index of ghost position g (ghosted coordinate) along a line of n

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgks.so")
 
 GKS_OK, GKS_EINVAL, GKS_ENOMEM, GKS_ECUDA, GKS_ENONPHYSICAL, GKS_ETIMEOUT, GKS_EUNSUPPORTED = range(7)
-BC = {"periodic": 0, "zerograd": 1, "symmetry": 2, "noslip": 3, "reflect": 4}
+BC = {"periodic": 0, "zerograd": 1, "symmetry": 2, "noslip": 3, "reflect": 4,
+      "inflow": 5, "wall_after_x0": 6, "moving_shock": 7}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32x2": 2}
 TAU = {"zero": 0, "euler": 1, "ns": 2}
 RECON = {"teno_d": 0, "weno_ao": 1, "weno_z": 2, "teno5": 3}
@@ -30,6 +31,11 @@ class GridDesc(C.Structure):
 
 class Gas(C.Structure):
     _fields_ = [("gamma", C.c_double), ("mu", C.c_double), ("Pr", C.c_double)]
+
+
+class BoundaryStates(C.Structure):
+    _fields_ = [("inflow", C.c_double * 4), ("pre", C.c_double * 4), ("shock_x0", C.c_double),
+                ("shock_theta", C.c_double), ("shock_speed", C.c_double)]
 
 
 class Scheme(C.Structure):
@@ -184,6 +190,22 @@ class Solver:
     def set_scheme(self, **kw):
         self._check(lib().gks_set_scheme(self.h, C.byref(default_scheme(**kw))))
 
+    def set_boundary_states(self, bc_in=None, bc_pre=None, shock_x0=0.0, shock_theta=np.pi / 3, shock_speed=0.0):
+        """States of the state-setting boundary rules (inflow, wall after x0,
+        moving shock): conserved (rho, rho u, rho v, E) (1-D: (rho, rho u, E))."""
+        b = BoundaryStates()
+        for dst, st in ((b.inflow, bc_in), (b.pre, bc_pre)):
+            if st is not None:
+                st = [float(x) for x in st]
+                if len(st) == 3:
+                    st = [st[0], st[1], 0.0, st[2]]
+                dst[:] = st
+        b.shock_x0, b.shock_theta, b.shock_speed = shock_x0, shock_theta, shock_speed
+        L = lib()
+        L.gks_set_boundary_states.argtypes = [_vp, C.POINTER(BoundaryStates)]
+        L.gks_set_boundary_states.restype = C.c_int
+        self._check(L.gks_set_boundary_states(self.h, C.byref(b)))
+
     def set_stream(self, stream_handle: int):
         self._check(lib().gks_set_stream(self.h, _vp(stream_handle)))
 
@@ -283,6 +305,8 @@ def solver_for(setup, precision="fp64", **kw) -> Solver:
                 mu=setup.mu, Pr=setup.Pr, tau=setup.tau, cfl=setup.cfl)
     args.update(kw)
     s = Solver(setup.dim, setup.nx, setup.ny, **args)
+    if setup.bcstate:
+        s.set_boundary_states(**setup.bcstate)
     s.set_state(setup.W)
     return s
 

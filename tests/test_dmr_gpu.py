@@ -1,0 +1,123 @@
+"""The double Mach reflection (Sec. 5.7: inflow, wall after x = 1/6 and the
+exact moving Mach 10 shock as boundaries) and the Riemann configuration 6
+(Sec. 5.6 b) through the GPU path against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2309_10534_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gks():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_10534_gb300 import build, gks as G
+    build.build()
+    return G
+
+
+def rel_l1(a, b):
+    a = np.asarray(a).reshape(a.shape[0], -1)
+    b = np.asarray(b).reshape(b.shape[0], -1)
+    return float(np.abs(a - b).sum() / np.abs(b).sum())
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_dmr_first_step(gks, precision, tol):
+    """One CFL step from the initial Mach 10 shock on 96 x 24 (ragged tiles):
+    the ghosts of W at t = 0 and of W* at dt/2 come from the state-setting
+    rules on the left, bottom and top."""
+    s = WL.double_mach(96, 24)
+    P = O.make_problem(2, 96, 24, **s.problem_kwargs())
+    dt = O.dt(P, s.W)
+    Wo = O.step(P, s.W, dt)
+    S = gks.solver_for(s, precision)
+    S.step(dt)
+    err = rel_l1(S.get_state(), Wo)
+    print(f"{precision}: {err:.3e}")
+    assert err < tol
+
+
+def test_dmr_run_fp64(gks):
+    """25 CFL steps (t ~ 0.04: the top boundary's shock moves ~9 cells) on
+    96 x 24, float64, against the oracle's own round-off envelope."""
+    s = WL.double_mach(96, 24)
+    P = O.make_problem(2, 96, 24, **s.problem_kwargs())
+    Wa, steps, t, _ = O.run(P, s.W, 1.0, max_steps=25)
+    rng = np.random.default_rng(0)
+    Wb = O.run(P, s.W * (1 + 1e-15 * rng.standard_normal(s.W.shape)), 1.0, max_steps=25)[0]
+    spread = rel_l1(Wb, Wa)
+    S = gks.solver_for(s, "fp64")
+    n, t_gpu = S.advance_to(1.0, max_steps=25)
+    assert n == steps and t_gpu == pytest.approx(t, rel=1e-12)
+    err = rel_l1(S.get_state(), Wa)
+    print(f"DMR 25 steps: {err:.3e} (envelope {spread:.2e})")
+    assert err <= max(1e-10, 10 * spread)
+
+
+def test_dmr_run_fp32(gks):
+    """The same run with the float32 flux: within 1e-3 relative L1 of the
+    float64 oracle (Mach 10 shocks: float32 rounding moves TENO-D switches)."""
+    s = WL.double_mach(96, 24)
+    P = O.make_problem(2, 96, 24, **s.problem_kwargs())
+    Wa, steps, t, _ = O.run(P, s.W, 1.0, max_steps=25)
+    S = gks.solver_for(s, "fp32")
+    S.advance_to(t)
+    err = rel_l1(S.get_state(), Wa)
+    print(f"DMR fp32: {err:.3e}")
+    assert err < 1e-3
+    assert S.diagnostics().error_word == 0
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", None), ("fp32", 1e-3)])
+def test_riemann_config6_run(gks, precision, tol):
+    """Configuration 6 (four contact discontinuities, Sec. 5.6 b) on 64 x 64
+    to t = 0.1 at CFL 0.8: float64 within 10x the oracle's envelope, float32
+    within 1e-3."""
+    s = WL.riemann2d_config6(64, t_end=0.1)
+    P = O.make_problem(2, 64, 64, **s.problem_kwargs())
+    Wa = O.run(P, s.W, 0.1)[0]
+    if tol is None:
+        rng = np.random.default_rng(1)
+        Wb = O.run(P, s.W * (1 + 1e-15 * rng.standard_normal(s.W.shape)), 0.1)[0]
+        tol = max(1e-10, 10 * rel_l1(Wb, Wa))
+    S = gks.solver_for(s, precision)
+    S.advance_to(0.1)
+    err = rel_l1(S.get_state(), Wa)
+    print(f"config 6 {precision}: {err:.3e} (bound {tol:.2e})")
+    assert err < tol
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_inflow_1d_step(gks, precision, tol):
+    """1-D inflow rule: Sod's tube with the left ghosts set to a state other
+    than the edge cell's (the tube is fed with a faster flow)."""
+    s = WL.sod(200)
+    bcs = dict(bc_in=tuple(WL.conserved_1d(1.2, 0.4, 1.3, 1.4)))
+    kw = dict(s.problem_kwargs(), bc=("inflow", "zerograd", "zerograd", "zerograd"), **bcs)
+    P = O.make_problem(1, 200, **kw)
+    dt = O.dt(P, s.W)
+    Wo = O.step(P, s.W, dt)
+    Wo = O.step(P, Wo, dt)
+    S = gks.Solver(1, 200, precision=precision, bc=kw["bc"])
+    S.set_boundary_states(**bcs)
+    S.set_state(s.W)
+    S.step(dt)
+    S.step(dt)
+    assert rel_l1(S.get_state(), Wo) < tol
+
+
+def test_adjoint_refuses_state_setting_boundaries(gks):
+    S = gks.Solver(2, 16, 16, bc=("inflow", "zerograd", "zerograd", "zerograd"), precision="fp64", tau="zero")
+    S.set_state(WL.random_smooth_2d(16, 16, seed=1, kmax=2))
+    with pytest.raises(gks.GKSError):
+        gks.Adjoint(S, 2).forward(2, 0.01)
+
+
+def test_state_setting_rules_only_on_y_sides(gks):
+    with pytest.raises(gks.GKSError):
+        gks.Solver(2, 16, 16, bc=("moving_shock", "zerograd", "zerograd", "zerograd"))
