@@ -152,6 +152,19 @@ def sweep_traffic_from_profiles():
     return float(m.group(1)) if m else None
 
 
+def sweep_pipe_from_profiles():
+    """FMA-pipe activity of the sweep (ncu sm__pipe_fma_cycles_active, launch
+    1, fraction) from the committed ncu summary, if any: the FP32 pipe
+    throughput against its peak, beside the flop-based fraction."""
+    path = os.path.join(ROOT, "profiles", "sweep_fp32_riemann1024.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"^\| FMA pipe % \| ([0-9.]+)", text, re.M)
+    return float(m.group(1)) / 100.0 if m else None
+
+
 def cpu_baseline(steps_budget_s=15.0, n=96):
     """The oracle as it stands, on the host cores, on a bounded sample: the
     same problem on an n x n grid, CFL steps until ~steps_budget_s."""
@@ -602,7 +615,8 @@ def main():
                      "flops_per_launch": flops_per_launch, "launch_ms": sweep_avg_ms,
                      "peak_basis": "measured FP32 FMA-chain throughput on this GPU (gks_alu_peak)",
                      "peak_nominal": nominal,
-                     "sweep_share_of_step": sms32 / ms32 if ms32 else None},
+                     "sweep_share_of_step": sms32 / ms32 if ms32 else None,
+                     "fma_pipe_active_ncu": sweep_pipe_from_profiles()},
         "flops_per_cell_update": fm["flops_per_cell_update"],
         "clocks": clk,
     }

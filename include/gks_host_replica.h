@@ -25,11 +25,10 @@ int gks_host_time_coeffs(int precision, double s, double *cF, double *cD);
 /* TENO-D (Sec. 4.2) on five cell averages q[0..4] = Qbar_{i-2..i+2}:
  * faces[0..3] = value and xi-derivative at xi = +1/2, then at xi = -1/2;
  * gauss[0..3] = value and xi-derivative at xi = -1/(2 sqrt 3), then +1/(2 sqrt 3);
- * returns the large-stencil flag (1/0) or -1.  precision 2: the Gauss points
- * from the packed-pair float32 selection of the 2-D sweep's tangential
- * reconstruction (packed products and fused multiply-adds emulated on the
- * host with the same IEEE rounding; faces as precision 1); -2 if its two
- * lanes disagree. */
+ * returns the large-stencil flag (1/0) or -1.  precision 2: the packed-pair
+ * float32 selection, faces and Gauss points of the 2-D sweep (packed
+ * products and fused multiply-adds emulated on the host with the same IEEE
+ * rounding); -2 if its two lanes disagree. */
 int gks_host_teno(int precision, const double *q, double eps, int qpow, double ct1, double ct2,
                   double *faces, double *gauss);
 

@@ -37,8 +37,8 @@ int teno_t(const double* q, double eps, int qpow, double ct1, double ct2, double
 
 // packed TENO-D of the float32 2-D sweep: lane x holds q, lane y -q (the
 // selection is sign-symmetric, so lane y must give exactly the negated
-// values: a check that the lanes stay independent); faces from the scalar
-// float32 code, Gauss points from lane x; -2 if the lanes disagree
+// values: a check that the lanes stay independent); faces and Gauss points
+// from lane x; -2 if the lanes disagree
 int teno_packed(const double* q, double eps, int qpow, double ct1, double ct2, double* faces, double* gauss)
 {
     const int large = teno_t<float>(q, eps, qpow, ct1, ct2, faces, gauss);
@@ -47,6 +47,12 @@ int teno_packed(const double* q, double eps, int qpow, double ct1, double ct2, d
     const gks::TenoParams P{eps, qpow, ct1, ct2};
     gks::TenoSel2 S;
     gks::teno_select_x2(qq, gks::teno_t<float>(P), S);
+    gks::f2 fv[4];
+    gks::teno_faces_x2(S, fv[0], fv[1], fv[2], fv[3]);
+    for (int i = 0; i < 4; ++i) {
+        if (fv[i].y() != -fv[i].x()) return -2;
+        faces[i] = fv[i].x();
+    }
     const float gp[2] = {-0.28867513459481288f, 0.28867513459481288f};
     for (int i = 0; i < 2; ++i) {
         gks::f2 v, d;

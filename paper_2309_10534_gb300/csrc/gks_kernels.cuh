@@ -412,7 +412,31 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
     __syncthreads();
 
     // phase 1: normal TENO-D per (cell, row, var): cell c <-> normal n0-1+c
-    {
+    if constexpr (sizeof(T) == 4 && REC == 0) {
+        // float32 TENO-D: variables (0, 1) and (2, 3) as packed pairs
+        const float ih = (float)a.ihn;
+        constexpr int NC = TN + 2, NR = TT + 4;
+        for (int k = tid; k < 2 * NC * NR; k += NT) {
+            const int vv = 2 * (k / (NC * NR)), e = k % (NC * NR);
+            const int r = e / NC, c = e % NC;
+            f2 q[5];
+#pragma unroll
+            for (int s = 0; s < 5; ++s) q[s] = f2(sm.w[vv][r][c + s], sm.w[vv + 1][r][c + s]);
+            TenoSel2 S;
+            teno_select_x2(q, tnn, S);
+            f2 vp, dp, vm, dm;
+            teno_faces_x2(S, vp, dp, vm, dm);
+            const f2 dpi = dp * f2(ih), dmi = dm * f2(ih);
+            if (c <= TN) {
+                sm.rec[0][vv][r][c] = vp.x(); sm.rec[0][vv + 1][r][c] = vp.y();
+                sm.rec[1][vv][r][c] = dpi.x(); sm.rec[1][vv + 1][r][c] = dpi.y();
+            }
+            if (c >= 1) {
+                sm.rec[2][vv][r][c - 1] = vm.x(); sm.rec[2][vv + 1][r][c - 1] = vm.y();
+                sm.rec[3][vv][r][c - 1] = dmi.x(); sm.rec[3][vv + 1][r][c - 1] = dmi.y();
+            }
+        }
+    } else {
         const T ih = (T)a.ihn;
         constexpr int NC = TN + 2, NR = TT + 4;
         for (int k = tid; k < 4 * NC * NR; k += NT) {

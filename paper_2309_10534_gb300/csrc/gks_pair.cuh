@@ -154,6 +154,31 @@ GKS_HD void teno_select_x2(const f2 q[5], const TenoT<float>& P, TenoSel2& S)
     S.u4 = C.u4 * lm;
 }
 
+// values and xi-derivatives at the faces xi = +-1/2 of both lanes' selection:
+// the quartic in the Legendre-type basis (P2(1/2) = 1/6, P3(1/2) = 1/20,
+// P4(1/2) = 1/70; P2' = 1, P3' = 3/5, P4' = 2/7 at 1/2, odd ones change sign
+// at -1/2), equal to Eqs. (4.8), (4.9) and their mirror, plus the
+// sub-stencil blend of Eqs. (4.13), (4.14)
+GKS_HD void teno_faces_x2(const TenoSel2& S, f2& vp, f2& dp, f2& vm, f2& dm)
+{
+    const f2 even = S.q2 + S.u2 * f2(1.0f / 6.0f) + S.u4 * f2(1.0f / 70.0f);
+    const f2 odd = S.u1 * f2(0.5f) + S.u3 * f2(0.05f);
+    const f2 deven = S.u1 + S.u3 * f2(0.6f);
+    const f2 dodd = S.u2 + S.u4 * f2(2.0f / 7.0f);
+    vp = even + odd;
+    vm = even - odd;
+    dp = deven + dodd;
+    dm = deven - dodd;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const f2 bh = f2(0.5f) * S.b[k], c6 = S.c[k] * f2(1.0f / 6.0f);
+        vp += S.w[k] * (bh + c6);
+        vm += S.w[k] * (c6 - bh);
+        dp += S.w[k] * (S.b[k] + S.c[k]);
+        dm += S.w[k] * (S.b[k] - S.c[k]);
+    }
+}
+
 // value and xi-derivative at the Gauss point xi = g of both lanes' selection
 // (quartic: P2(g) = 0, P3(g) = -g/15, P4(g) = -1/180, P3'(g) = 1/10,
 // P4'(g) = -2g/21; quadratics: q2 + b g + c (g^2 - 1/12) = q2 + b g)

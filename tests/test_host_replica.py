@@ -61,8 +61,9 @@ def test_teno_matches_oracle(G):
             assert np.allclose(f32, faces, rtol=0, atol=2e-5 * (1 + abs(q).max()))
             # packed-pair selection of the float32 2-D sweep (lanes checked
             # against each other inside): the same choice, float32 values
-            _, gp2, lp2 = G.host_teno(q, "fp32x2")
+            f2_, gp2, lp2 = G.host_teno(q, "fp32x2")
             assert lp2 == l32, q
+            assert np.allclose(f2_, faces, rtol=0, atol=2e-5 * (1 + abs(q).max())), q
             assert np.allclose(gp2, g32, rtol=0, atol=2e-5 * (1 + abs(q).max())), q
             assert np.allclose(gp2, gauss, rtol=0, atol=2e-5 * (1 + abs(q).max())), q
 
