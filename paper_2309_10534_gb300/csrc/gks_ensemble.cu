@@ -117,17 +117,16 @@ __device__ void stage_chunk(ChunkSmem<T, NT>& sm, double* W, T* Ws, T* A, long l
     __syncthreads();
     const T ih = (T)idx;
     for (int c = tid; c < TN + 2; c += NT) {  // cell c0-1+c
+        T q[3][5], vp[3], dp[3], vm[3], dm[3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v)
+#pragma unroll
+            for (int s = 0; s < 5; ++s) q[v][s] = sm.q[v][c + s];
+        recon_cell3<0>(q, tn, vp, dp, vm, dm);  // the single-grid 1-D kernel's arithmetic
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-            T q[5];
-#pragma unroll
-            for (int s = 0; s < 5; ++s) q[s] = sm.q[v][c + s];
-            TenoSel<T> S;
-            teno_select(q, tn, S);
-            T vp, dp, vm, dm;
-            teno_faces(q, S, vp, dp, vm, dm);
-            if (c <= TN) { sm.L[v][0][c] = vp; sm.L[v][1][c] = dp * ih; }
-            if (c >= 1) { sm.R[v][0][c - 1] = vm; sm.R[v][1][c - 1] = dm * ih; }
+            if (c <= TN) { sm.L[v][0][c] = vp[v]; sm.L[v][1][c] = dp[v] * ih; }
+            if (c >= 1) { sm.R[v][0][c - 1] = vm[v]; sm.R[v][1][c - 1] = dm[v] * ih; }
         }
     }
     __syncthreads();

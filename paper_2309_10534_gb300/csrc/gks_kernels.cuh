@@ -212,19 +212,18 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
     }
     __syncthreads();
     const T idx_ = (T)a.idx;
-    // phase 1: TENO-D per cell c (interior i0 - 1 + c), both faces
+    // phase 1: reconstruction per cell c (interior i0 - 1 + c), both faces
     for (int c = tid; c < TN + 2; c += NT) {
+        T q[3][5], vp[3], dp[3], vm[3], dm[3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v)
+#pragma unroll
+            for (int s = 0; s < 5; ++s) q[v][s] = sq[v][c + s];
+        recon_cell3<REC>(q, tn, vp, dp, vm, dm);
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-            T q[5];
-#pragma unroll
-            for (int s = 0; s < 5; ++s) q[s] = sq[v][c + s];
-            TenoSel<T> S;
-            rec_select<REC>(q, tn, S);
-            T vp, dp, vm, dm;
-            rec_faces<REC>(q, S, vp, dp, vm, dm);
-            if (c <= TN) { sL[v][0][c] = vp; sL[v][1][c] = dp * idx_; }
-            if (c >= 1) { sR[v][0][c - 1] = vm; sR[v][1][c - 1] = dm * idx_; }
+            if (c <= TN) { sL[v][0][c] = vp[v]; sL[v][1][c] = dp[v] * idx_; }
+            if (c >= 1) { sR[v][0][c - 1] = vm[v]; sR[v][1][c - 1] = dm[v] * idx_; }
         }
     }
     __syncthreads();

@@ -179,6 +179,38 @@ GKS_HD void teno_faces_x2(const TenoSel2& S, f2& vp, f2& dp, f2& vm, f2& dm)
     }
 }
 
+// Normal reconstruction of one 1-D cell's three variables (rho, rho u, E):
+// float32 TENO-D runs (rho, rho u) as one packed pair and E alone; otherwise
+// variable by variable with the scheme's reconstruction.  Face values and
+// xi-slopes at +1/2 (vp, dp) and -1/2 (vm, dm).
+template <int REC, typename T>
+GKS_HD void recon_cell3(const T q[3][5], const TenoT<T>& P, T* vp, T* dp, T* vm, T* dm)
+{
+    if constexpr (sizeof(T) == 4 && REC == 0) {
+        f2 qq[5];
+#pragma unroll
+        for (int s = 0; s < 5; ++s) qq[s] = f2(q[0][s], q[1][s]);
+        TenoSel2 S2;
+        teno_select_x2(qq, P, S2);
+        f2 a, b, c, d;
+        teno_faces_x2(S2, a, b, c, d);
+        vp[0] = a.x(); vp[1] = a.y();
+        dp[0] = b.x(); dp[1] = b.y();
+        vm[0] = c.x(); vm[1] = c.y();
+        dm[0] = d.x(); dm[1] = d.y();
+        TenoSel<T> S;
+        teno_select(q[2], P, S);
+        teno_faces(q[2], S, vp[2], dp[2], vm[2], dm[2]);
+    } else {
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            TenoSel<T> S;
+            rec_select<REC>(q[v], P, S);
+            rec_faces<REC>(q[v], S, vp[v], dp[v], vm[v], dm[v]);
+        }
+    }
+}
+
 // value and xi-derivative at the Gauss point xi = g of both lanes' selection
 // (quartic: P2(g) = 0, P3(g) = -g/15, P4(g) = -1/180, P3'(g) = 1/10,
 // P4'(g) = -2g/21; quadratics: q2 + b g + c (g^2 - 1/12) = q2 + b g)

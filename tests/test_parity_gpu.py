@@ -278,6 +278,33 @@ def test_riemann_1024_sampled_windows(precision):
         assert rel_l1(g, ref) < TOL[precision], (i0, j0)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_viscous_2048_sampled_windows(precision):
+    """Full size of the viscous shock tube (Sec. 5.8: 2048 x 1024, Re = 200,
+    Pr = 0.73, no-slip walls, symmetric top, NS collision time with the
+    Prandtl fix), one step in the launch configuration the bench times after
+    20 float64 steps; oracle on windows at the walls, the corners, the top and
+    across the shock."""
+    s = WL.viscous_shock_tube(2048, 1024)
+    P = O.make_problem(2, 2048, 1024, **s.problem_kwargs())
+    S = G().solver_for(s, "fp64")
+    for _ in range(20):
+        S.step(0.0)
+    W1 = S.get_state()
+    dt = O.dt(P, W1)
+    S2 = G().solver_for(s, precision)
+    S2.set_state(W1)
+    S2.step(dt)
+    got = S2.get_state()
+    rng = np.random.default_rng(2)
+    corners = [(0, 0), (2040, 0), (0, 1016), (2040, 1016), (1020, 0), (1020, 1016), (1020, 500)]
+    corners += [tuple(int(x) for x in rng.integers(0, 1016, 2)) for _ in range(2)]
+    for (i0, j0) in corners:
+        ref = _window_step(P, W1, dt, i0, j0, 8)
+        g = got[:, j0:j0 + 8, i0:i0 + 8]
+        assert rel_l1(g, ref) < TOL[precision], (i0, j0, rel_l1(g, ref))
+
+
 def test_nonphysical_state_reported():
     W = WL.random_smooth_2d(16, 16, 3)
     W[0, 5, 5] = -1.0  # negative density
