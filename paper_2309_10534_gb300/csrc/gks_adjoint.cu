@@ -438,6 +438,13 @@ struct gks_adjoint {
     double *lam = nullptr, *lams = nullptr, *gacc = nullptr, *nxt = nullptr;
     void *lines = nullptr, *contrib = nullptr, *dcell = nullptr;
     long long launches = 0;
+    // one full segment's recomputation and reverse sweep, captured once and
+    // replayed for every full segment (fixed buffers; dt and the context's
+    // parameters are baked in)
+    cudaGraphExec_t seg_exec = nullptr;
+    double seg_dt = 0.0;
+    long long seg_version = -1, seg_kernels = 0, seg_ctx_kernels = 0;
+    bool seg_eager = false;  // the segment does not return its buffers to place: no graph
 };
 
 namespace {
@@ -655,6 +662,7 @@ gks_status gks_adjoint_create(gks_ctx* c, int checkpoint_every, gks_adjoint** ou
 void gks_adjoint_destroy(gks_adjoint* A)
 {
     if (!A) return;
+    if (A->seg_exec) cudaGraphExecDestroy(A->seg_exec);
     for (double* p : A->ckpt) cudaFree(p);
     for (double* p : A->seg) cudaFree(p);
     for (void* p : A->segs) cudaFree(p);
@@ -689,6 +697,75 @@ gks_status gks_adjoint_forward(gks_adjoint* A, int nsteps, double dt)
     return GKS_OK;
 }
 
+namespace {
+
+// recompute a segment of len steps from the state in the context, stage by
+// stage (the same kernels and W as the forward pass's steps), keeping W and
+// W* of every step, then reverse its steps
+gks_status run_segment(gks_adjoint* A, int len)
+{
+    gks_ctx* c = A->c;
+    gks_status s;
+    const void* ws = c->Wsf ? static_cast<const void*>(c->Wsf) : static_cast<const void*>(c->Ws);
+    for (int n = 0; n < len; ++n) {
+        CK(cudaMemcpyAsync(A->seg[n], c->W, c->arr_bytes, cudaMemcpyDeviceToDevice, c->stream));
+        if ((s = gks_stage(c, 1, A->dt))) return s;
+        CK(cudaMemcpyAsync(A->segs[n], ws, wstar_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+        if (n + 1 < len && (s = gks_stage(c, 2, A->dt))) return s;
+    }
+    for (int n = len - 1; n >= 0; --n)
+        if ((s = adjoint_step(A, A->seg[n], A->segs[n]))) return s;
+    return GKS_OK;
+}
+
+// capture run_segment(k) as a graph (once per dt and context parameters);
+// leaves seg_exec null where the segment's buffer rotation does not return
+// to its start (odd k) so that replays would read the wrong buffers
+gks_status segment_graph(gks_adjoint* A)
+{
+    gks_ctx* c = A->c;
+    if (A->seg_eager) return GKS_OK;
+    if (A->seg_exec && A->seg_dt == A->dt && A->seg_version == c->param_version) return GKS_OK;
+    if (A->seg_exec) {
+        cudaGraphExecDestroy(A->seg_exec);
+        A->seg_exec = nullptr;
+    }
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    double* const before[4] = {A->lam, A->lams, A->gacc, A->nxt};
+    const long long L0 = A->launches, C0 = c->launches;
+    cudaStream_t keep = c->stream;
+    c->stream = c->cap_stream;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    gks_status s = run_segment(A, A->k);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    c->capturing = false;
+    c->stream = keep;
+    A->seg_kernels = A->launches - L0;
+    A->seg_ctx_kernels = c->launches - C0;
+    A->launches = L0;  // captured, not launched
+    c->launches = C0;
+    const bool in_place = A->lam == before[0] && A->lams == before[1] && A->gacc == before[2] && A->nxt == before[3];
+    A->lam = before[0], A->lams = before[1], A->gacc = before[2], A->nxt = before[3];
+    if (s != GKS_OK || e != cudaSuccess || !in_place) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (s != GKS_OK) return s;
+        if (e != cudaSuccess) return rt::fail(c, GKS_ECUDA, "capturing the adjoint segment: %s", cudaGetErrorString(e));
+        A->seg_eager = true;
+        return GKS_OK;
+    }
+    e = cudaGraphInstantiate(&A->seg_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    A->seg_dt = A->dt;
+    A->seg_version = c->param_version;
+    return GKS_OK;
+}
+
+}  // namespace
+
 gks_status gks_adjoint_backward(gks_adjoint* A, const double* gWN, double* gW0, int on_device)
 {
     if (!A || !gWN || !gW0) return GKS_EINVAL;
@@ -702,17 +779,16 @@ gks_status gks_adjoint_backward(gks_adjoint* A, const double* gWN, double* gW0, 
     for (int sgi = ncp - 1; sgi >= 0; --sgi) {
         const int n0 = sgi * A->k, n1 = std::min(n0 + A->k, A->nsteps);
         if ((s = load_state(A, A->ckpt[sgi]))) return s;
-        // recompute the segment stage by stage (the same kernels and W as the
-        // forward pass's steps), keeping W and W* of every step
-        const void* ws = c->Wsf ? static_cast<const void*>(c->Wsf) : static_cast<const void*>(c->Ws);
-        for (int n = n0; n < n1; ++n) {
-            CK(cudaMemcpyAsync(A->seg[n - n0], c->W, c->arr_bytes, cudaMemcpyDeviceToDevice, c->stream));
-            if ((s = gks_stage(c, 1, A->dt))) return s;
-            CK(cudaMemcpyAsync(A->segs[n - n0], ws, wstar_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
-            if (n + 1 < n1 && (s = gks_stage(c, 2, A->dt))) return s;
+        if (n1 - n0 == A->k) {
+            if ((s = segment_graph(A))) return s;
+            if (A->seg_exec) {
+                CK(cudaGraphLaunch(A->seg_exec, c->stream));
+                A->launches += A->seg_kernels;
+                c->launches += A->seg_ctx_kernels;
+                continue;
+            }
         }
-        for (int n = n1 - 1; n >= n0; --n)
-            if ((s = adjoint_step(A, A->seg[n - n0], A->segs[n - n0]))) return s;
+        if ((s = run_segment(A, n1 - n0))) return s;
     }
     if ((s = rt::copy_interior(c, A->lam, gW0, on_device, false))) return s;
     // leave the context at the forward pass's final state
