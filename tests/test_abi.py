@@ -60,6 +60,12 @@ def test_create_rejects_bad_descriptors_before_touching_the_device(libpath):
     d.bc[0], d.bc[1] = 0, 1  # periodic on one side only
     assert L.gks_create(ctypes.byref(d), ctypes.byref(h)) == gks.GKS_EINVAL
     assert L.gks_create(None, ctypes.byref(h)) == gks.GKS_EINVAL
+    d.bc[0], d.bc[1] = 1, 1
+    d.nx, d.ny = 65536, 32769  # above the 2^31-cell limit of 32-bit plane offsets
+    assert L.gks_create(ctypes.byref(d), ctypes.byref(h)) == gks.GKS_EINVAL
+    d.nx, d.ny = 10, 10
+    d.bc[0] = 6  # the wall-after-x0 rule belongs to the y sides
+    assert L.gks_create(ctypes.byref(d), ctypes.byref(h)) == gks.GKS_EINVAL
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
