@@ -152,16 +152,16 @@ def sweep_traffic_from_profiles():
     return float(m.group(1)) if m else None
 
 
-def sweep_pipe_from_profiles():
-    """FMA-pipe activity of the sweep (ncu sm__pipe_fma_cycles_active, launch
-    1, fraction) from the committed ncu summary, if any: the FP32 pipe
-    throughput against its peak, beside the flop-based fraction."""
-    path = os.path.join(ROOT, "profiles", "sweep_fp32_riemann1024.md")
+def sweep_pipe_from_profiles(name="sweep_fp32_riemann1024.md", pipe="FMA"):
+    """Pipe activity of a sweep kernel (ncu sm__pipe_*_cycles_active, launch
+    1, fraction) from the committed ncu summary, if any: the FP32 (FMA) or
+    FP64 pipe throughput against its peak, beside the flop-based fraction."""
+    path = os.path.join(ROOT, "profiles", name)
     try:
         text = open(path).read()
     except OSError:
         return None
-    m = re.search(r"^\| FMA pipe % \| ([0-9.]+)", text, re.M)
+    m = re.search(r"^\| %s pipe %% \| ([0-9.]+)" % pipe, text, re.M)
     return float(m.group(1)) / 100.0 if m else None
 
 
@@ -605,7 +605,8 @@ def main():
         "fp64": {"value": cells * k64 * world / (ms64 * 1e-3), "unit": UNIT, "steps": k64,
                  "ms_per_step": ms64 / k64, "flops_per_cell_update": fm64["flops_per_cell_update"],
                  "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": peak64, "unit": "TFLOP/s",
-                              "frac": fp64_tflops / peak64, "basis": "whole step vs measured FP64 FMA peak"}},
+                              "frac": fp64_tflops / peak64, "basis": "whole step vs measured FP64 FMA peak",
+                              "fp64_pipe_active_ncu": sweep_pipe_from_profiles("sweep_fp64_riemann1024.md", "FP64")}},
         "fp32_rel_l1_vs_fp64": rel_l1,
         "gpu_launches": launches32,
         "e2e": {"value": cells * args.steps * world / e2e_s, "unit": UNIT,
