@@ -1,15 +1,18 @@
-// gks_pair.cuh -- packed float32 pairs for the tangential reconstruction of
-// the float32 2-D sweep.
+// gks_pair.cuh -- packed float32 pairs for the reconstructions of the
+// float32 kernels.
 //
 // GB300's FP32 units execute two-lane packed instructions (FFMA2, FADD2,
-// FMUL2: one issue slot, two IEEE round-to-nearest results).  The 2-D sweep
-// is issue-bound, so the tangential TENO-D of a face side, which runs the
-// same arithmetic on two independent line-average streams (the value W and
-// the normal slope W_n), runs them as one packed stream (W in .x, W_n in .y).
-// `f2` is a drop-in arithmetic type for the templated kernel arithmetic: a
-// product stays unevaluated (`Prod`) until it is added, so `a * b + c`
-// becomes one fused multiply-add, as the compiler's contraction does for
-// scalar code.  Divisions and comparisons run per lane.
+// FMUL2: one issue slot, two IEEE round-to-nearest results).  Where the same
+// TENO-D arithmetic runs on two independent streams, the float32 kernels run
+// them as one packed stream: in the 2-D sweep the normal reconstruction of
+// variables (0, 1) and (2, 3) and the tangential reconstruction of a face
+// side's value and normal-slope line averages; in the 1-D kernels the
+// normal reconstruction of (rho, rho u).  (The flux's two sides were
+// measured packed the same way and kept scalar: no gain.)  `f2` is a drop-in
+// arithmetic type for the templated kernel arithmetic: a product stays
+// unevaluated (`Prod`) until it is added, so `a * b + c` becomes one fused
+// multiply-add, as the compiler's contraction does for scalar code.
+// Divisions and comparisons run per lane.
 #pragma once
 
 #include "gks_device.cuh"
