@@ -43,7 +43,9 @@ int gks_host_point_flux(int dim, int precision, int tau_mode, double gamma, doub
                         const double *Wr, const double *Wrn, const double *Wrt,
                         double *F, double *dF);
 
-/* WENO5-AO (Sec. 3.2) on five cell averages, outputs as gks_host_teno. */
+/* WENO5-AO (Sec. 3.2) on five cell averages, outputs as gks_host_teno;
+ * precision 2: the packed-pair float32 form of the 2-D sweep (-2 if its two
+ * lanes disagree). */
 int gks_host_weno_ao(int precision, const double *q, double eps_ao, double d_hi, double d_lo,
                      double *faces, double *gauss);
 

@@ -172,12 +172,37 @@ int weno_ao_t(const double* q, double eps_ao, double d_hi, double d_lo, double* 
     return 0;
 }
 
+// packed WENO5-AO of the float32 2-D sweep: lane x holds q, lane y -q (its
+// weights are sign-symmetric, so lane y must give exactly the negated
+// values); -2 if the lanes disagree
+int weno_ao_packed(const double* q, double eps_ao, double d_hi, double d_lo, double* faces, double* gauss)
+{
+    gks::f2 qq[5];
+    for (int k = 0; k < 5; ++k) qq[k] = gks::f2((float)q[k], -(float)q[k]);
+    gks::TenoParams P{1e-40, 7, 1e-7, 1e-5};
+    P.recon = 1;
+    P.d_hi = d_hi;
+    P.d_lo = d_lo;
+    P.eps_ao = eps_ao;
+    const gks::TenoT<float> Pf = gks::teno_t<float>(P);
+    gks::f2 fv[4], gv[4];
+    gks::packed_faces<1>(qq, Pf, fv[0], fv[1], fv[2], fv[3]);
+    gks::packed_gauss<1>(qq, Pf, -0.28867513459481288f, 0.28867513459481288f, gv[0], gv[1], gv[2], gv[3]);
+    for (int i = 0; i < 4; ++i) {
+        if (fv[i].y() != -fv[i].x() || gv[i].y() != -gv[i].x()) return -2;
+        faces[i] = fv[i].x();
+        gauss[i] = gv[i].x();
+    }
+    return 0;
+}
+
 }  // namespace
 
 extern "C" int gks_host_weno_ao(int precision, const double* q, double eps_ao, double d_hi, double d_lo,
                                 double* faces, double* gauss)
 {
     if (!q || !faces || !gauss || !(d_hi > 0.0)) return -1;
+    if (precision == 2) return weno_ao_packed(q, eps_ao, d_hi, d_lo, faces, gauss);
     return precision == 1 ? weno_ao_t<float>(q, eps_ao, d_hi, d_lo, faces, gauss)
                           : weno_ao_t<double>(q, eps_ao, d_hi, d_lo, faces, gauss);
 }

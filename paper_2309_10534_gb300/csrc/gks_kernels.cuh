@@ -411,8 +411,8 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
     __syncthreads();
 
     // phase 1: normal TENO-D per (cell, row, var): cell c <-> normal n0-1+c
-    if constexpr (sizeof(T) == 4 && REC == 0) {
-        // float32 TENO-D: variables (0, 1) and (2, 3) as packed pairs
+    if constexpr (sizeof(T) == 4 && REC <= 1) {
+        // float32 TENO-D / WENO5-AO: variables (0, 1) and (2, 3) as packed pairs
         const float ih = (float)a.ihn;
         constexpr int NC = TN + 2, NR = TT + 4;
         for (int k = tid; k < 2 * NC * NR; k += NT) {
@@ -421,10 +421,8 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
             f2 q[5];
 #pragma unroll
             for (int s = 0; s < 5; ++s) q[s] = f2(sm.w[vv][r][c + s], sm.w[vv + 1][r][c + s]);
-            TenoSel2 S;
-            teno_select_x2(q, tnn, S);
             f2 vp, dp, vm, dm;
-            teno_faces_x2(S, vp, dp, vm, dm);
+            packed_faces<REC>(q, tnn, vp, dp, vm, dm);
             const f2 dpi = dp * f2(ih), dmi = dm * f2(ih);
             if (c <= TN) {
                 sm.rec[0][vv][r][c] = vp.x(); sm.rec[0][vv + 1][r][c] = vp.y();
@@ -476,16 +474,13 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
             // the two Gauss points: value and tangential derivative of W,
             // value of Wn
             T wa, wda, wb, wdb, na, nb;
-            if constexpr (sizeof(T) == 4 && REC == 0) {
+            if constexpr (sizeof(T) == 4 && REC <= 1) {
                 // both streams as one packed pair (x: W, y: Wn)
                 f2 q[5];
 #pragma unroll
                 for (int s = 0; s < 5; ++s) q[s] = f2(sm.rec[2 * gpi][v][r + s][f], sm.rec[2 * gpi + 1][v][r + s][f]);
-                TenoSel2 S;
-                teno_select_x2(q, tnt, S);
                 f2 va, da, vb, db;
-                teno_gauss_x2(S, gA, va, da);
-                teno_gauss_x2(S, gB, vb, db);
+                packed_gauss<REC>(q, tnt, gA, gB, va, da, vb, db);
                 wa = va.x(), wda = da.x(), wb = vb.x(), wdb = db.x(), na = va.y(), nb = vb.y();
             } else {
                 T q[5];

@@ -229,4 +229,57 @@ GKS_HD void teno_gauss_x2(const TenoSel2& S, float g, f2& v, f2& d)
     }
 }
 
+GKS_HD f2 fabs(f2 a) { return f2(fabsf(a.v.x), fabsf(a.v.y)); }
+
+// the reconstruction parameters broadcast to both lanes (WENO5-AO)
+GKS_HD TenoT<f2> pair_teno(const TenoT<float>& P)
+{
+    TenoT<f2> Q;
+    Q.eps = f2(P.eps);
+    Q.ct1 = f2(P.ct1);
+    Q.ct2 = f2(P.ct2);
+    Q.q = P.q;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Q.g[k] = f2(P.g[k]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Q.gr[k] = f2(P.gr[k]);
+    Q.ig3 = f2(P.ig3);
+    Q.eps_ao = f2(P.eps_ao);
+    return Q;
+}
+
+// The scheme's reconstruction of two stencils at once: face values and
+// xi-slopes (normal direction), or values and xi-derivatives at the two
+// Gauss points (tangential).  REC 0: TENO-D with the folded selection above;
+// REC 1: WENO5-AO through its templated arithmetic, whose weights have no
+// branches.
+template <int REC>
+GKS_HD void packed_faces(const f2 q[5], const TenoT<float>& P, f2& vp, f2& dp, f2& vm, f2& dm)
+{
+    if constexpr (REC == 0) {
+        TenoSel2 S;
+        teno_select_x2(q, P, S);
+        teno_faces_x2(S, vp, dp, vm, dm);
+    } else {
+        TenoSel<f2> S;
+        ao_select(q, pair_teno(P), S);
+        ao_faces(q, S, vp, dp, vm, dm);
+    }
+}
+template <int REC>
+GKS_HD void packed_gauss(const f2 q[5], const TenoT<float>& P, float gA, float gB, f2& va, f2& da, f2& vb, f2& db)
+{
+    if constexpr (REC == 0) {
+        TenoSel2 S;
+        teno_select_x2(q, P, S);
+        teno_gauss_x2(S, gA, va, da);
+        teno_gauss_x2(S, gB, vb, db);
+    } else {
+        TenoSel<f2> S;
+        ao_select(q, pair_teno(P), S);
+        ao_gauss(S, f2(gA), va, da);
+        ao_gauss(S, f2(gB), vb, db);
+    }
+}
+
 }  // namespace gks

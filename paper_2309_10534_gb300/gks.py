@@ -386,7 +386,10 @@ def host_weno_ao(q, precision="fp64", eps_ao=1e-8, d_hi=0.85, d_lo=0.85):
     qq, pq = _arr(q, 5)
     f, pf = _arr(None, 4)
     g, pg = _arr(None, 4)
-    if _replica().gks_host_weno_ao(PRECISION[precision], pq, eps_ao, d_hi, d_lo, pf, pg):
+    r = _replica().gks_host_weno_ao(PRECISION[precision], pq, eps_ao, d_hi, d_lo, pf, pg)
+    if r == -2:
+        raise AssertionError("packed WENO5-AO lanes disagree")
+    if r:
         raise ValueError("bad argument")
     return f, g
 

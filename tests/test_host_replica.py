@@ -132,6 +132,10 @@ def test_weno_ao_matches_oracle(G):
         assert np.abs(gp - want_g).max() <= 1e-14 * scale
         f32, _ = G.host_weno_ao(q, precision="fp32")
         assert np.abs(f32 - want_f).max() <= 2e-6 * scale
+        # packed-pair form of the float32 sweep (lanes checked against each other inside)
+        fp2, gp2 = G.host_weno_ao(q, precision="fp32x2")
+        assert np.abs(fp2 - want_f).max() <= 2e-6 * scale
+        assert np.abs(gp2 - want_g).max() <= 2e-6 * scale
 
 
 @pytest.mark.parametrize("teno5", [False, True])
