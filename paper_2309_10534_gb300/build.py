@@ -68,7 +68,7 @@ def build(force: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         objs = list(ex.map(_compile, UNITS))
     tmp = OUT + ".tmp%d" % os.getpid()
-    subprocess.run([_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"], check=True)
+    subprocess.run([_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-ldl"], check=True)
     os.replace(tmp, OUT)
     return OUT
 

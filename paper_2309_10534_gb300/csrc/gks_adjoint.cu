@@ -679,6 +679,7 @@ void gks_adjoint_destroy(gks_adjoint* A)
 
 gks_status gks_adjoint_forward(gks_adjoint* A, int nsteps, double dt)
 {
+    const NvtxRange range("gks_adjoint_forward");
     if (!A || nsteps < 1 || !(dt > 0.0) || !std::isfinite(dt)) return GKS_EINVAL;
     gks_ctx* c = A->c;
     gks_status s = check_supported(c);
@@ -768,6 +769,7 @@ gks_status segment_graph(gks_adjoint* A)
 
 gks_status gks_adjoint_backward(gks_adjoint* A, const double* gWN, double* gW0, int on_device)
 {
+    const NvtxRange range("gks_adjoint_backward");
     if (!A || !gWN || !gW0) return GKS_EINVAL;
     gks_ctx* c = A->c;
     if (!A->have_forward) return rt::fail(c, GKS_EINVAL, "gks_adjoint_backward needs a completed forward pass");
@@ -778,6 +780,7 @@ gks_status gks_adjoint_backward(gks_adjoint* A, const double* gWN, double* gW0, 
     const int ncp = (A->nsteps + A->k - 1) / A->k;
     for (int sgi = ncp - 1; sgi >= 0; --sgi) {
         const int n0 = sgi * A->k, n1 = std::min(n0 + A->k, A->nsteps);
+        const NvtxRange seg_range("adjoint segment");
         if ((s = load_state(A, A->ckpt[sgi]))) return s;
         if (n1 - n0 == A->k) {
             if ((s = segment_graph(A))) return s;

@@ -682,6 +682,7 @@ gks_status gks_compute_dt(gks_ctx* c, double* dt)
 
 gks_status gks_stage(gks_ctx* c, int stage, double dt)
 {
+    const NvtxRange range("gks_stage");
     if (!c || (stage != 1 && stage != 2) || !(dt > 0.0) || !std::isfinite(dt)) return GKS_EINVAL;
     c->cfl_dt_ready = false;
     k_prepare<<<1, 32, 0, c->stream>>>(c->ds, 0, dt, 0.0, 0);
@@ -694,6 +695,7 @@ gks_status gks_stage(gks_ctx* c, int stage, double dt)
 
 gks_status gks_step(gks_ctx* c, double dt)
 {
+    const NvtxRange range("gks_step");
     if (!c || !std::isfinite(dt)) return GKS_EINVAL;
     gks_status s;
     if (dt > 0.0) {
@@ -716,6 +718,7 @@ gks_status gks_step(gks_ctx* c, double dt)
 
 gks_status gks_advance_to(gks_ctx* c, double t_end, long long max_steps, long long* steps_done, double* t_out)
 {
+    const NvtxRange range("gks_advance_to");
     if (!c || !std::isfinite(t_end)) return GKS_EINVAL;
     c->cfl_dt_ready = false;
     gks_status s;

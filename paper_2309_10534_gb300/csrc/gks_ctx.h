@@ -10,6 +10,7 @@
 #include "../../include/gks.h"
 #include "gks_kernels.cuh"
 #include "gks_launch.h"
+#include "gks_nvtx.h"
 
 struct gks_ctx {
     gks_grid_desc desc{};

@@ -29,6 +29,7 @@
 
 #include "../../include/gks.h"
 #include "gks_launch.h"
+#include "gks_nvtx.h"
 
 using namespace gks;
 
@@ -648,6 +649,7 @@ gks_status gks_batch_set_launch(gks_batch* b, int threads, int blocks_per_sm)
 
 gks_status gks_batch_advance_to(gks_batch* b, double t_end, long long max_steps)
 {
+    const NvtxRange range("gks_batch_advance_to");
     if (!b || !std::isfinite(t_end)) return GKS_EINVAL;
     gks_status s = run_batch(b, t_end, max_steps, b->threads, b->blocks_per_sm);
     if (s) return s;
