@@ -103,6 +103,90 @@ __device__ __forceinline__ void map2(const AdjDir& a, int& n, int& t, int n0, in
     else { n = n0 + y; t = t0 + x; }
 }
 
+// frozen selection as 4 bits: large, and the kept small stencils
+template <typename T>
+__device__ __forceinline__ unsigned sel_code(const TenoSel<T>& S)
+{
+    if (S.large) return 1u;
+    return (S.w[0] > T(0) ? 2u : 0u) | (S.w[1] > T(0) ? 4u : 0u) | (S.w[2] > T(0) ? 8u : 0u);
+}
+
+template <typename T>
+__device__ __forceinline__ void sel_decode(unsigned c, TenoSel<T>& S)
+{
+    S.large = (c & 1u) != 0;
+    const T d0 = (c & 2u) ? T(1) : T(0), d1 = (c & 4u) ? T(1) : T(0), d2 = (c & 8u) ? T(1) : T(0);
+    const T dsum = d0 + d1 + d2;
+    const T inv = S.large ? T(0) : T(1) / dsum;  // as teno_select: d_k / sum d
+    S.w[0] = d0 * inv;
+    S.w[1] = d1 * inv;
+    S.w[2] = d2 * inv;
+}
+
+// The forward's TENO-D of two stencils (qa, qb) in the forward's arithmetic:
+// the float32 sweep reconstructs variable pairs (0, 1), (2, 3) and, per face
+// side, the value and normal-slope streams as packed pairs, so the same
+// pairs here reproduce its values and selections bit for bit.  Returns the
+// two selection codes (qa in bits 0-3, qb in bits 4-7).
+template <typename T>
+__device__ __forceinline__ unsigned fwd_faces2(const T qa[5], const T qb[5], const TenoT<T>& P, T* vp, T* dp, T* vm,
+                                               T* dm)
+{
+    if constexpr (sizeof(T) == 4) {
+        f2 qq[5];
+#pragma unroll
+        for (int s = 0; s < 5; ++s) qq[s] = f2(qa[s], qb[s]);
+        TenoSel2 S2;
+        teno_select_x2(qq, P, S2);
+        f2 a, b, c, d;
+        teno_faces_x2(S2, a, b, c, d);
+        vp[0] = a.x(); dp[0] = b.x(); vm[0] = c.x(); dm[0] = d.x();
+        vp[1] = a.y(); dp[1] = b.y(); vm[1] = c.y(); dm[1] = d.y();
+        return sel_code_x(S2) | (sel_code_y(S2) << 4);
+    } else {
+        unsigned code = 0;
+        const T* q[2] = {qa, qb};
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            TenoSel<T> S;
+            teno_select(q[l], P, S);
+            teno_faces(q[l], S, vp[l], dp[l], vm[l], dm[l]);
+            code |= sel_code(S) << (4 * l);
+        }
+        return code;
+    }
+}
+template <typename T>
+__device__ __forceinline__ unsigned fwd_gauss2(const T qa[5], const T qb[5], const TenoT<T>& P, T gA, T gB, T* va,
+                                               T* da, T* vb, T* db)
+{
+    if constexpr (sizeof(T) == 4) {
+        f2 qq[5];
+#pragma unroll
+        for (int s = 0; s < 5; ++s) qq[s] = f2(qa[s], qb[s]);
+        TenoSel2 S2;
+        teno_select_x2(qq, P, S2);
+        f2 a, b, c, d;
+        teno_gauss_x2(S2, gA, a, b);
+        teno_gauss_x2(S2, gB, c, d);
+        va[0] = a.x(); da[0] = b.x(); vb[0] = c.x(); db[0] = d.x();
+        va[1] = a.y(); da[1] = b.y(); vb[1] = c.y(); db[1] = d.y();
+        return sel_code_x(S2) | (sel_code_y(S2) << 4);
+    } else {
+        unsigned code = 0;
+        const T* q[2] = {qa, qb};
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            TenoSel<T> S;
+            teno_select(q[l], P, S);
+            teno_gauss(S, gA, va[l], da[l]);
+            teno_gauss(S, gB, vb[l], db[l]);
+            code |= sel_code(S) << (4 * l);
+        }
+        return code;
+    }
+}
+
 // ---- phase 1: normal TENO-D of the stage input (as the forward sweep)
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_lines(GridDev g, AdjDir a, TenoT<T> tn)
@@ -116,43 +200,29 @@ __global__ void __launch_bounds__(256) k_adj_lines(GridDev g, AdjDir a, TenoT<T>
     T* L = static_cast<T*>(a.lines);
     const T ih = (T)a.ihn;
 #pragma unroll 1
-    for (int v = 0; v < 4; ++v) {
-        const long long base = (long long)gvar_(v, swap) * g.plane + org + r * a.st;
-        T q[5];
+    for (int vv = 0; vv < 4; vv += 2) {  // variable pairs (0, 1), (2, 3), as the forward
+        T q[2][5];
 #pragma unroll
-        for (int s = 0; s < 5; ++s) q[s] = load_src<T>(a, base + (i - 2 + s) * a.sn);
-        TenoSel<T> S;
-        teno_select(q, tn, S);
-        T vp, dp, vm, dm;
-        teno_faces(q, S, vp, dp, vm, dm);
-        if (i + 1 <= a.nn) {
-            L[(0 * 4 + v) * LP + lidx(a, i + 1, r)] = vp;
-            L[(1 * 4 + v) * LP + lidx(a, i + 1, r)] = dp * ih;
+        for (int l = 0; l < 2; ++l) {
+            const long long base = (long long)gvar_(vv + l, swap) * g.plane + org + r * a.st;
+#pragma unroll
+            for (int s = 0; s < 5; ++s) q[l][s] = load_src<T>(a, base + (i - 2 + s) * a.sn);
         }
-        if (i >= 0) {
-            L[(2 * 4 + v) * LP + lidx(a, i, r)] = vm;
-            L[(3 * 4 + v) * LP + lidx(a, i, r)] = dm * ih;
+        T vp[2], dp[2], vm[2], dm[2];
+        fwd_faces2(q[0], q[1], tn, vp, dp, vm, dm);
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const int v = vv + l;
+            if (i + 1 <= a.nn) {
+                L[(0 * 4 + v) * LP + lidx(a, i + 1, r)] = vp[l];
+                L[(1 * 4 + v) * LP + lidx(a, i + 1, r)] = dp[l] * ih;
+            }
+            if (i >= 0) {
+                L[(2 * 4 + v) * LP + lidx(a, i, r)] = vm[l];
+                L[(3 * 4 + v) * LP + lidx(a, i, r)] = dm[l] * ih;
+            }
         }
     }
-}
-
-// frozen selection as 4 bits: large, and the kept small stencils
-template <typename T>
-__device__ __forceinline__ unsigned sel_code(const TenoSel<T>& S)
-{
-    if (S.large) return 1u;
-    return (S.w[0] > T(0) ? 2u : 0u) | (S.w[1] > T(0) ? 4u : 0u) | (S.w[2] > T(0) ? 8u : 0u);
-}
-template <typename T>
-__device__ __forceinline__ void sel_decode(unsigned c, TenoSel<T>& S)
-{
-    S.large = (c & 1u) != 0;
-    const T d0 = (c & 2u) ? T(1) : T(0), d1 = (c & 4u) ? T(1) : T(0), d2 = (c & 8u) ? T(1) : T(0);
-    const T dsum = d0 + d1 + d2;
-    const T inv = S.large ? T(0) : T(1) / dsum;  // as teno_select: d_k / sum d
-    S.w[0] = d0 * inv;
-    S.w[1] = d1 * inv;
-    S.w[2] = d2 * inv;
 }
 
 // ---- Gauss points: forward tangential TENO-D, reverse point flux, transposed
@@ -184,30 +254,25 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4) ? 4 : 1) k_adj_gauss(Gri
     const T gA = T(-0.28867513459481288), gB = T(0.28867513459481288);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        T q[5];
-        TenoSel<T> S;
-        T va, da, vb, db;
+        // the side's value and normal-slope streams as one pair, as the forward
+        T q[2][5];
+        T va[2], da[2], vb[2], db[2];
 #pragma unroll
-        for (int s = 0; s < 5; ++s) q[s] = Lq[((2 * gp) * 4 + v) * LP + lidx(a, fc, rc - 2 + s)];
-        teno_select(q, tt, S);
-        codes |= sel_code(S) << (4 * v);
-        teno_gauss(S, gA, va, da);
-        teno_gauss(S, gB, vb, db);
-        T own = gp ? vb : va, got = __shfl_xor_sync(0xffffffffu, gp ? va : vb, 1);
+        for (int l = 0; l < 2; ++l)
+#pragma unroll
+            for (int s = 0; s < 5; ++s) q[l][s] = Lq[((2 * gp + l) * 4 + v) * LP + lidx(a, fc, rc - 2 + s)];
+        const unsigned c2 = fwd_gauss2(q[0], q[1], tt, gA, gB, va, da, vb, db);
+        codes |= (c2 & 15u) << (4 * v);
+        codes |= (c2 >> 4) << (4 * (4 + v));
+        T own = gp ? vb[0] : va[0], got = __shfl_xor_sync(0xffffffffu, gp ? va[0] : vb[0], 1);
         L.W[v] = gp ? got : own;
         R.W[v] = gp ? own : got;
-        own = (gp ? db : da) * iht;
-        got = __shfl_xor_sync(0xffffffffu, (gp ? da : db) * iht, 1);
+        own = (gp ? db[0] : da[0]) * iht;
+        got = __shfl_xor_sync(0xffffffffu, (gp ? da[0] : db[0]) * iht, 1);
         L.Wt[v] = gp ? got : own;
         R.Wt[v] = gp ? own : got;
-#pragma unroll
-        for (int s = 0; s < 5; ++s) q[s] = Lq[((2 * gp + 1) * 4 + v) * LP + lidx(a, fc, rc - 2 + s)];
-        teno_select(q, tt, S);
-        codes |= sel_code(S) << (4 * (4 + v));
-        teno_gauss(S, gA, va, da);
-        teno_gauss(S, gB, vb, db);
-        own = gp ? vb : va;
-        got = __shfl_xor_sync(0xffffffffu, gp ? va : vb, 1);
+        own = gp ? vb[1] : va[1];
+        got = __shfl_xor_sync(0xffffffffu, gp ? va[1] : vb[1], 1);
         L.Wn[v] = gp ? got : own;
         R.Wn[v] = gp ? own : got;
     }
@@ -325,26 +390,35 @@ __global__ void __launch_bounds__(256) k_adj_normal(GridDev g, AdjDir a, TenoT<T
         return acc;
     };
 #pragma unroll 1
-    for (int v = 0; v < 4; ++v) {
-        T gvp = T(0), gdp = T(0), gvm = T(0), gdm = T(0);
-        if (i + 1 <= a.nn) {
-            gvp = gline(0 * 4 + v, i + 1);
-            gdp = gline(1 * 4 + v, i + 1) * ih;
-        }
-        if (i >= 0) {
-            gvm = gline(2 * 4 + v, i);
-            gdm = gline(3 * 4 + v, i) * ih;
-        }
-        const long long base = (long long)gvar_(v, swap) * g.plane + org + r * a.st;
-        T q[5];
+    for (int vv = 0; vv < 4; vv += 2) {  // variable pairs, as the forward's selection
+        T q[2][5];
 #pragma unroll
-        for (int s = 0; s < 5; ++s) q[s] = load_src<T>(a, base + (i - 2 + s) * a.sn);
-        TenoSel<T> S;
-        teno_select(q, tn, S);
-        T gq[5] = {T(0), T(0), T(0), T(0), T(0)};
-        teno_faces_T(S, gvp, gdp, gvm, gdm, gq);
+        for (int l = 0; l < 2; ++l) {
+            const long long base = (long long)gvar_(vv + l, swap) * g.plane + org + r * a.st;
 #pragma unroll
-        for (int s = 0; s < 5; ++s) D[(long long)(s * 4 + v) * DP + didx(a, i, r)] = gq[s];
+            for (int s = 0; s < 5; ++s) q[l][s] = load_src<T>(a, base + (i - 2 + s) * a.sn);
+        }
+        T fvp[2], fdp[2], fvm[2], fdm[2];
+        const unsigned c2 = fwd_faces2(q[0], q[1], tn, fvp, fdp, fvm, fdm);
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const int v = vv + l;
+            T gvp = T(0), gdp = T(0), gvm = T(0), gdm = T(0);
+            if (i + 1 <= a.nn) {
+                gvp = gline(0 * 4 + v, i + 1);
+                gdp = gline(1 * 4 + v, i + 1) * ih;
+            }
+            if (i >= 0) {
+                gvm = gline(2 * 4 + v, i);
+                gdm = gline(3 * 4 + v, i) * ih;
+            }
+            TenoSel<T> S;
+            sel_decode((c2 >> (4 * l)) & 15u, S);  // the forward's selection
+            T gq[5] = {T(0), T(0), T(0), T(0), T(0)};
+            teno_faces_T(S, gvp, gdp, gvm, gdm, gq);
+#pragma unroll
+            for (int s = 0; s < 5; ++s) D[(long long)(s * 4 + v) * DP + didx(a, i, r)] = gq[s];
+        }
     }
 }
 

@@ -157,6 +157,19 @@ GKS_HD void teno_select_x2(const f2 q[5], const TenoT<float>& P, TenoSel2& S)
     S.u4 = C.u4 * lm;
 }
 
+// the selection of lane x (y) as 4 bits (bit 0: large stencil; bits 1-3:
+// the kept sub-stencils): a lane that keeps sub-stencils has a positive weight
+GKS_HD unsigned sel_code_x(const TenoSel2& S)
+{
+    const unsigned c = (S.w[0].x() > 0.0f ? 2u : 0u) | (S.w[1].x() > 0.0f ? 4u : 0u) | (S.w[2].x() > 0.0f ? 8u : 0u);
+    return c ? c : 1u;
+}
+GKS_HD unsigned sel_code_y(const TenoSel2& S)
+{
+    const unsigned c = (S.w[0].y() > 0.0f ? 2u : 0u) | (S.w[1].y() > 0.0f ? 4u : 0u) | (S.w[2].y() > 0.0f ? 8u : 0u);
+    return c ? c : 1u;
+}
+
 // values and xi-derivatives at the faces xi = +-1/2 of both lanes' selection:
 // the quartic in the Legendre-type basis (P2(1/2) = 1/6, P3(1/2) = 1/20,
 // P4(1/2) = 1/70; P2' = 1, P3' = 3/5, P4' = 2/7 at 1/2, odd ones change sign
