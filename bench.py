@@ -229,8 +229,11 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "riemann2d_config3", "grid": "%dx%d" % (n, n),
-                                            "note": "FP64 CPU oracle"},
+            "data": "synthetic",
+            "config": {"workload": "riemann2d_config3", "grid": "%dx%d" % (N_GRID, N_GRID), "cfl": 0.5, "split": 0.8,
+                       "precision": "fp64 (the oracle)", "parallelism": "1 host thread",
+                       "sample": "each step a %dx%d grid of the same problem (bounded sample; the metric is "
+                                 "per cell-update)" % (n, n)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
