@@ -819,3 +819,30 @@ def test_double_mach_ghost_rules():
             y = (jt - 3 + 0.5) * dy
             xs = 1.0 / 6.0 + (y + 20 * 0.05) / np.sqrt(3.0)
             assert np.array_equal(Wg[:, jt, i], Wpost if x < xs else Wpre), (i, jt)
+
+
+def _vortex_l1(run_steps, n, t_end=0.5, c=0.1):
+    s = WL.isentropic_vortex(n, seed=None)
+    h = s.dx
+    steps = int(np.ceil(t_end / (c * h)))
+    W = run_steps(s, n, steps, t_end / steps)
+    exact = WL.isentropic_vortex(n, center=(5.0 + t_end, 5.0 + t_end), seed=None).W
+    return np.mean(np.abs(W[0] - exact[0]))
+
+
+def test_isentropic_vortex_converges_at_fifth_order():
+    """The oracle on the isentropic vortex (strength 5, periodic [0, 10]^2,
+    mean flow (1, 1), tau = 0) to t = 0.5 with dt = 0.1 h (the time error is
+    negligible: halving dt changes the N = 40 error by 5 %): the density L1
+    error against the exact translated vortex falls at order >= 4.5 from
+    N = 20 to 40 to 80 (measured 4.66, 4.60: the fifth-order scheme on a
+    vortex core of radius 1 resolved by 2-8 cells)."""
+    def run(s, n, steps, dt):
+        P = O.make_problem(2, n, n, **s.problem_kwargs())
+        W = s.W.copy()
+        for _ in range(steps):
+            W = O.step(P, W, dt)
+        return W
+    e = [_vortex_l1(run, n) for n in (20, 40, 80)]
+    orders = np.log2(np.array(e[:-1]) / np.array(e[1:]))
+    assert np.all(orders >= 4.5), (e, orders)
