@@ -302,8 +302,19 @@ void or_weno_ao(const double *q5, double eps, double d_hi, double d_lo, int n, c
  * Qbar_{i-2} enters only p_0 and Qbar_{i+2} only p_2, which fixes d_0 and
  * d_2, and d_1 = 1 - d_0 - d_2 (every p_k reproduces constants); the other
  * coefficients are checked.  At xi = 1/2 this gives (0.1, 0.6, 0.3). */
+static int weno3_core(const double *q5, int teno5, double eps, double zpow, double q, double ct, int n,
+                      const double *xs, double *val, double *dval, double *wbar);
+
 int or_weno3(const double *q5, int teno5, double eps, double zpow, double q, double ct, int n,
              const double *xs, double *val, double *wbar)
+{
+    return weno3_core(q5, teno5, eps, zpow, q, ct, n, xs, val, NULL, wbar);
+}
+
+/* values (and, where dval is given, xi-derivatives: the derivative of the
+ * same weighted blend of the quadratics, reading R30) */
+static int weno3_core(const double *q5, int teno5, double eps, double zpow, double q, double ct, int n,
+                      const double *xs, double *val, double *dval, double *wbar)
 {
     init_fits();
     double c3[3][3], beta[3], d5[5];
@@ -359,9 +370,13 @@ int or_weno3(const double *q5, int teno5, double eps, double zpow, double q, dou
             }
             for (int k = 0; k < 3; ++k) w[k] /= ds;
         }
-        double v = 0.0;
-        for (int k = 0; k < 3; ++k) v += w[k] * or_poly_eval(2, c3[k], xi);
+        double v = 0.0, dv = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            v += w[k] * or_poly_eval(2, c3[k], xi);
+            dv += w[k] * or_poly_deriv(2, c3[k], xi);
+        }
         val[e] = v;
+        if (dval) dval[e] = dv;
         if (wbar)
             for (int k = 0; k < 3; ++k) wbar[k] = w[k];
     }
@@ -649,11 +664,32 @@ int or_flux_point(const or_problem *P,
     return or_flux_point_eq(P, Wl_in, Wln_in, Wlt_in, Wr_in, Wrn_in, Wrt_in, Wcl, Wcr, NULL, dt, Fdt, Fhalf);
 }
 
+static int flux_point_lin(const or_problem *P,
+                          const double *Wl_in, const double *Wln_in, const double *Wlt_in,
+                          const double *Wr_in, const double *Wrn_in, const double *Wrt_in,
+                          const double *Wcl, const double *Wcr, const double *W0_lin,
+                          const double *W0n_lin, const double *W0t_lin,
+                          double dt, double *Fdt, double *Fhalf);
+
 int or_flux_point_eq(const or_problem *P,
                      const double *Wl_in, const double *Wln_in, const double *Wlt_in,
                      const double *Wr_in, const double *Wrn_in, const double *Wrt_in,
                      const double *Wcl, const double *Wcr, const double *W0n_lin,
                      double dt, double *Fdt, double *Fhalf)
+{
+    return flux_point_lin(P, Wl_in, Wln_in, Wlt_in, Wr_in, Wrn_in, Wrt_in, Wcl, Wcr, NULL, W0n_lin, NULL, dt, Fdt,
+                          Fhalf);
+}
+
+/* the interface flux with any of the equilibrium state W0 and its normal and
+ * tangential slopes given (the conventional path's linear reconstructions,
+ * Sec. 3.1 Steps 2 and 4) instead of the kinetic merge; NULL: merged */
+static int flux_point_lin(const or_problem *P,
+                          const double *Wl_in, const double *Wln_in, const double *Wlt_in,
+                          const double *Wr_in, const double *Wrn_in, const double *Wrt_in,
+                          const double *Wcl, const double *Wcr, const double *W0_lin,
+                          const double *W0n_lin, const double *W0t_lin,
+                          double dt, double *Fdt, double *Fhalf)
 {
     const int dim = P->dim, nv = dim + 2;
     const double gamma = P->gamma, K = internal_dof(dim, gamma);
@@ -716,6 +752,10 @@ int or_flux_point_eq(const or_problem *P,
     }
     if (W0n_lin) /* conventional path: the equilibrium slope by Eq. (3.12) */
         for (int k = 0; k < nv; ++k) W0n[k] = W0n_lin[k];
+    if (W0_lin) /* conventional path in 2-D: linear reconstructions (Step 4) */
+        for (int k = 0; k < nv; ++k) W0[k] = W0_lin[k];
+    if (W0t_lin)
+        for (int k = 0; k < nv; ++k) W0t[k] = W0t_lin[k];
 
     double r0, U0, V0, lam0, p0;
     if (primitives(dim, gamma, W0, &r0, &U0, &V0, &lam0, &p0)) return -1;
@@ -905,6 +945,38 @@ static void to_ghosted(const grid_t *g, const double *W, double *Wg)
                 Wg[GIDX(*g, v, j + jo, i + NG)] = W[((size_t)v * g->ny + j) * g->nx + i];
 }
 
+/* kinetic merge of two reconstructed values (Eq. 3.25; reading R2): the
+ * equilibrium state of the conventional path's Step 2 (local frame) */
+static int merge_values(const or_problem *P, const double *Wl, const double *Wr, double *W0)
+{
+    const int dim = P->dim, nv = dim + 2;
+    const double K = internal_dof(dim, P->gamma);
+    double rl, Ul, Vl, laml, pl, rr, Ur, Vr, lamr, pr;
+    if (primitives(dim, P->gamma, Wl, &rl, &Ul, &Vl, &laml, &pl)) return -1;
+    if (primitives(dim, P->gamma, Wr, &rr, &Ur, &Vr, &lamr, &pr)) return -1;
+    mom_t mlp, mrm;
+    make_moments(dim, K, Ul, Vl, laml, +1, &mlp);
+    make_moments(dim, K, Ur, Vr, lamr, -1, &mrm);
+    double tl[4], tr[4];
+    moment_vec(dim, &mlp, 0, 0, NULL, tl);
+    moment_vec(dim, &mrm, 0, 0, NULL, tr);
+    for (int k = 0; k < nv; ++k) W0[k] = rl * tl[k] + rr * tr[k];
+    return 0;
+}
+
+/* the linear 5-point reconstruction (the quartic through five line
+ * averages, Step 4) at the points xs: values and xi-derivatives */
+static void linear5(const double *q5, int n, const double *xs, double *val, double *dval)
+{
+    init_fits();
+    double c5[5];
+    apply_fit(5, FIT5, q5, c5);
+    for (int e = 0; e < n; ++e) {
+        val[e] = or_poly_eval(4, c5, xs[e]);
+        dval[e] = or_poly_deriv(4, c5, xs[e]);
+    }
+}
+
 /* time-integrated face flux, averaged over the Gauss points (Sec. 3.2).
  * dir 0: x face between ghosted cells (ic, jc) and (ic+1, jc);
  * dir 1: y face between (ic, jc) and (ic, jc+1).  F in global variable order. */
@@ -968,11 +1040,69 @@ static int face_flux(const or_problem *P, const grid_t *g, const double *Wg, int
         return 0;
     }
 
-    /* the conventional path (WENO5-Z / TENO5 GKS) is built in 1-D only */
-    if (P->recon == OR_RECON_WENO_Z || P->recon == OR_RECON_TENO5) return -1;
+    const double xg[2] = {-0.5 / sqrt(3.0), 0.5 / sqrt(3.0)};
+    if (P->recon == OR_RECON_WENO_Z || P->recon == OR_RECON_TENO5) {
+        /* the conventional path in 2-D (Sec. 3.1, Steps 1-4).
+         * Step 2: per row, the line-averaged equilibrium state by the kinetic
+         * merge of the row's face values, and its normal slope by Eq. (3.12)
+         * on the row's cell averages */
+        const int t5 = P->recon == OR_RECON_TENO5;
+        const double eps = t5 ? P->eps : P->eps_ao;
+        double w0[5][4], w0x[5][4];
+        for (int r = 0; r < 5; ++r) {
+            const int off = r - 2;
+            if (merge_values(P, lv[r], rv[r], w0[r])) return -1;
+            for (int v = 0; v < nv; ++v) {
+                double q[4];
+                for (int s = 0; s < 4; ++s)
+                    q[s] = (dir == 0) ? Wg[GIDX(*g, perm[v], jc + off, ic - 1 + s)]
+                                      : Wg[GIDX(*g, perm[v], jc - 1 + s, ic + off)];
+                w0x[r][v] = (-(q[3] - q[0]) / 12.0 + 1.25 * (q[2] - q[1])) / hn;
+            }
+        }
+        /* Step 3: WENO-Z / TENO5 values of the non-equilibrium line averages
+         * (values and normal slopes) at the Gauss points, tangential
+         * derivatives from the same weighted blend (reading R30);
+         * Step 4: the quartic through the five line averages of W0 and of
+         * its normal slope, value and derivative at the Gauss points */
+        double Wl[2][4], Wln[2][4], Wlt[2][4], Wr[2][4], Wrn[2][4], Wrt[2][4];
+        double W0g[2][4], W0n[2][4], W0t[2][4];
+        for (int v = 0; v < nv; ++v) {
+            double q[5], val[2], dval[2];
+            for (int r = 0; r < 5; ++r) q[r] = lv[r][v];
+            if (weno3_core(q, t5, eps, P->zpow, P->qpow, P->ct1_t, 2, xg, val, dval, NULL)) return -1;
+            for (int m = 0; m < 2; ++m) { Wl[m][v] = val[m]; Wlt[m][v] = dval[m] / ht; }
+            for (int r = 0; r < 5; ++r) q[r] = lx[r][v];
+            if (weno3_core(q, t5, eps, P->zpow, P->qpow, P->ct1_t, 2, xg, val, dval, NULL)) return -1;
+            for (int m = 0; m < 2; ++m) Wln[m][v] = val[m];
+            for (int r = 0; r < 5; ++r) q[r] = rv[r][v];
+            if (weno3_core(q, t5, eps, P->zpow, P->qpow, P->ct1_t, 2, xg, val, dval, NULL)) return -1;
+            for (int m = 0; m < 2; ++m) { Wr[m][v] = val[m]; Wrt[m][v] = dval[m] / ht; }
+            for (int r = 0; r < 5; ++r) q[r] = rx[r][v];
+            if (weno3_core(q, t5, eps, P->zpow, P->qpow, P->ct1_t, 2, xg, val, dval, NULL)) return -1;
+            for (int m = 0; m < 2; ++m) Wrn[m][v] = val[m];
+            for (int r = 0; r < 5; ++r) q[r] = w0[r][v];
+            linear5(q, 2, xg, val, dval);
+            for (int m = 0; m < 2; ++m) { W0g[m][v] = val[m]; W0t[m][v] = dval[m] / ht; }
+            for (int r = 0; r < 5; ++r) q[r] = w0x[r][v];
+            linear5(q, 2, xg, val, dval);
+            for (int m = 0; m < 2; ++m) W0n[m][v] = val[m];
+        }
+        for (int m = 0; m < 2; ++m) {
+            double fd[4], fh[4];
+            int rc = flux_point_lin(P, Wl[m], Wln[m], Wlt[m], Wr[m], Wrn[m], Wrt[m], Wcl, Wcr, W0g[m], W0n[m],
+                                    W0t[m], dt, fd, fh);
+            if (rc < 0) return -1;
+            if (rc > 0 && nfb) ++*nfb;
+            for (int k = 0; k < nv; ++k) {
+                Fdt[perm[k]] += 0.5 * fd[k];
+                Fhalf[perm[k]] += 0.5 * fh[k];
+            }
+        }
+        return 0;
+    }
 
     /* step 2: tangential TENO-D to the two Gauss points */
-    const double xg[2] = {-0.5 / sqrt(3.0), 0.5 / sqrt(3.0)};
     double Wl[2][4], Wln[2][4], Wlt[2][4], Wr[2][4], Wrn[2][4], Wrt[2][4];
     for (int v = 0; v < nv; ++v) {
         double q[5], val[2], dval[2];

@@ -65,8 +65,11 @@ typedef struct {
 } or_problem;
 
 /* TENO-D (Sec. 4.2), WENO5-AO (Sec. 3.2), and the conventional path
- * (Sec. 3.1, 4.1; 1-D only): WENO5-Z or TENO5 face values, slopes from the
- * quadratic of Eq. (3.11), equilibrium slope from the linear Eq. (3.12) */
+ * (Sec. 3.1, 4.1): WENO5-Z or TENO5 face values, slopes from the quadratic of
+ * Eq. (3.11), equilibrium slope from the linear Eq. (3.12); in 2-D the
+ * equilibrium state and slopes at the Gauss points are the linear (quartic)
+ * reconstructions of the line-averaged kinetic merges and Eq. (3.12) slopes
+ * (Steps 2 and 4), the non-equilibrium ones WENO-Z / TENO5 (Step 3) */
 enum { OR_RECON_TENO_D = 0, OR_RECON_WENO_AO = 1, OR_RECON_WENO_Z = 2, OR_RECON_TENO5 = 3 };
 /* kinetic weighting of Eqs. (3.25)-(3.26), or the arithmetic average of the
  * two sides that Sec. 3.2 allows for smooth flow */
