@@ -122,14 +122,17 @@ typedef struct {
  * quadratics, gamma_3 = d_hi, gamma_1 = (1-d_hi) d_lo, gamma_0 = gamma_2 =
  * (1-d_hi)(1-d_lo)/2.  Batches and the adjoint take TENO-D only
  * (GKS_EUNSUPPORTED otherwise).
- * WENO5-Z and TENO5 (Sec. 3.1, 4.1) are the paper's conventional path, on
- * 1-D grids only (GKS_EUNSUPPORTED in 2-D): face values from the three
+ * WENO5-Z and TENO5 (Sec. 3.1, 4.1) are the paper's conventional path: face
+ * values from the three
  * quadratics with WENO-Z weights d_k (1 + tau/(beta_k + eps_ao)), tau =
  * |beta_0 - beta_2| (Eq. 3.5), or TENO5 weights (Eqs. 4.1-4.4: power q, the
  * paper's q = 6, cut-off ct1, epsilon eps); non-equilibrium slopes from the
  * quadratic through the cell average and both face values (Eq. 3.11); the
  * equilibrium state by the kinetic merge of the face values and its slope by
- * the linear Eq. (3.12).  Set q = 6 for TENO5 (the default 7 is TENO-D's). */
+ * the linear Eq. (3.12); in 2-D the non-equilibrium values at the Gauss
+ * points by WENO-Z / TENO5 across the rows, the equilibrium state and slopes
+ * there by the quartic through the rows' line-averaged merges and Eq. (3.12)
+ * slopes (Steps 2-4).  Set q = 6 for TENO5 (the default 7 is TENO-D's). */
 typedef enum { GKS_RECON_TENO_D = 0, GKS_RECON_WENO_AO = 1, GKS_RECON_WENO_Z = 2, GKS_RECON_TENO5 = 3 } gks_recon;
 
 /* Equilibrium state W0 and its slopes at an interface point (Sec. 3.2):

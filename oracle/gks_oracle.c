@@ -1051,7 +1051,17 @@ static int face_flux(const or_problem *P, const grid_t *g, const double *Wg, int
         double w0[5][4], w0x[5][4];
         for (int r = 0; r < 5; ++r) {
             const int off = r - 2;
-            if (merge_values(P, lv[r], rv[r], w0[r])) return -1;
+            /* a non-physical side takes its adjacent cell average (reading R14) */
+            double wl[4], wr[4], d1, d2, d3, d4, d5;
+            for (int v = 0; v < nv; ++v) { wl[v] = lv[r][v]; wr[v] = rv[r][v]; }
+            if (primitives(dim, P->gamma, wl, &d1, &d2, &d3, &d4, &d5))
+                for (int v = 0; v < nv; ++v)
+                    wl[v] = (dir == 0) ? Wg[GIDX(*g, perm[v], jc + off, ic)] : Wg[GIDX(*g, perm[v], jc, ic + off)];
+            if (primitives(dim, P->gamma, wr, &d1, &d2, &d3, &d4, &d5))
+                for (int v = 0; v < nv; ++v)
+                    wr[v] = (dir == 0) ? Wg[GIDX(*g, perm[v], jc + off, ic + 1)]
+                                       : Wg[GIDX(*g, perm[v], jc + 1, ic + off)];
+            if (merge_values(P, wl, wr, w0[r])) return -1;
             for (int v = 0; v < nv; ++v) {
                 double q[4];
                 for (int s = 0; s < 4; ++s)
@@ -1089,9 +1099,15 @@ static int face_flux(const or_problem *P, const grid_t *g, const double *Wg, int
             for (int m = 0; m < 2; ++m) W0n[m][v] = val[m];
         }
         for (int m = 0; m < 2; ++m) {
-            double fd[4], fh[4];
-            int rc = flux_point_lin(P, Wl[m], Wln[m], Wlt[m], Wr[m], Wrn[m], Wrt[m], Wcl, Wcr, W0g[m], W0n[m],
-                                    W0t[m], dt, fd, fh);
+            double fd[4], fh[4], d1, d2, d3, d4, d5;
+            /* a non-physical linear equilibrium state (the quartic across a
+             * discontinuity) falls back to the kinetic merge at the point with
+             * its slopes (reading R32); counted as a fallback */
+            const int lin_ok = !primitives(dim, P->gamma, W0g[m], &d1, &d2, &d3, &d4, &d5);
+            if (!lin_ok && nfb) ++*nfb;
+            int rc = flux_point_lin(P, Wl[m], Wln[m], Wlt[m], Wr[m], Wrn[m], Wrt[m], Wcl, Wcr,
+                                    lin_ok ? W0g[m] : NULL, lin_ok ? W0n[m] : NULL, lin_ok ? W0t[m] : NULL, dt, fd,
+                                    fh);
             if (rc < 0) return -1;
             if (rc > 0 && nfb) ++*nfb;
             for (int k = 0; k < nv; ++k) {

@@ -602,8 +602,6 @@ gks_status gks_set_scheme(gks_ctx* c, const gks_scheme* s)
                                            !(s->eps_ao > 0.0))) ||
         (s->recon == GKS_RECON_WENO_Z && !(s->eps_ao > 0.0)))
         return fail(c, GKS_EINVAL, "reconstruction parameters out of range");
-    if ((s->recon == GKS_RECON_WENO_Z || s->recon == GKS_RECON_TENO5) && c->desc.dim != 1)
-        return fail(c, GKS_EUNSUPPORTED, "WENO5-Z and TENO5 (the conventional path) are built for 1-D grids");
     if (s->merge != GKS_MERGE_KINETIC && s->merge != GKS_MERGE_AVERAGE)
         return fail(c, GKS_EINVAL, "merge must be GKS_MERGE_KINETIC or GKS_MERGE_AVERAGE");
     if (!s->positivity_fallback)

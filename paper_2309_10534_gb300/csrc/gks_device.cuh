@@ -384,8 +384,44 @@ GKS_HD void weno3_faces(const T q[5], const TenoSel<T>& S, T& vp, T& dp, T& vm, 
     (void)q;
 }
 
+// WENO5-Z / TENO5 value and xi-derivative at the Gauss point xi = g
+// (g^2 = 1/12): the quadratics blended with the point's linear weights (from
+// their definition, sum d_k p_k(g) = p_3(g): (210 + sqrt 3)/1080, 11/18,
+// (210 - sqrt 3)/1080 at g = -1/(2 sqrt 3), mirrored at +), and the same
+// blend's derivative (the tangential derivative of Step 3)
+template <typename T>
+GKS_HD void weno3_gauss(const TenoSel<T>& S, T g, T& v, T& d)
+{
+    const T r = T(1.7320508075688772 / 1080.0);
+    const T sgn = (g < T(0)) ? T(1) : T(-1);
+    const T dk[3] = {T(7.0 / 36.0) + sgn * r, T(11.0 / 18.0), T(7.0 / 36.0) - sgn * r};
+    T num = T(0), dnum = T(0), den = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T a = dk[k] * S.w[k];
+        num += a * (S.b[k] * g);                 // p_k(g) - q2 = b g + c (g^2 - 1/12)
+        dnum += a * (S.b[k] + T(2) * S.c[k] * g);
+        den += a;
+    }
+    const T iden = T(1) / den;
+    v = S.q2 + num * iden;
+    d = dnum * iden;
+}
+
+// the large-stencil quartic through five averages, value and xi-derivative
+// at the Gauss point xi = g (the conventional path's linear reconstruction
+// of the equilibrium line averages, Step 4)
+template <typename T>
+GKS_HD void quartic_gauss(const T q[5], T g, T& v, T& d)
+{
+    TenoSel<T> S;
+    stencil_coeffs(q, S);
+    v = S.q2 + S.u1 * g - S.u3 * g * T(1.0 / 15.0) - S.u4 * T(1.0 / 180.0);
+    d = S.u1 + T(2) * S.u2 * g + T(0.1) * S.u3 - T(2.0 / 21.0) * S.u4 * g;
+}
+
 // the scheme's reconstruction: REC 0 = TENO-D, 1 = WENO5-AO, 2 = WENO5-Z and
-// 3 = TENO5 (conventional path, faces only)
+// 3 = TENO5 (the conventional path)
 template <int REC, typename T>
 GKS_HD void rec_select(const T q[5], const TenoT<T>& P, TenoSel<T>& S)
 {
@@ -404,7 +440,8 @@ template <int REC, typename T>
 GKS_HD void rec_gauss(const TenoSel<T>& S, T g, T& v, T& d)
 {
     if constexpr (REC == 0) teno_gauss(S, g, v, d);
-    else ao_gauss(S, g, v, d);
+    else if constexpr (REC == 1) ao_gauss(S, g, v, d);
+    else weno3_gauss(S, g, v, d);
 }
 
 // ------------------------------------------------------------------ kinetic layer
@@ -721,6 +758,37 @@ GKS_HD bool physical(const T* W, T gm1)
     return r > T(0) && p > T(0) && isfinite(p);
 }
 
+// Kinetic merge of two states (values only; Eq. 3.25 with reading R2): the
+// conventional path's line-averaged equilibrium state (Step 2).  Both sides
+// must be physical.
+template <typename T, int DIM>
+GKS_HD void merge_values(const T* Wl, const T* Wr, const FluxParams<T>& P, T* W0)
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) W0[i] = T(0);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const T* W = side ? Wr : Wl;
+        const T sg = side ? T(-1) : T(1);
+        const T r = W[0], ir = T(1) / r;
+        const T U = W[1] * ir;
+        const T V = (DIM == 2) ? W[2] * ir : T(0);
+        const T p = P.gm1 * (W[3] - T(0.5) * r * (U * U + V * V));
+        const T inv2l = p * ir;
+        const T lam = T(0.5) / inv2l;
+        const T sl = M<T>::sqrt_(lam);
+        T u0, gexp;
+        half_space_start<T>(sl * U, sg, u0, gexp);
+        const T u1 = U * u0 + sg * T(0.28209479177387814) * gexp / sl;
+        const T u2 = U * u1 + inv2l * u0;
+        const T v2 = (DIM == 2) ? V * V + inv2l : T(0);
+        W0[0] += r * u0;
+        W0[1] += r * u1;
+        if (DIM == 2) W0[2] += r * u0 * V;
+        W0[3] += r * T(0.5) * (u2 + u0 * v2 + u0 * P.K * inv2l);
+    }
+}
+
 // Accumulated contributions of the non-equilibrium side terms and of the
 // equilibrium state, built side by side to keep few values alive.
 template <typename T, int DIM, bool NONEQ, bool PRFIX>
@@ -822,11 +890,13 @@ GKS_HD void side_terms(const Side<T>& S, bool upper, const FluxParams<T>& P,
 
 // F and dF/dt (per unit time; Sec. 2.2) at one interface point in the local
 // frame.  Both sides must be physical (the caller applies the fallback).
-// W0n_lin: the equilibrium normal slope of the conventional path (Eq. 3.12),
-// replacing the kinetic merge of the side slopes; nullptr otherwise
+// W0n_lin, W0_lin, W0t_lin: the conventional path's equilibrium normal
+// slope (Eq. 3.12, in 2-D reconstructed to the point), state and tangential
+// slope (2-D: linear reconstructions of line-averaged merges, Step 4),
+// replacing the kinetic merge at the point; nullptr otherwise
 template <typename T, int DIM, bool NONEQ, bool PRFIX>
 GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& P, T* F, T* dF,
-                       const T* W0n_lin = nullptr)
+                       const T* W0n_lin = nullptr, const T* W0_lin = nullptr, const T* W0t_lin = nullptr)
 {
     T W0[4] = {0, 0, 0, 0}, W0n[4] = {0, 0, 0, 0}, W0t[4] = {0, 0, 0, 0};
     T S3[4] = {0, 0, 0, 0}, S4[4] = {0, 0, 0, 0}, S5[4] = {0, 0, 0, 0};
@@ -834,6 +904,11 @@ GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& 
     T pl, pr;
     side_terms<T, DIM, NONEQ, PRFIX>(L, true, P, W0, W0n, W0t, S3, S4, S5, N4, N5, pl);
     side_terms<T, DIM, NONEQ, PRFIX>(R, false, P, W0, W0n, W0t, S3, S4, S5, N4, N5, pr);
+    // the kinetic merge is also the density moment of the side terms (the
+    // heat flux needs it even where W0 is replaced below)
+    T W0k[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) W0k[i] = W0[i];
     if (P.merge == 1) {
         // arithmetic average of the two sides in place of the kinetic
         // weighting (Sec. 3.2, for smooth flow); the side terms stay
@@ -847,6 +922,14 @@ GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& 
     if (W0n_lin) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) W0n[i] = W0n_lin[i];
+    }
+    if (W0_lin) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) W0[i] = W0_lin[i];
+    }
+    if (W0t_lin) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) W0t[i] = W0t_lin[i];
     }
 
     // equilibrium state g0: rho0 <u psi>_0 is the Euler flux of W0 and
@@ -918,14 +1001,15 @@ GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& 
         // Prandtl correction: F_E += (1/Pr - 1) q, q the heat flux relative to
         // (U0, V0) expanded in raw moments of the same time-dependent f.
         // Density moments: rho0 <psi>_0 = W0, rho0 <(a_n u + a_t v) psi>_0 =
-        // -W0_time, rho0 <A0 psi>_0 = W0_time; side terms W0, N4, N5.
+        // -W0_time, rho0 <A0 psi>_0 = W0_time; side terms W0k (the kinetic
+        // merge), N4, N5.
         const T ke = T(0.5) * (U0 * U0 + V0 * V0);
         const T cf = ke + U0 * U0;
         T MF[4], MD[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            MF[i] = qF0 * W0[i] + (qF2 - qF1) * W0time[i] + qF3 * W0[i] + qF4 * N4[i] + qF5 * N5[i];
-            MD[i] = qD0 * W0[i] + (qD2 - qD1) * W0time[i] + qD3 * W0[i] + qD4 * N4[i] + qD5 * N5[i];
+            MF[i] = qF0 * W0[i] + (qF2 - qF1) * W0time[i] + qF3 * W0k[i] + qF4 * N4[i] + qF5 * N5[i];
+            MD[i] = qD0 * W0[i] + (qD2 - qD1) * W0time[i] + qD3 * W0k[i] + qD4 * N4[i] + qD5 * N5[i];
         }
         const T qh = F[3] - U0 * F[1] - V0 * F[2] + cf * F[0] + U0 * V0 * MF[2] - U0 * MF[3] - U0 * ke * MF[0];
         const T qd = dF[3] - U0 * dF[1] - V0 * dF[2] + cf * dF[0] + U0 * V0 * MD[2] - U0 * MD[3]

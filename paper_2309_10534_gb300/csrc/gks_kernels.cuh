@@ -352,10 +352,13 @@ struct SweepArgs {
 // global variable index of local variable v (swap: faces normal to y)
 __device__ __forceinline__ int gvar(int v, bool swap) { return (swap && (v == 1 || v == 2)) ? 3 - v : v; }
 
-template <typename T, int TN, int TT> struct SweepSmem {
+template <typename T, int TN, int TT, bool CONV = false> struct SweepSmem {
     T w[4][TT + 4][TN + 6];           // cells: tangential rows t0-2.., normal n0-3..
     T rec[4][4][TT + 4][TN + 1];      // [vL, sL, vR, sR][var][row][face]
     T flux[8 * (TN + 1) * (TT + 1)];  // face fluxes for the update (layout: sfi)
+    // conventional path: line-averaged equilibrium state and its normal
+    // slope per face and row (Step 2)
+    T w0[CONV ? 2 : 1][4][CONV ? TT + 4 : 1][CONV ? TN + 1 : 1];
 };
 
 template <typename T, bool NONEQ, bool PRFIX, int TN, int TT, int REC = 0>
@@ -367,8 +370,9 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
     constexpr int NF = TN + 1;           // faces per tile row
     constexpr int NP = TT * NF;          // (face, row) pairs
     static_assert(NP == NT, "one (face,row) pair per thread");
+    constexpr bool CONV = REC >= 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SweepSmem<T, TN, TT>& sm = *reinterpret_cast<SweepSmem<T, TN, TT>*>(smem_raw);
+    SweepSmem<T, TN, TT, CONV>& sm = *reinterpret_cast<SweepSmem<T, TN, TT, CONV>*>(smem_raw);
     // face fluxes for the update: [k][row][face] for x faces; [k][face][row]
     // (rows padded) for y faces, so that phase 3 runs along the unit-stride x
     // direction in both sweeps
@@ -452,12 +456,47 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
     }
     __syncthreads();
 
+    unsigned int nfb = 0, err = 0;
+    if constexpr (CONV) {
+        // phase 1b (conventional path, Step 2): per face and row, the
+        // line-averaged equilibrium state by the kinetic merge of the face
+        // values (a non-physical side takes its adjacent cell average), and
+        // its normal slope by Eq. (3.12) on the row's cell averages
+        const T ih = (T)a.ihn;
+        for (int k = tid; k < NF * (TT + 4); k += NT) {
+            const int r = k / NF, f = k % NF;
+            // faces n0+f <= nn on rows t0-2+r <= nt+1 (ghosted extent) exist;
+            // the rest of the tile is padding that no Gauss point reads
+            if (n0 + f > a.nn || t0 - 2 + r > a.nt + 1) continue;
+            T wl[4], wr[4], w0[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) { wl[v] = sm.rec[0][v][r][f]; wr[v] = sm.rec[2][v][r][f]; }
+            if (!physical<T, 2>(wl, fp.gm1)) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) wl[v] = sm.w[v][r][f + 2];
+                if (!physical<T, 2>(wl, fp.gm1)) err |= 2u;
+            }
+            if (!physical<T, 2>(wr, fp.gm1)) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) wr[v] = sm.w[v][r][f + 3];
+                if (!physical<T, 2>(wr, fp.gm1)) err |= 2u;
+            }
+            merge_values<T, 2>(wl, wr, fp, w0);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                sm.w0[0][v][r][f] = w0[v];
+                sm.w0[1][v][r][f] = (T(1.25) * (sm.w[v][r][f + 3] - sm.w[v][r][f + 2])
+                                     - T(1.0 / 12.0) * (sm.w[v][r][f + 4] - sm.w[v][r][f + 1])) * ih;
+            }
+        }
+        __syncthreads();
+    }
+
     // phase 2: per (face segment, Gauss point): tangential TENO-D of the line
     // averages to the Gauss point, then merge + flux.  The two lanes of a face
     // segment split the work: lane gpi reconstructs side gpi (0: left, 1:
     // right) at both Gauss points, keeps its own point and hands the other
     // point's values to its partner; after the flux they average (weights 1/2).
-    unsigned int nfb = 0, err = 0;
     const T tdt = (T)dt;
     const T iht = (T)a.iht;
     const T gA = T(-0.28867513459481288), gB = T(0.28867513459481288);  // -+1/(2 sqrt 3)
@@ -524,7 +563,33 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
                 ++nfb;
                 if (!physical<T, 2>(R.W, fp.gm1)) err |= 2u;
             }
-            point_flux<T, 2, NONEQ, PRFIX>(L, R, fp, F, dF);
+            if constexpr (CONV) {
+                // Step 4: the equilibrium state and slopes at this lane's Gauss
+                // point, linear (quartic) reconstructions of the rows' merges
+                T w0g[4], w0t[4], w0n[4];
+                const T gme = gpi ? gB : gA;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    T q[5], dd;
+#pragma unroll
+                    for (int s = 0; s < 5; ++s) q[s] = sm.w0[0][v][r + s][f];
+                    quartic_gauss(q, gme, w0g[v], dd);
+                    w0t[v] = dd * iht;
+#pragma unroll
+                    for (int s = 0; s < 5; ++s) q[s] = sm.w0[1][v][r + s][f];
+                    quartic_gauss(q, gme, w0n[v], dd);
+                }
+                // a non-physical linear state (the quartic across a
+                // discontinuity) falls back to the kinetic merge at the point
+                if (physical<T, 2>(w0g, fp.gm1)) {
+                    point_flux<T, 2, NONEQ, PRFIX>(L, R, fp, F, dF, w0n, w0g, w0t);
+                } else {
+                    ++nfb;
+                    point_flux<T, 2, NONEQ, PRFIX>(L, R, fp, F, dF);
+                }
+            } else {
+                point_flux<T, 2, NONEQ, PRFIX>(L, R, fp, F, dF);
+            }
         }
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
