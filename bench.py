@@ -17,7 +17,8 @@ library's event profiler for the roofline.
 Further legs on the same GPU, reported as objects of the same JSON line:
 "ensemble" (4096 independent 1-D Riemann problems of 200..4000 cells to
 t = 0.15 in one persistent launch, cell-updates/s), "weno_ao" (the main
-workload with the WENO5-AO reconstruction), "recon_1d" (Sod's tube on 2^22
+workload with the WENO5-AO reconstruction), "conventional_2d" (the same with
+the WENO5-Z and TENO5 GKS of Sec. 3.1, 4.1), "recon_1d" (Sod's tube on 2^22
 cells with the TENO-D, WENO5-Z and TENO5 face reconstructions), "viscous" (Navier-Stokes
 viscous shock tube on 2048 x 1024, 200 steps from t = 0), "errors_vs_oracle"
 (both GPU paths against the FP64 oracle on the CPU baseline's sample) and
@@ -74,7 +75,7 @@ def parse():
     p.add_argument("--no-viscous", dest="viscous", action="store_false",
                    help="omit the viscous shock tube leg")
     p.add_argument("--no-weno-ao", dest="weno_ao", action="store_false",
-                   help="omit the WENO5-AO leg")
+                   help="omit the WENO5-AO and conventional (WENO5-Z, TENO5) 2-D legs")
     p.add_argument("--no-recon-1d", dest="recon_1d", action="store_false",
                    help="omit the 1-D leg that times TENO-D, WENO5-Z and TENO5 face reconstructions")
     return p.parse_args()
@@ -296,14 +297,15 @@ def ensemble_leg(gks, WL, stream, peak32, max_steps=0, launch=None, rank=0, worl
                          "basis": "whole launch vs measured FP32 FMA peak"}}
 
 
-def weno_ao_leg(gks, WL, stream, peak32, steps, warmup):
-    """The same 1024^2 Riemann workload with the WENO5-AO reconstruction
-    (Sec. 3.2, the scheme the paper compares against): float32 flux, CUDA
-    events around each step, 256 MB L2 flush between steps, sweep kernels
-    timed by the library's event profiler for the roofline."""
+def weno_ao_leg(gks, WL, stream, peak32, steps, warmup, recon="weno_ao"):
+    """The same 1024^2 Riemann workload with another reconstruction: WENO5-AO
+    (Sec. 3.2, the scheme the paper compares against), or the conventional
+    WENO5-Z / TENO5 GKS (Sec. 3.1, 4.1); float32 flux, CUDA events around
+    each step, 256 MB L2 flush between steps, sweep kernels timed by the
+    library's event profiler for the roofline."""
     import torch
     s = WL.riemann2d(N_GRID, split=0.8, t_end=0.8)
-    S = gks.solver_for(s, "fp32", recon="weno_ao")
+    S = gks.solver_for(s, "fp32", recon=recon)
     S.set_stream(stream.cuda_stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=stream.device)
     for _ in range(warmup):
@@ -324,13 +326,13 @@ def weno_ao_leg(gks, WL, stream, peak32, steps, warmup):
     S.profile(False)
     S.close()
     cells = N_GRID * N_GRID
-    fm = gks.count_flops(2, "fp32", "euler", 1.0, recon="weno_ao")
+    fm = gks.count_flops(2, "fp32", "euler", 1.0, recon=recon)
     launch_ms = sms / max(sn, 1)
     tf = fm["flops_per_cell_sweep"] * cells / (launch_ms * 1e-3) / 1e12
-    return {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "workload": "riemann2d_config3_weno_ao",
+    return {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "workload": "riemann2d_config3_" + recon,
             "grid": "%dx%d" % (N_GRID, N_GRID), "steps": steps, "ms_per_step": ms / steps,
             "flops_per_cell_update": fm["flops_per_cell_update"],
-            "roofline": {"bound": "alu", "kernel": "k2d_sweep<float, WENO5-AO>", "achieved": tf, "peak": peak32,
+            "roofline": {"bound": "alu", "kernel": "k2d_sweep<float, %s>" % recon, "achieved": tf, "peak": peak32,
                          "unit": "TFLOP/s", "frac": tf / peak32, "launch_ms": launch_ms}}
 
 
@@ -534,6 +536,8 @@ def main():
         launch = tuple(int(x) for x in args.ensemble_launch.split(",")) if args.ensemble_launch else None
         ens = ensemble_leg(gks, WL, stream, peak32, args.ensemble_max_steps, launch, rank, world, dist)
     ao = weno_ao_leg(gks, WL, stream, peak32, args.steps, args.warmup) if args.weno_ao else None
+    conv2d = ({r: weno_ao_leg(gks, WL, stream, peak32, args.steps, args.warmup, recon=r) for r in ("weno_z", "teno5")}
+              if args.weno_ao else None)
     r1d = recon_1d_leg(gks, WL, stream, peak32, args.steps, args.warmup) if args.recon_1d else None
     visc = None
     if args.viscous:
@@ -628,6 +632,8 @@ def main():
         line["ensemble"] = ens
     if ao:
         line["weno_ao"] = ao
+    if conv2d:
+        line["conventional_2d"] = conv2d
     if r1d:
         line["recon_1d"] = r1d
     if visc:

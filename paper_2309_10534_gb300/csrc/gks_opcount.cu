@@ -126,15 +126,36 @@ void count(int tau_mode, double Pr, gks_flop_model* out)
         T a, b, c, d;
         rec_faces<REC>(q, S, a, b, c, d);
     });
-    Counts tang;
-    if constexpr (REC < 2)
-        tang = measure([&] {
-            TenoSel<T> S;
-            rec_select<REC>(q, tp, S);
-            T a, b;
-            rec_gauss<REC>(S, T(0.28867513459481288), a, b);
-            rec_gauss<REC>(S, T(-0.28867513459481288), a, b);
+    const Counts tang = measure([&] {
+        TenoSel<T> S;
+        rec_select<REC>(q, tp, S);
+        T a, b;
+        rec_gauss<REC>(S, T(0.28867513459481288), a, b);
+        rec_gauss<REC>(S, T(-0.28867513459481288), a, b);
+    });
+    Side<T> L0_, R0_;
+    sample_side<T, DIM>(L0_, 1.0, 0.3, 0.2, 1.0, gamma, 0.0);
+    sample_side<T, DIM>(R0_, 1.0, 0.3, 0.2, 1.0, gamma, 1e-4);
+    // the conventional path in 2-D: per face one line merge and four
+    // Eq. (3.12) slopes (Step 2), per Gauss point eight quartic evaluations
+    // (Step 4)
+    Counts conv2d;
+    if constexpr (REC >= 2 && DIM == 2) {
+        const Counts merge = measure([&] {
+            T w0[4];
+            merge_values<T, 2>(L0_.W, R0_.W, fp, w0);
         });
+        const Counts quart = measure([&] {
+            T v, d;
+            quartic_gauss(q, T(0.28867513459481288), v, d);
+        });
+        Counts lin;
+        lin.add = 4 * 3;
+        lin.mul = 4 * 3;
+        conv2d += merge;
+        conv2d += lin;
+        conv2d += quart.scaled(16);
+    }
     Side<T> L, R;
     sample_side<T, DIM>(L, 1.0, 0.3, 0.2, 1.0, gamma, 0.0);
     sample_side<T, DIM>(R, 1.0, 0.3, 0.2, 1.0, gamma, 1e-4);
@@ -150,6 +171,7 @@ void count(int tau_mode, double Pr, gks_flop_model* out)
         // per face: 2 sides x 4 variables x (value, normal slope) tangential selections
         sweep += tang.scaled(16);
         sweep += flux.scaled(2);                   // two Gauss points
+        sweep += conv2d;
         Counts avg;
         avg.add = 8;                               // average of F, dF over the Gauss points
         avg.mul = 8;
@@ -212,11 +234,10 @@ extern "C" gks_status gks_count_flops_recon(int dim, int precision, int tau_mode
     std::lock_guard<std::mutex> lock(mu);
     if (!out || (dim != 1 && dim != 2) || tau_mode < 0 || tau_mode > 2 || !(Pr > 0.0) || recon < 0 || recon > 3)
         return GKS_EINVAL;
-    if (recon >= 2 && dim != 1) return GKS_EUNSUPPORTED;
     const bool f32 = precision == GKS_FP32_FLUX;
     if (recon == 1) count_rec<1>(dim, f32, tau_mode, Pr, out);
-    else if (recon == 2) count_rec<2>(1, f32, tau_mode, Pr, out);
-    else if (recon == 3) count_rec<3>(1, f32, tau_mode, Pr, out);
+    else if (recon == 2) count_rec<2>(dim, f32, tau_mode, Pr, out);
+    else if (recon == 3) count_rec<3>(dim, f32, tau_mode, Pr, out);
     else count_rec<0>(dim, f32, tau_mode, Pr, out);
     return GKS_OK;
 }
