@@ -55,6 +55,17 @@ int gks_host_weno_ao(int precision, const double *q, double eps_ao, double d_hi,
  * = value and xi-slope (Eq. 3.11) at xi = +1/2, then at -1/2. */
 int gks_host_weno3(int precision, int teno5, const double *q, double eps, int qpow, double ct, double *faces);
 
+/* The same reconstruction at the Gauss points xi = -+1/(2 sqrt 3) (the 2-D
+ * conventional path's Step 3): gauss[0..3] = value and xi-derivative (the
+ * derivative of the same weighted blend) at -, then at +. */
+int gks_host_weno3_gauss(int precision, int teno5, const double *q, double eps, int qpow, double ct,
+                         double *gauss);
+
+/* Kinetic merge of two states' values (Eq. 3.25; the conventional path's
+ * line-averaged equilibrium state, Step 2): W0 = rho_l <psi>_{u>0} +
+ * rho_r <psi>_{u<0}; 4 slots (energy in slot 3; 1-D slot 2 unused). */
+int gks_host_merge(int dim, int precision, double gamma, const double *Wl, const double *Wr, double *W0);
+
 /* Transpose of TENO-D with the selection of q held fixed (the adjoint's
  * frozen selection; with it the reconstruction is linear in q): the
  * cotangents gfaces[0..3] of faces[] and ggauss[0..3] of gauss[] as in

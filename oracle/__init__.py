@@ -111,6 +111,8 @@ def _declare(L):
     L.or_weno_ao.restype = None
     L.or_weno3.argtypes = [_dp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, _dp, _dp, _dp]
     L.or_weno3.restype = C.c_int
+    L.or_weno3_dv.argtypes = [_dp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, _dp, _dp, _dp]
+    L.or_weno3_dv.restype = C.c_int
     L.or_recon_faces.argtypes = [C.POINTER(Problem), _dp, _dp]
     L.or_recon_faces.restype = C.c_int
     L.or_moments_u.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int, _dp]
@@ -201,6 +203,19 @@ def weno3(q5, xs, teno5=False, eps=None, zpow=1.0, q=6.0, ct=1e-7):
     if lib().or_weno3(_d(q5), int(bool(teno5)), eps, zpow, q, ct, len(xs), _d(xs), _d(val), _d(wbar)):
         raise ValueError("no linear weights at these points")
     return val, wbar
+
+
+def weno3_dv(q5, xs, teno5=False, eps=None, zpow=1.0, q=6.0, ct=1e-7):
+    """WENO5-Z / TENO5 values and xi-derivatives (the same blend) at xs."""
+    q5 = _f64(q5)
+    xs = _f64(np.atleast_1d(xs))
+    if eps is None:
+        eps = 1e-40 if teno5 else 1e-8
+    val = np.zeros(len(xs))
+    dval = np.zeros(len(xs))
+    if lib().or_weno3_dv(_d(q5), int(bool(teno5)), eps, zpow, q, ct, len(xs), _d(xs), _d(val), _d(dval)):
+        raise ValueError("no linear weights at these points")
+    return val, dval
 
 
 def recon_faces(P: Problem, q5):

@@ -311,6 +311,12 @@ int or_weno3(const double *q5, int teno5, double eps, double zpow, double q, dou
     return weno3_core(q5, teno5, eps, zpow, q, ct, n, xs, val, NULL, wbar);
 }
 
+int or_weno3_dv(const double *q5, int teno5, double eps, double zpow, double q, double ct, int n,
+                const double *xs, double *val, double *dval)
+{
+    return weno3_core(q5, teno5, eps, zpow, q, ct, n, xs, val, dval, NULL);
+}
+
 /* values (and, where dval is given, xi-derivatives: the derivative of the
  * same weighted blend of the quadratics, reading R30) */
 static int weno3_core(const double *q5, int teno5, double eps, double zpow, double q, double ct, int n,

@@ -121,6 +121,10 @@ void   or_time_coeffs(double delta, double tau, double *q);
  * Returns 0, or -1 if xs admits no linear weights. */
 int    or_weno3(const double *q5, int teno5, double eps, double zpow, double q, double ct, int n,
                 const double *xs, double *val, double *wbar);
+/* the same with xi-derivatives: the derivative of the same weighted blend of
+ * the quadratics (the tangential derivative of the 2-D conventional path) */
+int    or_weno3_dv(const double *q5, int teno5, double eps, double zpow, double q, double ct, int n,
+                   const double *xs, double *val, double *dval);
 /* the problem's normal reconstruction of one cell's five averages q5:
  * out = (value, xi-derivative at xi = +1/2, value, xi-derivative at -1/2) */
 int    or_recon_faces(const or_problem *P, const double *q5, double *out);

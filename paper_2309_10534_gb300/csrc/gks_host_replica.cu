@@ -223,6 +223,56 @@ int weno3_t(const double* q, double eps, int qpow, double ct, double* faces)
     return 0;
 }
 
+template <typename T, int REC>
+int weno3_gauss_t(const double* q, double eps, int qpow, double ct, double* gauss)
+{
+    T qq[5];
+    for (int k = 0; k < 5; ++k) qq[k] = (T)q[k];
+    gks::TenoParams P{eps, qpow, ct, 0.0};
+    P.recon = REC;
+    P.eps_ao = eps;
+    gks::TenoSel<T> S;
+    gks::rec_select<REC>(qq, gks::teno_t<T>(P), S);
+    T v, d;
+    gks::rec_gauss<REC>(S, T(-0.28867513459481288), v, d);
+    gauss[0] = v; gauss[1] = d;
+    gks::rec_gauss<REC>(S, T(0.28867513459481288), v, d);
+    gauss[2] = v; gauss[3] = d;
+    return 0;
+}
+
+template <typename T>
+int merge_t(int dim, double gamma, const double* Wl, const double* Wr, double* W0)
+{
+    const double K = dim == 2 ? (5.0 - 3.0 * gamma) / (gamma - 1.0) + 1.0 : (3.0 - gamma) / (gamma - 1.0);
+    gks::FluxParams<T> p{};
+    p.gm1 = (T)(gamma - 1.0);
+    p.K = (T)K;
+    T l[4], r[4], w0[4];
+    for (int k = 0; k < 4; ++k) { l[k] = (T)Wl[k]; r[k] = (T)Wr[k]; }
+    if (dim == 2) gks::merge_values<T, 2>(l, r, p, w0);
+    else gks::merge_values<T, 1>(l, r, p, w0);
+    for (int k = 0; k < 4; ++k) W0[k] = (double)w0[k];
+    return 0;
+}
+
+extern "C" int gks_host_weno3_gauss(int precision, int teno5, const double* q, double eps, int qpow, double ct,
+                                    double* gauss)
+{
+    if (!q || !gauss || qpow < 1 || !(eps > 0.0)) return -1;
+    if (teno5)
+        return precision == 1 ? weno3_gauss_t<float, 3>(q, eps, qpow, ct, gauss)
+                              : weno3_gauss_t<double, 3>(q, eps, qpow, ct, gauss);
+    return precision == 1 ? weno3_gauss_t<float, 2>(q, eps, qpow, ct, gauss)
+                          : weno3_gauss_t<double, 2>(q, eps, qpow, ct, gauss);
+}
+
+extern "C" int gks_host_merge(int dim, int precision, double gamma, const double* Wl, const double* Wr, double* W0)
+{
+    if ((dim != 1 && dim != 2) || !Wl || !Wr || !W0) return -1;
+    return precision == 1 ? merge_t<float>(dim, gamma, Wl, Wr, W0) : merge_t<double>(dim, gamma, Wl, Wr, W0);
+}
+
 extern "C" int gks_host_weno3(int precision, int teno5, const double* q, double eps, int qpow, double ct,
                               double* faces)
 {

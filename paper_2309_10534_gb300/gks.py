@@ -322,8 +322,11 @@ def _replica():
         L.gks_host_weno_ao.argtypes = [C.c_int, _dp, C.c_double, C.c_double, C.c_double, _dp, _dp]
         L.gks_host_point_flux_vjp.argtypes = [C.c_int, C.c_double] + [_dp] * 10
         L.gks_host_weno3.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_int, C.c_double, _dp]
+        L.gks_host_weno3_gauss.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_int, C.c_double, _dp]
+        L.gks_host_merge.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp, _dp]
         for f in (L.gks_host_time_coeffs, L.gks_host_teno, L.gks_host_point_flux, L.gks_host_teno_vjp,
-                  L.gks_host_point_flux_vjp, L.gks_host_weno_ao, L.gks_host_weno3):
+                  L.gks_host_point_flux_vjp, L.gks_host_weno_ao, L.gks_host_weno3, L.gks_host_weno3_gauss,
+                  L.gks_host_merge):
             f.restype = C.c_int
         L._replica_declared = True
     return L
@@ -379,6 +382,26 @@ def host_weno3(q, teno5=False, precision="fp64", eps=None, q_pow=6, ct=1e-7):
     if _replica().gks_host_weno3(PRECISION[precision], int(bool(teno5)), pq, eps, int(q_pow), ct, pf):
         raise ValueError("bad argument")
     return f
+
+
+def host_weno3_gauss(q, teno5=False, precision="fp64", eps=None, q_pow=6, ct=1e-7):
+    """(v-, d-, v+, d+) of WENO5-Z / TENO5 at the Gauss points for one stencil."""
+    if eps is None:
+        eps = 1e-40 if teno5 else 1e-8
+    qq, pq = _arr(q, 5)
+    g, pg = _arr(None, 4)
+    if _replica().gks_host_weno3_gauss(PRECISION[precision], int(bool(teno5)), pq, eps, int(q_pow), ct, pg):
+        raise ValueError("bad argument")
+    return g
+
+
+def host_merge(dim, Wl, Wr, precision="fp64", gamma=1.4):
+    """Kinetic merge of two states' values (4 slots)."""
+    keep = [_arr(a, 4) for a in (Wl, Wr)]
+    W0, p0 = _arr(None, 4)
+    if _replica().gks_host_merge(dim, PRECISION[precision], gamma, keep[0][1], keep[1][1], p0):
+        raise ValueError("bad argument")
+    return W0
 
 
 def host_weno_ao(q, precision="fp64", eps_ao=1e-8, d_hi=0.85, d_lo=0.85):

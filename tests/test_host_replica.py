@@ -154,3 +154,52 @@ def test_weno3_matches_oracle(G, teno5):
         assert np.abs(got - want).max() <= 1e-13 * scale, (q, got, want)
         g32 = G.host_weno3(q, teno5, precision="fp32")
         assert np.abs(g32 - want).max() <= 2e-6 * scale, (q, g32, want)  # measured 4.4e-7
+
+
+@pytest.mark.parametrize("teno5", [False, True])
+def test_weno3_gauss_matches_oracle(G, teno5):
+    """The 2-D conventional path's tangential WENO5-Z / TENO5 at the Gauss
+    points (values and the blend's derivative), host build of the device
+    code against the oracle: float64 to 1e-13, float32 to 2e-6."""
+    rng = np.random.default_rng(9)
+    g = 0.5 / np.sqrt(3.0)
+    stencils = [np.array([1.0, 1.1, 1.25, 1.45, 1.7]), np.array([1.0, 1.0, 1.0, 0.125, 0.125]),
+                np.ones(5)] + [rng.normal(size=5) for _ in range(30)]
+    for q in stencils:
+        v, d = O.weno3_dv(q, [-g, g], teno5=teno5)
+        want = np.array([v[0], d[0], v[1], d[1]])
+        scale = max(1.0, np.abs(q).max())
+        assert np.abs(G.host_weno3_gauss(q, teno5) - want).max() <= 1e-13 * scale, q
+        assert np.abs(G.host_weno3_gauss(q, teno5, precision="fp32") - want).max() <= 2e-6 * scale, q
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_merge_matches_half_space_quadrature(G, dim):
+    """The line-averaged equilibrium state of the conventional path (Step 2):
+    the kinetic merge rho_l <psi>_{u>0} + rho_r <psi>_{u<0} against adaptive
+    quadrature of the Maxwellians over the half spaces (v and the internal
+    degrees of freedom integrated in closed form), float64 to 1e-10."""
+    from scipy.integrate import quad
+    gamma = 1.4
+    K = 3.0 if dim == 2 else 4.0
+    rng = np.random.default_rng(10 + dim)
+    for _ in range(8):
+        sides = []
+        for _s in range(2):
+            rho, p = np.exp(rng.uniform(-0.5, 0.5, 2))
+            U, V = rng.uniform(-1.5, 1.5, 2)
+            V = V if dim == 2 else 0.0
+            E = p / (gamma - 1) + 0.5 * rho * (U * U + V * V)
+            sides.append((rho, U, V, p, np.array([rho, rho * U, rho * V, E])))
+        want = np.zeros(4)
+        for (rho, U, V, p, _W), (lo, hi) in zip(sides, ((0.0, np.inf), (-np.inf, 0.0))):
+            lam = rho / (2 * p)
+            f = lambda u, k: u ** k * np.sqrt(lam / np.pi) * np.exp(-lam * (u - U) ** 2)
+            m = [quad(f, lo, hi, args=(k,), epsabs=0, epsrel=1e-13)[0] for k in range(3)]
+            vv = V * V + 1 / (2 * lam) if dim == 2 else 0.0
+            want += rho * np.array([m[0], m[1], V * m[0], 0.5 * (m[2] + m[0] * vv + m[0] * K / (2 * lam))])
+        got = G.host_merge(dim, sides[0][4], sides[1][4])
+        assert np.allclose(got, want, rtol=1e-10, atol=1e-12), (got, want)
+    # equal states: the two half spaces add up to the state
+    W = sides[0][4]
+    assert np.allclose(G.host_merge(dim, W, W), W, rtol=1e-13)
