@@ -320,21 +320,28 @@ gks_status gks_alu_peak(int precision, double target_ms, double *tflops);
  * callers that cannot call cudaMalloc: a host whose device memory belongs to
  * another allocator (a framework's caching allocator or a fixed budget) or a
  * latency-critical loop that cannot take cudaMalloc's implicit device-wide
- * synchronisation.  It computes what gks_create + gks_set_state + gks_step(dt)
- * would, without a context.
+ * synchronisation.  It computes what gks_create + gks_set_gas +
+ * gks_set_scheme + gks_set_state + gks_step(dt) would, without a context.
  *   W_in, W_out: caller-owned device arrays, conserved variables [3][nx]
  *                float64 (rho, rho U, rho E); may not overlap.
- *   dx > 0, dt > 0 (no CFL choice here), bc[2] = x-low, x-high (gks_bc),
- *   gas and scheme as for gks_set_gas / gks_set_scheme, precision as gks_grid_desc.
+ *   dx > 0, dt > 0 (no CFL choice here), bc[2] = x-low, x-high (gks_bc
+ *   GKS_BC_PERIODIC .. GKS_BC_REFLECT; periodic on both ends or neither),
+ *   gas as for gks_set_gas, precision as gks_grid_desc.
+ *   scheme: checked as by gks_set_scheme except that cfl is not used; every
+ *   reconstruction (gks_recon) and both merges (gks_merge) are taken;
+ *   positivity_fallback must be 1 (the kernels always apply it), else
+ *   GKS_EUNSUPPORTED.
  *   stream: cudaStream_t or NULL; the call synchronises it before returning.
+ *   It must not be a capturing stream (the call reads its error word back and
+ *   synchronises): a stream under capture gives GKS_EINVAL.
  *   error_word (may be NULL): the step's error word (see gks_diag).
  * Working buffers live in one file-scope static device array sized for
  * GKS_NOALLOC_MAX_NX cells (about 1.6 MB on every GPU that loads the
  * library, kept until the process exits).  nx > GKS_NOALLOC_MAX_NX returns
  * GKS_EUNSUPPORTED; bad arguments GKS_EINVAL; a non-physical result
- * GKS_ENONPHYSICAL.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call reuses the same array and
+ * GKS_ENONPHYSICAL.  The first call in a device's context looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current and
+ * caches it with the context's id.  Every call reuses the same array and
  * resets what must start at zero, so calls that overlap on the GPU (other
  * streams, other threads) race and must be serialised by the caller. */
 gks_status gks_step1d_noalloc(const double *W_in, double *W_out, int nx, double dx, const int *bc,

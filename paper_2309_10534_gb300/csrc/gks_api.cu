@@ -422,6 +422,30 @@ gks_status prepare_kernels(gks_ctx* c)
 }  // namespace
 
 // ====================================================================== C ABI
+namespace gks {
+const char* scheme_problem(const gks_scheme* s, int check_cfl, gks_status* code)
+{
+    *code = GKS_EINVAL;
+    if (check_cfl && !(s->cfl > 0.0)) return "scheme parameters out of range: cfl must be > 0";
+    if (s->q < 1 || s->q > 32 || !(s->eps >= 0.0) || !(s->ct1 >= 0.0) || !(s->ct2 >= 0.0) || !(s->ct1_t >= 0.0) ||
+        !(s->ct2_t >= 0.0) || s->tau_mode < 0 || s->tau_mode > 2 || !(s->c1 >= 0.0) || !(s->c2 >= 0.0))
+        return "scheme parameters out of range";
+    if (s->recon < GKS_RECON_TENO_D || s->recon > GKS_RECON_TENO5 ||
+        (s->recon == GKS_RECON_WENO_AO && (!(s->d_hi > 0.0 && s->d_hi <= 1.0) || !(s->d_lo >= 0.0 && s->d_lo <= 1.0) ||
+                                           !(s->eps_ao > 0.0))) ||
+        (s->recon == GKS_RECON_WENO_Z && !(s->eps_ao > 0.0)))
+        return "reconstruction parameters out of range";
+    if (s->merge != GKS_MERGE_KINETIC && s->merge != GKS_MERGE_AVERAGE)
+        return "merge must be GKS_MERGE_KINETIC or GKS_MERGE_AVERAGE";
+    if (!s->positivity_fallback) {
+        *code = GKS_EUNSUPPORTED;
+        return "the kernels always apply the positivity fallback";
+    }
+    *code = GKS_OK;
+    return nullptr;
+}
+}  // namespace gks
+
 extern "C" {
 
 const char* gks_status_string(int s)
@@ -591,21 +615,12 @@ gks_status gks_set_boundary_states(gks_ctx* c, const gks_boundary_states* b)
     return GKS_OK;
 }
 
+
 gks_status gks_set_scheme(gks_ctx* c, const gks_scheme* s)
 {
     if (!c || !s) return GKS_EINVAL;
-    if (!(s->cfl > 0.0) || s->q < 1 || s->q > 32 || !(s->eps >= 0.0) || !(s->ct1 >= 0.0) || !(s->ct2 >= 0.0) ||
-        !(s->ct1_t >= 0.0) || !(s->ct2_t >= 0.0) || s->tau_mode < 0 || s->tau_mode > 2)
-        return fail(c, GKS_EINVAL, "scheme parameters out of range");
-    if (s->recon < GKS_RECON_TENO_D || s->recon > GKS_RECON_TENO5 ||
-        (s->recon == GKS_RECON_WENO_AO && (!(s->d_hi > 0.0 && s->d_hi <= 1.0) || !(s->d_lo >= 0.0 && s->d_lo <= 1.0) ||
-                                           !(s->eps_ao > 0.0))) ||
-        (s->recon == GKS_RECON_WENO_Z && !(s->eps_ao > 0.0)))
-        return fail(c, GKS_EINVAL, "reconstruction parameters out of range");
-    if (s->merge != GKS_MERGE_KINETIC && s->merge != GKS_MERGE_AVERAGE)
-        return fail(c, GKS_EINVAL, "merge must be GKS_MERGE_KINETIC or GKS_MERGE_AVERAGE");
-    if (!s->positivity_fallback)
-        return fail(c, GKS_EUNSUPPORTED, "the kernels always apply the positivity fallback");
+    gks_status code = GKS_OK;
+    if (const char* why = gks::scheme_problem(s, 1, &code)) return fail(c, code, "%s", why);
     c->sch = *s;
     ++c->param_version;
     c->cfl_dt_ready = false;

@@ -600,12 +600,9 @@ gks_status gks_batch_set_gas(gks_batch* b, const gks_gas* gas)
 gks_status gks_batch_set_scheme(gks_batch* b, const gks_scheme* s)
 {
     if (!b || !s) return GKS_EINVAL;
-    if (!(s->cfl > 0.0) || s->q < 1 || s->q > 32 || !(s->eps >= 0.0) || s->tau_mode < 0 || s->tau_mode > 2)
-        return bfail(b, GKS_EINVAL, "scheme parameters out of range");
-    if (!s->positivity_fallback) return bfail(b, GKS_EUNSUPPORTED, "the kernels always apply the positivity fallback");
+    gks_status code = GKS_OK;
+    if (const char* why = gks::scheme_problem(s, 1, &code)) return bfail(b, code, "%s", why);
     if (s->recon != GKS_RECON_TENO_D) return bfail(b, GKS_EUNSUPPORTED, "batches reconstruct with TENO-D only");
-    if (s->merge != GKS_MERGE_KINETIC && s->merge != GKS_MERGE_AVERAGE)
-        return bfail(b, GKS_EINVAL, "merge must be GKS_MERGE_KINETIC or GKS_MERGE_AVERAGE");
     b->sch = *s;
     ++b->version;
     return GKS_OK;

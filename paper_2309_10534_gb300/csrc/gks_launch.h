@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/gks.h"
 #include "gks_kernels.cuh"
 
 namespace gks {
@@ -33,6 +34,13 @@ cudaError_t prepare_sweep_f32();
 cudaError_t prepare_sweep_f64();
 cudaError_t launch_stage1d(int fp32, const GridDev& g, const Stage1DArgs& a, const HostFlux& hf,
                            const TenoParams& tn, DevState* ds, cudaStream_t st);
+
+// Range checks of a gks_scheme shared by every entry point that takes one
+// (gks_set_scheme, gks_batch_set_scheme, gks_step1d_noalloc).  Returns
+// nullptr when the scheme is valid, else the reason, with *code set to the
+// status to return.  The CFL number is checked only where it is used
+// (check_cfl != 0).
+const char* scheme_problem(const gks_scheme* s, int check_cfl, gks_status* code);
 
 template <typename T>
 inline FluxParams<T> make_flux_params(const HostFlux& h)

@@ -13,9 +13,11 @@
 // input and output only.
 //
 // Host code must not use the array's name as a device address (in host code
-// it names a host-side stand-in).  The device address is looked up once per
-// device with cudaGetSymbolAddress, on the first call made with that device
-// current, and cached.
+// it names a host-side stand-in).  The device address is looked up with
+// cudaGetSymbolAddress on the first call made in a CUDA context (the first
+// call on each device, and again after that device's context was destroyed
+// and re-created, e.g. by cudaDeviceReset), with that device current, and
+// cached per device together with the context's unique id.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -39,10 +41,44 @@ constexpr long long SCRATCH_DOUBLES = 4 * ARRAY + STATE_DOUBLES;
 static __device__ __align__(256) double g_scratch[SCRATCH_DOUBLES];
 
 constexpr int MAX_DEVICES = 64;
-double* g_addr[MAX_DEVICES] = {nullptr};
+struct ScratchAddr {
+    unsigned long long ctx_id;  // unique id of the context the address belongs to (0: none)
+    double* addr;
+};
+ScratchAddr g_addr[MAX_DEVICES] = {};
 std::mutex g_mu;
 
-// device address of g_scratch on the current device (looked up once)
+// driver entry points for the current context's unique id (looked up through
+// the runtime, so the library needs no link against the driver library)
+typedef int (*PfnCtxGetCurrent)(void**);
+typedef int (*PfnCtxGetId)(void*, unsigned long long*);
+
+// unique id of the current context, 0 if there is none or it is unknown
+unsigned long long current_context_id()
+{
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PfnCtxGetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PfnCtxGetId>(f);
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// device address of g_scratch in the current device's context
 cudaError_t scratch_address(double** out)
 {
     int dev = 0;
@@ -50,13 +86,15 @@ cudaError_t scratch_address(double** out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    const unsigned long long id = current_context_id();
+    if (id == 0 || g_addr[dev].ctx_id != id || !g_addr[dev].addr) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
+        e = cudaGetSymbolAddress(&p, g_scratch);  // makes the device's primary context current if none is
         if (e != cudaSuccess) return e;
-        g_addr[dev] = static_cast<double*>(p);
+        g_addr[dev].addr = static_cast<double*>(p);
+        g_addr[dev].ctx_id = current_context_id();  // 0 (unknown): looked up again next call
     }
-    *out = g_addr[dev];
+    *out = g_addr[dev].addr;
     return cudaSuccess;
 }
 
@@ -129,9 +167,14 @@ extern "C" gks_status gks_step1d_noalloc(const double* W_in, double* W_out, int 
         if (bc[k] < GKS_BC_PERIODIC || bc[k] > GKS_BC_REFLECT) return GKS_EINVAL;
     if ((bc[0] == GKS_BC_PERIODIC) != (bc[1] == GKS_BC_PERIODIC)) return GKS_EINVAL;
     if (!(gas->gamma > 1.0 && gas->gamma < 3.0) || !(gas->mu >= 0.0) || !(gas->Pr > 0.0)) return GKS_EINVAL;
-    if (sch->q < 1 || sch->q > 32 || sch->tau_mode < 0 || sch->tau_mode > 2) return GKS_EINVAL;
-    if (sch->recon != GKS_RECON_TENO_D && sch->recon != GKS_RECON_WENO_AO) return GKS_EINVAL;
-    if (!sch->positivity_fallback) return GKS_EUNSUPPORTED;
+    gks_status code = GKS_OK;
+    if (gks::scheme_problem(sch, 0, &code)) return code;  // the CFL number is not used here
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the call ends by reading the error word back and synchronising the
+    // stream, neither of which a capturing stream allows
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return GKS_ECUDA;
+    if (cap != cudaStreamCaptureStatusNone) return GKS_EINVAL;
 
     double* base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return GKS_ECUDA;
@@ -140,7 +183,6 @@ extern "C" gks_status gks_step1d_noalloc(const double* W_in, double* W_out, int 
     double* Ac = base + 2 * ARRAY;
     double* Wn = base + 3 * ARRAY;
     DevState* ds = reinterpret_cast<DevState*>(base + 4 * ARRAY);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     GridDev g{};
     g.dim = 1;
@@ -166,6 +208,7 @@ extern "C" gks_status gks_step1d_noalloc(const double* W_in, double* W_out, int 
     hf.mu = gas->mu;
     hf.prfac = (sch->tau_mode == GKS_TAU_NS) ? 1.0 / gas->Pr - 1.0 : 0.0;
     hf.tau_mode = sch->tau_mode;
+    hf.merge = sch->merge;
     TenoParams tn{sch->eps, sch->q, sch->ct1, sch->ct2, sch->recon, sch->d_hi, sch->d_lo, sch->eps_ao};
     const int f32 = precision == GKS_FP32_FLUX;
 

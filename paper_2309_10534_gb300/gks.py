@@ -444,14 +444,25 @@ def step1d_noalloc(W_in, W_out, dx, dt, bc=("zerograd", "zerograd"), precision="
                    Pr=1.0, stream=0, **scheme):
     """One 1-D S2O4 step through gks_step1d_noalloc (no device allocation by
     the library).  W_in, W_out: contiguous float64 CUDA tensors [3][nx] (or
-    [3][1][nx]).  Returns the error word; raises GKSError on a bad status."""
+    [3][1][nx]) on the current device.  Returns the error word; raises
+    GKSError on a bad status, and GKSError(GKS_EINVAL) before any library
+    call when a tensor is not of that kind."""
+    nx = int(W_in.shape[-1]) if hasattr(W_in, "shape") and len(W_in.shape) else 0
+    for t in (W_in, W_out):
+        ok = (hasattr(t, "data_ptr") and t.is_cuda and t.dtype.is_floating_point and t.dtype.itemsize == 8
+              and t.is_contiguous() and t.numel() == 3 * nx and nx > 0)
+        if ok:
+            import torch
+            ok = t.device.index == torch.cuda.current_device()
+        if not ok:
+            raise GKSError(GKS_EINVAL, "gks_step1d_noalloc: W_in and W_out must be contiguous float64 CUDA "
+                                       "tensors of 3 * nx values on the current device")
     L = lib()
     if not getattr(L, "_noalloc_declared", False):
         L.gks_step1d_noalloc.argtypes = [_vp, _vp, C.c_int, C.c_double, C.POINTER(C.c_int), C.POINTER(Gas),
                                          C.POINTER(Scheme), C.c_int, C.c_double, _vp, C.POINTER(C.c_uint)]
         L.gks_step1d_noalloc.restype = C.c_int
         L._noalloc_declared = True
-    nx = W_in.shape[-1]
     bcs = (C.c_int * 2)(*[BC[b] if isinstance(b, str) else int(b) for b in bc])
     err = C.c_uint(0)
     st = L.gks_step1d_noalloc(_vp(W_in.data_ptr()), _vp(W_out.data_ptr()), int(nx), float(dx), bcs,

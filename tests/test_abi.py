@@ -74,3 +74,25 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(gks, "_lib", None)
     with pytest.raises(ImportError):
         gks.lib()
+
+
+def test_noalloc_wrapper_refuses_bad_tensors_before_any_call():
+    """step1d_noalloc hands raw device pointers to the library, so every
+    tensor that is not a contiguous float64 CUDA tensor of 3 * nx values is
+    refused on the host, before the library is called."""
+    torch = pytest.importorskip("torch")
+    import numpy as np
+
+    from paper_2309_10534_gb300 import gks
+
+    good_shape = (3, 32)
+    cases = [
+        (torch.ones(good_shape, dtype=torch.float64), torch.ones(good_shape, dtype=torch.float64)),  # CPU
+        (np.ones(good_shape), np.ones(good_shape)),                                                   # numpy
+        (torch.ones(good_shape, dtype=torch.float32), torch.ones(good_shape, dtype=torch.float32)),  # float32
+        (torch.ones((32, 3), dtype=torch.float64).t(), torch.ones(good_shape, dtype=torch.float64)),  # strided
+    ]
+    for a, b in cases:
+        with pytest.raises(gks.GKSError) as e:
+            gks.step1d_noalloc(a, b, 1.0 / 32, 1e-4)
+        assert e.value.status == gks.GKS_EINVAL
