@@ -42,6 +42,7 @@ class Problem(C.Structure):
         ("merge", C.c_int), ("zpow", C.c_double),
         ("t", C.c_double), ("bc_in", C.c_double * 4), ("bc_pre", C.c_double * 4),
         ("shock_x0", C.c_double), ("shock_theta", C.c_double), ("shock_speed", C.c_double),
+        ("charvars", C.c_int),
     ]
 
 
@@ -56,7 +57,7 @@ def make_problem(dim, nx, ny=1, *, lx=1.0, ly=1.0, bc=("zerograd",) * 4, gamma=1
                  tau="euler", c1=0.01, c2=1.0, cfl=0.5, eps=1e-40, q=None, ct1=1e-7, ct2=1e-5,
                  ct1_t=None, ct2_t=None, positivity_fallback=1, recon="teno_d", d_hi=0.85, d_lo=0.85,
                  eps_ao=1e-8, merge="kinetic", zpow=1.0, t=0.0, bc_in=None, bc_pre=None, shock_x0=0.0,
-                 shock_theta=np.pi / 3, shock_speed=0.0) -> Problem:
+                 shock_theta=np.pi / 3, shock_speed=0.0, charvars=0) -> Problem:
     p = Problem()
     p.dim, p.nx, p.ny = dim, nx, (ny if dim == 2 else 1)
     p.dx = lx / nx
@@ -87,6 +88,7 @@ def make_problem(dim, nx, ny=1, *, lx=1.0, ly=1.0, bc=("zerograd",) * 4, gamma=1
             getattr(p, name)[:] = [float(x) for x in st]
     p.t = t
     p.shock_x0, p.shock_theta, p.shock_speed = shock_x0, shock_theta, shock_speed
+    p.charvars = int(charvars)
     return p
 
 
@@ -121,6 +123,8 @@ def _declare(L):
     L.or_micro_slope.restype = C.c_int
     L.or_time_coeffs.argtypes = [C.c_double, C.c_double, _dp]
     L.or_time_coeffs.restype = None
+    L.or_char_basis.argtypes = [C.c_int, C.c_double, _dp, _dp, _dp]
+    L.or_char_basis.restype = C.c_int
     L.or_flux_point.argtypes = [C.POINTER(Problem)] + [_dp] * 8 + [C.c_double, _dp, _dp]
     L.or_flux_point.restype = C.c_int
     L.or_stage1.argtypes = [C.POINTER(Problem), _dp, C.c_double, _dp, _lp]
@@ -239,6 +243,19 @@ def micro_slope(dim, K, U, V, lam, b):
     if lib().or_micro_slope(dim, K, U, V, lam, _d(b), _d(a)):
         raise RuntimeError("singular moment matrix")
     return a
+
+
+def char_basis(dim, gamma, Wm):
+    """(R, L) of the normal Euler flux Jacobian at the conserved state Wm
+    (local frame; Sec. 3.1, the characteristic variables): R's columns are
+    the right eigenvectors, L = R^-1."""
+    nv = dim + 2
+    Wm = _f64(Wm)
+    R = np.zeros((nv, nv))
+    Lm = np.zeros((nv, nv))
+    if lib().or_char_basis(dim, gamma, _d(Wm), _d(R), _d(Lm)):
+        raise ValueError("non-physical state")
+    return R, Lm
 
 
 def time_coeffs(delta, tau):

@@ -57,6 +57,15 @@
  *       garbled), d_Hi = d_Lo = 0.85, tau's third term with beta_2.
  *   R24 WENO5-AO weights with the squared ratio (tau/(beta_k+eps))^2; the
  *       2-D WENO-AO accuracy table is reproduced only with it.
+ *   R33 characteristic variables (Sec. 3.1: Q "should be changed" to the
+ *       characteristic variables for Euler systems; the projection is not
+ *       stated): with charvars = 1 the normal reconstruction of every face
+ *       (and, in 2-D, of every row of its tangential stencil) runs on
+ *       C = L W, with L = R^-1 and R the right eigenvectors of the Jacobian
+ *       of the normal Euler flux in the face's local frame, evaluated at the
+ *       arithmetic mean of the two cells adjacent to the face in that row;
+ *       the reconstructed values and slopes are mapped back by R.  The
+ *       tangential (Gauss-point) reconstruction stays component-wise.
  */
 #include "gks_oracle.h"
 
@@ -610,6 +619,52 @@ static int primitives(int dim, double gamma, const double *W, double *rho, doubl
 }
 
 /* ------------------------------------------------------------------ */
+/* characteristic variables (Sec. 3.1; reading R33)                     */
+/* ------------------------------------------------------------------ */
+/* Right eigenvectors of the Jacobian dF/dW of the normal Euler flux
+ * F = (rho U, rho U^2 + p, rho U V, U (E + p)) in the local frame (normal
+ * velocity first) at the conserved state Wm, as the columns of R (row-major
+ * nv x nv), ordered by eigenvalue U - c, U (entropy), U (shear, 2-D), U + c,
+ * with c the sound speed and H = (E + p)/rho; L = R^-1, solved column by
+ * column by Gaussian elimination.  Returns -1 when Wm is not physical. */
+int or_char_basis(int dim, double gamma, const double *Wm, double *R, double *L)
+{
+    const int nv = dim + 2;
+    double rho, U, V, lam, p;
+    if (primitives(dim, gamma, Wm, &rho, &U, &V, &lam, &p)) return -1;
+    const double c = sqrt(gamma * p / rho);
+    const double H = (Wm[dim + 1] + p) / rho;
+    const double k = 0.5 * (U * U + V * V);
+    double col[4][4];
+    if (dim == 2) {
+        const double c0[4] = {1.0, U - c, V, H - U * c};
+        const double c1[4] = {1.0, U, V, k};
+        const double c2[4] = {0.0, 0.0, 1.0, V};
+        const double c3[4] = {1.0, U + c, V, H + U * c};
+        memcpy(col[0], c0, sizeof c0);
+        memcpy(col[1], c1, sizeof c1);
+        memcpy(col[2], c2, sizeof c2);
+        memcpy(col[3], c3, sizeof c3);
+    } else {
+        const double c0[3] = {1.0, U - c, H - U * c};
+        const double c1[3] = {1.0, U, k};
+        const double c2[3] = {1.0, U + c, H + U * c};
+        memcpy(col[0], c0, sizeof c0);
+        memcpy(col[1], c1, sizeof c1);
+        memcpy(col[2], c2, sizeof c2);
+    }
+    for (int i = 0; i < nv; ++i)
+        for (int j = 0; j < nv; ++j) R[i * nv + j] = col[j][i];
+    for (int j = 0; j < nv; ++j) {
+        double e[4] = {0.0, 0.0, 0.0, 0.0}, x[4];
+        e[j] = 1.0;
+        if (gauss_solve(nv, R, e, x)) return -1;
+        for (int i = 0; i < nv; ++i) L[i * nv + j] = x[i];
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* time integrals of the coefficients of Eq. (2.5) over [0, delta]      */
 /* ------------------------------------------------------------------ */
 /*   q0 = int (1 - e^{-t/tau})                 = delta - tau(1-e^{-x})
@@ -1002,22 +1057,51 @@ static int face_flux(const or_problem *P, const grid_t *g, const double *Wg, int
     double lv[5][4], lx[5][4], rv[5][4], rx[5][4];
     for (int r = 0; r < nrow; ++r) {
         int off = (dim == 2) ? r - 2 : 0;
-        for (int v = 0; v < nv; ++v) {
-            double ql[5], qr[5];
-            for (int s = 0; s < 5; ++s) {
-                if (dir == 0) {
-                    ql[s] = Wg[GIDX(*g, perm[v], jc + off, ic - 2 + s)];
-                    qr[s] = Wg[GIDX(*g, perm[v], jc + off, ic - 1 + s)];
-                } else {
-                    ql[s] = Wg[GIDX(*g, perm[v], jc - 2 + s, ic + off)];
-                    qr[s] = Wg[GIDX(*g, perm[v], jc - 1 + s, ic + off)];
-                }
+        /* the six cells ic-2 .. ic+3 along the normal, local variable order */
+        double Q[6][4];
+        for (int s = 0; s < 6; ++s)
+            for (int v = 0; v < nv; ++v)
+                Q[s][v] = (dir == 0) ? Wg[GIDX(*g, perm[v], jc + off, ic - 2 + s)]
+                                     : Wg[GIDX(*g, perm[v], jc - 2 + s, ic + off)];
+        if (!P->charvars) {
+            for (int v = 0; v < nv; ++v) {
+                double ql[5], qr[5];
+                for (int s = 0; s < 5; ++s) { ql[s] = Q[s][v]; qr[s] = Q[s + 1][v]; }
+                double val, dval;
+                recon5(P, ql, 0, 1, &xl, &val, &dval);
+                lv[r][v] = val; lx[r][v] = dval / hn;
+                recon5(P, qr, 0, 1, &xr, &val, &dval);
+                rv[r][v] = val; rx[r][v] = dval / hn;
             }
-            double val, dval;
-            recon5(P, ql, 0, 1, &xl, &val, &dval);
-            lv[r][v] = val; lx[r][v] = dval / hn;
-            recon5(P, qr, 0, 1, &xr, &val, &dval);
-            rv[r][v] = val; rx[r][v] = dval / hn;
+            continue;
+        }
+        /* characteristic variables of the face (reading R33): C = L Q with
+         * the basis at the mean of the two adjacent cells, each field
+         * reconstructed on its own, values and slopes mapped back by R */
+        double Wm[4], R[16], L[16], C[6][4], cl[4], cdl[4], cr[4], cdr[4];
+        for (int v = 0; v < nv; ++v) Wm[v] = 0.5 * (Q[2][v] + Q[3][v]);
+        if (or_char_basis(dim, P->gamma, Wm, R, L)) return -1;
+        for (int s = 0; s < 6; ++s)
+            for (int k = 0; k < nv; ++k) {
+                C[s][k] = 0.0;
+                for (int v = 0; v < nv; ++v) C[s][k] += L[k * nv + v] * Q[s][v];
+            }
+        for (int k = 0; k < nv; ++k) {
+            double ql[5], qr[5];
+            for (int s = 0; s < 5; ++s) { ql[s] = C[s][k]; qr[s] = C[s + 1][k]; }
+            recon5(P, ql, 0, 1, &xl, &cl[k], &cdl[k]);
+            recon5(P, qr, 0, 1, &xr, &cr[k], &cdr[k]);
+        }
+        for (int v = 0; v < nv; ++v) {
+            double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+            for (int k = 0; k < nv; ++k) {
+                a += R[v * nv + k] * cl[k];
+                b += R[v * nv + k] * cdl[k];
+                c += R[v * nv + k] * cr[k];
+                d += R[v * nv + k] * cdr[k];
+            }
+            lv[r][v] = a; lx[r][v] = b / hn;
+            rv[r][v] = c; rx[r][v] = d / hn;
         }
     }
 

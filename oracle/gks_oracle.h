@@ -62,6 +62,8 @@ typedef struct {
     double bc_pre[4];     /* conserved state ahead of the shock */
     double shock_x0, shock_theta, shock_speed; /* shock foot on y = 0, angle to the
                                                   x-axis (rad), normal speed */
+    int charvars;         /* 1: normal reconstruction in characteristic variables
+                             (Sec. 3.1; see or_char_basis), 0: component-wise */
 } or_problem;
 
 /* TENO-D (Sec. 4.2), WENO5-AO (Sec. 3.2), and the conventional path
@@ -95,6 +97,12 @@ void   or_weno_ao(const double *q5, double eps, double d_hi, double d_lo, int n,
                   double *val, double *dval, double *wbar);
 int    or_teno_d(const double *q5, double eps, double qpow, double ct1, double ct2,
                  int n, const double *xs, double *val, double *dval, int *sel);
+
+/* characteristic basis of the normal Euler flux (Sec. 3.1): R holds the right
+ * eigenvectors of dF/dW at the conserved state Wm as columns (row-major
+ * nv x nv, nv = dim + 2; eigenvalues U - c, U, [U,] U + c), L = R^-1.
+ * Returns -1 when Wm is not physical. */
+int    or_char_basis(int dim, double gamma, const double *Wm, double *R, double *L);
 
 /* ---- kinetic layer (Sec. 2.1) ---- */
 /* u-moments <u^n>, n = 0..nmax, of a 1-D unit-mass Maxwellian with mean U and

@@ -862,3 +862,145 @@ def test_isentropic_vortex_converges_at_fifth_order():
     e = [_vortex_l1(run, n) for n in (20, 40, 80)]
     orders = np.log2(np.array(e[:-1]) / np.array(e[1:]))
     assert np.all(orders >= 4.5), (e, orders)
+
+
+# ---------------------------------------------------------------- characteristic variables
+def _flux_jacobian(W, gamma, dim, h=1e-6):
+    """dF/dW of the normal Euler flux by central differences of its definition."""
+    nv = dim + 2
+    A = np.zeros((nv, nv))
+    for j in range(nv):
+        d = np.zeros(nv)
+        d[j] = h * max(1.0, abs(W[j]))
+        A[:, j] = (_euler_flux(W + d, gamma, dim) - _euler_flux(W - d, gamma, dim)) / (2 * d[j])
+    return A
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_char_basis_diagonalises_the_euler_flux_jacobian(dim):
+    """Sec. 3.1, characteristic variables: the columns of R are right and the
+    rows of L left eigenvectors of dF/dW (central differences of the Euler
+    flux), with eigenvalues U - c, U, [U,] U + c, and L R = I."""
+    rng = np.random.default_rng(33 + dim)
+    for _ in range(6):
+        rho, p = rng.uniform(0.2, 3.0, 2)
+        U, V = rng.uniform(-2, 2, 2)
+        if dim == 1:
+            W = np.array([rho, rho * U, p / (GAMMA - 1) + 0.5 * rho * U * U])
+        else:
+            W = np.array([rho, rho * U, rho * V, p / (GAMMA - 1) + 0.5 * rho * (U * U + V * V)])
+        R, L = O.char_basis(dim, GAMMA, W)
+        A = _flux_jacobian(W, GAMMA, dim)
+        c = math.sqrt(GAMMA * p / rho)
+        lam = [U - c, U] + ([U] if dim == 2 else []) + [U + c]
+        scale = np.abs(A).max()
+        for k in range(dim + 2):
+            assert np.allclose(A @ R[:, k], lam[k] * R[:, k], atol=1e-7 * scale * np.abs(R[:, k]).max())
+            assert np.allclose(L[k] @ A, lam[k] * L[k], atol=1e-7 * scale * np.abs(L[k]).max())
+        assert np.allclose(L @ R, np.eye(dim + 2), atol=1e-13)
+
+
+def test_char_recon_equals_componentwise_on_smooth_data():
+    """Density advection (Sec. 5.1 workload) varies only along the entropy
+    eigenvector (1, U, U^2/2) at constant U and p: the entropy field is smooth
+    and takes the large stencil as every conserved variable does, the two
+    acoustic fields are constant (to round-off), where any selection returns
+    the constant.  So the first stage equals the component-wise one to
+    round-off.  (Later stages differ by ~1e-10: the stage state carries tiny
+    acoustic variations, comparable to round-off, on which TENO-D may keep
+    sub-stencils.)"""
+    for n in (20, 40):
+        s = WL.advection_1d(n)
+        P0 = O.make_problem(1, n, **s.problem_kwargs())
+        P1 = O.make_problem(1, n, charvars=1, **s.problem_kwargs())
+        dt = 0.2 * s.dx
+        a, b = O.stage1(P0, s.W, dt), O.stage1(P1, s.W, dt)
+        assert np.abs(a - b).max() <= 1e-14 * np.abs(a).max()
+        a, b = O.step(P0, s.W, dt), O.step(P1, s.W, dt)
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(a).max()
+
+
+def test_char_recon_accuracy_1d_table_and_order():
+    """Sec. 5.1 with characteristic variables: the same fifth-order errors
+    as the component-wise scheme (the printed table within the same 1 %)."""
+    tab = _acc_table("accuracy_1d_tenod.txt")
+    got = {}
+    for n in (10, 20, 40):
+        s = WL.advection_1d(n)
+        P = O.make_problem(1, n, charvars=1, **s.problem_kwargs())
+        W = s.W.copy()
+        dt = 0.2 * s.dx
+        for _ in range(int(round(2.0 / dt))):
+            W = O.step(P, W, dt)
+        e = W[0, 0] - WL.advection_1d_exact_rho(n, 2.0)
+        got[n] = np.array([np.mean(abs(e)), np.sqrt(np.mean(e * e)), abs(e).max()])
+        assert np.allclose(got[n], tab[n], rtol=1e-2), (n, got[n], tab[n])
+    assert np.all(np.log2(got[20] / got[40]) > 4.8)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_char_recon_reduces_to_componentwise_on_one_direction_data(dim):
+    """Data that varies along one fixed direction r of state space, W_j =
+    Wbar + alpha_j r, is proportional in every characteristic field as in
+    every conserved variable, so the TENO-D selection (scale invariant) and
+    the reconstruction agree: the first stage equals the component-wise one,
+    here across a jump of alpha, where the sub-stencils are selected.  (The
+    stage state leaves that line of states, so later stages differ.)"""
+    n = 32
+    alpha = np.where(np.arange(n) < n // 2, 0.0, 1.0) + 0.05 * np.sin(2 * np.pi * np.arange(n) / n)
+    if dim == 1:
+        Wbar, r = np.array([1.0, 0.2, 2.6]), np.array([0.4, -0.1, 0.9])
+        W = (Wbar[:, None] + alpha[None, :] * r[:, None])[:, None, :]
+        kw = dict(tau="euler")
+        P0, P1 = O.make_problem(1, n, **kw), O.make_problem(1, n, charvars=1, **kw)
+    else:
+        Wbar, r = np.array([1.0, 0.2, -0.1, 2.6]), np.array([0.4, -0.1, 0.15, 0.9])
+        a2 = alpha[None, :] + 0.3 * alpha[:, None]
+        W = Wbar[:, None, None] + a2[None] * r[:, None, None]
+        kw = dict(tau="euler", bc=("zerograd",) * 4)
+        P0, P1 = O.make_problem(2, n, n, **kw), O.make_problem(2, n, n, charvars=1, **kw)
+    dt = 0.4 * O.dt(P0, W)
+    a, b = O.stage1(P0, W, dt), O.stage1(P1, W, dt)
+    assert np.abs(a - W).max() > 1e-3  # the jump moved
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+
+
+def test_char_recon_sod_against_exact_riemann_solution():
+    """Sec. 5.2 (b) with characteristic variables: the plateau between
+    contact and shock hits the exact star state, and the L1 distance to the
+    exact cell averages is no larger than the component-wise scheme's."""
+    s = WL.sod(400)
+    left, right = s.extra["left"], s.extra["right"]
+    ps, us = ER.star_state(left, right)
+    ex = ER.cell_averages(left, right, 400, 0.2)
+    l1 = {}
+    for cv in (0, 1):
+        P = O.make_problem(1, 400, charvars=cv, **s.problem_kwargs())
+        W, steps, t, nfb = O.run(P, s.W, 0.2)
+        assert t == 0.2 and nfb == 0
+        l1[cv] = np.mean(abs(W[0, 0] - ex[0]))
+        if cv:
+            x = (np.arange(400) + 0.5) / 400
+            u = W[1, 0] / W[0, 0]
+            p = (GAMMA - 1) * (W[2, 0] - 0.5 * W[0, 0] * u * u)
+            plateau = (x > 0.55) & (x < 0.65)
+            assert np.allclose(p[plateau], ps, rtol=3e-3) and np.allclose(u[plateau], us, rtol=5e-3)
+    assert l1[1] <= 1.02 * l1[0], l1
+
+
+def test_char_recon_2d_on_y_uniform_data_equals_1d():
+    """The 2-D characteristic basis on y-uniform data (V = 0) separates the
+    shear field and reduces to the 1-D one: identical steps to round-off."""
+    s = WL.sod(40)
+    P1 = O.make_problem(1, 40, tau="euler", charvars=1)
+    P2 = O.make_problem(2, 40, 5, ly=0.125, bc=("zerograd", "zerograd", "periodic", "periodic"), tau="euler",
+                        charvars=1)
+    W1 = s.W.copy()
+    W2 = np.zeros((4, 5, 40))
+    W2[0], W2[1], W2[3] = s.W[0, 0], s.W[1, 0], s.W[2, 0]
+    for _ in range(4):
+        dt = 0.5 * O.dt(P1, W1)
+        W1 = O.step(P1, W1, dt)
+        W2 = O.step(P2, W2, dt)
+    for k1, k2 in ((0, 0), (1, 1), (2, 3)):
+        assert np.allclose(W2[k2], W1[k1, 0][None, :], rtol=1e-12, atol=1e-13)
