@@ -113,6 +113,8 @@ typedef struct {
     double d_hi, d_lo;       /* WENO5-AO linear-weight parameters (Sec. 3.2; default 0.85, 0.85) */
     double eps_ao;           /* WENO5-AO and WENO5-Z epsilon (default 1e-8) */
     int merge;               /* gks_merge: equilibrium state at the interface (default kinetic) */
+    int charvars;            /* 1: normal reconstruction in characteristic variables (Sec. 3.1; see
+                                below), 0: component-wise on the conserved variables (default) */
 } gks_scheme;
 
 /* Reconstruction of the non-equilibrium states (values and slopes at the
@@ -135,14 +137,27 @@ typedef struct {
  * slopes (Steps 2-4).  Set q = 6 for TENO5 (the default 7 is TENO-D's). */
 typedef enum { GKS_RECON_TENO_D = 0, GKS_RECON_WENO_AO = 1, GKS_RECON_WENO_Z = 2, GKS_RECON_TENO5 = 3 } gks_recon;
 
+/* Reconstruction variables (gks_scheme.charvars, Sec. 3.1: for Euler
+ * systems the reconstructed quantities may be the characteristic variables;
+ * the paper does not state the projection).  With charvars = 1 the normal
+ * reconstruction of each face (in 2-D: of each row of its tangential
+ * stencil) runs on C = L W: L = R^-1, R the right eigenvectors of the
+ * Jacobian of the normal Euler flux in the face's local frame (normal
+ * velocity first; eigenvalues U - c, U, [U,] U + c), evaluated at the
+ * arithmetic mean of the two cells adjacent to the face in that row; each
+ * characteristic field is reconstructed with TENO-D on its own and the
+ * values and slopes are mapped back by R.  The 2-D tangential reconstruction
+ * to the Gauss points stays component-wise.  Taken with GKS_RECON_TENO_D on
+ * single grids only: other reconstructions, batches and the adjoint return
+ * GKS_EUNSUPPORTED. */
+
 /* Equilibrium state W0 and its slopes at an interface point (Sec. 3.2):
  * the kinetic weighting of Eqs. (3.25)-(3.26) (W0 = rho_l <psi>_{u>0} +
  * rho_r <psi>_{u<0}, likewise for the slopes; the paper's scheme), or the
  * arithmetic average of the two reconstructed sides, W0 = (W_l + W_r)/2,
  * W0_n = (W_l,n + W_r,n)/2, W0_t = (W_l,t + W_r,t)/2, which the paper allows
  * for smooth flow.  The non-equilibrium terms are the same either way.  The
- * adjoint takes the kinetic merge only (GKS_EUNSUPPORTED otherwise);
- * gks_step1d_noalloc always uses the kinetic merge. */
+ * adjoint takes the kinetic merge only (GKS_EUNSUPPORTED otherwise). */
 typedef enum { GKS_MERGE_KINETIC = 0, GKS_MERGE_AVERAGE = 1 } gks_merge;
 
 typedef struct {
@@ -152,6 +167,20 @@ typedef struct {
     long long steps;         /* S2O4 steps taken since the state was last set */
     double dt;               /* the time step the next gks_advance_to step will use */
 } gks_diag;
+
+/* TENO-D selection flips between the two precisions (Sec. 4.2: the cut-offs
+ * of Eqs. 4.7 and 4.12 act on ratios of smoothness indicators, so near a
+ * discontinuity float32 rounding can move a choice; both choices are valid
+ * results of the scheme).  Counts on one state: */
+typedef struct {
+    long long normal_flips;          /* normal selections (per cell, variable and sweep direction)
+                                        where the float32 path chooses otherwise than the float64 path */
+    long long normal_selections;     /* normal selections compared */
+    long long tangential_flips;      /* 2-D: tangential selections (per face, side, variable, stream
+                                        [value, normal slope] and direction), each precision on its own
+                                        line averages; 0 in 1-D */
+    long long tangential_selections; /* tangential selections compared */
+} gks_flip_count;
 
 /* Create a context for one grid; allocates the ghosted device state.
  * Defaults: gamma 1.4, mu 0, Pr 1, cfl 0.5, c1 0.01, c2 1, C_T 1e-7/1e-5 in
@@ -189,6 +218,15 @@ gks_status gks_step(gks_ctx *ctx, double dt);
 gks_status gks_advance_to(gks_ctx *ctx, double t_end, long long max_steps,
                           long long *steps_done, double *t_out);
 gks_status gks_get_diagnostics(gks_ctx *ctx, gks_diag *out);
+
+/* Selection flips on the context's current state W (the input of the next
+ * step's first stage): the stencil choices of the float32 path (state
+ * rounded to float32, the float32 kernels' arithmetic) compared with the
+ * float64 path's, every normal and, in 2-D, tangential selection of both
+ * sweep directions.  Fills W's ghost layers; allocates and frees a 32-byte
+ * counter; synchronises the context's stream.  TENO-D with component-wise
+ * variables only (GKS_EUNSUPPORTED otherwise).  Either precision. */
+gks_status gks_selection_flips(gks_ctx *ctx, gks_flip_count *out);
 /* Text of the last error on this context (never NULL). */
 const char *gks_last_error(const gks_ctx *ctx);
 const char *gks_status_string(int status);
@@ -300,7 +338,9 @@ typedef struct {
     double fp64_flops_per_cell_update;       /* float64 share (all flops on the float64 path) */
 } gks_flop_model;
 gks_status gks_count_flops(int dim, int precision, int tau_mode, double Pr, gks_flop_model *out);
-/* the same for either reconstruction (gks_recon) */
+/* the same for either reconstruction (gks_recon), or GKS_COUNT_TENO_CHARVARS:
+ * TENO-D in characteristic variables (gks_scheme.charvars = 1) */
+#define GKS_COUNT_TENO_CHARVARS 4
 gks_status gks_count_flops_recon(int dim, int precision, int tau_mode, double Pr, int recon,
                                  gks_flop_model *out);
 

@@ -81,6 +81,16 @@ int gks_host_point_flux_vjp(int precision, double gamma,
                             const double *Wr, const double *Wrn, const double *Wrt,
                             const double *gF, const double *gdF, double *gl, double *gr);
 
+/* Both sides of one face in characteristic variables (Sec. 3.1; the
+ * kernels' normal reconstruction with gks_scheme.charvars = 1): w[24] are
+ * the six cells i-2 .. i+3 around the face between cells i and i+1, 4 slots
+ * each (rho, normal momentum, tangential momentum, energy; 1-D slot 2 = 0).
+ * out[16] = left value, left xi-derivative (TENO-D of cells i-2 .. i+2 at
+ * xi = +1/2), right value, right xi-derivative (cells i-1 .. i+3 at
+ * xi = -1/2), 4 slots each, in conserved variables.  precision 0 or 1. */
+int gks_host_char_face(int dim, int precision, double gamma, const double *w, double eps, int qpow,
+                       double ct1, double ct2, double *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,7 +42,7 @@ class Problem(C.Structure):
         ("merge", C.c_int), ("zpow", C.c_double),
         ("t", C.c_double), ("bc_in", C.c_double * 4), ("bc_pre", C.c_double * 4),
         ("shock_x0", C.c_double), ("shock_theta", C.c_double), ("shock_speed", C.c_double),
-        ("charvars", C.c_int),
+        ("charvars", C.c_int), ("ox", C.c_double), ("oy", C.c_double),
     ]
 
 
@@ -57,7 +57,7 @@ def make_problem(dim, nx, ny=1, *, lx=1.0, ly=1.0, bc=("zerograd",) * 4, gamma=1
                  tau="euler", c1=0.01, c2=1.0, cfl=0.5, eps=1e-40, q=None, ct1=1e-7, ct2=1e-5,
                  ct1_t=None, ct2_t=None, positivity_fallback=1, recon="teno_d", d_hi=0.85, d_lo=0.85,
                  eps_ao=1e-8, merge="kinetic", zpow=1.0, t=0.0, bc_in=None, bc_pre=None, shock_x0=0.0,
-                 shock_theta=np.pi / 3, shock_speed=0.0, charvars=0) -> Problem:
+                 shock_theta=np.pi / 3, shock_speed=0.0, charvars=0, ox=0.0, oy=0.0) -> Problem:
     p = Problem()
     p.dim, p.nx, p.ny = dim, nx, (ny if dim == 2 else 1)
     p.dx = lx / nx
@@ -89,6 +89,7 @@ def make_problem(dim, nx, ny=1, *, lx=1.0, ly=1.0, bc=("zerograd",) * 4, gamma=1
     p.t = t
     p.shock_x0, p.shock_theta, p.shock_speed = shock_x0, shock_theta, shock_speed
     p.charvars = int(charvars)
+    p.ox, p.oy = float(ox), float(oy)
     return p
 
 

@@ -943,9 +943,9 @@ static void ghost_from(const or_problem *P, const grid_t *g, double *Wg, int bc,
     int n = (dir == 0) ? g->nx : g->ny;
     for (int k = 1; k <= NG; ++k) {
         int gidx = (side == 0) ? NG - k : NG + n - 1 + k;  /* ghost position */
-        /* ghost centre (the grid starts at the origin) */
+        /* ghost centre (the domain starts at (ox, oy)) */
         const int gi = (dir == 0) ? gidx : line, gj = (dir == 0) ? line : gidx;
-        const double *st = ghost_state(P, bc, (gi - NG + 0.5) * P->dx, (gj - NG + 0.5) * P->dy, t);
+        const double *st = ghost_state(P, bc, P->ox + (gi - NG + 0.5) * P->dx, P->oy + (gj - NG + 0.5) * P->dy, t);
         if (st) {
             const int ie = g->nv - 1; /* energy slot */
             for (int v = 0; v < g->nv; ++v) {

@@ -64,6 +64,8 @@ typedef struct {
                                                   x-axis (rad), normal speed */
     int charvars;         /* 1: normal reconstruction in characteristic variables
                              (Sec. 3.1; see or_char_basis), 0: component-wise */
+    double ox, oy;        /* domain origin: cell (i, j) is centred at
+                             (ox + (i + 1/2) dx, oy + (j + 1/2) dy); default 0 */
 } or_problem;
 
 /* TENO-D (Sec. 4.2), WENO5-AO (Sec. 3.2), and the conventional path

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 OUT = os.path.join(HERE, "libgks.so")
 ROOT = os.path.dirname(HERE)
 
-UNITS = ["gks_api", "gks_k1d", "gks_k2d_f32", "gks_k2d_f64", "gks_opcount", "gks_host_replica", "gks_noalloc", "gks_probe", "gks_ensemble", "gks_adjoint"]
+UNITS = ["gks_api", "gks_k1d", "gks_k2d_f32", "gks_k2d_f64", "gks_opcount", "gks_host_replica", "gks_noalloc", "gks_probe", "gks_ensemble", "gks_adjoint", "gks_flips"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
           "-I" + os.path.join(ROOT, "include")]
@@ -43,7 +43,8 @@ def _sources():
 FAST_F32 = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
 # (the adjoint recomputes the forward pass's float32 selections and
 # reconstructions, so it takes the same flags as the forward kernels)
-EXTRA = {"gks_k2d_f32": FAST_F32, "gks_k1d": FAST_F32, "gks_ensemble": FAST_F32, "gks_adjoint": FAST_F32}
+EXTRA = {"gks_k2d_f32": FAST_F32, "gks_k1d": FAST_F32, "gks_ensemble": FAST_F32, "gks_adjoint": FAST_F32,
+         "gks_flips": FAST_F32}
 
 
 def _compile(unit):

@@ -693,8 +693,9 @@ gks_status check_supported(gks_ctx* c)
     if (c->desc.dim != 2) return rt::fail(c, GKS_EUNSUPPORTED, "the adjoint is built for 2-D grids");
     if (c->sch.tau_mode != GKS_TAU_ZERO)
         return rt::fail(c, GKS_EUNSUPPORTED, "the adjoint is built for the collision-free flux (tau_mode = zero)");
-    if (c->sch.recon != GKS_RECON_TENO_D)
-        return rt::fail(c, GKS_EUNSUPPORTED, "the adjoint is built for TENO-D (frozen stencil selection)");
+    if (c->sch.recon != GKS_RECON_TENO_D || c->sch.charvars)
+        return rt::fail(c, GKS_EUNSUPPORTED,
+                        "the adjoint is built for component-wise TENO-D (frozen stencil selection)");
     for (int k = 0; k < 4; ++k)
         if (c->desc.bc[k] > GKS_BC_REFLECT)
             return rt::fail(c, GKS_EUNSUPPORTED, "the adjoint is built for the copying boundary rules");

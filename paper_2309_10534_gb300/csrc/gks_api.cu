@@ -116,7 +116,7 @@ TenoParams teno_params(const gks_ctx* c, bool tangential)
     t.q = c->sch.q;
     t.ct1 = tangential ? c->sch.ct1_t : c->sch.ct1;
     t.ct2 = tangential ? c->sch.ct2_t : c->sch.ct2;
-    t.recon = c->sch.recon;
+    t.recon = c->sch.charvars ? REC_TENO_CHAR : c->sch.recon;
     t.d_hi = c->sch.d_hi;
     t.d_lo = c->sch.d_lo;
     t.eps_ao = c->sch.eps_ao;
@@ -190,6 +190,16 @@ gks_status enqueue_ghosts(gks_ctx* c, double* arr, cudaStream_t st)
     else k_fill_ghosts<double><<<(n + 127) / 128, 128, 0, st>>>(c->g, arr, c->ds, toff);
     CK(cudaGetLastError());
     prof_end(c, st, pi);
+    ++c->launches;
+    return GKS_OK;
+}
+
+gks_status fill_ghosts_f64(gks_ctx* c, double* arr, cudaStream_t st)
+{
+    const int gx = c->desc.nx + 2 * NG;
+    const int n = (c->desc.dim == 1) ? 2 * NG : 2 * NG * gx + 2 * NG * c->desc.ny;
+    k_fill_ghosts<double><<<(n + 127) / 128, 128, 0, st>>>(c->g, arr, c->ds, 0.0);
+    CK(cudaGetLastError());
     ++c->launches;
     return GKS_OK;
 }
@@ -437,6 +447,11 @@ const char* scheme_problem(const gks_scheme* s, int check_cfl, gks_status* code)
         return "reconstruction parameters out of range";
     if (s->merge != GKS_MERGE_KINETIC && s->merge != GKS_MERGE_AVERAGE)
         return "merge must be GKS_MERGE_KINETIC or GKS_MERGE_AVERAGE";
+    if (s->charvars != 0 && s->charvars != 1) return "charvars must be 0 or 1";
+    if (s->charvars && s->recon != GKS_RECON_TENO_D) {
+        *code = GKS_EUNSUPPORTED;
+        return "characteristic variables are taken with TENO-D only";
+    }
     if (!s->positivity_fallback) {
         *code = GKS_EUNSUPPORTED;
         return "the kernels always apply the positivity fallback";
@@ -503,6 +518,7 @@ gks_status gks_create(const gks_grid_desc* d, gks_ctx** out)
     c->sch.d_hi = c->sch.d_lo = 0.85;
     c->sch.eps_ao = 1e-8;
     c->sch.merge = GKS_MERGE_KINETIC;
+    c->sch.charvars = 0;
 
     GridDev& g = c->g;
     g.dim = d->dim;

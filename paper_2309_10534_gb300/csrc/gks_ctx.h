@@ -56,6 +56,9 @@ namespace rt {
 gks_status fail(gks_ctx* c, gks_status s, const char* fmt, ...);
 // fill the ghost layers of W or W* (the float32 shadow on the 2-D float32 path)
 gks_status enqueue_ghosts(gks_ctx* c, double* arr, cudaStream_t st);
+// fill the ghost layers of a float64 array at the state's time (whatever the
+// context's precision; diagnostics that read W itself)
+gks_status fill_ghosts_f64(gks_ctx* c, double* arr, cudaStream_t st);
 // copy the interior [nv][ny][nx] between a caller's buffer and a ghosted array
 gks_status copy_interior(gks_ctx* c, double* arr, const double* W, int on_device, bool in);
 HostFlux host_flux(const gks_ctx* c);

@@ -251,6 +251,35 @@ GKS_HD void teno_faces(const T q[5], const TenoSel<T>& S, T& vp, T& dp, T& vm, T
     vm += S.q2;
 }
 
+// one face of teno_faces: value and xi-derivative at xi = +1/2 (PLUS) or -1/2
+template <bool PLUS, typename T>
+GKS_HD void teno_face(const T q[5], const TenoSel<T>& S, T& v, T& d)
+{
+    if (S.large) {
+        if (PLUS) {
+            v = (T(2) * q[0] - T(13) * q[1] + T(47) * q[2] + T(27) * q[3] - T(3) * q[4]) * T(1.0 / 60.0);
+            d = (q[1] - T(15) * q[2] + T(15) * q[3] - q[4]) * T(1.0 / 12.0);
+        } else {
+            v = (T(-3) * q[0] + T(27) * q[1] + T(47) * q[2] - T(13) * q[3] + T(2) * q[4]) * T(1.0 / 60.0);
+            d = (q[0] - T(15) * q[1] + T(15) * q[2] - q[3]) * T(1.0 / 12.0);
+        }
+        return;
+    }
+    v = d = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T w = S.w[k], bh = T(0.5) * S.b[k], c6 = S.c[k] * T(1.0 / 6.0);
+        if (PLUS) {
+            v += w * (bh + c6);
+            d += w * (S.b[k] + S.c[k]);
+        } else {
+            v += w * (c6 - bh);
+            d += w * (S.b[k] - S.c[k]);
+        }
+    }
+    v += S.q2;
+}
+
 // WENO5-AO values and xi-derivatives at the faces: the quartic's (Eqs. 4.8,
 // 4.9 and mirror) and the quadratics' (Eqs. 4.13, 4.14) blended by S.w3, S.w
 template <typename T>
@@ -442,6 +471,123 @@ GKS_HD void rec_gauss(const TenoSel<T>& S, T g, T& v, T& d)
     if constexpr (REC == 0) teno_gauss(S, g, v, d);
     else if constexpr (REC == 1) ao_gauss(S, g, v, d);
     else weno3_gauss(S, g, v, d);
+}
+
+// ------------------------------------------------------------------ characteristic variables
+// Sec. 3.1: for Euler systems the reconstructed quantities may be the
+// characteristic variables.  Reconstruction code REC_TENO_CHAR is TENO-D on
+// C = L W per face: L = R^-1, R the right eigenvectors of the Jacobian of the
+// normal Euler flux in the face's local frame (normal velocity first),
+// evaluated at the arithmetic mean of the two cells adjacent to the face;
+// the reconstructed values and slopes are mapped back by R.  The tangential
+// (Gauss-point) reconstruction of the 2-D sweep stays component-wise TENO-D.
+constexpr int REC_TENO_CHAR = 4;
+// the per-quantity reconstruction a kernel with code REC runs
+__host__ __device__ constexpr int rec_base(int REC) { return REC == REC_TENO_CHAR ? 0 : REC; }
+// WENO5-Z and TENO5: the conventional path (equilibrium state and slopes
+// from their own linear reconstructions)
+__host__ __device__ constexpr bool rec_conventional(int REC) { return REC == 2 || REC == 3; }
+
+// Eigen-system of dF/dW at a state with velocity (U, V), sound speed c and
+// total enthalpy H: eigenvalues U - c, U (entropy), U (shear; 2-D), U + c in
+// slots 0..3 (1-D: slot 2 unused).  b1 = (gamma - 1)/c^2, k = |U|^2/2.
+template <typename T> struct CharBasis {
+    T U, V, c, ic, H, k, b1;
+    bool ok;  // false: the mean state is not physical; projection = identity
+};
+
+// basis at the arithmetic mean of the conserved states wa, wb (4 slots,
+// energy in slot 3)
+template <typename T, int DIM>
+GKS_HD void char_basis(const T* wa, const T* wb, T gm1, CharBasis<T>& B)
+{
+    const T r = T(0.5) * (wa[0] + wb[0]);
+    const T ir = T(1) / r;
+    B.U = T(0.5) * (wa[1] + wb[1]) * ir;
+    B.V = (DIM == 2) ? T(0.5) * (wa[2] + wb[2]) * ir : T(0);
+    const T E = T(0.5) * (wa[3] + wb[3]);
+    B.k = T(0.5) * (B.U * B.U + B.V * B.V);
+    const T p = gm1 * (E - r * B.k);
+    B.ok = r > T(0) && p > T(0) && isfinite(p);
+    const T c2 = (gm1 + T(1)) * p * ir;
+    B.c = B.ok ? M<T>::sqrt_(c2) : T(1);
+    B.ic = T(1) / B.c;
+    B.H = (E + p) * ir;
+    B.b1 = gm1 / c2;
+}
+
+// C = L q: with pt = b1 (q3 - U q1 - V q2 + k q0) and t = (q1 - U q0)/c,
+// C = ((pt - t)/2, q0 - pt, q2 - V q0, (pt + t)/2)
+template <typename T, int DIM>
+GKS_HD void char_project(const CharBasis<T>& B, const T* q, T* C)
+{
+    if (!B.ok) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) C[i] = q[i];
+        return;
+    }
+    const T q2 = (DIM == 2) ? q[2] : T(0);
+    const T pt = B.b1 * (q[3] - B.U * q[1] - B.V * q2 + B.k * q[0]);
+    const T t = B.ic * (q[1] - B.U * q[0]);
+    C[0] = T(0.5) * (pt - t);
+    C[1] = q[0] - pt;
+    C[2] = (DIM == 2) ? q2 - B.V * q[0] : T(0);
+    C[3] = T(0.5) * (pt + t);
+}
+
+// q = R C: the columns (1, U - c, V, H - U c), (1, U, V, k), (0, 0, 1, V),
+// (1, U + c, V, H + U c)
+template <typename T, int DIM>
+GKS_HD void char_back(const CharBasis<T>& B, const T* C, T* q)
+{
+    if (!B.ok) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q[i] = C[i];
+        return;
+    }
+    const T s = C[0] + C[3], d = C[3] - C[0];
+    const T c2 = (DIM == 2) ? C[2] : T(0);
+    q[0] = s + C[1];
+    q[1] = B.U * q[0] + B.c * d;
+    q[2] = (DIM == 2) ? B.V * q[0] + c2 : T(0);
+    q[3] = B.H * s + B.U * B.c * d + B.k * C[1] + B.V * c2;
+}
+
+// Both sides of one face in characteristic variables: w[0..5] are the six
+// cells i-2 .. i+3 around the face between cells i and i+1 (4 slots each;
+// 1-D slot 2 = 0).  Left side: TENO-D of cells i-2 .. i+2 at xi = +1/2;
+// right side: of cells i-1 .. i+3 at xi = -1/2; values and xi-derivatives
+// back in conserved variables.
+template <typename T, int DIM>
+GKS_HD void char_face(const T (*w)[4], const TenoT<T>& P, T gm1, T* vl, T* dl, T* vr, T* dr)
+{
+    CharBasis<T> B;
+    char_basis<T, DIM>(w[2], w[3], gm1, B);
+    T C[6][4];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) char_project<T, DIM>(B, w[s], C[s]);
+    T cvl[4], cdl[4], cvr[4], cdr[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (DIM == 1 && k == 2) {
+            cvl[k] = cdl[k] = cvr[k] = cdr[k] = T(0);
+            continue;
+        }
+        T q[5];
+        TenoSel<T> S;
+#pragma unroll
+        for (int s = 0; s < 5; ++s) q[s] = C[s][k];
+        teno_select(q, P, S);
+        teno_face<true>(q, S, cvl[k], cdl[k]);
+#pragma unroll
+        for (int s = 0; s < 5; ++s) q[s] = C[s + 1][k];
+        teno_select(q, P, S);
+        teno_face<false>(q, S, cvr[k], cdr[k]);
+    }
+    char_back<T, DIM>(B, cvl, vl);
+    char_back<T, DIM>(B, cdl, dl);
+    char_back<T, DIM>(B, cvr, vr);
+    char_back<T, DIM>(B, cdr, dr);
 }
 
 // ------------------------------------------------------------------ kinetic layer

@@ -602,7 +602,8 @@ gks_status gks_batch_set_scheme(gks_batch* b, const gks_scheme* s)
     if (!b || !s) return GKS_EINVAL;
     gks_status code = GKS_OK;
     if (const char* why = gks::scheme_problem(s, 1, &code)) return bfail(b, code, "%s", why);
-    if (s->recon != GKS_RECON_TENO_D) return bfail(b, GKS_EUNSUPPORTED, "batches reconstruct with TENO-D only");
+    if (s->recon != GKS_RECON_TENO_D || s->charvars)
+        return bfail(b, GKS_EUNSUPPORTED, "batches reconstruct with component-wise TENO-D only");
     b->sch = *s;
     ++b->version;
     return GKS_OK;

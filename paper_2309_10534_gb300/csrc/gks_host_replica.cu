@@ -241,6 +241,20 @@ int weno3_gauss_t(const double* q, double eps, int qpow, double ct, double* gaus
     return 0;
 }
 
+template <typename T, int DIM>
+int char_face_t(double gamma, const double* w, double eps, int qpow, double ct1, double ct2, double* out)
+{
+    T ww[6][4];
+    for (int c = 0; c < 6; ++c)
+        for (int v = 0; v < 4; ++v) ww[c][v] = (T)w[4 * c + v];
+    const gks::TenoParams P{eps, qpow, ct1, ct2};
+    T o[4][4];
+    gks::char_face<T, DIM>(ww, gks::teno_t<T>(P), (T)(gamma - 1.0), o[0], o[1], o[2], o[3]);
+    for (int k = 0; k < 4; ++k)
+        for (int v = 0; v < 4; ++v) out[4 * k + v] = (double)o[k][v];
+    return 0;
+}
+
 template <typename T>
 int merge_t(int dim, double gamma, const double* Wl, const double* Wr, double* W0)
 {
@@ -326,4 +340,15 @@ extern "C" int gks_host_point_flux(int dim, int precision, int tau_mode, double 
                               : flux_dispatch<double, 2>(tau_mode, gamma, mu, Pr, c1, c2, dt, Wl, Wln, Wlt, Wr, Wrn, Wrt, F, dF);
     return precision == 1 ? flux_dispatch<float, 1>(tau_mode, gamma, mu, Pr, c1, c2, dt, Wl, Wln, Wlt, Wr, Wrn, Wrt, F, dF)
                           : flux_dispatch<double, 1>(tau_mode, gamma, mu, Pr, c1, c2, dt, Wl, Wln, Wlt, Wr, Wrn, Wrt, F, dF);
+}
+
+extern "C" int gks_host_char_face(int dim, int precision, double gamma, const double* w, double eps, int qpow,
+                                  double ct1, double ct2, double* out)
+{
+    if (!w || !out || (dim != 1 && dim != 2) || (precision != 0 && precision != 1) || qpow < 1) return -1;
+    if (precision == 1)
+        return dim == 2 ? char_face_t<float, 2>(gamma, w, eps, qpow, ct1, ct2, out)
+                        : char_face_t<float, 1>(gamma, w, eps, qpow, ct1, ct2, out);
+    return dim == 2 ? char_face_t<double, 2>(gamma, w, eps, qpow, ct1, ct2, out)
+                    : char_face_t<double, 1>(gamma, w, eps, qpow, ct1, ct2, out);
 }

@@ -33,6 +33,9 @@ cudaError_t launch_stage1d(int fp32, const GridDev& g, const Stage1DArgs& a, con
         return fp32 ? dispatch<float, 2>(g, a, hf, tn, ds, st) : dispatch<double, 2>(g, a, hf, tn, ds, st);
     if (tn.recon == 3)
         return fp32 ? dispatch<float, 3>(g, a, hf, tn, ds, st) : dispatch<double, 3>(g, a, hf, tn, ds, st);
+    if (tn.recon == REC_TENO_CHAR)
+        return fp32 ? dispatch<float, REC_TENO_CHAR>(g, a, hf, tn, ds, st)
+                    : dispatch<double, REC_TENO_CHAR>(g, a, hf, tn, ds, st);
     return fp32 ? dispatch<float, 0>(g, a, hf, tn, ds, st) : dispatch<double, 0>(g, a, hf, tn, ds, st);
 }
 

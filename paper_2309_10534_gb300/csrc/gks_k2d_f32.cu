@@ -10,7 +10,7 @@ cudaError_t launch_one(const GridDev& g, const SweepArgs& a, const FluxParams<fl
 {
     constexpr int TN = SWEEP_TN, TT = SWEEP_TT32;
     auto kern = k2d_sweep<float, NONEQ, PRFIX, TN, TT, REC>;
-    const size_t smem = sizeof(SweepSmem<float, TN, TT, (REC >= 2)>);
+    const size_t smem = sizeof(SweepSmem<float, TN, TT, rec_conventional(REC)>);
     dim3 grid((a.nn + TN - 1) / TN, (a.nt + TT - 1) / TT);
     kern<<<grid, TT * (TN + 1), smem, st>>>(g, a, fp, teno_t<float>(tn), teno_t<float>(tt), ds);
     return cudaGetLastError();
@@ -20,7 +20,7 @@ cudaError_t set_smem()
 {
     return cudaFuncSetAttribute(k2d_sweep<float, NONEQ, PRFIX, SWEEP_TN, SWEEP_TT32, REC>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(SweepSmem<float, SWEEP_TN, SWEEP_TT32, (REC >= 2)>));
+                                (int)sizeof(SweepSmem<float, SWEEP_TN, SWEEP_TT32, rec_conventional(REC)>));
 }
 template <int REC>
 cudaError_t set_smem_all()
@@ -47,6 +47,7 @@ cudaError_t prepare_sweep_f32()
     if (e == cudaSuccess) e = set_smem_all<1>();
     if (e == cudaSuccess) e = set_smem_all<2>();
     if (e == cudaSuccess) e = set_smem_all<3>();
+    if (e == cudaSuccess) e = set_smem_all<REC_TENO_CHAR>();
     return e;
 }
 
@@ -57,6 +58,7 @@ cudaError_t launch_sweep_f32(const GridDev& g, const SweepArgs& a, const HostFlu
     case 1: return launch_rec<1>(g, a, hf, tn, tt, ds, st);
     case 2: return launch_rec<2>(g, a, hf, tn, tt, ds, st);
     case 3: return launch_rec<3>(g, a, hf, tn, tt, ds, st);
+    case REC_TENO_CHAR: return launch_rec<REC_TENO_CHAR>(g, a, hf, tn, tt, ds, st);
     default: return launch_rec<0>(g, a, hf, tn, tt, ds, st);
     }
 }

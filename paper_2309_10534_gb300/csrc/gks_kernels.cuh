@@ -212,18 +212,42 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
     }
     __syncthreads();
     const T idx_ = (T)a.idx;
-    // phase 1: reconstruction per cell c (interior i0 - 1 + c), both faces
-    for (int c = tid; c < TN + 2; c += NT) {
-        T q[3][5], vp[3], dp[3], vm[3], dm[3];
+    if constexpr (REC == REC_TENO_CHAR) {
+        // phase 1 in characteristic variables: per face f (between interior
+        // i0 + f - 1 and i0 + f), the six cells around it projected with the
+        // face's basis, both sides reconstructed
+        for (int f = tid; f <= TN; f += NT) {
+            T w[6][4], vl[4], dl[4], vr[4], dr[4];
 #pragma unroll
-        for (int v = 0; v < 3; ++v)
+            for (int c = 0; c < 6; ++c) {
+                w[c][0] = sq[0][f + c];
+                w[c][1] = sq[1][f + c];
+                w[c][2] = T(0);
+                w[c][3] = sq[2][f + c];
+            }
+            char_face<T, 1>(w, tn, fp.gm1, vl, dl, vr, dr);
 #pragma unroll
-            for (int s = 0; s < 5; ++s) q[v][s] = sq[v][c + s];
-        recon_cell3<REC>(q, tn, vp, dp, vm, dm);
+            for (int v = 0; v < 3; ++v) {
+                sL[v][0][f] = vl[slot[v]];
+                sL[v][1][f] = dl[slot[v]] * idx_;
+                sR[v][0][f] = vr[slot[v]];
+                sR[v][1][f] = dr[slot[v]] * idx_;
+            }
+        }
+    } else {
+        // phase 1: reconstruction per cell c (interior i0 - 1 + c), both faces
+        for (int c = tid; c < TN + 2; c += NT) {
+            T q[3][5], vp[3], dp[3], vm[3], dm[3];
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-            if (c <= TN) { sL[v][0][c] = vp[v]; sL[v][1][c] = dp[v] * idx_; }
-            if (c >= 1) { sR[v][0][c - 1] = vm[v]; sR[v][1][c - 1] = dm[v] * idx_; }
+            for (int v = 0; v < 3; ++v)
+#pragma unroll
+                for (int s = 0; s < 5; ++s) q[v][s] = sq[v][c + s];
+            recon_cell3<REC>(q, tn, vp, dp, vm, dm);
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                if (c <= TN) { sL[v][0][c] = vp[v]; sL[v][1][c] = dp[v] * idx_; }
+                if (c >= 1) { sR[v][0][c - 1] = vm[v]; sR[v][1][c - 1] = dm[v] * idx_; }
+            }
         }
     }
     __syncthreads();
@@ -254,7 +278,7 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
             if (!physical<T, 1>(R.W, fp.gm1)) err |= 2u;
         }
         T F[4], dF[4];
-        if constexpr (REC >= 2) {
+        if constexpr (rec_conventional(REC)) {
             // conventional path: equilibrium slope from the cell averages
             // i-1 .. i+2 around the face by the linear Eq. (3.12)
             T w0n[4] = {T(0), T(0), T(0), T(0)};
@@ -370,7 +394,8 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
     constexpr int NF = TN + 1;           // faces per tile row
     constexpr int NP = TT * NF;          // (face, row) pairs
     static_assert(NP == NT, "one (face,row) pair per thread");
-    constexpr bool CONV = REC >= 2;
+    constexpr bool CONV = rec_conventional(REC);
+    constexpr int RB = rec_base(REC);  // the tangential (per-quantity) reconstruction
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SweepSmem<T, TN, TT, CONV>& sm = *reinterpret_cast<SweepSmem<T, TN, TT, CONV>*>(smem_raw);
     // face fluxes for the update: [k][row][face] for x faces; [k][face][row]
@@ -415,7 +440,29 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
     __syncthreads();
 
     // phase 1: normal TENO-D per (cell, row, var): cell c <-> normal n0-1+c
-    if constexpr (sizeof(T) == 4 && REC <= 1) {
+    if constexpr (REC == REC_TENO_CHAR) {
+        // characteristic variables: per (face, row), the six cells around
+        // face f (between normal n0-1+f and n0+f) projected with the face's
+        // basis, both sides reconstructed
+        const T ih = (T)a.ihn;
+        constexpr int NR = TT + 4;
+        for (int k = tid; k < NF * NR; k += NT) {
+            const int r = k / NF, f = k % NF;
+            T w[6][4], vl[4], dl[4], vr[4], dr[4];
+#pragma unroll
+            for (int c = 0; c < 6; ++c)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) w[c][v] = sm.w[v][r][f + c];
+            char_face<T, 2>(w, tnn, fp.gm1, vl, dl, vr, dr);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                sm.rec[0][v][r][f] = vl[v];
+                sm.rec[1][v][r][f] = dl[v] * ih;
+                sm.rec[2][v][r][f] = vr[v];
+                sm.rec[3][v][r][f] = dr[v] * ih;
+            }
+        }
+    } else if constexpr (sizeof(T) == 4 && REC <= 1) {
         // float32 TENO-D / WENO5-AO: variables (0, 1) and (2, 3) as packed pairs
         const float ih = (float)a.ihn;
         constexpr int NC = TN + 2, NR = TT + 4;
@@ -513,13 +560,13 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
             // the two Gauss points: value and tangential derivative of W,
             // value of Wn
             T wa, wda, wb, wdb, na, nb;
-            if constexpr (sizeof(T) == 4 && REC <= 1) {
+            if constexpr (sizeof(T) == 4 && RB <= 1) {
                 // both streams as one packed pair (x: W, y: Wn)
                 f2 q[5];
 #pragma unroll
                 for (int s = 0; s < 5; ++s) q[s] = f2(sm.rec[2 * gpi][v][r + s][f], sm.rec[2 * gpi + 1][v][r + s][f]);
                 f2 va, da, vb, db;
-                packed_gauss<REC>(q, tnt, gA, gB, va, da, vb, db);
+                packed_gauss<RB>(q, tnt, gA, gB, va, da, vb, db);
                 wa = va.x(), wda = da.x(), wb = vb.x(), wdb = db.x(), na = va.y(), nb = vb.y();
             } else {
                 T q[5];
@@ -527,14 +574,14 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
                 T dn;
 #pragma unroll
                 for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * gpi][v][r + s][f];
-                rec_select<REC>(q, tnt, S);
-                rec_gauss<REC>(S, gA, wa, wda);
-                rec_gauss<REC>(S, gB, wb, wdb);
+                rec_select<RB>(q, tnt, S);
+                rec_gauss<RB>(S, gA, wa, wda);
+                rec_gauss<RB>(S, gB, wb, wdb);
 #pragma unroll
                 for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * gpi + 1][v][r + s][f];
-                rec_select<REC>(q, tnt, S);
-                rec_gauss<REC>(S, gA, na, dn);
-                rec_gauss<REC>(S, gB, nb, dn);
+                rec_select<RB>(q, tnt, S);
+                rec_gauss<RB>(S, gA, na, dn);
+                rec_gauss<RB>(S, gB, nb, dn);
             }
             // own side at own point; the partner's point goes to the partner
             T own = gpi ? wb : wa, got = __shfl_xor_sync(0xffffffffu, gpi ? wa : wb, 1);

@@ -209,7 +209,8 @@ extern "C" gks_status gks_step1d_noalloc(const double* W_in, double* W_out, int 
     hf.prfac = (sch->tau_mode == GKS_TAU_NS) ? 1.0 / gas->Pr - 1.0 : 0.0;
     hf.tau_mode = sch->tau_mode;
     hf.merge = sch->merge;
-    TenoParams tn{sch->eps, sch->q, sch->ct1, sch->ct2, sch->recon, sch->d_hi, sch->d_lo, sch->eps_ao};
+    TenoParams tn{sch->eps, sch->q, sch->ct1, sch->ct2, sch->charvars ? REC_TENO_CHAR : sch->recon, sch->d_hi,
+                  sch->d_lo, sch->eps_ao};
     const int f32 = precision == GKS_FP32_FLUX;
 
     // the float32 path keeps W* and the accumulator increment in float32, in

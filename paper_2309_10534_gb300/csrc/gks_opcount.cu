@@ -120,19 +120,38 @@ void count(int tau_mode, double Pr, gks_flop_model* out)
     }
 
     const T q[5] = {T(1.00), T(1.011), T(1.023), T(1.036), T(1.050)};
+    constexpr int RB = rec_base(REC);
     const Counts recon = measure([&] {
         TenoSel<T> S;
-        rec_select<REC>(q, tp, S);
+        rec_select<RB>(q, tp, S);
         T a, b, c, d;
-        rec_faces<REC>(q, S, a, b, c, d);
+        rec_faces<RB>(q, S, a, b, c, d);
     });
     const Counts tang = measure([&] {
         TenoSel<T> S;
-        rec_select<REC>(q, tp, S);
+        rec_select<RB>(q, tp, S);
         T a, b;
-        rec_gauss<REC>(S, T(0.28867513459481288), a, b);
-        rec_gauss<REC>(S, T(-0.28867513459481288), a, b);
+        rec_gauss<RB>(S, T(0.28867513459481288), a, b);
+        rec_gauss<RB>(S, T(-0.28867513459481288), a, b);
     });
+    // characteristic variables: per face the basis, six projections, two
+    // sides of every field and four back-projections
+    Counts charface;
+    if constexpr (REC == REC_TENO_CHAR) {
+        T w[6][4];
+        for (int c = 0; c < 6; ++c) {
+            const double rho = 1.0 + 0.01 * c, U = 0.3 + 0.002 * c, V = DIM == 2 ? 0.2 - 0.001 * c : 0.0;
+            const double p = 1.0 + 0.015 * c;
+            w[c][0] = T(rho);
+            w[c][1] = T(rho * U);
+            w[c][2] = T(rho * V);
+            w[c][3] = T(p / (gamma - 1.0) + 0.5 * rho * (U * U + V * V));
+        }
+        charface = measure([&] {
+            T vl[4], dl[4], vr[4], dr[4];
+            char_face<T, DIM>(w, tp, fp.gm1, vl, dl, vr, dr);
+        });
+    }
     Side<T> L0_, R0_;
     sample_side<T, DIM>(L0_, 1.0, 0.3, 0.2, 1.0, gamma, 0.0);
     sample_side<T, DIM>(R0_, 1.0, 0.3, 0.2, 1.0, gamma, 1e-4);
@@ -140,7 +159,7 @@ void count(int tau_mode, double Pr, gks_flop_model* out)
     // Eq. (3.12) slopes (Step 2), per Gauss point eight quartic evaluations
     // (Step 4)
     Counts conv2d;
-    if constexpr (REC >= 2 && DIM == 2) {
+    if constexpr (rec_conventional(REC) && DIM == 2) {
         const Counts merge = measure([&] {
             T w0[4];
             merge_values<T, 2>(L0_.W, R0_.W, fp, w0);
@@ -166,7 +185,8 @@ void count(int tau_mode, double Pr, gks_flop_model* out)
 
     const int nv = DIM + 2;
     Counts sweep;  // per cell, one stage kernel of one direction
-    sweep += recon.scaled(nv);                     // normal TENO-D, one per cell and variable
+    if (REC == REC_TENO_CHAR) sweep += charface;   // normal TENO-D per face in characteristic variables
+    else sweep += recon.scaled(nv);                // normal TENO-D, one per cell and variable
     if (DIM == 2) {
         // per face: 2 sides x 4 variables x (value, normal slope) tangential selections
         sweep += tang.scaled(16);
@@ -178,7 +198,7 @@ void count(int tau_mode, double Pr, gks_flop_model* out)
         sweep += avg;
     } else {
         sweep += flux;
-        if (REC >= 2) {  // the equilibrium slope of Eq. (3.12) per face
+        if (rec_conventional(REC)) {  // the equilibrium slope of Eq. (3.12) per face
             Counts lin;
             lin.add = 3 * nv;
             lin.mul = 3 * nv;
@@ -232,10 +252,12 @@ extern "C" gks_status gks_count_flops_recon(int dim, int precision, int tau_mode
 {
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
-    if (!out || (dim != 1 && dim != 2) || tau_mode < 0 || tau_mode > 2 || !(Pr > 0.0) || recon < 0 || recon > 3)
+    if (!out || (dim != 1 && dim != 2) || tau_mode < 0 || tau_mode > 2 || !(Pr > 0.0) || recon < 0 ||
+        (recon > 3 && recon != GKS_COUNT_TENO_CHARVARS))
         return GKS_EINVAL;
     const bool f32 = precision == GKS_FP32_FLUX;
-    if (recon == 1) count_rec<1>(dim, f32, tau_mode, Pr, out);
+    if (recon == GKS_COUNT_TENO_CHARVARS) count_rec<gks::REC_TENO_CHAR>(dim, f32, tau_mode, Pr, out);
+    else if (recon == 1) count_rec<1>(dim, f32, tau_mode, Pr, out);
     else if (recon == 2) count_rec<2>(dim, f32, tau_mode, Pr, out);
     else if (recon == 3) count_rec<3>(dim, f32, tau_mode, Pr, out);
     else count_rec<0>(dim, f32, tau_mode, Pr, out);

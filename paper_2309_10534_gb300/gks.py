@@ -43,12 +43,17 @@ class Scheme(C.Structure):
                 ("ct1", C.c_double), ("ct2", C.c_double), ("ct1_t", C.c_double), ("ct2_t", C.c_double),
                 ("eps", C.c_double), ("q", C.c_int), ("tau_mode", C.c_int),
                 ("positivity_fallback", C.c_int), ("recon", C.c_int), ("d_hi", C.c_double),
-                ("d_lo", C.c_double), ("eps_ao", C.c_double), ("merge", C.c_int)]
+                ("d_lo", C.c_double), ("eps_ao", C.c_double), ("merge", C.c_int), ("charvars", C.c_int)]
 
 
 class Diag(C.Structure):
     _fields_ = [("error_word", C.c_uint), ("fallbacks", C.c_longlong), ("t", C.c_double),
                 ("steps", C.c_longlong), ("dt", C.c_double)]
+
+
+class FlipCount(C.Structure):
+    _fields_ = [("normal_flips", C.c_longlong), ("normal_selections", C.c_longlong),
+                ("tangential_flips", C.c_longlong), ("tangential_selections", C.c_longlong)]
 
 
 class FlopModel(C.Structure):
@@ -89,6 +94,7 @@ def lib():
             "gks_step": ([_vp, C.c_double], C.c_int),
             "gks_advance_to": ([_vp, C.c_double, C.c_longlong, C.POINTER(C.c_longlong), _dp], C.c_int),
             "gks_get_diagnostics": ([_vp, C.POINTER(Diag)], C.c_int),
+            "gks_selection_flips": ([_vp, C.POINTER(FlipCount)], C.c_int),
             "gks_last_error": ([_vp], C.c_char_p),
             "gks_status_string": ([C.c_int], C.c_char_p),
             "gks_kernel_launches": ([_vp], C.c_longlong),
@@ -114,7 +120,7 @@ def _status_string(s):
 def default_scheme(**kw) -> Scheme:
     s = Scheme(cfl=0.5, c1=0.01, c2=1.0, ct1=1e-7, ct2=1e-5, ct1_t=1e-7, ct2_t=1e-5, eps=1e-40, q=7,
                tau_mode=TAU["euler"], positivity_fallback=1, recon=0, d_hi=0.85, d_lo=0.85, eps_ao=1e-8,
-               merge=0)
+               merge=0, charvars=0)
     if kw.get("recon") in ("teno5", 3) and "q" not in kw:
         kw = dict(kw, q=6)  # TENO5's power (Eq. 4.1); TENO-D's default is 7
     for k, v in kw.items():
@@ -258,6 +264,13 @@ class Solver:
         self._check(lib().gks_get_diagnostics(self.h, C.byref(d)))
         return d
 
+    def selection_flips(self):
+        """TENO-D selections the float32 path makes otherwise than the float64
+        path on the current state: dict of counts (gks_selection_flips)."""
+        f = FlipCount()
+        self._check(lib().gks_selection_flips(self.h, C.byref(f)))
+        return {k: int(getattr(f, k)) for k, _ in FlipCount._fields_}
+
     def kernel_launches(self):
         return lib().gks_kernel_launches(self.h)
 
@@ -285,8 +298,14 @@ def alu_peak(precision="fp32", target_ms=200.0):
     return v.value
 
 
-def count_flops(dim, precision="fp32", tau="euler", Pr=1.0, recon="teno_d"):
-    """Algorithmic operation count of the library's stage arithmetic per cell."""
+GKS_COUNT_TENO_CHARVARS = 4
+
+
+def count_flops(dim, precision="fp32", tau="euler", Pr=1.0, recon="teno_d", charvars=0):
+    """Algorithmic operation count of the library's stage arithmetic per cell
+    (charvars=1: TENO-D in characteristic variables)."""
+    if charvars:
+        recon = GKS_COUNT_TENO_CHARVARS
     m = FlopModel()
     L = lib()
     L.gks_count_flops_recon.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(FlopModel)]
@@ -324,9 +343,11 @@ def _replica():
         L.gks_host_weno3.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_int, C.c_double, _dp]
         L.gks_host_weno3_gauss.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_int, C.c_double, _dp]
         L.gks_host_merge.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp, _dp]
+        L.gks_host_char_face.argtypes = [C.c_int, C.c_int, C.c_double, _dp, C.c_double, C.c_int, C.c_double,
+                                         C.c_double, _dp]
         for f in (L.gks_host_time_coeffs, L.gks_host_teno, L.gks_host_point_flux, L.gks_host_teno_vjp,
                   L.gks_host_point_flux_vjp, L.gks_host_weno_ao, L.gks_host_weno3, L.gks_host_weno3_gauss,
-                  L.gks_host_merge):
+                  L.gks_host_merge, L.gks_host_char_face):
             f.restype = C.c_int
         L._replica_declared = True
     return L
@@ -393,6 +414,16 @@ def host_weno3_gauss(q, teno5=False, precision="fp64", eps=None, q_pow=6, ct=1e-
     if _replica().gks_host_weno3_gauss(PRECISION[precision], int(bool(teno5)), pq, eps, int(q_pow), ct, pg):
         raise ValueError("bad argument")
     return g
+
+
+def host_char_face(dim, w6, precision="fp64", gamma=1.4, eps=1e-40, q_pow=7, ct1=1e-7, ct2=1e-5):
+    """(vl, dl, vr, dr), 4 slots each: both sides of one face reconstructed
+    in characteristic variables from the six cells w6[6][4] around it."""
+    ww, pw = _arr(np.asarray(w6, dtype=np.float64).reshape(24), 24)
+    o, po = _arr(None, 16)
+    if _replica().gks_host_char_face(dim, PRECISION[precision], gamma, pw, eps, int(q_pow), ct1, ct2, po):
+        raise ValueError("bad argument")
+    return o.reshape(4, 4)
 
 
 def host_merge(dim, Wl, Wr, precision="fp64", gamma=1.4):

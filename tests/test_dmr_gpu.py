@@ -124,3 +124,47 @@ def test_adjoint_refuses_state_setting_boundaries(gks):
 def test_state_setting_rules_only_on_y_sides(gks):
     with pytest.raises(gks.GKSError):
         gks.Solver(2, 16, 16, bc=("moving_shock", "zerograd", "zerograd", "zerograd"))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_dmr_960x240_sampled_windows(gks, precision, tol):
+    """Full size of the double Mach reflection (Sec. 5.7: 960 x 240 on
+    [0, 4] x [0, 1]) in the launch configuration the bench times: 20 CFL
+    steps on the GPU, then one step of the oracle's time step, checked on
+    8 x 8 windows against the oracle stepping a cut-out of the same state with
+    the window's origin and time (cut edges zero-gradient, 6 cells away), so
+    the position- and time-dependent rules are exercised: the inflow edge,
+    the foot of the wall at x = 1/6, the top boundary under the moving shock,
+    the right edge and the interior across the shocks."""
+    nx, ny = 960, 240
+    s = WL.double_mach(nx, ny)
+    P = O.make_problem(2, nx, ny, **s.problem_kwargs())
+    S = gks.solver_for(s, precision)
+    for _ in range(20):
+        S.step(0.0)
+    t = S.diagnostics().t
+    W1 = S.get_state()
+    P.t = t
+    dt = O.dt(P, W1)
+    S.step(dt)
+    got = S.get_state()
+    assert S.diagnostics().error_word == 0
+    h = 4.0 / nx
+    xs_top = 1.0 / 6.0 + (1.0 + 20.0 * t) / np.sqrt(3.0)  # the moving shock on y = 1
+    it = int(xs_top / h) - 4
+    corners = [(0, 0), (0, 116), (36, 0), (40, 0), (it, ny - 8), (it - 40, ny - 8), (nx - 8, 116), (600, 0),
+               (100, 116), (int((1.0 / 6.0 + 0.5 / np.sqrt(3.0)) / h), 116)]
+    M = 6
+    for (i0, j0) in corners:
+        xa, xb = max(i0 - M, 0), min(i0 + 8 + M, nx)
+        ya, yb = max(j0 - M, 0), min(j0 + 8 + M, ny)
+        bc = [P.bc[0] if xa == 0 else 1, P.bc[1] if xb == nx else 1, P.bc[2] if ya == 0 else 1,
+              P.bc[3] if yb == ny else 1]
+        kw = s.problem_kwargs()
+        kw.update(bc=bc, lx=h * (xb - xa), ly=h * (yb - ya), ox=h * xa, oy=h * ya, t=t)
+        Pw = O.make_problem(2, xb - xa, yb - ya, **kw)
+        ref = O.step(Pw, np.ascontiguousarray(W1[:, ya:yb, xa:xb]), dt)[:, j0 - ya:j0 - ya + 8, i0 - xa:i0 - xa + 8]
+        g = got[:, j0:j0 + 8, i0:i0 + 8]
+        err = rel_l1(g, ref)
+        print(f"{precision} window ({i0}, {j0}): {err:.3e}")
+        assert err < tol, (i0, j0, err)

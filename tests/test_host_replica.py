@@ -203,3 +203,40 @@ def test_merge_matches_half_space_quadrature(G, dim):
     # equal states: the two half spaces add up to the state
     W = sides[0][4]
     assert np.allclose(G.host_merge(dim, W, W), W, rtol=1e-13)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_char_face_matches_oracle(G, dim, precision, tol):
+    """The kernels' characteristic-variable face reconstruction (closed-form
+    L and R) against the oracle's pieces: its basis (R's columns from the
+    eigenvectors, L by Gaussian elimination) and its fitted TENO-D per
+    field, on smooth stencils and on stencils across a jump."""
+    rng = np.random.default_rng(40 + dim)
+    nv = dim + 2
+    for trial in range(12):
+        rho = rng.uniform(0.3, 2.0, 6)
+        U = rng.uniform(-1, 1, 6)
+        V = rng.uniform(-1, 1, 6) if dim == 2 else np.zeros(6)
+        p = rng.uniform(0.3, 2.0, 6)
+        if trial % 2 == 0:  # smooth stencil
+            x = np.arange(6)
+            rho, U, V, p = 1 + 0.05 * x, 0.2 + 0.01 * x, (0.1 - 0.02 * x) * (dim == 2), 1 + 0.03 * x
+        E = p / 0.4 + 0.5 * rho * (U * U + V * V)
+        w4 = np.stack([rho, rho * U, rho * V, E], axis=1)
+        got = G.host_char_face(dim, w4, precision=precision)
+        act = [0, 1, 2, 3] if dim == 2 else [0, 1, 3]
+        Q = w4[:, act]
+        R, L = O.char_basis(dim, 1.4, 0.5 * (Q[2] + Q[3]))
+        C = Q @ L.T
+        cl, cdl, cr, cdr = (np.zeros(nv) for _ in range(4))
+        for k in range(nv):
+            v, d, _, _ = O.teno_d(C[0:5, k], [0.5])
+            cl[k], cdl[k] = v[0], d[0]
+            v, d, _, _ = O.teno_d(C[1:6, k], [-0.5])
+            cr[k], cdr[k] = v[0], d[0]
+        for row, ref in zip(got, (R @ cl, R @ cdl, R @ cr, R @ cdr)):
+            scale = np.abs(Q).max()
+            assert np.abs(row[act] - ref).max() <= tol * scale, (trial, row[act], ref)
+            if dim == 1:
+                assert row[2] == 0.0
