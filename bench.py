@@ -24,7 +24,17 @@ viscous shock tube on 2048 x 1024, 200 steps from t = 0), "errors_vs_oracle"
 (both GPU paths against the FP64 oracle on the CPU baseline's sample) and
 "adjoint" (the
 hand-written adjoint on a 512 x 512 isentropic vortex, 700 steps to t = 2,
-checkpoint every 20 steps: backward ms per step, float32 and float64).
+checkpoint every 20 steps: backward ms per step, float32 and float64),
+"developed" / "value_developed" (the main workload timed again from
+t = 0.4, where the quadrant waves have developed), "charvars" (the main
+workload with TENO-D in characteristic variables, Sec. 3.1),
+"paper_workloads" (the double Mach reflection at 960 x 240 to t = 0.2, the
+Titarev-Toro wave at 1000 cells to t = 5 and the Riemann configuration 6 at
+400^2 to t = 0.6, whole runs in both precisions), "flips" (TENO-D
+selections the float32 path makes otherwise than the float64 path, per step
+of both timed windows), "oracle_by_config" (the oracle's throughput on
+bounded samples of the other configurations, one copy per host core) and
+"errors_vs_oracle" per configuration.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -57,7 +67,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--fp64-steps", type=int, default=10)
     p.add_argument("--cpu-sample", type=int, default=96, help="grid of the oracle's bounded sample")
     p.add_argument("--skip-cpu", action="store_true", help="omit the CPU-oracle baseline (profiling runs)")
     p.add_argument("--no-ensemble", dest="ensemble", action="store_false",
@@ -78,6 +88,14 @@ def parse():
                    help="omit the WENO5-AO and conventional (WENO5-Z, TENO5) 2-D legs")
     p.add_argument("--no-recon-1d", dest="recon_1d", action="store_false",
                    help="omit the 1-D leg that times TENO-D, WENO5-Z and TENO5 face reconstructions")
+    p.add_argument("--no-paper", dest="paper", action="store_false",
+                   help="omit the paper-size workload legs (double Mach reflection, Titarev-Toro, config 6)")
+    p.add_argument("--no-charvars", dest="charvars", action="store_false",
+                   help="omit the characteristic-variable TENO-D leg")
+    p.add_argument("--no-developed", dest="developed", action="store_false",
+                   help="omit the developed-flow timing window (t = 0.4)")
+    p.add_argument("--cpu-budget", type=float, default=4.0,
+                   help="seconds of oracle time per configuration on all host cores")
     return p.parse_args()
 
 
@@ -166,9 +184,56 @@ def sweep_pipe_from_profiles(name="sweep_fp32_riemann1024.md", pipe="FMA"):
     return float(m.group(1)) / 100.0 if m else None
 
 
-def cpu_baseline(steps_budget_s=15.0, n=96):
+def host_info():
+    """Host cores available to this process and the CPU model."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return cores, model
+
+
+def _oracle_on_threads(make, advance, budget_s, threads):
+    """The oracle as it stands on `threads` host threads: every thread steps
+    its own copy of a sample (make(k) -> state; advance(state) -> (state,
+    cell-updates)) until budget_s has passed (the oracle's C calls release
+    the interpreter lock, so the threads run in parallel).  Returns
+    (cell-updates/s over all threads, cell-updates, seconds)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def work(k):
+        st = make(k)
+        cu = 0.0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget_s:
+            st, c = advance(st)
+            cu += c
+        return cu
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        cus = list(ex.map(work, range(threads)))
+    el = time.perf_counter() - t0
+    return sum(cus) / el, sum(cus), el
+
+
+def cpu_baseline(steps_budget_s=10.0, n=96, budget_all=4.0):
     """The oracle as it stands, on the host cores, on a bounded sample: the
-    same problem on an n x n grid, CFL steps until ~steps_budget_s."""
+    same problem on an n x n grid, CFL steps, single thread for
+    ~steps_budget_s (its state is the errors' sample), then one copy per
+    host core for ~budget_all.  The headline value is the all-core one."""
     import oracle as O
     from paper_2309_10534_gb300 import workloads as WL
 
@@ -183,28 +248,199 @@ def cpu_baseline(steps_budget_s=15.0, n=96):
         if time.perf_counter() - t0 > steps_budget_s:
             break
     el = time.perf_counter() - t0
-    return {"value": n * n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%dx%d grid of the same problem, %d CFL steps, single thread" % (n, n, steps)}, (s, W, steps)
+    single = n * n * steps / el
+    cores, model = host_info()
+
+    def adv(st):
+        return O.step(P, st, O.dt(P, st)), n * n
+
+    allv, cu, el_all = _oracle_on_threads(lambda k: s.W.copy(), adv, budget_all, cores)
+    return ({"value": allv, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": model,
+             "sample": "%dx%d grid of the same problem, CFL steps from t = 0, one copy per host core for %.0f s "
+                       "(%.3g cell-updates)" % (n, n, el_all, cu),
+             "single_thread": {"value": single, "cores": 1,
+                               "sample": "%dx%d grid, %d CFL steps, one thread" % (n, n, steps)}},
+            (s, W, steps))
+
+
+def oracle_by_config(budget_s, cores):
+    """The oracle's throughput on bounded samples of the other workloads, one
+    copy per host core (cell-updates/s; one cell-update = one cell advanced
+    by one S2O4 step)."""
+    import numpy as np
+    import oracle as O
+    from paper_2309_10534_gb300 import workloads as WL
+    out = {}
+
+    def restartable(s, P, t_end):
+        def make(k):
+            return [s.W.copy(), 0.0]
+
+        def adv(st):
+            W, t = st
+            if t >= t_end:
+                W, t = s.W.copy(), 0.0
+            dt = min(O.dt(P, W), t_end - t)
+            return [O.step(P, W, dt), t + dt], s.nx * s.ny
+        return make, adv
+
+    s = WL.sod(400)
+    P = O.make_problem(1, 400, **s.problem_kwargs())
+    v, cu, el = _oracle_on_threads(*restartable(s, P, 0.2), budget_s, cores)
+    out["1_sod400"] = {"value": v, "unit": UNIT, "cores": cores, "sample": "Sod 400 cells, CFL steps to t = 0.2 "
+                       "(restarted), one run per core"}
+    s = WL.viscous_shock_tube(64, 32)
+    P = O.make_problem(2, 64, 32, **s.problem_kwargs())
+    v, cu, el = _oracle_on_threads(*restartable(s, P, 1.0), budget_s, cores)
+    out["3_viscous"] = {"value": v, "unit": UNIT, "cores": cores,
+                        "sample": "viscous shock tube (Re 200, Pr 0.73, walls) on 64 x 32, CFL steps from t = 0"}
+    E = WL.ensemble_1d()
+    order = np.argsort(E.ncells, kind="stable")
+
+    def make_e(k):
+        return [k, None, 0.0, None]
+
+    def adv_e(st):
+        k, W, t, P = st
+        if W is None or t >= E.t_end:
+            k = (k + cores) % E.ncells.size if W is not None else k
+            idx = int(order[k % E.ncells.size])
+            n = int(E.ncells[idx])
+            W = E.W[:, E.offsets[idx]:E.offsets[idx] + n][:, None, :].copy()
+            P = O.make_problem(1, n, tau="euler")
+            t = 0.0
+        dt = min(O.dt(P, W), E.t_end - t)
+        n = W.shape[-1]
+        try:
+            W = O.step(P, W, dt)
+        except RuntimeError:  # a member whose state turns non-physical: next problem
+            return [k, None, E.t_end, P], n
+        return [k, W, t + dt, P], n
+    v, cu, el = _oracle_on_threads(make_e, adv_e, budget_s, cores)
+    out["4_ensemble"] = {"value": v, "unit": UNIT, "cores": cores,
+                         "sample": "members of the seeded 4096-problem ensemble, smallest first, one per core at a "
+                                   "time, to t = 0.15"}
+    s = WL.isentropic_vortex(n=32, seed=2309, amplitude=1e-3)
+    P = O.make_problem(2, 32, 32, lx=10.0, ly=10.0, bc=("periodic",) * 4, tau="zero")
+    dtv = 2.0 / 700 * 16
+
+    def adv_v(st):
+        return O.step(P, st, dtv), 32 * 32
+    v, cu, el = _oracle_on_threads(lambda k: s.W.copy(), adv_v, budget_s, cores)
+    out["5_adjoint_forward"] = {"value": v, "unit": UNIT, "cores": cores,
+                                "sample": "forward S2O4 steps of the isentropic vortex (tau = 0) on 32 x 32; the "
+                                          "oracle has no adjoint (its reference gradient is central differences: "
+                                          "two forward runs per direction)"}
+    return out
+
+
+def _errs(got, ref):
+    import numpy as np
+    e = np.abs(got - ref)
+    return {"l1_rel": float(e.sum() / np.abs(ref).sum()), "linf_rel": float(e.max() / np.abs(ref).max())}
 
 
 def oracle_errors(gks, sample):
-    """Stated errors of both GPU paths against the FP64 oracle on the CPU
-    baseline's sample (same grid, same initial state, same number of CFL
-    steps): relative L1 (sum |e| / sum |W|) and relative Linf (max |e| /
-    max |W|) over all conserved variables."""
+    """Stated errors of both GPU paths against the FP64 oracle, per
+    configuration, on samples the oracle finishes in seconds: relative L1
+    (sum |e| / sum |W|) and relative Linf (max |e| / max |W|) over all
+    conserved variables.  For the float32 path the oracle's own spread under
+    float32-level perturbations (1e-7 of the state before every step) is
+    given beside it (1e-7 of the initial state, or of the state before every
+    step, the larger): TENO-D's cut-offs make shock runs depend
+    discontinuously on rounding (see "flips")."""
     import numpy as np
+    import oracle as O
+    from paper_2309_10534_gb300 import workloads as WL
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from oracle_envelope import fp32_envelope
+    out = {}
+    # config 2: the CPU baseline's own sample
     s, W_or, steps = sample
-    out = {"sample": "%dx%d riemann2d_config3, %d CFL steps" % (s.nx, s.ny, steps)}
+    e = {"sample": "%dx%d riemann2d_config3, %d CFL steps" % (s.nx, s.ny, steps)}
     for precision in ("fp64", "fp32"):
         S = gks.solver_for(s, precision)
         for _ in range(steps):
             S.step(0.0)
-        W = S.get_state()
-        S.diagnostics()
-        e = np.abs(W - W_or)
-        out[precision] = {"l1_rel": float(e.sum() / np.abs(W_or).sum()),
-                          "linf_rel": float(e.max() / np.abs(W_or).max())}
+        e[precision] = _errs(S.get_state(), W_or)
         S.close()
+    out["2_riemann2d"] = e
+    # config 1: Sod, 400 cells, the whole run
+    s = WL.sod(400)
+    P = O.make_problem(1, 400, **s.problem_kwargs())
+    Wo, spread = fp32_envelope(P, s.W, 0.2, seeds=(0, 1))
+    e = {"sample": "Sod 400 cells to t = 0.2 (the whole run)", "fp32_oracle_spread_l1_rel": spread}
+    for precision in ("fp64", "fp32"):
+        S = gks.solver_for(s, precision)
+        S.advance_to(0.2)
+        e[precision] = _errs(S.get_state(), Wo)
+        S.close()
+    out["1_sod400"] = e
+    # config 3: the viscous shock tube on a reduced grid
+    s = WL.viscous_shock_tube(64, 32)
+    P = O.make_problem(2, 64, 32, **s.problem_kwargs())
+    Wo, spread = fp32_envelope(P, s.W, 1.0, seeds=(0, 1), max_steps=10)
+    e = {"sample": "viscous shock tube (Re 200, Pr 0.73) on 64 x 32, 10 CFL steps",
+         "fp32_oracle_spread_l1_rel": spread}
+    for precision in ("fp64", "fp32"):
+        S = gks.solver_for(s, precision)
+        S.advance_to(1.0, max_steps=10)
+        e[precision] = _errs(S.get_state(), Wo)
+        S.close()
+    out["3_viscous"] = e
+    # config 4: the 16 smallest members of the seeded ensemble to t = 0.15
+    from concurrent.futures import ThreadPoolExecutor
+    E = WL.ensemble_1d()
+    pick = [int(k) for k in np.argsort(E.ncells, kind="stable")[:16]]
+
+    def one(k):
+        n = int(E.ncells[k])
+        P = O.make_problem(1, n, tau="euler")
+        try:
+            return O.run(P, E.W[:, E.offsets[k]:E.offsets[k] + n][:, None, :], E.t_end)[0][:, 0, :]
+        except RuntimeError:
+            return None
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        refs = list(ex.map(one, pick))
+    sizes = E.ncells[pick]
+    Wsub = np.concatenate([E.W[:, E.offsets[k]:E.offsets[k] + E.ncells[k]] for k in pick], axis=1)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    e = {"sample": "the 16 smallest members of the seeded ensemble (%d..%d cells) to t = 0.15; errors over the "
+                   "members the oracle completes" % (sizes.min(), sizes.max())}
+    for precision in ("fp64", "fp32"):
+        B = gks.Batch(sizes, np.ones(len(pick)), precision=precision)
+        B.set_state(Wsub)
+        B.advance_to(E.t_end, allow_failed=True)
+        got = B.get_state()
+        _, _, err, _ = B.progress()
+        B.close()
+        l1, linf, used = [], [], 0
+        for j, ref in enumerate(refs):
+            if ref is None or err[j]:
+                continue
+            r = _errs(got[:, off[j]:off[j + 1]], ref)
+            l1.append(r["l1_rel"])
+            linf.append(r["linf_rel"])
+            used += 1
+        e[precision] = {"l1_rel_max": max(l1), "l1_rel_mean": float(np.mean(l1)), "linf_rel_max": max(linf),
+                        "members": used}
+    out["4_ensemble"] = e
+    # config 5: the adjoint's forward map (isentropic vortex, tau = 0) on 32 x 32
+    s = WL.isentropic_vortex(n=32, seed=2309, amplitude=1e-3)
+    P = O.make_problem(2, 32, 32, lx=10.0, ly=10.0, bc=("periodic",) * 4, tau="zero")
+    dtv = 2.0 / 700 * 16
+    Wo = s.W.copy()
+    for _ in range(20):
+        Wo = O.step(P, Wo, dtv)
+    e = {"sample": "isentropic vortex (tau = 0, smooth: no selection switches) on 32 x 32, 20 steps"}
+    for precision in ("fp64", "fp32"):
+        S = gks.Solver(2, 32, 32, lx=10.0, ly=10.0, bc=("periodic",) * 4, precision=precision, tau="zero")
+        S.set_state(s.W)
+        for _ in range(20):
+            S.step(dtv)
+        e[precision] = _errs(S.get_state(), Wo)
+        S.close()
+    out["5_adjoint_forward"] = e
     return out
 
 
@@ -277,9 +513,11 @@ def ensemble_leg(gks, WL, stream, peak32, max_steps=0, launch=None, rank=0, worl
     ms = e0.elapsed_time(e1)
     t, steps, err, _ = B.progress()
     cu = float((E.ncells.astype(np.float64) * steps).sum())
+    done = (err == 0)
+    cu_done = float((E.ncells.astype(np.float64) * steps)[done].sum())
     dev = stream.device if dist is not None and dist.get_backend() == "nccl" else None
     ms = gks.reduce_scalars([ms], "max", dist, dev)[0]
-    cu, nbad = gks.reduce_scalars([cu, nbad], "sum", dist, dev)
+    cu, nbad, cu_done = gks.reduce_scalars([cu, nbad, cu_done], "sum", dist, dev)
     fpc = gks.count_flops(1, "fp32", "euler", 1.0)["flops_per_cell_update"]
     tf = fpc * cu / (ms * 1e-3) / 1e12
     launches = B.launches() - L0   # graph replays, one kernel each
@@ -288,7 +526,11 @@ def ensemble_leg(gks, WL, stream, peak32, max_steps=0, launch=None, rank=0, worl
             "problems_per_rank": int(E.ncells.size), "cells_per_rank": int(E.ncells.sum()), "t_end": E.t_end,
             "scaling": "strong", "n_gpus": world,
             "ms": ms, "cell_updates": cu, "max_steps_per_problem": int(steps.max()),
-            "flagged_nonphysical": int(nbad), "launch": {"threads": th, "blocks_per_sm": bp},
+            "flagged_nonphysical": int(nbad),
+            "completed_set": {"value": cu_done / (ms * 1e-3), "unit": UNIT, "cell_updates": cu_done,
+                              "problems": int(E.ncells.size - nbad),
+                              "note": "cell-updates of the problems that reached t_end only, over the same time"},
+            "launch": {"threads": th, "blocks_per_sm": bp},
             "gpu_launches": launches,
             "precision": "fp32 reconstruction+flux, fp64 state and S2O4 accumulation",
             "flops_per_cell_update": fpc,
@@ -461,6 +703,122 @@ def adjoint_leg(gks, WL, stream, precision, steps=700):
                           else "fp64")}
 
 
+def flips_leg(gks, WL, s, steps, warmup, t_dev=None):
+    """TENO-D selection flips between the precisions (gks_selection_flips) on
+    the input state of every step of the timed window (steps warmup+1 ..
+    warmup+steps from t = 0), and of as many steps from t_dev: per step the
+    selections the float32 path would make otherwise than the float64 path
+    on the same float64 state (normal and tangential, both directions).  The
+    states are those of the float32-flux run (its state is float64)."""
+    S = gks.solver_for(s, "fp32")
+
+    def window(k):
+        nf = tf = ns = ts = uf = 0
+        for _ in range(k):
+            f = S.selection_flips()
+            nf += f["normal_flips"]
+            tf += f["tangential_flips"]
+            ns += f["normal_selections"]
+            ts += f["tangential_selections"]
+            uf += f["unresolved_flips"]
+            S.step(0.0)
+        return {"normal_per_step": nf / k, "tangential_per_step": tf / k,
+                "fraction_of_selections": (nf + tf) / max(ns + ts, 1),
+                "selections_per_step": (ns + ts) / k,
+                "unresolved_per_step": uf / k}
+    for _ in range(warmup):
+        S.step(0.0)
+    out = {"timed_window": window(steps)}
+    if t_dev:
+        S.advance_to(t_dev)
+        out["developed_window"] = window(steps)
+        out["developed_window"]["t_start"] = t_dev
+    S.close()
+    return out
+
+
+def timed_steps(S, stream, flush, K):
+    """K steps, each bracketed by CUDA events on the solver's stream, with
+    an L2 flush before each (outside the events); ms in total."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(stream)
+        S.step(0.0)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
+def charvars_leg(gks, WL, stream, peak32, steps, warmup):
+    """The main workload with TENO-D in characteristic variables (Sec. 3.1),
+    float32 flux: cell-updates/s and the sweep's flop rate."""
+    import torch
+    s = WL.riemann2d(N_GRID, split=0.8, t_end=0.8)
+    S = gks.solver_for(s, "fp32", charvars=1)
+    S.set_stream(stream.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=stream.device)
+    for _ in range(warmup):
+        S.step(0.0)
+    torch.cuda.synchronize()
+    S.profile(True)
+    S.profile_read(0)
+    ms = timed_steps(S, stream, flush, steps)
+    S.diagnostics()
+    sn, sms = S.profile_read(0)
+    S.profile(False)
+    S.close()
+    cells = N_GRID * N_GRID
+    fm = gks.count_flops(2, "fp32", "euler", 1.0, charvars=1)
+    launch_ms = sms / max(sn, 1)
+    tf = fm["flops_per_cell_sweep"] * cells / (launch_ms * 1e-3) / 1e12
+    return {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "workload": "riemann2d_config3_charvars",
+            "grid": "%dx%d" % (N_GRID, N_GRID), "steps": steps, "ms_per_step": ms / steps,
+            "flops_per_cell_update": fm["flops_per_cell_update"],
+            "roofline": {"bound": "alu", "kernel": "k2d_sweep<float, charvars>", "achieved": tf, "peak": peak32,
+                         "unit": "TFLOP/s", "frac": tf / peak32, "launch_ms": launch_ms}}
+
+
+def paper_run(gks, s, precision, stream, max_steps=0):
+    """A whole run of a paper workload to its end time (CFL steps, CUDA-graph
+    replays of the library's advance), timed with CUDA events on the
+    library's stream after an untimed warm-up run; cell-updates/s."""
+    import torch
+    S = gks.solver_for(s, precision)
+    S.set_stream(stream.cuda_stream)
+    S.advance_to(s.t_end, max_steps=16)  # warm-up: graphs captured
+    S.set_state(s.W)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    steps, t = S.advance_to(s.t_end, max_steps=max_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    S.diagnostics()
+    S.close()
+    cells = s.nx * s.ny
+    return {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "steps": int(steps), "t": t, "ms": ms}
+
+
+def paper_legs(gks, WL, stream):
+    """The paper's other workloads at the paper's sizes: the double Mach
+    reflection (Sec. 5.7, 960 x 240 to t = 0.2), the Titarev-Toro
+    shock-entropy wave (Sec. 5.3, 1000 cells to t = 5) and the Riemann
+    configuration 6 (Sec. 5.6 (b), 400^2 to t = 0.6), both precisions."""
+    out = {}
+    for name, s in (("dmr", WL.double_mach(960, 240, t_end=0.2)),
+                    ("titarev_toro", WL.titarev_toro(1000)),
+                    ("riemann_cfg6", WL.riemann2d_config6(400, t_end=0.6))):
+        d = {"grid": "%dx%d" % (s.nx, s.ny) if s.dim == 2 else "%d" % s.nx, "t_end": s.t_end}
+        d["fp32"] = paper_run(gks, s, "fp32", stream)
+        d["fp64"] = paper_run(gks, s, "fp64", stream)
+        out[name] = d
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -528,6 +886,19 @@ def main():
     clocks.start()
     S32 = solver("fp32")
     ms32, launches32, sn32, sms32 = timed(S32, args.steps, args.warmup)
+    devw = None
+    T_DEV = 0.4
+    if args.developed:
+        # the same solver advanced (untimed) to t = 0.4, where the quadrant
+        # waves have developed, then K more timed steps
+        S32.advance_to(T_DEV)
+        S32.profile(True)
+        S32.profile_read(0)
+        msd = timed_steps(S32, stream, flush, args.steps)
+        dn, dms = S32.profile_read(0)
+        S32.profile(False)
+        devw = {"value": cells * args.steps * world / (msd * 1e-3), "unit": UNIT, "t_start": T_DEV,
+               "steps": args.steps, "ms_per_step": msd / args.steps, "sweep_launch_ms": dms / max(dn, 1)}
     S64 = solver("fp64")
     k64 = max(1, args.fp64_steps)
     ms64, launches64, sn64, sms64 = timed(S64, k64, min(args.warmup, 3))
@@ -543,6 +914,8 @@ def main():
     if args.viscous:
         visc = viscous_leg(gks, WL, stream, "fp32", 200)
         visc["fp64"] = viscous_leg(gks, WL, stream, "fp64", 10)
+    chv = charvars_leg(gks, WL, stream, peak32, args.steps, args.warmup) if args.charvars else None
+    pap = paper_legs(gks, WL, stream) if args.paper else None
     adj = None
     if args.adjoint:
         adj = adjoint_leg(gks, WL, stream, "fp32", args.adjoint_steps)
@@ -640,8 +1013,17 @@ def main():
         line["viscous"] = visc
     if adj:
         line["adjoint"] = adj
+    if devw:
+        line["value_developed"] = devw["value"]
+        line["developed"] = devw
+    if chv:
+        line["charvars"] = chv
+    if pap:
+        line["paper_workloads"] = pap
+    line["flips"] = flips_leg(gks, WL, s, args.steps, args.warmup, T_DEV if args.developed else None)
     if world == 1 and not args.skip_cpu:
-        line["cpu_baseline"], sample = cpu_baseline(n=args.cpu_sample)
+        line["cpu_baseline"], sample = cpu_baseline(n=args.cpu_sample, budget_all=args.cpu_budget)
+        line["oracle_by_config"] = oracle_by_config(args.cpu_budget, line["cpu_baseline"]["cores"])
         line["errors_vs_oracle"] = oracle_errors(gks, sample)
     print(json.dumps(line))
     if dist:

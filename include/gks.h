@@ -180,6 +180,13 @@ typedef struct {
                                         [value, normal slope] and direction), each precision on its own
                                         line averages; 0 in 1-D */
     long long tangential_selections; /* tangential selections compared */
+    long long unresolved_flips;      /* flips on stencils whose data vary by less than 2^-16 of the
+                                        magnitude of the quantity they resolve (cell and line averages:
+                                        their own; line-averaged normal slopes: the values' over dx) --
+                                        below float32 resolution: uniform regions, where float32
+                                        rounding makes the data constant and the float64 choice follows
+                                        round-off noise; no value changes beyond rounding.  Not included
+                                        in the two counts above */
 } gks_flip_count;
 
 /* Create a context for one grid; allocates the ghosted device state.
@@ -223,7 +230,7 @@ gks_status gks_get_diagnostics(gks_ctx *ctx, gks_diag *out);
  * step's first stage): the stencil choices of the float32 path (state
  * rounded to float32, the float32 kernels' arithmetic) compared with the
  * float64 path's, every normal and, in 2-D, tangential selection of both
- * sweep directions.  Fills W's ghost layers; allocates and frees a 32-byte
+ * sweep directions.  Fills W's ghost layers; allocates and frees a 40-byte
  * counter; synchronises the context's stream.  TENO-D with component-wise
  * variables only (GKS_EUNSUPPORTED otherwise).  Either precision. */
 gks_status gks_selection_flips(gks_ctx *ctx, gks_flip_count *out);

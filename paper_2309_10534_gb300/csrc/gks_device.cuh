@@ -663,6 +663,23 @@ GKS_HD void hmv(const T* H, const T* a, T* o)
     }
 }
 
+// o += H a for the symmetric moment matrix of hmat, as fused multiply-add
+// chains into the accumulator (no separate product and sum)
+template <typename T, int DIM>
+GKS_HD void hmv_acc(const T* H, const T* a, T* o)
+{
+    if constexpr (DIM == 2) {
+        o[0] = fma(H[3], a[3], fma(H[2], a[2], fma(H[1], a[1], fma(H[0], a[0], o[0]))));
+        o[1] = fma(H[6], a[3], fma(H[5], a[2], fma(H[4], a[1], fma(H[1], a[0], o[1]))));
+        o[2] = fma(H[8], a[3], fma(H[7], a[2], fma(H[5], a[1], fma(H[2], a[0], o[2]))));
+        o[3] = fma(H[9], a[3], fma(H[8], a[2], fma(H[6], a[1], fma(H[3], a[0], o[3]))));
+    } else {
+        o[0] = fma(H[3], a[3], fma(H[1], a[1], fma(H[0], a[0], o[0])));
+        o[1] = fma(H[6], a[3], fma(H[4], a[1], fma(H[1], a[0], o[1])));
+        o[3] = fma(H[9], a[3], fma(H[6], a[1], fma(H[3], a[0], o[3])));
+    }
+}
+
 // Euler flux rho <u psi> of a Maxwellian state (local frame, normal first):
 // (m, m U + p, m V, U (E + p))
 template <typename T, int DIM>
@@ -959,77 +976,50 @@ GKS_HD void side_terms(const Side<T>& S, bool upper, const FluxParams<T>& P,
     u_recursion<T, DIM>(uh, U, inv2l);
     v_moments<T, DIM>(v, V, inv2l);
 
-    // micro slopes, Eq. (2.7)
-    T an[4], at[4] = {T(0), T(0), T(0), T(0)}, b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) b[i] = S.Wn[i] * ir;
-    micro_slope<T, DIM>(b, U, V, lam, inv2l, P.ntot, P.inv_ntot, an);
-    if constexpr (DIM == 2) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) b[i] = S.Wt[i] * ir;
-        micro_slope<T, DIM>(b, U, V, lam, inv2l, P.ntot, P.inv_ntot, at);
-    }
+    // micro slopes, Eq. (2.7).  The solve is linear in its right-hand side,
+    // so rho a = M^-1 W_d: the slopes are formed already multiplied by the
+    // side's density, which every moment below carries (rho <(a.psi) psi>)
+    T ran[4], rat[4] = {T(0), T(0), T(0), T(0)};
+    micro_slope<T, DIM>(S.Wn, U, V, lam, inv2l, P.ntot, P.inv_ntot, ran);
+    if constexpr (DIM == 2) micro_slope<T, DIM>(S.Wt, U, V, lam, inv2l, P.ntot, P.inv_ntot, rat);
 
     // kinetic merge, Eqs. (2.6), (3.25), (3.26): W0 += rho <psi>_half,
     // W0_n += rho <(a_n.psi) psi>_half, W0_t += rho <(a_t.psi) psi>_half
-    T H[10], t[4];
+    T H[10];
     hmat<0, 0, T, DIM>(uh, v, xi2, xi4, H);
-    W0[0] += r * H[0];
-    W0[1] += r * H[1];
-    W0[2] += r * H[2];
-    W0[3] += r * H[3];
-    hmv<T, DIM>(H, an, t);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) W0n[i] += r * t[i];
-    T A[4];
-    if constexpr (DIM == 2) {
-        hmv<T, DIM>(H, at, t);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) W0t[i] += r * t[i];
-    }
+    W0[0] = fma(r, H[0], W0[0]);
+    W0[1] = fma(r, H[1], W0[1]);
+    W0[2] = fma(r, H[2], W0[2]);
+    W0[3] = fma(r, H[3], W0[3]);
+    hmv_acc<T, DIM>(H, ran, W0n);
+    if constexpr (DIM == 2) hmv_acc<T, DIM>(H, rat, W0t);
 
     if constexpr (NONEQ) {
         // time derivative of the side's Maxwellian: <a_n u + a_t v + A> = 0
         const T h = (S.W[3] + p) * ir;
-        T Wtime[4];
+        T Wtime[4], rA[4];
         compat_time_derivative<T, DIM>(S.Wn, S.Wt, U, V, h, P.gm1, Wtime);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) b[i] = Wtime[i] * ir;
-        micro_slope<T, DIM>(b, U, V, lam, inv2l, P.ntot, P.inv_ntot, A);
-        if constexpr (PRFIX) {  // density moments of the A and slope terms, for the heat flux
-            hmv<T, DIM>(H, A, t);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) N5[i] += r * t[i];
-        }
+        micro_slope<T, DIM>(Wtime, U, V, lam, inv2l, P.ntot, P.inv_ntot, rA);
+        if constexpr (PRFIX) hmv_acc<T, DIM>(H, rA, N5);  // density moments of the A and slope terms (heat flux)
         // flux moments of the side terms of Eq. (2.5) over the half space
         hmat<1, 0, T, DIM>(uh, v, xi2, xi4, H);
-        S3[0] += r * H[0];
-        S3[1] += r * H[1];
-        S3[2] += r * H[2];
-        S3[3] += r * H[3];
-        hmv<T, DIM>(H, A, t);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) S5[i] += r * t[i];
+        S3[0] = fma(r, H[0], S3[0]);
+        S3[1] = fma(r, H[1], S3[1]);
+        S3[2] = fma(r, H[2], S3[2]);
+        S3[3] = fma(r, H[3], S3[3]);
+        hmv_acc<T, DIM>(H, rA, S5);
         if constexpr (PRFIX) {
-            hmv<T, DIM>(H, an, t);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) N4[i] += r * t[i];
+            hmv_acc<T, DIM>(H, ran, N4);
             if constexpr (DIM == 2) {
                 hmat<0, 1, T, DIM>(uh, v, xi2, xi4, H);
-                hmv<T, DIM>(H, at, t);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) N4[i] += r * t[i];
+                hmv_acc<T, DIM>(H, rat, N4);
             }
         }
         hmat<2, 0, T, DIM>(uh, v, xi2, xi4, H);
-        hmv<T, DIM>(H, an, t);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) S4[i] += r * t[i];
+        hmv_acc<T, DIM>(H, ran, S4);
         if constexpr (DIM == 2) {
             hmat<1, 1, T, DIM>(uh, v, xi2, xi4, H);
-            hmv<T, DIM>(H, at, t);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) S4[i] += r * t[i];
+            hmv_acc<T, DIM>(H, rat, S4);
         }
     }
 }
@@ -1111,26 +1101,19 @@ GKS_HD void point_flux(const Side<T>& L, const Side<T>& R, const FluxParams<T>& 
     if constexpr (NONEQ) {
         const T inv2l = p0 * ir0, lam = T(0.5) / inv2l;
         const T xi2 = P.K * inv2l, xi4 = P.K * (P.K + T(2)) * inv2l * inv2l;
-        T u[7], v[6], an[4], at[4] = {T(0), T(0), T(0), T(0)}, b[4], H[10], t[4];
+        // rho0 a0 = M^-1 W0_d (the solve is linear in its right-hand side)
+        T u[7], v[6], ran[4], rat[4], H[10];
         u[0] = T(1);
         u[1] = U0;
         u_recursion<T, DIM>(u, U0, inv2l);
         v_moments<T, DIM>(v, V0, inv2l);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) b[i] = W0n[i] * ir0;
-        micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, P.inv_ntot, an);
+        micro_slope<T, DIM>(W0n, U0, V0, lam, inv2l, P.ntot, P.inv_ntot, ran);
         hmat<2, 0, T, DIM>(u, v, xi2, xi4, H);
-        hmv<T, DIM>(H, an, t);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) F1[i] = r0 * t[i];
+        hmv_acc<T, DIM>(H, ran, F1);
         if constexpr (DIM == 2) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) b[i] = W0t[i] * ir0;
-            micro_slope<T, DIM>(b, U0, V0, lam, inv2l, P.ntot, P.inv_ntot, at);
+            micro_slope<T, DIM>(W0t, U0, V0, lam, inv2l, P.ntot, P.inv_ntot, rat);
             hmat<1, 1, T, DIM>(u, v, xi2, xi4, H);
-            hmv<T, DIM>(H, at, t);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) F1[i] += r0 * t[i];
+            hmv_acc<T, DIM>(H, rat, F1);
         }
     }
     const T dt = P.dt, idt = T(1) / dt;

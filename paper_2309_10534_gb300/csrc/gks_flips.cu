@@ -23,6 +23,32 @@ namespace {
 
 using namespace gks;
 
+// A stencil whose data vary by less than 2^-16 of their magnitude (about 100
+// float32 ulps) is below float32 resolution: where float32 rounding makes
+// it constant any choice reproduces the constant, and where the float64 data
+// vary at round-off level the float64 choice follows that noise.  Flips on
+// such stencils change no value beyond rounding; they are counted apart.
+// scale: the magnitude of the quantity the stencil's data resolve (cell and
+// line averages: their own largest magnitude; line-averaged normal slopes:
+// the largest magnitude of the values they are the slope of, over dx).
+__device__ double magnitude(const double* q)
+{
+    double mx = fabs(q[0]);
+#pragma unroll
+    for (int s = 1; s < 5; ++s) mx = fmax(mx, fabs(q[s]));
+    return mx;
+}
+__device__ bool resolved(const double* q, double scale)
+{
+    double lo = q[0], hi = q[0];
+#pragma unroll
+    for (int s = 1; s < 5; ++s) {
+        lo = fmin(lo, q[s]);
+        hi = fmax(hi, q[s]);
+    }
+    return hi - lo > ldexp(scale, -16);
+}
+
 // the selection as 4 bits: bit 0 large stencil, bits 1-3 kept sub-stencils
 template <typename T>
 __device__ unsigned sel_code(const TenoSel<T>& S)
@@ -31,21 +57,29 @@ __device__ unsigned sel_code(const TenoSel<T>& S)
     return (S.w[0] > T(0) ? 2u : 0u) | (S.w[1] > T(0) ? 4u : 0u) | (S.w[2] > T(0) ? 8u : 0u);
 }
 
-__device__ void add_counts(unsigned long long* out, unsigned a, unsigned b, unsigned c, unsigned d)
+// counters: normal flips, normal selections, tangential flips, tangential
+// selections, unresolved flips (both kinds)
+constexpr int NCOUNT = 5;
+
+__device__ void add_counts(unsigned long long* out, unsigned (&c)[NCOUNT])
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        c += __shfl_xor_sync(0xffffffffu, c, o);
-        d += __shfl_xor_sync(0xffffffffu, d, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (a) atomicAdd(out + 0, (unsigned long long)a);
-        if (b) atomicAdd(out + 1, (unsigned long long)b);
-        if (c) atomicAdd(out + 2, (unsigned long long)c);
-        if (d) atomicAdd(out + 3, (unsigned long long)d);
-    }
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NCOUNT; ++k) c[k] += __shfl_xor_sync(0xffffffffu, c[k], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < NCOUNT; ++k)
+            if (c[k]) atomicAdd(out + k, (unsigned long long)c[k]);
+}
+
+// one compared selection: a flip on a resolved stencil counts in slot k,
+// on an unresolved one in slot 4
+__device__ void tally(unsigned (&c)[NCOUNT], int k, unsigned code64, unsigned code32, const double* q,
+                      double scale)
+{
+    c[k + 1] += 1;
+    if (code64 != code32) c[resolved(q, scale) ? k : 4] += 1;
 }
 
 // 1-D: per cell, the normal selection of (rho, rho u, E)
@@ -53,7 +87,7 @@ __global__ void k_flips1d(GridDev g, const double* __restrict__ W, TenoT<double>
                           unsigned long long* out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;  // interior cell
-    unsigned nflip = 0, ntot = 0;
+    unsigned cnt[NCOUNT] = {0, 0, 0, 0, 0};
     if (i < g.nx) {
         const int pl = (int)g.plane;
         double q[3][5];
@@ -83,10 +117,9 @@ __global__ void k_flips1d(GridDev g, const double* __restrict__ W, TenoT<double>
         teno_select(qe, pf, S);
         cf[2] = sel_code(S);
 #pragma unroll
-        for (int v = 0; v < 3; ++v) nflip += cd[v] != cf[v];
-        ntot = 3;
+        for (int v = 0; v < 3; ++v) tally(cnt, 0, cd[v], cf[v], q[v], magnitude(q[v]));
     }
-    add_counts(out, nflip, ntot, 0u, 0u);
+    add_counts(out, cnt);
 }
 
 // 2-D, one direction: per (face, row) of the interior.  Cell f (f < nn):
@@ -98,7 +131,7 @@ __global__ void k_flips2d(GridDev g, const double* __restrict__ W, int dirn, Ten
 {
     const int nn = dirn ? g.ny : g.nx, nt = dirn ? g.nx : g.ny;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned nflip = 0, ntot = 0, tflip = 0, ttot = 0;
+    unsigned cnt[NCOUNT] = {0, 0, 0, 0, 0};
     if (idx < (long long)(nn + 1) * nt) {
         const int f = (int)(idx % (nn + 1)), t = (int)(idx / (nn + 1));
         // variable v of the local frame (normal momentum first) at normal
@@ -125,10 +158,9 @@ __global__ void k_flips2d(GridDev g, const double* __restrict__ W, int dirn, Ten
                 const unsigned cf0 = sel_code_x(S2), cf1 = sel_code_y(S2);
                 TenoSel<double> S;
                 teno_select(q[0], nd, S);
-                nflip += sel_code(S) != cf0;
+                tally(cnt, 0, sel_code(S), cf0, q[0], magnitude(q[0]));
                 teno_select(q[1], nd, S);
-                nflip += sel_code(S) != cf1;
-                ntot += 2;
+                tally(cnt, 0, sel_code(S), cf1, q[1], magnitude(q[1]));
             }
             // line averages of the two sides (side 0: cell f-1 at +1/2,
             // side 1: cell f at -1/2), rows t-2 .. t+2, per precision
@@ -173,15 +205,15 @@ __global__ void k_flips2d(GridDev g, const double* __restrict__ W, int dirn, Ten
                     teno_select_x2(qq, tf, S2);
                     TenoSel<double> S;
                     teno_select(lv[k], td, S);
-                    tflip += sel_code(S) != sel_code_x(S2);
+                    const double mv = magnitude(lv[k]);
+                    tally(cnt, 2, sel_code(S), sel_code_x(S2), lv[k], mv);
                     teno_select(ls[k], td, S);
-                    tflip += sel_code(S) != sel_code_y(S2);
-                    ttot += 2;
+                    tally(cnt, 2, sel_code(S), sel_code_y(S2), ls[k], mv * ihn);
                 }
             }
         }
     }
-    add_counts(out, nflip, ntot, tflip, ttot);
+    add_counts(out, cnt);
 }
 
 }  // namespace
@@ -193,8 +225,8 @@ extern "C" gks_status gks_selection_flips(gks_ctx* c, gks_flip_count* out)
         return rt::fail(c, GKS_EUNSUPPORTED, "selection flips are counted for component-wise TENO-D");
     const TenoParams tn = rt::teno_params(c, false), tt = rt::teno_params(c, true);
     unsigned long long* d = nullptr;
-    unsigned long long h[4] = {0, 0, 0, 0};
-    if (cudaMalloc(&d, sizeof h) != cudaSuccess) return rt::fail(c, GKS_ENOMEM, "cudaMalloc of 32 bytes failed");
+    unsigned long long h[NCOUNT] = {0, 0, 0, 0, 0};
+    if (cudaMalloc(&d, sizeof h) != cudaSuccess) return rt::fail(c, GKS_ENOMEM, "cudaMalloc of 40 bytes failed");
     gks_status st = GKS_OK;
     do {
         if (cudaMemsetAsync(d, 0, sizeof h, c->stream) != cudaSuccess) { st = GKS_ECUDA; break; }
@@ -226,5 +258,6 @@ extern "C" gks_status gks_selection_flips(gks_ctx* c, gks_flip_count* out)
     out->normal_selections = (long long)h[1];
     out->tangential_flips = (long long)h[2];
     out->tangential_selections = (long long)h[3];
+    out->unresolved_flips = (long long)h[4];
     return GKS_OK;
 }

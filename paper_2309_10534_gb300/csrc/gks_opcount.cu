@@ -39,6 +39,7 @@ template <typename B> struct Cnt {
     friend Cnt operator*(Cnt a, Cnt b) { g_cnt.mul += 1; return Cnt(a.v * b.v); }
     friend Cnt operator/(Cnt a, Cnt b) { g_cnt.div += 1; return Cnt(a.v / b.v); }
     friend Cnt operator-(Cnt a) { return Cnt(-a.v); }
+    friend Cnt fma(Cnt a, Cnt b, Cnt c) { g_cnt.mul += 1; g_cnt.add += 1; return Cnt(a.v * b.v + c.v); }
     Cnt& operator+=(Cnt b) { *this = *this + b; return *this; }
     Cnt& operator-=(Cnt b) { *this = *this - b; return *this; }
     Cnt& operator*=(Cnt b) { *this = *this * b; return *this; }

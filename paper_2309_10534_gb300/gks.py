@@ -53,7 +53,8 @@ class Diag(C.Structure):
 
 class FlipCount(C.Structure):
     _fields_ = [("normal_flips", C.c_longlong), ("normal_selections", C.c_longlong),
-                ("tangential_flips", C.c_longlong), ("tangential_selections", C.c_longlong)]
+                ("tangential_flips", C.c_longlong), ("tangential_selections", C.c_longlong),
+                ("unresolved_flips", C.c_longlong)]
 
 
 class FlopModel(C.Structure):
@@ -322,6 +323,7 @@ def solver_for(setup, precision="fp64", **kw) -> Solver:
     """Solver configured from a ``workloads.Setup``."""
     args = dict(lx=setup.lx, ly=setup.ly, bc=setup.bc, precision=precision, gamma=setup.gamma,
                 mu=setup.mu, Pr=setup.Pr, tau=setup.tau, cfl=setup.cfl)
+    args.update(getattr(setup, "scheme", {}))
     args.update(kw)
     s = Solver(setup.dim, setup.nx, setup.ny, **args)
     if setup.bcstate:

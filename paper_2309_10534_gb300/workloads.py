@@ -45,6 +45,9 @@ class Setup:
     # state-setting boundary data (bc_in, bc_pre: conserved (rho, rho u,
     # rho v, E); shock_x0, shock_theta, shock_speed), passed to both sides
     bcstate: dict = field(default_factory=dict)
+    # scheme parameters the workload prescribes (the paper's settings for
+    # that test), passed to both sides
+    scheme: dict = field(default_factory=dict)
 
     @property
     def dx(self):
@@ -56,7 +59,7 @@ class Setup:
 
     def problem_kwargs(self):
         return dict(lx=self.lx, ly=self.ly, bc=self.bc, gamma=self.gamma, mu=self.mu, Pr=self.Pr,
-                    tau=self.tau, cfl=self.cfl, **self.bcstate)
+                    tau=self.tau, cfl=self.cfl, **self.bcstate, **self.scheme)
 
 
 def conserved_1d(rho, u, p, gamma):
@@ -279,8 +282,11 @@ def double_mach(nx=960, ny=240, t_end=0.2, cfl=0.5, gamma=1.4):
     W = frac[None] * Wpost[:, None, None] + (1.0 - frac[None]) * Wpre[:, None, None]
     bcstate = dict(bc_in=tuple(float(x) for x in Wpost), bc_pre=tuple(float(x) for x in Wpre),
                    shock_x0=x0, shock_theta=theta, shock_speed=us)
+    # Sec. 5.7: TENO-D GKS runs this problem only with C_T > 1e-5 in the
+    # tangential reconstruction (no limit in the normal one)
     return Setup(2, nx, ny, 4.0, 1.0, W, bc=("inflow", "zerograd", "wall_after_x0", "moving_shock"),
-                 gamma=gamma, cfl=cfl, t_end=t_end, name="double_mach", bcstate=bcstate)
+                 gamma=gamma, cfl=cfl, t_end=t_end, name="double_mach", bcstate=bcstate,
+                 scheme=dict(ct1_t=1e-4))
 
 
 def viscous_shock_tube(nx=2048, ny=1024, Re=200.0, Pr=0.73, gamma=1.4, t_end=1.0, cfl=0.2):

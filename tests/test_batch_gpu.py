@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from oracle_envelope import fp32_envelope
 from paper_2309_10534_gb300 import workloads as WL
 
 pytestmark = pytest.mark.gpu
@@ -57,12 +58,25 @@ def test_batch_fp64_matches_oracle_per_problem(gks, small, threads):
     assert B.launches() == 1  # one persistent launch (graph replay) per advance
 
 
+@pytest.fixture(scope="module")
+def small_spread32(small):
+    """Per problem of `small`, the oracle's spread under 1e-7 perturbations
+    of every step's state (float32 rounding)."""
+    E, _ = small
+    out = []
+    for k in range(E.ncells.size):
+        n, W = _problem(E, k)
+        P = O.make_problem(1, n, tau="euler")
+        out.append(fp32_envelope(P, W[:, None, :], 0.03, seeds=(0, 1))[1])
+    return out
+
+
 @pytest.mark.parametrize("threads", [128, 256])
-def test_batch_fp32_against_oracle_and_exact(gks, small, threads):
-    """float32 flux / float64 state through shocks: per problem <= 1e-3
-    relative L1 against the float64 oracle (float32 rounding moves TENO-D
-    switches, as on Sod), and the ensemble's distance to the exact Riemann
-    solutions within 5 % of the oracle's."""
+def test_batch_fp32_against_oracle_and_exact(gks, small, small_spread32, threads):
+    """float32 flux / float64 state through shocks: per problem within 10x
+    the oracle's spread under float32-level perturbations (float32 rounding
+    moves TENO-D switches, as on Sod), and the ensemble's distance to the
+    exact Riemann solutions within 5 % of the oracle's."""
     import exact_riemann as ER
     E, ref = small
     B = gks.Batch(E.ncells, np.ones(E.ncells.size), precision="fp32")
@@ -77,12 +91,12 @@ def test_batch_fp32_against_oracle_and_exact(gks, small, threads):
     for k in range(E.ncells.size):
         n, _ = _problem(E, k)
         got = out[:, E.offsets[k]:E.offsets[k] + n]
-        worst = max(worst, _rel(got, ref[k]))
+        worst = max(worst, _rel(got, ref[k]) / small_spread32[k])
         ex = ER.cell_averages(tuple(E.left[k]), tuple(E.right[k]), n, 0.03, gamma=E.gamma)
         e_gpu += np.abs(got[0] - ex[0]).mean()
         e_ora += np.abs(ref[k][0] - ex[0]).mean()
-    print(f"fp32 batch worst rel L1 vs oracle {worst:.3e}; exact distance {e_gpu:.6e} vs {e_ora:.6e}")
-    assert worst < 1e-3, worst
+    print(f"fp32 batch worst rel L1 / oracle spread {worst:.3f}; exact distance {e_gpu:.6e} vs {e_ora:.6e}")
+    assert worst < 10, worst
     assert e_gpu == pytest.approx(e_ora, rel=5e-2)
 
 
@@ -185,7 +199,8 @@ def test_full_size_ensemble_first_steps_fp64(gks, full):
 def test_full_size_ensemble_to_t_end_fp32(gks, full):
     """The bench's launch: the full ensemble to t = 0.15 in float32 flux /
     float64 state.  The smallest surviving problems (whose oracle runs take
-    seconds) agree with the oracle within the stated shock-run bound, and
+    seconds) agree with the oracle within 10x its spread under float32-level
+    perturbations of every step's state, and
     their distance to the exact Riemann solutions is within 10 % of the
     oracle's (float32 rounding moves TENO-D switches; on 200 cells that shows
     at the 5 % level); a flagged problem stopped before t_end and every other
@@ -206,10 +221,10 @@ def test_full_size_ensemble_to_t_end_fp32(gks, full):
     for k in picked:
         n, W = _problem(E, k)
         P = O.make_problem(1, n, tau="euler")
-        Wo, so, _, _ = O.run(P, W[:, None, :], E.t_end)
+        Wo, spread32 = fp32_envelope(P, W[:, None, :], E.t_end, seeds=(0, 1))
         Wo = Wo[:, 0, :]
         got = out[:, E.offsets[k]:E.offsets[k] + n]
-        assert _rel(got, Wo) < 1e-3, k
+        assert _rel(got, Wo) < 10 * spread32, (k, _rel(got, Wo), spread32)
         ex = ER.cell_averages(tuple(E.left[k]), tuple(E.right[k]), n, E.t_end, gamma=E.gamma)
         e_gpu += np.abs(got[0] - ex[0]).mean()
         e_ora += np.abs(Wo[0] - ex[0]).mean()
