@@ -353,7 +353,7 @@ def oracle_errors(gks, sample):
     import oracle as O
     from paper_2309_10534_gb300 import workloads as WL
     sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from oracle_envelope import fp32_envelope
+    from oracle_envelope import fp32_envelope, oracle_envelope
     out = {}
     # config 2: the CPU baseline's own sample
     s, W_or, steps = sample
@@ -396,17 +396,25 @@ def oracle_errors(gks, sample):
     def one(k):
         n = int(E.ncells[k])
         P = O.make_problem(1, n, tau="euler")
+        W0 = E.W[:, E.offsets[k]:E.offsets[k] + n][:, None, :]
         try:
-            return O.run(P, E.W[:, E.offsets[k]:E.offsets[k] + n][:, None, :], E.t_end)[0][:, 0, :]
+            ref = O.run(P, W0, E.t_end)[0][:, 0, :]
+            s64 = oracle_envelope(P, W0, E.t_end, rel=1e-15, seeds=(0,))[1]
+            s32 = fp32_envelope(P, W0, E.t_end, seeds=(0,))[1]
+            return ref, s64, s32
         except RuntimeError:
             return None
     with ThreadPoolExecutor(max_workers=16) as ex:
-        refs = list(ex.map(one, pick))
+        res = list(ex.map(one, pick))
+    refs = [r[0] if r else None for r in res]
+    spreads = {"fp64": [r[1] if r else None for r in res], "fp32": [r[2] if r else None for r in res]}
     sizes = E.ncells[pick]
     Wsub = np.concatenate([E.W[:, E.offsets[k]:E.offsets[k] + E.ncells[k]] for k in pick], axis=1)
     off = np.concatenate([[0], np.cumsum(sizes)])
     e = {"sample": "the 16 smallest members of the seeded ensemble (%d..%d cells) to t = 0.15; errors over the "
-                   "members the oracle completes" % (sizes.min(), sizes.max())}
+                   "members the oracle completes; each member's error is also divided by the oracle's own spread "
+                   "at that path's rounding level (1e-15 of the initial state for float64; 1e-7 of the initial "
+                   "state or of every step's state for float32)" % (sizes.min(), sizes.max())}
     for precision in ("fp64", "fp32"):
         B = gks.Batch(sizes, np.ones(len(pick)), precision=precision)
         B.set_state(Wsub)
@@ -414,16 +422,17 @@ def oracle_errors(gks, sample):
         got = B.get_state()
         _, _, err, _ = B.progress()
         B.close()
-        l1, linf, used = [], [], 0
+        l1, linf, ratio, used = [], [], [], 0
         for j, ref in enumerate(refs):
             if ref is None or err[j]:
                 continue
             r = _errs(got[:, off[j]:off[j + 1]], ref)
             l1.append(r["l1_rel"])
             linf.append(r["linf_rel"])
+            ratio.append(r["l1_rel"] / max(spreads[precision][j], 1e-300))
             used += 1
         e[precision] = {"l1_rel_max": max(l1), "l1_rel_mean": float(np.mean(l1)), "linf_rel_max": max(linf),
-                        "members": used}
+                        "members": used, "max_ratio_to_oracle_spread": max(ratio)}
     out["4_ensemble"] = e
     # config 5: the adjoint's forward map (isentropic vortex, tau = 0) on 32 x 32
     s = WL.isentropic_vortex(n=32, seed=2309, amplitude=1e-3)
@@ -804,12 +813,13 @@ def paper_run(gks, s, precision, stream, max_steps=0):
 
 
 def paper_legs(gks, WL, stream):
-    """The paper's other workloads at the paper's sizes: the double Mach
+    """The paper's other workloads at the paper's sizes: Sod's tube (Sec. 5.2,
+    400 cells to t = 0.2; launch-latency bound), the double Mach
     reflection (Sec. 5.7, 960 x 240 to t = 0.2), the Titarev-Toro
     shock-entropy wave (Sec. 5.3, 1000 cells to t = 5) and the Riemann
     configuration 6 (Sec. 5.6 (b), 400^2 to t = 0.6), both precisions."""
     out = {}
-    for name, s in (("dmr", WL.double_mach(960, 240, t_end=0.2)),
+    for name, s in (("sod400", WL.sod(400)), ("dmr", WL.double_mach(960, 240, t_end=0.2)),
                     ("titarev_toro", WL.titarev_toro(1000)),
                     ("riemann_cfg6", WL.riemann2d_config6(400, t_end=0.6))):
         d = {"grid": "%dx%d" % (s.nx, s.ny) if s.dim == 2 else "%d" % s.nx, "t_end": s.t_end}

@@ -29,6 +29,7 @@ template <> struct M<float> {
     static constexpr float tiny = 1.17549435e-38f;  // FLT_MIN: smallest eps kept normal
     static constexpr int nseries = 16;               // terms of the time-coefficient series
     static constexpr float s_series = 2.0f;          // series below, closed form above
+    static constexpr float s_noexp = 48.0f;          // above: exp(-s/2) < 4e-11, below float32 resolution
 };
 template <> struct M<double> {
     static GKS_HD double erfc_(double x) { return erfc(x); }
@@ -38,6 +39,7 @@ template <> struct M<double> {
     static constexpr double tiny = 0.0;
     static constexpr int nseries = 22;
     static constexpr double s_series = 1.0;
+    static constexpr double s_noexp = 90.0;           // above: exp(-s/2) < 3e-20, below float64 resolution
 };
 
 // integer power by squaring (q of Eq. 4.5 is a small positive integer)
@@ -878,8 +880,25 @@ GKS_HD void time_coeffs(T s, T* cF, T* cD)
         cF[5] -= is;
         return;
     }
-    const T y = M<T>::exp_(T(-0.5) * s), y2 = y * y;
     const T is = T(1) / s, is2 = is * is;
+    if (s > M<T>::s_noexp) {
+        // y = exp(-s/2) is below the working precision next to every other
+        // term: the closed forms below with y = 0
+        cF[0] = (s - T(3)) * is;
+        cD[0] = is;
+        cF[1] = (T(6) - s) * is2;
+        cD[1] = T(-2) * is2;
+        cF[2] = (T(3) - s) * is2;
+        cD[2] = (T(0.25) * s * s - T(1)) * is2;
+        cF[3] = T(3) * is;
+        cD[3] = -is;
+        cF[4] = T(-6) * is2;
+        cD[4] = T(2) * is2;
+        cF[5] = T(-3) * is2;
+        cD[5] = is2;
+        return;
+    }
+    const T y = M<T>::exp_(T(-0.5) * s), y2 = y * y;
     const T omy = T(1) - y;
     cF[0] = (s - T(3) + T(4) * y - y2) * is;
     cD[0] = omy * omy * is;

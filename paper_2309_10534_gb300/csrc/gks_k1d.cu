@@ -10,7 +10,7 @@ cudaError_t launch_one(const GridDev& g, const Stage1DArgs& a, const HostFlux& h
 {
     constexpr int TN = STAGE1D_TN;
     dim3 grid((g.nx + TN - 1) / TN);
-    k1d_stage<T, NONEQ, PRFIX, TN, REC><<<grid, TN + 1, 0, st>>>(g, a, make_flux_params<T>(hf), teno_t<T>(tn), ds);
+    k1d_stage<T, NONEQ, PRFIX, TN, REC><<<grid, TN + 2, 0, st>>>(g, a, make_flux_params<T>(hf), teno_t<T>(tn), ds);
     return cudaGetLastError();
 }
 

@@ -180,13 +180,25 @@ struct Stage1DArgs {
 };
 
 template <typename T, bool NONEQ, bool PRFIX, int TN, int REC = 0>
-__global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, FluxParams<T> fp, TenoT<T> tn,
+__global__ void __launch_bounds__(TN + 2) k1d_stage(GridDev g, Stage1DArgs a, FluxParams<T> fp, TenoT<T> tn,
                                                     DevState* ds)
 {
     if (ds->done) return;
-    constexpr int NT = TN + 1;
+    // TN cells per block, TN + 2 threads: the TN + 2 reconstructed cells,
+    // TN + 1 faces and TN updated cells each take one pass of the block
+    constexpr int NT = TN + 2;
     const double dt = ds->dt;
-    fp.dt = (T)dt;
+    // dt and dt/dx in the arithmetic type, converted once per block (a
+    // float64 -> float32 conversion runs on the slow float64 pipe)
+    __shared__ T s_scal[6];  // dt, dt/dx, 1/dx, gamma, mu, dx
+    if (threadIdx.x == 0) {
+        s_scal[0] = (T)dt;
+        s_scal[1] = (T)(dt * a.idx);
+        s_scal[2] = (T)a.idx;
+        s_scal[3] = (T)g.gamma;
+        s_scal[4] = (T)g.mu;
+        s_scal[5] = (T)g.dx;
+    }
     __shared__ T sq[3][TN + 6];
     __shared__ T sL[3][2][TN + 1], sR[3][2][TN + 1];  // [var][value, slope][face]
     __shared__ T sG[2][3][TN + 1];                     // face fluxes for the update
@@ -211,7 +223,8 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
         sq[v][c] = val;
     }
     __syncthreads();
-    const T idx_ = (T)a.idx;
+    fp.dt = s_scal[0];
+    const T idx_ = s_scal[2];
     if constexpr (REC == REC_TENO_CHAR) {
         // phase 1 in characteristic variables: per face f (between interior
         // i0 + f - 1 and i0 + f), the six cells around it projected with the
@@ -290,7 +303,7 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
         } else {
             point_flux<T, 1, NONEQ, PRFIX>(L, R, fp, F, dF);
         }
-        const T tdt = (T)dt;
+        const T tdt = s_scal[0];
 #pragma unroll
         for (int v = 0; v < 3; ++v) stage_comb<T>(a.stage, F[slot[v]], dF[slot[v]], tdt, sG[0][v][f], sG[1][v][f]);
     }
@@ -298,7 +311,7 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
     // phase 3: update
     T sig = T(0);
     const double cx = dt * a.idx;
-    const T cxt = (T)cx;
+    const T cxt = s_scal[1];
     for (int c = tid; c < TN; c += NT) {
         const int i = i0 + c;
         if (i >= g.nx) continue;
@@ -319,7 +332,7 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
                     a.out0[gi] = r;
                     w[v] = (T)r;
                 }
-                if (a.with_sigma) sig = fmax(sig, cell_sigma<T, T>(w, 1, (T)g.gamma, (T)g.mu, (T)g.dx, err));
+                if (a.with_sigma) sig = fmax(sig, cell_sigma<T, T>(w, 1, s_scal[3], s_scal[4], s_scal[5], err));
             }
         } else if (a.stage == 1) {
 #pragma unroll
@@ -336,7 +349,7 @@ __global__ void __launch_bounds__(TN + 1) k1d_stage(GridDev g, Stage1DArgs a, Fl
                 a.out0[v * pl + o] = r;
                 w[v] = r;
             }
-            if (a.with_sigma) sig = fmax(sig, cell_sigma<T>(w, 1, (T)g.gamma, (T)g.mu, (T)g.dx, err));
+            if (a.with_sigma) sig = fmax(sig, cell_sigma<T>(w, 1, s_scal[3], s_scal[4], s_scal[5], err));
         }
     }
     if (NT % 32 == 0) block_commit<NT, T>(sig, a.with_sigma != 0, err, nfb, ds);
@@ -405,9 +418,22 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
     const bool fy = a.dirn != 0;
     auto sfi = [&](int k, int r, int f) { return fy ? (k * NF + f) * (TT + 1) + r : (k * TT + r) * NF + f; };
 
-    const double dt = ds->dt;
-    fp.dt = (T)dt;
     const int tid = threadIdx.x;
+    // the stage's scalars in the arithmetic type, converted once per block
+    // (a float64 -> float32 conversion runs on the slow float64 pipe):
+    // dt, dt/h_n, 1/h_n, 1/h_t, gamma, mu, min(h_n, h_t); visible after the
+    // load phase's barrier
+    __shared__ T s_scal[7];
+    if (tid == 0) {
+        const double dt = ds->dt;
+        s_scal[0] = (T)dt;
+        s_scal[1] = (T)(dt * a.ihn);
+        s_scal[2] = (T)a.ihn;
+        s_scal[3] = (T)a.iht;
+        s_scal[4] = (T)g.gamma;
+        s_scal[5] = (T)g.mu;
+        s_scal[6] = (T)a.hmin;
+    }
     const int n0 = blockIdx.x * TN, t0 = blockIdx.y * TT;
     // local frame: normal momentum first; y faces swap the two momentum components
     const bool swap = a.dirn != 0;
@@ -438,13 +464,14 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
         }
     }
     __syncthreads();
+    fp.dt = s_scal[0];
 
     // phase 1: normal TENO-D per (cell, row, var): cell c <-> normal n0-1+c
     if constexpr (REC == REC_TENO_CHAR) {
         // characteristic variables: per (face, row), the six cells around
         // face f (between normal n0-1+f and n0+f) projected with the face's
         // basis, both sides reconstructed
-        const T ih = (T)a.ihn;
+        const T ih = s_scal[2];
         constexpr int NR = TT + 4;
         for (int k = tid; k < NF * NR; k += NT) {
             const int r = k / NF, f = k % NF;
@@ -464,7 +491,7 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
         }
     } else if constexpr (sizeof(T) == 4 && REC <= 1) {
         // float32 TENO-D / WENO5-AO: variables (0, 1) and (2, 3) as packed pairs
-        const float ih = (float)a.ihn;
+        const float ih = s_scal[2];
         constexpr int NC = TN + 2, NR = TT + 4;
         for (int k = tid; k < 2 * NC * NR; k += NT) {
             const int vv = 2 * (k / (NC * NR)), e = k % (NC * NR);
@@ -485,7 +512,7 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
             }
         }
     } else {
-        const T ih = (T)a.ihn;
+        const T ih = s_scal[2];
         constexpr int NC = TN + 2, NR = TT + 4;
         for (int k = tid; k < 4 * NC * NR; k += NT) {
             const int v = k / (NC * NR), e = k % (NC * NR);
@@ -509,7 +536,7 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
         // line-averaged equilibrium state by the kinetic merge of the face
         // values (a non-physical side takes its adjacent cell average), and
         // its normal slope by Eq. (3.12) on the row's cell averages
-        const T ih = (T)a.ihn;
+        const T ih = s_scal[2];
         for (int k = tid; k < NF * (TT + 4); k += NT) {
             const int r = k / NF, f = k % NF;
             // faces n0+f <= nn on rows t0-2+r <= nt+1 (ghosted extent) exist;
@@ -544,8 +571,8 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
     // segment split the work: lane gpi reconstructs side gpi (0: left, 1:
     // right) at both Gauss points, keeps its own point and hands the other
     // point's values to its partner; after the flux they average (weights 1/2).
-    const T tdt = (T)dt;
-    const T iht = (T)a.iht;
+    const T tdt = s_scal[0];
+    const T iht = s_scal[3];
     const T gA = T(-0.28867513459481288), gB = T(0.28867513459481288);  // -+1/(2 sqrt 3)
 #pragma unroll 1
     for (int task = tid; task < 2 * NP; task += NT) {
@@ -657,7 +684,7 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
 
     // phase 3: flux divergence; the y sweep updates the float64 state
     T sig = T(0);
-    const T cn = (T)(dt * a.ihn);
+    const T cn = s_scal[1];
     if (tid < TN * TT) {
         // x faces: the normal (x) index fastest; y faces: the tangential (x) index
         const int r = fy ? tid % TT : tid / TN, c = fy ? tid / TT : tid % TN;
@@ -699,8 +726,8 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
                 }
             }
             if (a.with_sigma) {
-                if constexpr (sizeof(T) == 4) sig = cell_sigma<T, T>(wf, 2, (T)g.gamma, (T)g.mu, (T)a.hmin, err);
-                else sig = cell_sigma<T>(wn, 2, (T)g.gamma, (T)g.mu, (T)a.hmin, err);
+                if constexpr (sizeof(T) == 4) sig = cell_sigma<T, T>(wf, 2, s_scal[4], s_scal[5], s_scal[6], err);
+                else sig = cell_sigma<T>(wn, 2, s_scal[4], s_scal[5], s_scal[6], err);
             }
         }
     }

@@ -15,8 +15,9 @@ namespace gks {
 constexpr int SWEEP_TN = 31;
 constexpr int SWEEP_TT32 = 16;
 constexpr int SWEEP_TT64 = 8;
-// cells per block of the 1-D stage (TN + 1 threads, one per face)
-constexpr int STAGE1D_TN = 127;
+// cells per block of the 1-D stage (TN + 2 = 128 threads: one per
+// reconstructed cell, face and updated cell)
+constexpr int STAGE1D_TN = 126;
 
 struct HostFlux {
     double gamma, K, ntot, c1, c2, mu, prfac;

@@ -62,6 +62,7 @@ template <typename B> struct M<opc::Cnt<B>> {
     static constexpr double tiny = M<B>::tiny;
     static constexpr int nseries = M<B>::nseries;
     static constexpr double s_series = M<B>::s_series;
+    static constexpr double s_noexp = M<B>::s_noexp;
 };
 
 namespace opc {

@@ -99,12 +99,7 @@ struct TenoSel2 {
     f2 q2, b[3], c[3], u1, u2, u3, u4, w[3];
 };
 
-GKS_HD float lane_min4(float a, float b, float c, float d)
-{
-    float m = a < b ? a : b;
-    m = m < c ? m : c;
-    return m < d ? m : d;
-}
+GKS_HD float lane_min4(float a, float b, float c, float d) { return fminf(fminf(a, b), fminf(c, d)); }
 
 GKS_HD void teno_select_x2(const f2 q[5], const TenoT<float>& P, TenoSel2& S)
 {

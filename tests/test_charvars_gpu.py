@@ -36,7 +36,7 @@ def per_var_rel(a, b):
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("tau", ["zero", "euler", "ns"])
 def test_1d_stage_and_step(gks, precision, tau):
-    """300 cells (two 127-cell tiles and a ragged tail), rough data with a
+    """300 cells (two 126-cell tiles and a ragged tail), rough data with a
     density jump, a reflecting end, every collision-time model."""
     rng = np.random.default_rng(12)
     n = 300

@@ -37,7 +37,7 @@ TOL = {"fp64": 1e-12, "fp32": 1e-5}
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("tau", ["zero", "euler", "ns"])
 def test_stage_and_step_random(gks, recon, precision, tau):
-    """Ragged grid (several 127-cell tiles), rough data with a jump."""
+    """Ragged grid (several 126-cell tiles), rough data with a jump."""
     rng = np.random.default_rng(21)
     n = 300
     a = 1.0 if tau != "ns" else 0.2

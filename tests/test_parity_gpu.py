@@ -57,7 +57,7 @@ TOL = {"fp64": 1e-12, "fp32": 1e-5}
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("tau", ["zero", "euler", "ns"])
 def test_1d_stage_and_step_random(precision, tau):
-    """Ragged 1-D grid (several 127-cell tiles), rough data, all collision-time models."""
+    """Ragged 1-D grid (several 126-cell tiles), rough data, all collision-time models."""
     rng = np.random.default_rng(11)
     n = 300
     a = 1.0 if tau != "ns" else 0.2  # cell-to-cell noise the viscous step keeps physical
