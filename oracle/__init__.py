@@ -126,6 +126,8 @@ def _declare(L):
     L.or_time_coeffs.restype = None
     L.or_char_basis.argtypes = [C.c_int, C.c_double, _dp, _dp, _dp]
     L.or_char_basis.restype = C.c_int
+    L.or_face_flux.argtypes = [C.POINTER(Problem), _dp, C.c_int, C.c_int, C.c_int, C.c_double, _dp, _dp, _lp]
+    L.or_face_flux.restype = C.c_int
     L.or_flux_point.argtypes = [C.POINTER(Problem)] + [_dp] * 8 + [C.c_double, _dp, _dp]
     L.or_flux_point.restype = C.c_int
     L.or_stage1.argtypes = [C.POINTER(Problem), _dp, C.c_double, _dp, _lp]
@@ -244,6 +246,19 @@ def micro_slope(dim, K, U, V, lam, b):
     if lib().or_micro_slope(dim, K, U, V, lam, _d(b), _d(a)):
         raise RuntimeError("singular moment matrix")
     return a
+
+
+def face_flux(P: Problem, Wg, direction, ic, jc, dt):
+    """(F(dt), F(dt/2), fallbacks) of one face of a ghost-filled array
+    [nvar][ny+6][nx+6] (ghosted indices of the left / lower cell)."""
+    Wg = _f64(Wg)
+    nv = P.dim + 2
+    Fd, Fh = np.zeros(nv), np.zeros(nv)
+    nfb = C.c_long(0)
+    if lib().or_face_flux(C.byref(P), _d(Wg), int(direction), int(ic), int(jc), float(dt), _d(Fd), _d(Fh),
+                          C.byref(nfb)):
+        raise RuntimeError("non-physical state")
+    return Fd, Fh, nfb.value
 
 
 def char_basis(dim, gamma, Wm):

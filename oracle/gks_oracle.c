@@ -1239,6 +1239,13 @@ static int face_flux(const or_problem *P, const grid_t *g, const double *Wg, int
     return 0;
 }
 
+int or_face_flux(const or_problem *P, const double *Wg, int dir, int ic, int jc, double dt, double *Fdt,
+                 double *Fhalf, long *nfb)
+{
+    grid_t g = make_grid(P);
+    return face_flux(P, &g, Wg, dir, ic, jc, dt, Fdt, Fhalf, nfb);
+}
+
 /* all face fluxes of one stage.  Fx: [nv][ny][nx+1] (face i is between
  * interior cells i-1 and i); Fy: [nv][ny+1][nx]. */
 static int all_fluxes(const or_problem *P, const grid_t *g, const double *Wg, double dt,

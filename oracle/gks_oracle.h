@@ -160,6 +160,14 @@ double or_dt(const or_problem *P, const double *W);
 /* advance to t_end with CFL time steps, the last one clipped to t_end */
 int    or_run(const or_problem *P, double *W, double t_end, long max_steps,
               long *steps_done, double *t_out, long *nfallback);
+/* the time-integrated flux of one face (Sec. 2.2, 3.2) on a ghost-filled
+ * array Wg [nvar][ny+6][nx+6]: dir 0 the x face between ghosted cells
+ * (ic, jc) and (ic+1, jc), dir 1 the y face between (ic, jc) and (ic, jc+1);
+ * Fdt, Fhalf = the Gauss-averaged F(dt), F(dt/2) in global variable order;
+ * *nfb (may be NULL) counts the fallbacks taken.  Returns -1 on a state no
+ * fallback fixes. */
+int    or_face_flux(const or_problem *P, const double *Wg, int dir, int ic, int jc, double dt, double *Fdt,
+                    double *Fhalf, long *nfb);
 /* ghost filling exposed for tests: Wg is [nvar][ny+6][nx+6] (1-D: ny+6 -> 1) */
 void   or_fill_ghosts(const or_problem *P, double *Wg);
 

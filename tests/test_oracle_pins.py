@@ -1027,3 +1027,71 @@ def test_window_with_origin_reproduces_the_full_problem():
         ia = 0 if xa == 0 else 6
         ib = (xb - xa) if xb == 48 else (xb - xa - 6)
         assert np.array_equal(out[:, :, ia:ib], full[:, ya:yb, xa + ia:xa + ib]), (xa, xb)
+
+
+def _quartic_at(q, x):
+    """Value at xi = x of the quartic whose averages over the five unit cells
+    centred at -2..2 are q (the fourth-degree interpolant, written out in the
+    Legendre-type basis of the centre cell)."""
+    q0, q1, q2, q3, q4 = q
+    u1 = (11 * q0 - 82 * q1 + 82 * q3 - 11 * q4) / 120
+    u3 = (-q0 + 2 * q1 - 2 * q3 + q4) / 12
+    u4 = (q0 - 4 * q1 + 6 * q2 - 4 * q3 + q4) / 24
+    return q2 + u1 * x - u3 * x / 15 - u4 / 180
+
+
+def test_conventional_2d_nonphysical_quartic_falls_back_to_the_kinetic_merge():
+    """Reading R32: on the 2-D conventional path (WENO5-Z here) the
+    equilibrium state at a Gauss point is the quartic through the five rows'
+    line-averaged merges (Step 4); where that quartic is not physical the
+    point takes the kinetic merge of its two reconstructed values.  Data
+    uniform along x in every row make every face value, line merge and line
+    average equal to its row's state and the normal slopes zero, so with
+    tau = 0 the face flux has a closed form: the mean over the two Gauss
+    points of the Euler flux of the quartic state, or, at a point where the
+    quartic has negative pressure, of the point's own (equal) reconstructed
+    value -- the kinetic merge of two equal states is that state."""
+    gam = 1.4
+    rho = np.array([0.52, 0.09, 1.18, 1.1, 0.07])
+    U = np.array([1.84, 1.72, 2.49, 1.02, 1.16])
+    V = np.array([-2.02, -2.86, -2.61, 2.79, 0.87])
+    p = np.array([2.09, 0.12, 0.81, 0.04, 0.05])
+    rows = np.stack([rho, rho * U, rho * V, p / (gam - 1) + 0.5 * rho * (U * U + V * V)])  # [4][5]
+    g = 0.5 / math.sqrt(3.0)
+    W0g = {x: np.array([_quartic_at(rows[k], x) for k in range(4)]) for x in (-g, g)}
+    pq = {x: (gam - 1) * (w[3] - 0.5 * (w[1] ** 2 + w[2] ** 2) / w[0]) for x, w in W0g.items()}
+    assert pq[-g] < 0 < pq[g]  # the quartic is non-physical at the lower Gauss point only
+    nx, ny = 8, 9
+    W = np.zeros((4, ny, nx))
+    for j in range(ny):
+        W[:, j, :] = rows[:, min(max(j - 2, 0), 4)][:, None]
+    P = O.make_problem(2, nx, ny, bc=("zerograd",) * 4, tau="zero", recon="weno_z")
+    Wg = np.zeros((4, ny + 6, nx + 6))
+    Wg[:, 3:3 + ny, 3:3 + nx] = W
+    O.fill_ghosts(P, Wg)
+    dt = 1e-3
+    Fd, Fh, nfb = O.face_flux(P, Wg, 0, 3 + 3, 3 + 4, dt)  # x face on the middle row (rows 2..6 = the five states)
+    F = (4 * Fh - Fd) / dt
+    # the point values: WENO5-Z of the rows at the Gauss points (both sides equal)
+    Wl = {x: np.array([O.weno3(rows[k], [x])[0][0] for k in range(4)]) for x in (-g, g)}
+    pl = (gam - 1) * (Wl[-g][3] - 0.5 * (Wl[-g][1] ** 2 + Wl[-g][2] ** 2) / Wl[-g][0])
+    assert Wl[-g][0] > 0 and pl > 0  # the point's own values are physical (no R14 fallback)
+    expect = 0.5 * (_euler_flux(Wl[-g], gam, 2) + _euler_flux(W0g[g], gam, 2))
+    assert nfb == 1
+    assert np.allclose(F, expect, rtol=1e-12, atol=1e-12 * np.abs(expect).max()), (F, expect)
+    # without the fallback's trigger (the quartic physical at both points) no fallback is counted
+    rows2 = rows.copy()
+    rows2[:, 1] = rows[:, 0]
+    W2 = np.zeros((4, ny, nx))
+    for j in range(ny):
+        W2[:, j, :] = rows2[:, min(max(j - 2, 0), 4)][:, None]
+    Wg2 = np.zeros((4, ny + 6, nx + 6))
+    Wg2[:, 3:3 + ny, 3:3 + nx] = W2
+    O.fill_ghosts(P, Wg2)
+    q2 = {x: np.array([_quartic_at(rows2[k], x) for k in range(4)]) for x in (-g, g)}
+    if all((gam - 1) * (w[3] - 0.5 * (w[1] ** 2 + w[2] ** 2) / w[0]) > 0 for w in q2.values()):
+        Fd2, Fh2, nfb2 = O.face_flux(P, Wg2, 0, 6, 7, dt)
+        F2 = (4 * Fh2 - Fd2) / dt
+        expect2 = 0.5 * (_euler_flux(q2[-g], gam, 2) + _euler_flux(q2[g], gam, 2))
+        assert nfb2 == 0
+        assert np.allclose(F2, expect2, rtol=1e-12, atol=1e-12 * np.abs(expect2).max())
