@@ -223,8 +223,8 @@ gks_status enqueue_stage(gks_ctx* c, int stage, int with_sigma, cudaStream_t st)
         if (f32) {
             // float32 W* (Wsf) and accumulator increment (inc1)
             float* inc = static_cast<float*>(c->inc1);
-            if (stage == 1) { a.src = c->W; a.out0f = c->Wsf; a.out1f = inc; }
-            else { a.srcf = c->Wsf; a.base = c->W; a.out0 = c->W; a.accf = inc; }
+            if (stage == 1) { a.src = c->W; a.srcf = c->Wf; a.out0f = c->Wsf; a.out1f = inc; }
+            else { a.srcf = c->Wsf; a.base = c->W; a.out0 = c->W; a.out0f = c->Wf; a.accf = inc; }
         } else if (stage == 1) {
             a.src = c->W; a.out0 = c->Ws; a.out1 = c->Ac;
         } else {
@@ -553,10 +553,12 @@ gks_status gks_create(const gks_grid_desc* d, gks_ctx** out)
             if (e6 == cudaSuccess) e6 = cudaMalloc(&c->Wsf, fb);
         }
     } else if (d->precision == GKS_FP32_FLUX) {
-        // 1-D float32 path: W* and the accumulator increment in float32
+        // 1-D float32 path: W* and the accumulator increment in float32, and a
+        // float32 shadow of W (the stage-1 input)
         const size_t fb = (size_t)c->nv * g.plane * sizeof(float);
         e6 = cudaMalloc(&c->Wsf, fb);
         e7 = cudaMalloc(&c->inc1, fb);
+        if (e6 == cudaSuccess) e6 = cudaMalloc(&c->Wf, fb);
     }
     if (e1 || e2 || e3 || e4 || e5 || e6 || e7) {
         gks_destroy(c);

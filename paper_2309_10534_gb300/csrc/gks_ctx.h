@@ -21,7 +21,7 @@ struct gks_ctx {
     double *W = nullptr, *Ws = nullptr, *Ac = nullptr;
     void *inc0 = nullptr, *inc1 = nullptr;  // 2-D: x-sweep increments, working precision;
                                              // 1-D float32: inc1 = accumulator increment
-    float* Wf = nullptr;                     // float32 shadow of W (2-D float32 path)
+    float* Wf = nullptr;                     // float32 shadow of W (float32 path)
     float* Wsf = nullptr;                    // W* in float32 (float32 path)
     double* stage = nullptr;                 // device staging of host arrays (allocated on first use)
     size_t arr_bytes = 0;

@@ -37,6 +37,9 @@ namespace {
 
 struct BatchDev {
     double* W;                    // packed [3][total] state
+    float* Wf;                    // float32 path: float32 shadow of W, written by the
+                                  // kernel (converted when a block takes a problem,
+                                  // kept with every update); float64 path: unused
     void *Ws, *A;                 // W* and the accumulator: float64 arrays on the
                                   // float64 path; on the float32 path W* in float32
                                   // and the accumulator increment in float32
@@ -90,15 +93,25 @@ template <typename T, int NT> struct ChunkSmem {
     T G[2][3][NT];              // face fluxes for the update
 };
 
+// The stage's scalars: dt and dt/dx in float64 (the float64 updates) and in
+// the arithmetic type, 1/dx in the arithmetic type; formed once per step by
+// one thread (a float64 operation in a float32 kernel runs on the slow
+// float64 pipe)
+template <typename T> struct StepScalars {
+    double dt, cx;
+    T tdt, cxt, ih;
+};
+
 // One stage over cells [c0, c0+TN) of a problem: load (clamped indices =
 // zero-gradient ghosts), TENO-D per cell, flux per face, update.  The update
 // follows the single-grid 1-D kernel: float64 W* and accumulator on the
 // float64 path; on the float32 path W* and the accumulator increment in
-// float32 and one float64 update of W per value and step.
+// float32 and one float64 update of W per value and step, its float32
+// shadow Wf (the stage-1 input) written beside it.
 template <typename T, int NT, bool NONEQ, bool PRFIX>
-__device__ void stage_chunk(ChunkSmem<T, NT>& sm, double* W, T* Ws, T* A, long long vstride, int n, int c0,
-                            int stage, double dt, double idx, const FluxParams<T>& fp, const TenoT<T>& tn, T& sig,
-                            unsigned int& err, unsigned int& nfb, T gamma, T mu, T hcell)
+__device__ void stage_chunk(ChunkSmem<T, NT>& sm, double* W, float* Wf, T* Ws, T* A, long long vstride, int n,
+                            int c0, int stage, const StepScalars<T>& sc, const FluxParams<T>& fp, const TenoT<T>& tn,
+                            T& sig, unsigned int& err, unsigned int& nfb, T gamma, T mu, T hcell)
 {
     constexpr int TN = NT - 6;
     const int tid = threadIdx.x;
@@ -106,17 +119,19 @@ __device__ void stage_chunk(ChunkSmem<T, NT>& sm, double* W, T* Ws, T* A, long l
     __syncthreads();  // shared memory of the previous chunk is free
     // each variable's array through its own base pointer; cell offsets in 32 bits
     double* Wv[3] = {W, W + vstride, W + 2 * vstride};
+    float* Wfv[3] = {Wf, Wf + vstride, Wf + 2 * vstride};
     T* Wsv[3] = {Ws, Ws + vstride, Ws + 2 * vstride};
     T* Av[3] = {A, A + vstride, A + 2 * vstride};
     for (int k = tid; k < 3 * (TN + 6); k += NT) {
         const int v = k / (TN + 6), c = k % (TN + 6);
         int i = c0 - 3 + c;
         i = i < 0 ? 0 : (i >= n ? n - 1 : i);
-        if (stage == 1) sm.q[v][c] = (T)(v == 0 ? W : (v == 1 ? Wv[1] : Wv[2]))[i];
-        else sm.q[v][c] = (v == 0 ? Ws : (v == 1 ? Wsv[1] : Wsv[2]))[i];
+        if (stage == 2) sm.q[v][c] = (v == 0 ? Ws : (v == 1 ? Wsv[1] : Wsv[2]))[i];
+        else if constexpr (sizeof(T) == 4) sm.q[v][c] = (v == 0 ? Wf : (v == 1 ? Wfv[1] : Wfv[2]))[i];
+        else sm.q[v][c] = (v == 0 ? W : (v == 1 ? Wv[1] : Wv[2]))[i];
     }
     __syncthreads();
-    const T ih = (T)idx;
+    const T ih = sc.ih;
     for (int c = tid; c < TN + 2; c += NT) {  // cell c0-1+c
         T q[3][5], vp[3], dp[3], vm[3], dm[3];
 #pragma unroll
@@ -131,7 +146,7 @@ __device__ void stage_chunk(ChunkSmem<T, NT>& sm, double* W, T* Ws, T* A, long l
         }
     }
     __syncthreads();
-    const T tdt = (T)dt;
+    const T tdt = sc.tdt;
     for (int f = tid; f <= TN; f += NT) {  // face between cells c0+f-1 and c0+f
         if (c0 + f > n) continue;
         Side<T> L, R;
@@ -162,8 +177,8 @@ __device__ void stage_chunk(ChunkSmem<T, NT>& sm, double* W, T* Ws, T* A, long l
         for (int v = 0; v < 3; ++v) stage_comb<T>(stage, F[slot[v]], dF[slot[v]], tdt, sm.G[0][v][f], sm.G[1][v][f]);
     }
     __syncthreads();
-    const double cx = dt * idx;
-    const T cxt = (T)cx;
+    const double cx = sc.cx;
+    const T cxt = sc.cxt;
     for (int c = tid; c < TN; c += NT) {
         const int i = c0 + c;
         if (i >= n) continue;
@@ -181,6 +196,7 @@ __device__ void stage_chunk(ChunkSmem<T, NT>& sm, double* W, T* Ws, T* A, long l
                     const double r = wnew32(Wv[v][i], Av[v][i], cxt, sm.G[0][v][c + 1] - sm.G[0][v][c]);
                     Wv[v][i] = r;
                     w[v] = (T)r;
+                    Wfv[v][i] = w[v];
                 }
                 sig = fmax(sig, cell_sigma<T, T>(w, 1, gamma, mu, hcell, err));
             }
@@ -209,7 +225,8 @@ __global__ void __launch_bounds__(NT) k_batch(BatchDev b, FluxParams<T> fp, Teno
     __shared__ ChunkSmem<T, NT> sm;
     __shared__ T red[NT / 32];
     __shared__ unsigned int redu[NT / 32];
-    __shared__ int s_prob;
+    __shared__ int s_prob, s_go;
+    __shared__ StepScalars<T> s_sc;
     constexpr int TN = NT - 6;
     const int tid = threadIdx.x;
     const T gamma = (T)b.gamma, mu = (T)b.mu;
@@ -225,35 +242,58 @@ __global__ void __launch_bounds__(NT) k_batch(BatchDev b, FluxParams<T> fp, Teno
         const double dx = b.dx[p], idx = 1.0 / dx;
         const T hcell = (T)dx;
         double* W = b.W + off;
+        float* Wf = b.Wf ? b.Wf + off : nullptr;
         T* Ws = static_cast<T*>(b.Ws) + off;
         T* A = static_cast<T*>(b.A) + off;
-        double t = b.t[p];
+        double t = b.t[p];          // thread 0 keeps the time and step count
         long long steps = 0;
         unsigned int err = 0, nfb = 0;
-        // CFL rate of the starting state
+        // CFL rate of the starting state (float32 path: from the state rounded
+        // to float32, which becomes the shadow the stage-1 loads read)
         T sig = T(0);
         for (int i = tid; i < n; i += NT) {
             const T w0[3] = {(T)W[i], (T)W[b.total + i], (T)W[2 * b.total + i]};
+            if constexpr (sizeof(T) == 4) {
+                Wf[i] = w0[0];
+                Wf[b.total + i] = w0[1];
+                Wf[2 * b.total + i] = w0[2];
+            }
             sig = fmax(sig, cell_sigma<T, T>(w0, 1, gamma, mu, hcell, err));
         }
         sig = block_max<T, NT>(sig, red);
         err = block_or(err, redu);
-        while (t < b.t_end && (b.max_steps <= 0 || steps < b.max_steps) && !err) {
-            double dt = b.cfl / (double)sig;
-            if (t + dt > b.t_end) dt = b.t_end - t;
+        for (;;) {
+            if (tid == 0) {
+                const int go = t < b.t_end && (b.max_steps <= 0 || steps < b.max_steps) && !err;
+                if (go) {
+                    double dt = b.cfl / (double)sig;
+                    if (t + dt > b.t_end) dt = b.t_end - t;
+                    s_sc.dt = dt;
+                    s_sc.cx = dt * idx;
+                    s_sc.tdt = (T)dt;
+                    s_sc.cxt = (T)(dt * idx);
+                    s_sc.ih = (T)idx;
+                }
+                s_go = go;
+            }
+            __syncthreads();
+            if (!s_go) break;
+            const StepScalars<T>& sc = s_sc;  // read where used: no registers held across the chunks
             FluxParams<T> f = fp;
-            f.dt = (T)dt;
+            f.dt = sc.tdt;
             for (int c0 = 0; c0 < n; c0 += TN)
-                stage_chunk<T, NT, NONEQ, PRFIX>(sm, W, Ws, A, b.total, n, c0, 1, dt, idx, f, tn, sig, err, nfb, gamma,
+                stage_chunk<T, NT, NONEQ, PRFIX>(sm, W, Wf, Ws, A, b.total, n, c0, 1, sc, f, tn, sig, err, nfb, gamma,
                                                  mu, hcell);
             T s2 = T(0);
             for (int c0 = 0; c0 < n; c0 += TN)
-                stage_chunk<T, NT, NONEQ, PRFIX>(sm, W, Ws, A, b.total, n, c0, 2, dt, idx, f, tn, s2, err, nfb, gamma,
+                stage_chunk<T, NT, NONEQ, PRFIX>(sm, W, Wf, Ws, A, b.total, n, c0, 2, sc, f, tn, s2, err, nfb, gamma,
                                                  mu, hcell);
             sig = block_max<T, NT>(s2, red);
             err = block_or(err, redu);
-            t += dt;
-            ++steps;
+            if (tid == 0) {
+                t += sc.dt;
+                ++steps;
+            }
         }
         if (nfb) atomicAdd(b.fallbacks, (unsigned long long)nfb);
         if (tid == 0) {
@@ -317,6 +357,7 @@ struct gks_batch {
     std::vector<double> len;
     std::vector<long long> off;
     double* W = nullptr;
+    float* Wf = nullptr;  // float32 path: float32 shadow of W (maintained by the kernel)
     void *Ws = nullptr, *A = nullptr;
     long long* d_off = nullptr;
     int *d_n = nullptr, *d_order = nullptr, *d_queue = nullptr;
@@ -362,6 +403,7 @@ BatchDev dev_view(gks_batch* b, double t_end, long long max_steps)
 {
     BatchDev d;
     d.W = b->W;
+    d.Wf = b->Wf;
     d.Ws = b->Ws;
     d.A = b->A;
     d.total = b->total;
@@ -533,6 +575,7 @@ gks_status gks_batch_create(int count, const int* ncells, const double* lengths,
     std::vector<double> dx(count);
     for (int k = 0; k < count; ++k) dx[k] = b->len[k] / b->n[k];
     bool ok = cudaMalloc(&b->W, arr) == cudaSuccess && cudaMalloc(&b->Ws, warr) == cudaSuccess &&
+              (precision != GKS_FP32_FLUX || cudaMalloc(&b->Wf, warr) == cudaSuccess) &&
               cudaMalloc(&b->A, warr) == cudaSuccess && cudaMalloc(&b->d_off, sizeof(long long) * count) == cudaSuccess &&
               cudaMalloc(&b->d_n, sizeof(int) * count) == cudaSuccess &&
               cudaMalloc(&b->d_order, sizeof(int) * count) == cudaSuccess &&
@@ -570,6 +613,7 @@ void gks_batch_destroy(gks_batch* b)
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
     cudaFree(b->W);
+    cudaFree(b->Wf);
     cudaFree(b->Ws);
     cudaFree(b->A);
     cudaFree(b->d_off);

@@ -166,11 +166,13 @@ __device__ __forceinline__ double wnew32(double w, float inc, float cx, float dG
 // final update W^{n+1} = W^n - (increment + dt/dx d(dt/3 dF*)).
 struct Stage1DArgs {
     const double* src;   // float64 reconstruction input (W; float64 path stage 2: W*), ghosts filled
-    const float* srcf;   // float32 path, stage 2: W* (float32, ghosts filled)
+    const float* srcf;   // float32 path: stage 1 the float32 shadow of W (or nullptr: src,
+                         // converted), stage 2 W* (float32); ghosts filled
     double* out0;        // float64 path stage 1: W*; stage 2: the new state
     double* out1;        // float64 path stage 1: accumulator A
     const double* acc;   // float64 path stage 2: accumulator A
-    float* out0f;        // float32 path stage 1: W*
+    float* out0f;        // float32 path stage 1: W*; stage 2: the new state's float32
+                         // shadow (or nullptr)
     float* out1f;        // float32 path stage 1: accumulator increment
     const float* accf;   // float32 path stage 2: accumulator increment
     const double* base;  // float32 path stage 2: W^n
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(TN + 2) k1d_stage(GridDev g, Stage1DArgs a, Fl
         T val = T(0);
         if (gi < gx) {
             if constexpr (sizeof(T) == 4) {
-                if (a.stage == 2) val = a.srcf[v * pl + gi];
+                if (a.srcf) val = a.srcf[v * pl + gi];
                 else val = (T)a.src[v * pl + gi];
             } else {
                 val = a.src[v * pl + gi];
@@ -331,6 +333,7 @@ __global__ void __launch_bounds__(TN + 2) k1d_stage(GridDev g, Stage1DArgs a, Fl
                     const double r = wnew32(a.base[gi], a.accf[gi], cxt, sG[0][v][c + 1] - sG[0][v][c]);
                     a.out0[gi] = r;
                     w[v] = (T)r;
+                    if (a.out0f) a.out0f[gi] = w[v];
                 }
                 if (a.with_sigma) sig = fmax(sig, cell_sigma<T, T>(w, 1, s_scal[3], s_scal[4], s_scal[5], err));
             }
