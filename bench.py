@@ -677,10 +677,13 @@ def adjoint_leg(gks, WL, stream, precision, steps=700):
     A = gks.Adjoint(S, k)
     dev = stream.device
     W0 = torch.from_numpy(s.W).to(dev)
-    # warm-up: every buffer of the timed passes, one short forward/backward
+    # warm-up: every buffer of the timed passes, and one full checkpoint
+    # segment forward and backward, so that the backward pass's segment graph
+    # is captured and instantiated before the timed region (a one-time host
+    # cost of ~800 captured launches)
     A.reserve(steps)
     S.set_state(W0)
-    A.forward(2, dt)
+    A.forward(k, dt)
     A.backward(torch.zeros_like(W0))
     S.set_state(W0)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]

@@ -287,24 +287,42 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4) ? 4 : 1) k_adj_gauss(Gri
             if (fbR) { R.W[v] = load_src<T>(a, b + fc * a.sn); R.Wn[v] = R.Wt[v] = T(0); }
         }
     }
-    // face cotangents (each Gauss point carries weight 1/2)
+    // face cotangents (each Gauss point carries weight 1/2).  The
+    // differences are taken in float64, the rest in the working precision;
+    // the two lanes of a face split the variables (lane gp: 2 gp, 2 gp + 1)
+    // and exchange them, so each float64 difference (the float64 pipe is the
+    // slow one) is formed once per face
     T gF[4], gdF[4];
+    {
+        const T cF1 = (T)a.cF1, cF2 = (T)a.cF2, cD1 = (T)a.cD1, cD2 = (T)a.cD2;
+        T mF[2], mD[2];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const long long b = (long long)gvar_(v, swap) * g.plane + org + rc * a.st;
-        double d1 = 0.0, d2 = 0.0;
-        if (fc < a.nn) {
-            d1 += a.lam1[b + fc * a.sn];
-            if (a.lam2) d2 += a.lam2[b + fc * a.sn];
+        for (int h = 0; h < 2; ++h) {
+            const int v = 2 * gp + h;
+            const long long b = (long long)gvar_(v, swap) * g.plane + org + rc * a.st;
+            double d1 = 0.0, d2 = 0.0;
+            if (fc < a.nn) {
+                d1 += a.lam1[b + fc * a.sn];
+                if (a.lam2) d2 += a.lam2[b + fc * a.sn];
+            }
+            if (fc >= 1) {
+                d1 -= a.lam1[b + (fc - 1) * a.sn];
+                if (a.lam2) d2 -= a.lam2[b + (fc - 1) * a.sn];
+            }
+            const T e1 = (T)d1, e2 = (T)d2;
+            mF[h] = T(0.5) * (cF1 * e1 + cF2 * e2);
+            mD[h] = T(0.5) * (cD1 * e1 + cD2 * e2);
         }
-        if (fc >= 1) {
-            d1 -= a.lam1[b + (fc - 1) * a.sn];
-            if (a.lam2) d2 -= a.lam2[b + (fc - 1) * a.sn];
-        }
-        // the differences in float64, the rest in the working precision
-        const T e1 = (T)d1, e2 = (T)d2;
-        gF[v] = T(0.5) * ((T)a.cF1 * e1 + (T)a.cF2 * e2);
-        gdF[v] = T(0.5) * ((T)a.cD1 * e1 + (T)a.cD2 * e2);
+        const T oF0 = __shfl_xor_sync(0xffffffffu, mF[0], 1), oF1 = __shfl_xor_sync(0xffffffffu, mF[1], 1);
+        const T oD0 = __shfl_xor_sync(0xffffffffu, mD[0], 1), oD1 = __shfl_xor_sync(0xffffffffu, mD[1], 1);
+        gF[0] = gp ? oF0 : mF[0];
+        gF[1] = gp ? oF1 : mF[1];
+        gF[2] = gp ? mF[0] : oF0;
+        gF[3] = gp ? mF[1] : oF1;
+        gdF[0] = gp ? oD0 : mD[0];
+        gdF[1] = gp ? oD1 : mD[1];
+        gdF[2] = gp ? mD[0] : oD0;
+        gdF[3] = gp ? mD[1] : oD1;
     }
     Side<T> gL, gR;
 #pragma unroll
