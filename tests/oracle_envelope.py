@@ -51,6 +51,13 @@ def fp32_envelope(P, W0, t_end, seeds=(0, 1, 2), max_steps=0):
     return Wa, max(s_each, s_init)
 
 
+def fp64_envelope(P, W0, t_end, seeds=(0, 1), max_steps=0):
+    """The same union for the float64 path, at float64 rounding (1e-15)."""
+    Wa, s_each = oracle_envelope(P, W0, t_end, rel=1e-15, seeds=seeds, max_steps=max_steps, each_step=True)
+    _, s_init = oracle_envelope(P, W0, t_end, rel=1e-15, seeds=seeds, max_steps=max_steps)
+    return Wa, max(s_each, s_init)
+
+
 def oracle_envelope(P, W0, t_end, rel=1e-15, seeds=(0, 1), max_steps=0, each_step=False):
     """(unperturbed oracle run, max relative-L1 spread of the perturbed runs,
     one per seed): initial state perturbed by (1 + rel N(0, 1)), or with
