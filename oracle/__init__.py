@@ -140,6 +140,10 @@ def _declare(L):
     L.or_run.restype = C.c_int
     L.or_fill_ghosts.argtypes = [C.POINTER(Problem), _dp]
     L.or_fill_ghosts.restype = None
+    L.or_trace_selections.argtypes = [C.c_void_p, C.c_long]
+    L.or_trace_selections.restype = None
+    L.or_trace_length.argtypes = []
+    L.or_trace_length.restype = C.c_long
 
 
 def _d(a):
@@ -349,6 +353,25 @@ def fill_ghosts(P: Problem, Wg):
         raise ValueError("need contiguous float64")
     lib().or_fill_ghosts(C.byref(P), _d(Wg))
     return Wg
+
+
+def trace_selections(fn, cap=1 << 24):
+    """Call fn() with the oracle's TENO-D selection trace on (one byte per
+    or_teno_d evaluation, in call order: delta_{3,1} + 2 delta_{0,2} +
+    4 delta_{1,2} + 8 delta_{2,2}, Eqs. 4.7 and 4.12); returns (fn's result,
+    the trace as uint8).  Two runs whose traces differ took a different
+    stencil somewhere."""
+    L = lib()
+    buf = np.zeros(cap, dtype=np.uint8)
+    L.or_trace_selections(buf.ctypes.data, cap)
+    try:
+        out = fn()
+        n = L.or_trace_length()
+    finally:
+        L.or_trace_selections(None, 0)
+    if n > cap:
+        raise RuntimeError("selection trace overflow: %d calls > %d" % (n, cap))
+    return out, buf[:n].copy()
 
 
 def internal_dof(dim, gamma):

@@ -200,6 +200,30 @@ static void apply_fit(int n, const double *minv, const double *q, double *c)
  * delta_{3,1} = 1: large-stencil value and slope (Eqs. 4.8, 4.9)
  * else chi_{k,2} = gamma_k / sum_{0..2} gamma (Eq. 4.11), delta_{k,2} (4.12)
  * and the d_k = 1/3 weighted average of the kept small stencils (4.13, 4.14). */
+/* Selection trace: test instrumentation, no effect on any result.  While a
+ * buffer is set, each TENO-D evaluation appends one byte holding its
+ * choice, delta_{3,1} + 2 delta_{0,2} + 4 delta_{1,2} + 8 delta_{2,2}
+ * (the small-stencil flags are 0 when the large stencil is taken).  The
+ * count goes on past the capacity, so an overflow is seen by the caller. */
+static unsigned char *trace_buf;
+static long trace_cap, trace_len;
+
+void or_trace_selections(unsigned char *buf, long cap)
+{
+    trace_buf = buf;
+    trace_cap = buf ? cap : 0;
+    trace_len = 0;
+}
+
+long or_trace_length(void) { return trace_len; }
+
+static void trace_put(int code)
+{
+    if (!trace_buf) return;
+    if (trace_len < trace_cap) trace_buf[trace_len] = (unsigned char)code;
+    ++trace_len;
+}
+
 int or_teno_d(const double *q5, double eps, double qpow, double ct1, double ct2,
               int n, const double *xs, double *val, double *dval, int *sel)
 {
@@ -230,17 +254,21 @@ int or_teno_d(const double *q5, double eps, double qpow, double ct1, double ct2,
             dval[e] = or_poly_deriv(4, c5, xs[e]);
         }
         if (sel) sel[0] = sel[1] = sel[2] = 0;
+        trace_put(1);
         return 1;
     }
     double s2 = gam[0] + gam[1] + gam[2];
     double d[3], dsum = 0.0;
+    int code = 0;
     for (int k = 0; k < 3; ++k) {
         double chi = gam[k] / s2;
         int dk = !(chi < ct2);
         d[k] = (1.0 / 3.0) * dk;
         dsum += d[k];
+        code |= dk << (k + 1);
         if (sel) sel[k] = dk;
     }
+    trace_put(code);
     for (int e = 0; e < n; ++e) {
         double v = 0.0, dv = 0.0;
         for (int k = 0; k < 3; ++k) {

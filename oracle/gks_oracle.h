@@ -99,6 +99,13 @@ void   or_weno_ao(const double *q5, double eps, double d_hi, double d_lo, int n,
                   double *val, double *dval, double *wbar);
 int    or_teno_d(const double *q5, double eps, double qpow, double ct1, double ct2,
                  int n, const double *xs, double *val, double *dval, int *sel);
+/* Selection trace (test instrumentation; changes no result): with a buffer
+ * set, every or_teno_d call, direct or inside a flux, appends one byte
+ * delta_{3,1} + 2 delta_{0,2} + 4 delta_{1,2} + 8 delta_{2,2};
+ * or_trace_length is the number of calls since the buffer was set (it may
+ * exceed cap; bytes past cap are not stored).  NULL stops the trace. */
+void   or_trace_selections(unsigned char *buf, long cap);
+long   or_trace_length(void);
 
 /* characteristic basis of the normal Euler flux (Sec. 3.1): R holds the right
  * eigenvectors of dF/dW at the conserved state Wm as columns (row-major

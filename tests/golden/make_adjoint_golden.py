@@ -14,7 +14,11 @@ the forward pass's choice held fixed.  Each gradient component is therefore
 taken at two step sizes, 1e-6 and 2.5e-7; where the two agree to 1e-6 of
 the largest component no choice flipped within the probe, and the value is
 the derivative of the map with its choices fixed.  Columns: component index
-(j * 24 + i, j the y index), dJ/d(delta rho) at h = 1e-6, at h = 2.5e-7.
+(j * 24 + i, j the y index), dJ/d(delta rho) at h = 1e-6, at h = 2.5e-7,
+and 1 where the oracle's TENO-D selection trace (every stencil choice of
+the run, Eqs. 4.7 and 4.12) differs between the +h and -h runs at either
+step size, else 0: a component whose two step sizes disagree must have a
+flipped choice inside its probe.
 
 Run from the repository root:  python tests/golden/make_adjoint_golden.py
 """
@@ -42,24 +46,41 @@ def primitives():
     return rho, u, v, p
 
 
-def objective(delta):
+def objective(delta, traced=False):
     import oracle as O
     from paper_2309_10534_gb300 import workloads as WL
     rho, u, v, p = primitives()
     P = O.make_problem(2, N, N, bc=("periodic",) * 4, tau="zero")
-    W = WL.conserved_2d(rho + delta, u, v, p, GAMMA)
-    for _ in range(STEPS):
-        W = O.step(P, W, DT)
-    return float((W[0] ** 2).sum() / (N * N))
+    W0 = WL.conserved_2d(rho + delta, u, v, p, GAMMA)
+
+    def run():
+        W = W0
+        for _ in range(STEPS):
+            W = O.step(P, W, DT)
+        return float((W[0] ** 2).sum() / (N * N))
+
+    return O.trace_selections(run) if traced else run()
+
+
+def flipped(k, h):
+    """True where the selection traces of the runs at +h and -h in
+    component k differ."""
+    e = np.zeros((N, N))
+    e.flat[k] = h
+    _, tp = objective(e, traced=True)
+    _, tm = objective(-e, traced=True)
+    return tp.size != tm.size or not np.array_equal(tp, tm)
 
 
 def component(k):
-    out = []
+    out, flip = [], False
     for h in HS:
         e = np.zeros((N, N))
         e.flat[k] = h
-        out.append((objective(e) - objective(-e)) / (2 * h))
-    return out
+        (jp, tp), (jm, tm) = objective(e, traced=True), objective(-e, traced=True)
+        out.append((jp - jm) / (2 * h))
+        flip = flip or tp.size != tm.size or not np.array_equal(tp, tm)
+    return out + [float(flip)]
 
 
 def main():
@@ -71,7 +92,7 @@ def main():
         f.write("# n=%d steps=%d dt=%r seed=%d kmax=%d h=%r,%r J=%.17e\n"
                 % (N, STEPS, DT, SEED, KMAX, HS[0], HS[1], objective(np.zeros((N, N)))))
         for k in range(N * N):
-            f.write("%d %.17e %.17e\n" % (k, g[k, 0], g[k, 1]))
+            f.write("%d %.17e %.17e %d\n" % (k, g[k, 0], g[k, 1], int(g[k, 2])))
     print(path)
 
 

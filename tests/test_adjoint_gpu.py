@@ -60,23 +60,28 @@ def _golden():
         f.readline()
         head = f.readline()
     J = float(head.split("J=")[1])
-    return d[:, 1], d[:, 2], J
+    return d[:, 1], d[:, 2], d[:, 3] > 0, J
 
 
 def test_adjoint_matches_oracle_reference_gradient(gks):
     """Full-field gradient on 24 x 24 (576 parameters, 6 steps) against the
-    oracle's central differences.  Where the two FD step sizes agree (no
-    TENO-D choice flipped inside the probe; at least 85 % of the cells) the
-    adjoint agrees to 2e-6 of the largest component; the forward J agrees
-    with the oracle's to 1e-12."""
-    g1, g2, J_or = _golden()
+    oracle's central differences.  Where the two FD step sizes agree the
+    adjoint agrees to 2e-6 of the largest component; every component where
+    they disagree has a TENO-D choice that flips inside its probe (the
+    oracle's selection trace differs between the +h and -h runs: the map
+    is not differentiable there at the probe's scale), and no more than
+    15 % of the cells are excluded.  The forward J agrees with the oracle's
+    to 1e-12."""
+    g1, g2, flip, J_or = _golden()
     g, J, _ = _smooth24_gradient(gks, "fp64", 3)
     assert J == pytest.approx(J_or, rel=1e-12)
     m = np.abs(g1).max()
     ok = np.abs(g1 - g2) <= 1e-6 * m
+    assert not np.any(~ok & ~flip), np.flatnonzero(~ok & ~flip)
     assert ok.mean() >= 0.85, ok.mean()
     err = np.abs(g - g1)[ok].max() / m
-    print(f"adjoint vs oracle FD: {ok.sum()} consistent components, max rel err {err:.3e}")
+    print(f"adjoint vs oracle FD: {ok.sum()} consistent components ({(~ok).sum()} excluded, all with a "
+          f"flipped selection), max rel err {err:.3e}")
     assert err <= 2e-6
 
 

@@ -1095,3 +1095,52 @@ def test_conventional_2d_nonphysical_quartic_falls_back_to_the_kinetic_merge():
         expect2 = 0.5 * (_euler_flux(q2[-g], gam, 2) + _euler_flux(q2[g], gam, 2))
         assert nfb2 == 0
         assert np.allclose(F2, expect2, rtol=1e-12, atol=1e-12 * np.abs(expect2).max())
+
+
+def test_selection_trace_records_each_teno_d_choice():
+    """The oracle's selection trace stores, per TENO-D evaluation, the choice
+    of Eqs. 4.7 and 4.12.  On a step, only the smooth sub-stencil survives:
+    jump between cells i and i+1 -> S0 alone (code 2), between i-1 and i ->
+    S2 alone (code 8); smooth data take the large stencil (code 1)."""
+    cases = [([0.0, 0.0, 0.0, 1.0, 1.0], 2), ([0.0, 0.0, 1.0, 1.0, 1.0], 8),
+             ([1.0, 1.2, 1.4, 1.6, 1.8], 1), ([3.0] * 5, 1)]
+
+    def evaluate():
+        return [O.teno_d(q, [0.5, -0.5]) for q in (c for c, _ in cases)]
+
+    outs, trace = O.trace_selections(evaluate)
+    assert trace.tolist() == [code for _, code in cases]
+    for (_, _, large, sel), code in zip(outs, trace):
+        assert code == int(large) + 2 * sel[0] + 4 * sel[1] + 8 * sel[2]
+
+
+def test_selection_trace_changes_no_result():
+    """A traced step is bit-identical to an untraced one; on a constant
+    state every evaluation takes the large stencil."""
+    W = WL.random_smooth_2d(12, 10, seed=3, kmax=2)
+    P = O.make_problem(2, 12, 10, bc=("periodic",) * 4, tau="euler")
+    dt = 0.4 * O.dt(P, W)
+    out, trace = O.trace_selections(lambda: O.step(P, W, dt))
+    assert np.array_equal(out, O.step(P, W, dt)) and trace.size > 0
+    Wc = np.broadcast_to(W.mean(axis=(1, 2))[:, None, None], W.shape).copy()
+    _, trace = O.trace_selections(lambda: O.step(P, Wc, dt))
+    assert trace.size > 0 and np.all(trace == 1)
+
+
+def test_adjoint_golden_exclusions_are_selection_flips():
+    """The adjoint golden file's last column (a flipped TENO-D choice inside
+    a component's probe, from the oracle's selection trace) covers every
+    component whose two FD step sizes disagree; re-derived here for a
+    seeded sample of excluded and of flip-free components."""
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
+    import make_adjoint_golden as MG
+    d = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "adjoint_smooth24.txt"))
+    g1, g2, flip = d[:, 1], d[:, 2], d[:, 3] > 0
+    bad = np.abs(g1 - g2) > 1e-6 * np.abs(g1).max()
+    assert bad.any() and not np.any(bad & ~flip)
+    rng = np.random.default_rng(0)
+    for k in rng.choice(np.flatnonzero(bad), 2, replace=False):
+        assert MG.flipped(int(k), MG.HS[0]) or MG.flipped(int(k), MG.HS[1]), k
+    k = int(rng.choice(np.flatnonzero(~flip)))
+    assert not MG.flipped(k, MG.HS[0]) and not MG.flipped(k, MG.HS[1]), k
