@@ -61,6 +61,9 @@ struct AdjDir {
     const double* lam1;   // cotangent fields (ghosted; interior used)
     const double* lam2;   // may be null
     double cF1, cD1, cF2, cD2;
+    // float32 copies of the scalars, converted on the host (a float64 ->
+    // float32 conversion in every thread would run on the slow float64 pipe)
+    float fcF1, fcD1, fcF2, fcD2, fihn, fiht;
     void* lines;          // [NQ][faces nn+1][rows nt+4]
     void* contrib;        // [5][NQ][faces nn+1][rows nt]
     void* dcell;          // [5][4][cells nn+2][rows nt+4]
@@ -85,6 +88,14 @@ __device__ __forceinline__ long long cidx(const AdjDir& a, int f, int r)
 __device__ __forceinline__ long long didx(const AdjDir& a, int i, int r)
 {
     return a.dirn == 0 ? (long long)(r + 2) * (a.nn + 2) + (i + 1) : (long long)(i + 1) * (a.nt + 4) + (r + 2);
+}
+
+// a direction scalar in the arithmetic type
+template <typename T>
+__device__ __forceinline__ T scal(double d, float f)
+{
+    if constexpr (sizeof(T) == 4) return f;
+    else return d;
 }
 
 template <typename T>
@@ -198,7 +209,7 @@ __global__ void __launch_bounds__(256) k_adj_lines(GridDev g, AdjDir a, TenoT<T>
     const long long org = (long long)NG * g.pitch + NG;
     const long long LP = (long long)(a.nn + 1) * (a.nt + 4);
     T* L = static_cast<T*>(a.lines);
-    const T ih = (T)a.ihn;
+    const T ih = scal<T>(a.ihn, a.fihn);
 #pragma unroll 1
     for (int vv = 0; vv < 4; vv += 2) {  // variable pairs (0, 1), (2, 3), as the forward
         T q[2][5];
@@ -244,7 +255,7 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4) ? 4 : 1) k_adj_gauss(Gri
     const long long CP = (long long)(a.nn + 1) * a.nt;
     const T* Lq = static_cast<const T*>(a.lines);
     const T gpos = gp ? T(0.28867513459481288) : T(-0.28867513459481288);
-    const T iht = (T)a.iht;
+    const T iht = scal<T>(a.iht, a.fiht);
 
     // forward, as the forward sweep: lane gp reconstructs side gp (0: left,
     // 1: right) at both Gauss points, keeps its own point and hands the other
@@ -294,22 +305,23 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4) ? 4 : 1) k_adj_gauss(Gri
     // slow one) is formed once per face
     T gF[4], gdF[4];
     {
-        const T cF1 = (T)a.cF1, cF2 = (T)a.cF2, cD1 = (T)a.cD1, cD2 = (T)a.cD2;
+        const T cF1 = scal<T>(a.cF1, a.fcF1), cF2 = scal<T>(a.cF2, a.fcF2);
+        const T cD1 = scal<T>(a.cD1, a.fcD1), cD2 = scal<T>(a.cD2, a.fcD2);
         T mF[2], mD[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int v = 2 * gp + h;
             const long long b = (long long)gvar_(v, swap) * g.plane + org + rc * a.st;
-            double d1 = 0.0, d2 = 0.0;
-            if (fc < a.nn) {
-                d1 += a.lam1[b + fc * a.sn];
-                if (a.lam2) d2 += a.lam2[b + fc * a.sn];
+            // lam of the cells on either side (zero outside the interior);
+            // one float64 subtraction per difference
+            const double p1 = fc < a.nn ? a.lam1[b + fc * a.sn] : 0.0;
+            const double m1 = fc >= 1 ? a.lam1[b + (fc - 1) * a.sn] : 0.0;
+            T e1 = (T)(p1 - m1), e2 = T(0);
+            if (a.lam2) {
+                const double p2 = fc < a.nn ? a.lam2[b + fc * a.sn] : 0.0;
+                const double m2 = fc >= 1 ? a.lam2[b + (fc - 1) * a.sn] : 0.0;
+                e2 = (T)(p2 - m2);
             }
-            if (fc >= 1) {
-                d1 -= a.lam1[b + (fc - 1) * a.sn];
-                if (a.lam2) d2 -= a.lam2[b + (fc - 1) * a.sn];
-            }
-            const T e1 = (T)d1, e2 = (T)d2;
             mF[h] = T(0.5) * (cF1 * e1 + cF2 * e2);
             mD[h] = T(0.5) * (cD1 * e1 + cD2 * e2);
         }
@@ -396,7 +408,7 @@ __global__ void __launch_bounds__(256) k_adj_normal(GridDev g, AdjDir a, TenoT<T
     const long long DP = (long long)(a.nn + 2) * (a.nt + 4);
     const T* C = static_cast<const T*>(a.contrib);
     T* D = static_cast<T*>(a.dcell);
-    const T ih = (T)a.ihn;
+    const T ih = scal<T>(a.ihn, a.fihn);
     // line row r receives from Gauss row r - s + 2 at stencil position s
     auto gline = [&](int q, int f) {
         T acc = T(0);
@@ -635,6 +647,12 @@ gks_status stage_vjp(gks_adjoint* A, bool stage2_input, const double* lam1, cons
             d.nn = c->desc.ny; d.nt = c->desc.nx; d.sn = c->g.pitch; d.st = 1;
             d.ihn = 1.0 / c->g.dy; d.iht = 1.0 / c->g.dx;
         }
+        d.fcF1 = (float)d.cF1;
+        d.fcD1 = (float)d.cD1;
+        d.fcF2 = (float)d.cF2;
+        d.fcD2 = (float)d.cD2;
+        d.fihn = (float)d.ihn;
+        d.fiht = (float)d.iht;
         gks_status s = f32 ? sweep_vjp_t<float>(A, d) : sweep_vjp_t<double>(A, d);
         if (s) return s;
     }
