@@ -210,8 +210,8 @@ __global__ void __launch_bounds__(256) k_adj_lines(GridDev g, AdjDir a, TenoT<T>
     const long long LP = (long long)(a.nn + 1) * (a.nt + 4);
     T* L = static_cast<T*>(a.lines);
     const T ih = scal<T>(a.ihn, a.fihn);
-#pragma unroll 1
-    for (int vv = 0; vv < 4; vv += 2) {  // variable pairs (0, 1), (2, 3), as the forward
+    {
+        const int vv = 2 * (int)blockIdx.z;  // variable pairs (0, 1), (2, 3), as the forward
         T q[2][5];
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
@@ -419,8 +419,8 @@ __global__ void __launch_bounds__(256) k_adj_normal(GridDev g, AdjDir a, TenoT<T
         }
         return acc;
     };
-#pragma unroll 1
-    for (int vv = 0; vv < 4; vv += 2) {  // variable pairs, as the forward's selection
+    {
+        const int vv = 2 * (int)blockIdx.z;  // variable pairs, as the forward's selection
         T q[2][5];
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
@@ -608,9 +608,12 @@ gks_status sweep_vjp_t(gks_adjoint* A, AdjDir d)
         return dim3((unsigned)((ex * xmul + blk.x - 1) / blk.x), (unsigned)((ey + blk.y - 1) / blk.y));
     };
     const dim3 b256(32, 8), b128(32, 4);
-    k_adj_lines<T><<<grid_for(d.nn + 2, d.nt + 4, b256, 1), b256, 0, st>>>(g, d, tn);
+    // the per-cell kernels take the two variable pairs in blockIdx.z
+    dim3 gcell = grid_for(d.nn + 2, d.nt + 4, b256, 1);
+    gcell.z = 2;
+    k_adj_lines<T><<<gcell, b256, 0, st>>>(g, d, tn);
     k_adj_gauss<T><<<grid_for(d.nn + 1, d.nt, b128, 2), b128, 0, st>>>(g, d, fp, tt);
-    k_adj_normal<T><<<grid_for(d.nn + 2, d.nt + 4, b256, 1), b256, 0, st>>>(g, d, tn);
+    k_adj_normal<T><<<gcell, b256, 0, st>>>(g, d, tn);
     k_adj_gather<T><<<grid_for(d.nn + 6, d.nt + 4, b256, 1), b256, 0, st>>>(g, d);
     CK(cudaGetLastError());
     A->launches += 4;
