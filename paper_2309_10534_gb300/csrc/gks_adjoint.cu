@@ -178,8 +178,7 @@ __device__ __forceinline__ unsigned fwd_gauss2(const T qa[5], const T qb[5], con
         TenoSel2 S2;
         teno_select_x2(qq, P, S2);
         f2 a, b, c, d;
-        teno_gauss_x2(S2, gA, a, b);
-        teno_gauss_x2(S2, gB, c, d);
+        teno_gauss_pm_x2(S2, gB, a, b, c, d);  // gA = -gB
         va[0] = a.x(); da[0] = b.x(); vb[0] = c.x(); db[0] = d.x();
         va[1] = a.y(); da[1] = b.y(); vb[1] = c.y(); db[1] = d.y();
         return sel_code_x(S2) | (sel_code_y(S2) << 4);
@@ -190,8 +189,7 @@ __device__ __forceinline__ unsigned fwd_gauss2(const T qa[5], const T qb[5], con
         for (int l = 0; l < 2; ++l) {
             TenoSel<T> S;
             teno_select(q[l], P, S);
-            teno_gauss(S, gA, va[l], da[l]);
-            teno_gauss(S, gB, vb[l], db[l]);
+            teno_gauss_pm(S, gB, va[l], da[l], vb[l], db[l]);  // gA = -gB, as the forward
             code |= sel_code(S) << (4 * l);
         }
         return code;

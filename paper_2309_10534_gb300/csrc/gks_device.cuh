@@ -114,22 +114,40 @@ template <typename T> struct TenoSel {
 // Legendre form.  Selection of Eqs. (4.5)-(4.7) and (4.11)-(4.12) on powers
 // normalised by the smallest beta + eps (below), without divisions and
 // without (beta+eps)^-q, which would overflow in float32.
-// the sub-stencil quadratics and the large-stencil quartic (Sec. 3.1)
+// the sub-stencil quadratics and the large-stencil quartic (Sec. 3.1),
+// formed from the sums and differences of the cells at equal distance from
+// the centre (the quartic's odd coefficients only see the differences, its
+// even ones only the sums): every coefficient is one to three fused
+// multiply-adds
 template <typename T>
 GKS_HD void stencil_coeffs(const T q[5], TenoSel<T>& S)
 {
     const T q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3], q4 = q[4];
+    const T s1 = q1 + q3, d1 = q3 - q1, s0 = q0 + q4, d0 = q4 - q0;
     S.q2 = q2;
-    S.b[0] = T(0.5) * (q0 - T(4) * q1 + T(3) * q2);
-    S.c[0] = T(0.5) * (q0 - T(2) * q1 + q2);
-    S.b[1] = T(0.5) * (q3 - q1);
-    S.c[1] = T(0.5) * (q1 - T(2) * q2 + q3);
-    S.b[2] = T(0.5) * (T(-3) * q2 + T(4) * q3 - q4);
-    S.c[2] = T(0.5) * (q2 - T(2) * q3 + q4);
-    S.u1 = (T(11) * q0 - T(82) * q1 + T(82) * q3 - T(11) * q4) * T(1.0 / 120.0);
-    S.u2 = (T(-3) * q0 + T(40) * q1 - T(74) * q2 + T(40) * q3 - T(3) * q4) * T(1.0 / 56.0);
-    S.u3 = (-q0 + T(2) * q1 - T(2) * q3 + q4) * T(1.0 / 12.0);
-    S.u4 = (q0 - T(4) * q1 + T(6) * q2 - T(4) * q3 + q4) * T(1.0 / 24.0);
+    S.b[0] = T(1.5) * q2 + (T(0.5) * q0 - T(2) * q1);  // (q0 - 4 q1 + 3 q2) / 2
+    S.c[0] = T(0.5) * (q0 + q2) - q1;                   // (q0 - 2 q1 + q2) / 2
+    S.b[1] = T(0.5) * d1;                               // (q3 - q1) / 2
+    S.c[1] = T(0.5) * s1 - q2;                          // (q1 - 2 q2 + q3) / 2
+    S.b[2] = T(2) * q3 - (T(1.5) * q2 + T(0.5) * q4);   // (-3 q2 + 4 q3 - q4) / 2
+    S.c[2] = T(0.5) * (q2 + q4) - q3;                   // (q2 - 2 q3 + q4) / 2
+    S.u1 = T(82.0 / 120.0) * d1 - T(11.0 / 120.0) * d0;                       // (11 q0 - 82 q1 + 82 q3 - 11 q4) / 120
+    S.u2 = T(40.0 / 56.0) * s1 - (T(3.0 / 56.0) * s0 + T(74.0 / 56.0) * q2);  // (-3 q0 + 40 q1 - 74 q2 + 40 q3 - 3 q4) / 56
+    S.u3 = T(1.0 / 12.0) * d0 - T(1.0 / 6.0) * d1;                            // (-q0 + 2 q1 - 2 q3 + q4) / 12
+    S.u4 = T(1.0 / 24.0) * s0 + (T(0.25) * q2 - T(1.0 / 6.0) * s1);          // (q0 - 4 q1 + 6 q2 - 4 q3 + q4) / 24
+}
+
+// smoothness indicators t_k = beta_k + eps of Eq. (3.7) (quadratics
+// b^2 + 13/3 c^2; the quartic in Balsara's Legendre form), each a chain of
+// fused multiply-adds onto eps
+template <typename T>
+GKS_HD void teno_indicators(const TenoSel<T>& S, T eps, T* t)
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t[k] = S.b[k] * S.b[k] + (T(13.0 / 3.0) * S.c[k] * S.c[k] + eps);
+    const T a = S.u1 + T(0.1) * S.u3, bq = S.u2 + T(123.0 / 455.0) * S.u4;
+    t[3] = a * a + (T(13.0 / 3.0) * bq * bq + (T(781.0 / 20.0) * S.u3 * S.u3
+                                              + (T(1421461.0 / 2275.0) * S.u4 * S.u4 + eps)));
 }
 
 // WENO5-AO (Sec. 3.2): beta by Eq. (3.7), global indicator
@@ -168,28 +186,9 @@ GKS_HD void ao_select(const T q[5], const TenoT<T>& P, TenoSel<T>& S)
 template <typename T>
 GKS_HD void teno_select(const T q[5], const TenoT<T>& P, TenoSel<T>& S)
 {
-    const T q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3], q4 = q[4];
-    S.q2 = q2;
-    S.b[0] = T(0.5) * (q0 - T(4) * q1 + T(3) * q2);
-    S.c[0] = T(0.5) * (q0 - T(2) * q1 + q2);
-    S.b[1] = T(0.5) * (q3 - q1);
-    S.c[1] = T(0.5) * (q1 - T(2) * q2 + q3);
-    S.b[2] = T(0.5) * (T(-3) * q2 + T(4) * q3 - q4);
-    S.c[2] = T(0.5) * (q2 - T(2) * q3 + q4);
-    S.u1 = (T(11) * q0 - T(82) * q1 + T(82) * q3 - T(11) * q4) * T(1.0 / 120.0);
-    S.u2 = (T(-3) * q0 + T(40) * q1 - T(74) * q2 + T(40) * q3 - T(3) * q4) * T(1.0 / 56.0);
-    S.u3 = (-q0 + T(2) * q1 - T(2) * q3 + q4) * T(1.0 / 12.0);
-    S.u4 = (q0 - T(4) * q1 + T(6) * q2 - T(4) * q3 + q4) * T(1.0 / 24.0);
-
-    const T eps = P.eps;
+    stencil_coeffs(q, S);
     T t[4];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) t[k] = S.b[k] * S.b[k] + T(13.0 / 3.0) * S.c[k] * S.c[k] + eps;
-    {
-        T a = S.u1 + T(0.1) * S.u3, bq = S.u2 + T(123.0 / 455.0) * S.u4;
-        t[3] = a * a + T(13.0 / 3.0) * bq * bq + T(781.0 / 20.0) * S.u3 * S.u3
-             + T(1421461.0 / 2275.0) * S.u4 * S.u4 + eps;
-    }
+    teno_indicators(S, P.eps, t);
     // chi_k = t_k^-q / sum_j t_j^-q.  With m = min_j t_j and r_j = m / t_j in
     // (0, 1], chi_k = r_k^q / sum_j r_j^q: nothing overflows, and an r^q that
     // underflows belongs to a chi far below any cut-off.  The same powers
@@ -343,6 +342,36 @@ GKS_HD void teno_gauss(const TenoSel<T>& S, T g, T& v, T& d)
     }
 }
 
+// teno_gauss at both Gauss points xi = -g (vm, dm) and xi = +g (vp, dp),
+// g = 1/(2 sqrt 3): each value is E + xi O and each derivative Ed + xi Od,
+// with E, O, Ed, Od formed once for the two points
+template <typename T>
+GKS_HD void teno_gauss_pm(const TenoSel<T>& S, T g, T& vm, T& dm, T& vp, T& dp)
+{
+    T E, O, Ed, Od;
+    if (S.large) {
+        E = S.q2 - S.u4 * T(1.0 / 180.0);
+        O = S.u1 - S.u3 * T(1.0 / 15.0);
+        Ed = S.u1 + T(0.1) * S.u3;
+        Od = T(2) * S.u2 - T(2.0 / 21.0) * S.u4;
+    } else {
+        T sb = S.w[0] * S.b[0], sc = S.w[0] * S.c[0];
+#pragma unroll
+        for (int k = 1; k < 3; ++k) {
+            sb += S.w[k] * S.b[k];
+            sc += S.w[k] * S.c[k];
+        }
+        E = S.q2;
+        O = sb;
+        Ed = sb;
+        Od = T(2) * sc;
+    }
+    vm = E - g * O;
+    vp = E + g * O;
+    dm = Ed - g * Od;
+    dp = Ed + g * Od;
+}
+
 // The conventional path (Sec. 3.1, 4.1): WENO5-Z (REC 2) or TENO5 (REC 3)
 // face values from the three quadratics, slopes from the quadratic through
 // the cell average and the two face values (Eq. 3.11).  The selection keeps,
@@ -473,6 +502,18 @@ GKS_HD void rec_gauss(const TenoSel<T>& S, T g, T& v, T& d)
     if constexpr (REC == 0) teno_gauss(S, g, v, d);
     else if constexpr (REC == 1) ao_gauss(S, g, v, d);
     else weno3_gauss(S, g, v, d);
+}
+
+// the same at both Gauss points xi = -g (vm, dm) and xi = +g (vp, dp)
+template <int REC, typename T>
+GKS_HD void rec_gauss_pm(const TenoSel<T>& S, T g, T& vm, T& dm, T& vp, T& dp)
+{
+    if constexpr (REC == 0) {
+        teno_gauss_pm(S, g, vm, dm, vp, dp);
+    } else {
+        rec_gauss<REC>(S, -g, vm, dm);
+        rec_gauss<REC>(S, g, vp, dp);
+    }
 }
 
 // ------------------------------------------------------------------ characteristic variables

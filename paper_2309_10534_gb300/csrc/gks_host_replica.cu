@@ -27,11 +27,9 @@ int teno_t(const double* q, double eps, int qpow, double ct1, double ct2, double
     T vp, dp, vm, dm;
     gks::teno_faces(qq, S, vp, dp, vm, dm);
     faces[0] = vp; faces[1] = dp; faces[2] = vm; faces[3] = dm;
-    T v, d;
-    gks::teno_gauss(S, T(-0.28867513459481288), v, d);
-    gauss[0] = v; gauss[1] = d;
-    gks::teno_gauss(S, T(0.28867513459481288), v, d);
-    gauss[2] = v; gauss[3] = d;
+    T g[4];
+    gks::teno_gauss_pm(S, T(0.28867513459481288), g[0], g[1], g[2], g[3]);
+    for (int i = 0; i < 4; ++i) gauss[i] = g[i];
     return S.large ? 1 : 0;
 }
 
@@ -53,13 +51,11 @@ int teno_packed(const double* q, double eps, int qpow, double ct1, double ct2, d
         if (fv[i].y() != -fv[i].x()) return -2;
         faces[i] = fv[i].x();
     }
-    const float gp[2] = {-0.28867513459481288f, 0.28867513459481288f};
-    for (int i = 0; i < 2; ++i) {
-        gks::f2 v, d;
-        gks::teno_gauss_x2(S, gp[i], v, d);
-        if (v.y() != -v.x() || d.y() != -d.x()) return -2;
-        gauss[2 * i] = v.x();
-        gauss[2 * i + 1] = d.x();
+    gks::f2 gv[4];
+    gks::teno_gauss_pm_x2(S, 0.28867513459481288f, gv[0], gv[1], gv[2], gv[3]);
+    for (int i = 0; i < 4; ++i) {
+        if (gv[i].y() != -gv[i].x()) return -2;
+        gauss[i] = gv[i].x();
     }
     return large;
 }
@@ -233,11 +229,9 @@ int weno3_gauss_t(const double* q, double eps, int qpow, double ct, double* gaus
     P.eps_ao = eps;
     gks::TenoSel<T> S;
     gks::rec_select<REC>(qq, gks::teno_t<T>(P), S);
-    T v, d;
-    gks::rec_gauss<REC>(S, T(-0.28867513459481288), v, d);
-    gauss[0] = v; gauss[1] = d;
-    gks::rec_gauss<REC>(S, T(0.28867513459481288), v, d);
-    gauss[2] = v; gauss[3] = d;
+    T g[4];
+    gks::rec_gauss_pm<REC>(S, T(0.28867513459481288), g[0], g[1], g[2], g[3]);
+    for (int i = 0; i < 4; ++i) gauss[i] = g[i];
     return 0;
 }
 

@@ -605,13 +605,11 @@ k2d_sweep(GridDev g, SweepArgs a, FluxParams<T> fp, TenoT<T> tnn, TenoT<T> tnt, 
 #pragma unroll
                 for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * gpi][v][r + s][f];
                 rec_select<RB>(q, tnt, S);
-                rec_gauss<RB>(S, gA, wa, wda);
-                rec_gauss<RB>(S, gB, wb, wdb);
+                rec_gauss_pm<RB>(S, gB, wa, wda, wb, wdb);  // gA = -gB
 #pragma unroll
                 for (int s = 0; s < 5; ++s) q[s] = sm.rec[2 * gpi + 1][v][r + s][f];
                 rec_select<RB>(q, tnt, S);
-                rec_gauss<RB>(S, gA, na, dn);
-                rec_gauss<RB>(S, gB, nb, dn);
+                rec_gauss_pm<RB>(S, gB, na, dn, nb, dn);
             }
             // own side at own point; the partner's point goes to the partner
             T own = gpi ? wb : wa, got = __shfl_xor_sync(0xffffffffu, gpi ? wa : wb, 1);

@@ -132,9 +132,8 @@ void count(int tau_mode, double Pr, gks_flop_model* out)
     const Counts tang = measure([&] {
         TenoSel<T> S;
         rec_select<RB>(q, tp, S);
-        T a, b;
-        rec_gauss<RB>(S, T(0.28867513459481288), a, b);
-        rec_gauss<RB>(S, T(-0.28867513459481288), a, b);
+        T a, b, c, d;
+        rec_gauss_pm<RB>(S, T(0.28867513459481288), a, b, c, d);
     });
     // characteristic variables: per face the basis, six projections, two
     // sides of every field and four back-projections

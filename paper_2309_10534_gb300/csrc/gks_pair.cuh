@@ -105,15 +105,8 @@ GKS_HD void teno_select_x2(const f2 q[5], const TenoT<float>& P, TenoSel2& S)
 {
     TenoSel<f2> C;
     stencil_coeffs(q, C);
-    const f2 eps(P.eps);
     f2 t[4];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) t[k] = C.b[k] * C.b[k] + f2(13.0 / 3.0) * C.c[k] * C.c[k] + eps;
-    {
-        const f2 a = C.u1 + f2(0.1) * C.u3, bq = C.u2 + f2(123.0 / 455.0) * C.u4;
-        t[3] = a * a + f2(13.0 / 3.0) * bq * bq + f2(781.0 / 20.0) * C.u3 * C.u3
-             + f2(1421461.0 / 2275.0) * C.u4 * C.u4 + eps;
-    }
+    teno_indicators(C, f2(P.eps), t);
     const f2 m(lane_min4(t[0].x(), t[1].x(), t[2].x(), t[3].x()), lane_min4(t[0].y(), t[1].y(), t[2].y(), t[3].y()));
     f2 p[4];
 #pragma unroll
@@ -222,19 +215,29 @@ GKS_HD void recon_cell3(const T q[3][5], const TenoT<T>& P, T* vp, T* dp, T* vm,
     }
 }
 
-// value and xi-derivative at the Gauss point xi = g of both lanes' selection
-// (quartic: P2(g) = 0, P3(g) = -g/15, P4(g) = -1/180, P3'(g) = 1/10,
-// P4'(g) = -2g/21; quadratics: q2 + b g + c (g^2 - 1/12) = q2 + b g)
-GKS_HD void teno_gauss_x2(const TenoSel2& S, float g, f2& v, f2& d)
+// values and xi-derivatives at the two Gauss points xi = -g and xi = +g
+// (g = 1/(2 sqrt 3)) of both lanes' selection.  At the Gauss points
+// g^2 = 1/12, so P2 = 0, P3 = -xi/15, P4 = -1/180, P3' = 1/10, P4' = -2 xi/21
+// for the quartic, and the quadratics reduce to q2 + b xi: every value is
+// E + xi O and every derivative Ed + xi Od, with E, O, Ed, Od shared by the
+// two points.
+GKS_HD void teno_gauss_pm_x2(const TenoSel2& S, float g, f2& vm, f2& dm, f2& vp, f2& dp)
 {
-    const f2 G(g);
-    v = S.q2 + S.u1 * G - S.u3 * f2(g * (1.0f / 15.0f)) - S.u4 * f2(1.0f / 180.0f);
-    d = S.u1 + f2(2.0f * g) * S.u2 + f2(0.1f) * S.u3 - f2(g * (2.0f / 21.0f)) * S.u4;
+    f2 sb = S.w[0] * S.b[0], sc = S.w[0] * S.c[0];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        v += S.w[k] * S.b[k] * G;
-        d += S.w[k] * (S.b[k] + f2(2.0f * g) * S.c[k]);
+    for (int k = 1; k < 3; ++k) {
+        sb += S.w[k] * S.b[k];
+        sc += S.w[k] * S.c[k];
     }
+    const f2 E = S.q2 - S.u4 * f2(1.0f / 180.0f);
+    const f2 O = (S.u1 - S.u3 * f2(1.0f / 15.0f)) + sb;
+    const f2 Ed = (S.u1 + S.u3 * f2(0.1f)) + sb;
+    const f2 Od = (f2(2.0f) * S.u2 - S.u4 * f2(2.0f / 21.0f)) + f2(2.0f) * sc;
+    const f2 G(g);
+    vm = E - G * O;
+    vp = E + G * O;
+    dm = Ed - G * Od;
+    dp = Ed + G * Od;
 }
 
 GKS_HD f2 fabs(f2 a) { return f2(fabsf(a.v.x), fabsf(a.v.y)); }
@@ -278,10 +281,10 @@ template <int REC>
 GKS_HD void packed_gauss(const f2 q[5], const TenoT<float>& P, float gA, float gB, f2& va, f2& da, f2& vb, f2& db)
 {
     if constexpr (REC == 0) {
+        // the Gauss points are symmetric: gA = -gB
         TenoSel2 S;
         teno_select_x2(q, P, S);
-        teno_gauss_x2(S, gA, va, da);
-        teno_gauss_x2(S, gB, vb, db);
+        teno_gauss_pm_x2(S, gB, va, da, vb, db);
     } else {
         TenoSel<f2> S;
         ao_select(q, pair_teno(P), S);
