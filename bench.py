@@ -813,7 +813,16 @@ def paper_run(gks, s, precision, stream, max_steps=0):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    steps, t = S.advance_to(s.t_end, max_steps=max_steps)
+    try:
+        steps, t = S.advance_to(s.t_end, max_steps=max_steps)
+    except gks.GKSError as e:
+        # a run that leaves the scheme's robustness (a cell average turns
+        # non-physical) is reported with the time it reached, not timed
+        torch.cuda.synchronize()
+        d = S.diagnostics(check=False)
+        S.close()
+        return {"value": None, "unit": UNIT, "failed": str(e)[:160], "t_reached": float(d.t),
+                "steps": int(d.steps)}
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)

@@ -22,6 +22,13 @@ extern "C" {
  * p = (1,2,2,1,2,2). */
 int gks_host_time_coeffs(int precision, double s, double *cF, double *cD);
 
+/* The kernels' test of a state before its flux (and of the cell average a
+ * positivity fallback takes): 1 if rho > 0 and p > 0 (finite) -- and, in
+ * float32, an internal energy of at least 1e-4 of E (below that a float32
+ * pressure has no reliable digits) -- else 0; -1 on a bad argument.
+ * W: 4 slots (1-D: slot 2 unused). */
+int gks_host_physical(int dim, int precision, double gamma, const double *W);
+
 /* TENO-D (Sec. 4.2) on five cell averages q[0..4] = Qbar_{i-2..i+2}:
  * faces[0..3] = value and xi-derivative at xi = +1/2, then at xi = -1/2;
  * gauss[0..3] = value and xi-derivative at xi = -1/(2 sqrt 3), then +1/(2 sqrt 3);

@@ -972,13 +972,29 @@ template <typename T> struct Side {  // one reconstructed side (local frame, 4 s
     T W[4], Wn[4], Wt[4];
 };
 
+// Smallest internal-energy fraction (rho e / E) a float32 state may have.
+// Below it the float32 pressure has no reliable digits: a reconstructed
+// value carries an absolute rounding of ~1e-7 of its stencil's largest
+// cell value, which is then a large part of E - rho |U|^2 / 2, and the micro
+// slopes scale that error by lambda^2 = (rho / 2p)^2.  (Such points are
+// reconstruction artefacts at strong shocks, e.g. a point with p = 7e-6
+// beside a cell at p = 21 in the Mach 10 double Mach reflection, where the
+// float32 flux came out -522 against 0.2 in float64.)  States of flows
+// colder than that need the float64 path.
+constexpr double kMinInternalFractionF32 = 1e-4;
+
+// rho > 0 and p > 0 (finite); float32 states also need an internal energy
+// of at least kMinInternalFractionF32 of E
 template <typename T, int DIM>
 GKS_HD bool physical(const T* W, T gm1)
 {
     const T r = W[0];
     const T ke = (DIM == 2) ? (W[1] * W[1] + W[2] * W[2]) : W[1] * W[1];
-    const T p = gm1 * (W[3] - T(0.5) * ke / r);
-    return r > T(0) && p > T(0) && isfinite(p);
+    const T e = W[3] - T(0.5) * ke / r;  // internal energy per volume
+    const T p = gm1 * e;
+    bool ok = r > T(0) && p > T(0) && isfinite(p);
+    if constexpr (sizeof(T) == 4) ok = ok && e >= T(kMinInternalFractionF32) * W[3];
+    return ok;
 }
 
 // Kinetic merge of two states (values only; Eq. 3.25 with reading R2): the

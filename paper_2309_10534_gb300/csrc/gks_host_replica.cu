@@ -307,6 +307,17 @@ extern "C" int gks_host_point_flux_vjp(int precision, double gamma, const double
                           : flux_vjp_t<double>(gamma, Wl, Wln, Wlt, Wr, Wrn, Wrt, gF, gdF, gl, gr);
 }
 
+extern "C" int gks_host_physical(int dim, int precision, double gamma, const double* W)
+{
+    if (!W || (dim != 1 && dim != 2) || (precision != 0 && precision != 1) || !(gamma > 1.0)) return -1;
+    if (precision == 1) {
+        float w[4];
+        for (int i = 0; i < 4; ++i) w[i] = (float)W[i];
+        return dim == 2 ? gks::physical<float, 2>(w, (float)(gamma - 1.0)) : gks::physical<float, 1>(w, (float)(gamma - 1.0));
+    }
+    return dim == 2 ? gks::physical<double, 2>(W, gamma - 1.0) : gks::physical<double, 1>(W, gamma - 1.0);
+}
+
 extern "C" int gks_host_time_coeffs(int precision, double s, double* cF, double* cD)
 {
     if (!cF || !cD || !(s > 0.0)) return -1;

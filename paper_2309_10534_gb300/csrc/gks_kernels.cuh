@@ -87,17 +87,29 @@ __device__ __forceinline__ int ghost_src(int bc, int n, int g, bool& flip_n, boo
 // sigma = max((|U| + a)/h, 4 nu / h^2), dt = cfl / sigma  (Sec. 5), in the
 // kernel's arithmetic type (the float32 path takes its time step in float32;
 // only the state and its accumulation are float64)
+// U^2 + V^2 with both products rounded before the sum (no fused
+// multiply-add): the same bits for (U, V) and (V, U), so a sweep that holds
+// the state in its local frame and the grid-order reduction pick the same
+// time step
+template <typename T>
+__device__ __forceinline__ T speed2(T U, T V)
+{
+    if constexpr (sizeof(T) == 4) return __fmul_rn(U, U) + __fmul_rn(V, V);
+    else return __dmul_rn(U, U) + __dmul_rn(V, V);
+}
+
 template <typename T, typename WT = double>
 __device__ __forceinline__ T cell_sigma(const WT* w, int dim, T gamma, T mu, T h, unsigned int& err)
 {
     const T r = (T)w[0], ir = T(1) / r;
     const T U = (T)w[1] * ir, V = (dim == 2) ? (T)w[2] * ir : T(0);
     const T E = (T)(dim == 2 ? w[3] : w[2]);  // no dynamic index: keeps w in registers
-    const T p = (gamma - T(1)) * (E - T(0.5) * r * (U * U + V * V));
+    const T q = speed2(U, V);
+    const T p = (gamma - T(1)) * (E - T(0.5) * r * q);
     if (!(r > T(0) && p > T(0) && isfinite(p))) err |= 1u;
     const T a = sqrt(gamma * p * ir);
     const T ih = T(1) / h;
-    T s = (sqrt(U * U + V * V) + a) * ih;
+    T s = (sqrt(q) + a) * ih;
     if (mu > T(0)) s = fmax(s, T(4) * mu * ir * ih * ih);
     return s;
 }

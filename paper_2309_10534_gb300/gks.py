@@ -260,9 +260,13 @@ class Solver:
         self._check(lib().gks_advance_to(self.h, float(t_end), int(max_steps), C.byref(n), C.byref(t)))
         return n.value, t.value
 
-    def diagnostics(self):
+    def diagnostics(self, check=True):
+        """Error word, fallbacks, t, steps and dt; check=False returns them
+        without raising on a set error word (a run that failed)."""
         d = Diag()
-        self._check(lib().gks_get_diagnostics(self.h, C.byref(d)))
+        st = lib().gks_get_diagnostics(self.h, C.byref(d))
+        if check:
+            self._check(st)
         return d
 
     def selection_flips(self):
@@ -347,9 +351,10 @@ def _replica():
         L.gks_host_merge.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp, _dp]
         L.gks_host_char_face.argtypes = [C.c_int, C.c_int, C.c_double, _dp, C.c_double, C.c_int, C.c_double,
                                          C.c_double, _dp]
+        L.gks_host_physical.argtypes = [C.c_int, C.c_int, C.c_double, _dp]
         for f in (L.gks_host_time_coeffs, L.gks_host_teno, L.gks_host_point_flux, L.gks_host_teno_vjp,
                   L.gks_host_point_flux_vjp, L.gks_host_weno_ao, L.gks_host_weno3, L.gks_host_weno3_gauss,
-                  L.gks_host_merge, L.gks_host_char_face):
+                  L.gks_host_merge, L.gks_host_char_face, L.gks_host_physical):
             f.restype = C.c_int
         L._replica_declared = True
     return L
@@ -358,6 +363,16 @@ def _replica():
 def _arr(a, n):
     x = np.zeros(n) if a is None else np.ascontiguousarray(a, dtype=np.float64)
     return x, x.ctypes.data_as(_dp)
+
+
+def host_physical(dim, W, precision="fp64", gamma=1.4):
+    """The kernels' state test (rho > 0, p > 0; float32 also an internal
+    energy of at least 1e-4 of E) on 4 slots."""
+    w, pw = _arr(W, 4)
+    r = _replica().gks_host_physical(int(dim), PRECISION[precision], float(gamma), pw)
+    if r < 0:
+        raise ValueError("bad argument")
+    return bool(r)
 
 
 def host_time_coeffs(s, precision="fp64"):

@@ -240,3 +240,21 @@ def test_char_face_matches_oracle(G, dim, precision, tol):
             assert np.abs(row[act] - ref).max() <= tol * scale, (trial, row[act], ref)
             if dim == 1:
                 assert row[2] == 0.0
+
+
+def test_float32_state_test_needs_resolvable_internal_energy(G):
+    """The kernels' state test (before a point's flux, and on the cell average
+    a positivity fallback takes): both precisions reject rho <= 0 and p <= 0;
+    float32 also rejects a state whose internal energy is below 1e-4 of E
+    (its float32 pressure has no reliable digits, and the micro slopes scale
+    that error by lambda^2), which float64 accepts."""
+    def state(rho, u, v, frac):
+        ke = 0.5 * rho * (u * u + v * v)
+        return [rho, rho * u, rho * v, ke / (1.0 - frac)]  # internal energy = frac * E
+    for dim, v in ((2, -0.27), (1, 0.0)):
+        cold, warm = state(1.7, 0.65, v, 5e-5), state(1.7, 0.65, v, 2e-4)
+        assert G.host_physical(dim, cold, "fp64") and not G.host_physical(dim, cold, "fp32")
+        assert G.host_physical(dim, warm, "fp64") and G.host_physical(dim, warm, "fp32")
+        for bad in ([1.0, 1.0, 0.0, 0.4], [-1.0, 0.0, 0.0, 2.5], [1.0, 0.0, 0.0, 0.0]):
+            assert not G.host_physical(dim, bad, "fp64") and not G.host_physical(dim, bad, "fp32")
+        assert G.host_physical(dim, [1.4, 0.0, 0.0, 2.5], "fp32")
