@@ -98,18 +98,35 @@ __device__ __forceinline__ T speed2(T U, T V)
     else return __dmul_rn(U, U) + __dmul_rn(V, V);
 }
 
+// division and square root rounded to nearest whatever the unit's float
+// flags: the sweeps' units take fast float32 division and square root, the
+// reduction before a call's first step (k_sigma) does not, and both must
+// form the same time step
+template <typename T>
+__device__ __forceinline__ T div_rn(T a, T b)
+{
+    if constexpr (sizeof(T) == 4) return __fdiv_rn(a, b);
+    else return __ddiv_rn(a, b);
+}
+template <typename T>
+__device__ __forceinline__ T sqrt_rn(T a)
+{
+    if constexpr (sizeof(T) == 4) return __fsqrt_rn(a);
+    else return __dsqrt_rn(a);
+}
+
 template <typename T, typename WT = double>
 __device__ __forceinline__ T cell_sigma(const WT* w, int dim, T gamma, T mu, T h, unsigned int& err)
 {
-    const T r = (T)w[0], ir = T(1) / r;
+    const T r = (T)w[0], ir = div_rn(T(1), r);
     const T U = (T)w[1] * ir, V = (dim == 2) ? (T)w[2] * ir : T(0);
     const T E = (T)(dim == 2 ? w[3] : w[2]);  // no dynamic index: keeps w in registers
     const T q = speed2(U, V);
     const T p = (gamma - T(1)) * (E - T(0.5) * r * q);
     if (!(r > T(0) && p > T(0) && isfinite(p))) err |= 1u;
-    const T a = sqrt(gamma * p * ir);
-    const T ih = T(1) / h;
-    T s = (sqrt(q) + a) * ih;
+    const T a = sqrt_rn(gamma * p * ir);
+    const T ih = div_rn(T(1), h);
+    T s = (sqrt_rn(q) + a) * ih;
     if (mu > T(0)) s = fmax(s, T(4) * mu * ir * ih * ih);
     return s;
 }
