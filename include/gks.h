@@ -201,6 +201,17 @@ gks_status gks_set_boundary_states(gks_ctx *ctx, const gks_boundary_states *stat
 /* cudaStream_t passed as void*; NULL = legacy default stream */
 gks_status gks_set_stream(gks_ctx *ctx, void *stream);
 
+/* Where a state array lives (on_device of gks_set_state / gks_get_state /
+ * gks_get_buffer and the batch calls): */
+#define GKS_HOST_MEMORY 0        /* host memory; the call returns when the copy is done */
+#define GKS_DEVICE_MEMORY 1      /* device memory */
+#define GKS_HOST_PINNED_ASYNC 2  /* page-locked host memory, gks_set_state / gks_get_state only: the
+                                    copy is enqueued on the context's stream and the call returns at
+                                    once; the caller keeps W unchanged (set) or unread (get) until the
+                                    stream has passed it (cudaStreamSynchronize or an event).  With
+                                    two contexts on two streams, one's copies overlap the other's
+                                    steps.  Other values: GKS_EINVAL */
+
 /* Copy conserved cell averages in / out ([nvar][ny][nx], float64).
  * gks_set_state resets t, step count, fallback count and the error word. */
 gks_status gks_set_state(gks_ctx *ctx, const double *W, int on_device);

@@ -358,10 +358,15 @@ gks_status copy_interior(gks_ctx* c, double* arr, const double* W, int on_device
     // arrays through a device staging buffer) and scattered into / gathered
     // from the ghosted layout by a kernel: one large transfer runs at the
     // link's rate, where a pitched copy of short rows does not.
+    // on_device: GKS_HOST_MEMORY (returns when the copy is done),
+    // GKS_DEVICE_MEMORY, GKS_HOST_PINNED_ASYNC (enqueued on the stream only)
+    if (on_device != GKS_HOST_MEMORY && on_device != GKS_DEVICE_MEMORY && on_device != GKS_HOST_PINNED_ASYNC)
+        return GKS_EINVAL;
+    const bool host = on_device != GKS_DEVICE_MEMORY;
     const long long n = (long long)c->nv * c->desc.nx * ((c->desc.dim == 2) ? c->desc.ny : 1);
     const double* src = W;
     double* dst = const_cast<double*>(W);
-    if (!on_device) {
+    if (host) {
         if (!c->stage) CK(cudaMalloc(&c->stage, sizeof(double) * (size_t)n));
         src = dst = c->stage;
         if (in) CK(cudaMemcpyAsync(c->stage, W, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
@@ -371,10 +376,10 @@ gks_status copy_interior(gks_ctx* c, double* arr, const double* W, int on_device
     else k_pack<<<blocks, 256, 0, c->stream>>>(c->g, arr, dst, n);
     CK(cudaGetLastError());
     ++c->launches;
-    if (!on_device && !in)
+    if (host && !in)
         CK(cudaMemcpyAsync(const_cast<double*>(W), c->stage, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost,
                            c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    if (on_device != GKS_HOST_PINNED_ASYNC) CK(cudaStreamSynchronize(c->stream));
     return GKS_OK;
 }
 
@@ -671,6 +676,13 @@ gks_status gks_set_state(gks_ctx* c, const double* W, int on_device)
     k_prepare<<<1, 32, 0, c->stream>>>(c->ds, 2, 0.0, INFINITY, 0);
     CK(cudaGetLastError());
     ++c->launches;
+    if (on_device == GKS_HOST_PINNED_ASYNC) {
+        // the host mirror of t and the counters is refreshed by the next
+        // synchronising call
+        c->hs->t = 0.0;
+        c->hs->steps = 0;
+        return GKS_OK;
+    }
     return sync_state(c);
 }
 
@@ -682,7 +694,8 @@ gks_status gks_get_state(gks_ctx* c, double* W, int on_device)
 
 gks_status gks_get_buffer(gks_ctx* c, int which, double* W, int on_device)
 {
-    if (!c || !W || which < 0 || which > 2) return GKS_EINVAL;
+    if (!c || !W || which < 0 || which > 2 || (on_device != GKS_HOST_MEMORY && on_device != GKS_DEVICE_MEMORY))
+        return GKS_EINVAL;
     double* arr = which == 0 ? c->W : (which == 1 ? c->Ws : c->Ac);
     if (c->Wsf && which > 0) {
         // float32 path: W* lives in float32, the accumulator as an increment

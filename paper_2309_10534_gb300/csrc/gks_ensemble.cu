@@ -662,7 +662,7 @@ gks_status gks_batch_set_stream(gks_batch* b, void* stream)
 
 gks_status gks_batch_set_state(gks_batch* b, const double* W, int on_device)
 {
-    if (!b || !W) return GKS_EINVAL;
+    if (!b || !W || (on_device != GKS_HOST_MEMORY && on_device != GKS_DEVICE_MEMORY)) return GKS_EINVAL;
     BCK(cudaMemcpyAsync(b->W, W, sizeof(double) * 3 * (size_t)b->total,
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
     BCK(cudaMemsetAsync(b->d_t, 0, sizeof(double) * b->count, b->stream));
@@ -674,7 +674,7 @@ gks_status gks_batch_set_state(gks_batch* b, const double* W, int on_device)
 
 gks_status gks_batch_get_state(gks_batch* b, double* W, int on_device)
 {
-    if (!b || !W) return GKS_EINVAL;
+    if (!b || !W || (on_device != GKS_HOST_MEMORY && on_device != GKS_DEVICE_MEMORY)) return GKS_EINVAL;
     BCK(cudaMemcpyAsync(W, b->W, sizeof(double) * 3 * (size_t)b->total,
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
     BCK(cudaStreamSynchronize(b->stream));

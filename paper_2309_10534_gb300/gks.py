@@ -46,6 +46,21 @@ class Scheme(C.Structure):
                 ("d_lo", C.c_double), ("eps_ao", C.c_double), ("merge", C.c_int), ("charvars", C.c_int)]
 
 
+GKS_HOST_MEMORY, GKS_DEVICE_MEMORY, GKS_HOST_PINNED_ASYNC = 0, 1, 2
+
+
+def _host_ptr(W, shape):
+    """Address of a contiguous float64 host array of the state's size (a
+    CPU torch tensor or a numpy array)."""
+    if hasattr(W, "data_ptr"):
+        if W.is_cuda or W.dtype.itemsize != 8 or not W.is_contiguous() or W.numel() != int(np.prod(shape)):
+            raise ValueError("need a contiguous float64 CPU tensor of the state's size")
+        return W.data_ptr()
+    if not (isinstance(W, np.ndarray) and W.dtype == np.float64 and W.flags.c_contiguous and W.size == int(np.prod(shape))):
+        raise ValueError("need a contiguous float64 array of the state's size")
+    return W.ctypes.data
+
+
 class Diag(C.Structure):
     _fields_ = [("error_word", C.c_uint), ("fallbacks", C.c_longlong), ("t", C.c_double),
                 ("steps", C.c_longlong), ("dt", C.c_double)]
@@ -222,6 +237,19 @@ class Solver:
         else:
             W = self._host(W)
             self._check(lib().gks_set_state(self.h, W.ctypes.data_as(_vp), 0))
+
+    def set_state_async(self, W):
+        """Enqueue the copy-in of W (page-locked host memory: a pinned CPU
+        torch tensor, or a numpy view of one) on the solver's stream and
+        return at once (GKS_HOST_PINNED_ASYNC); W must stay unchanged until
+        the stream has passed the copy."""
+        self._check(lib().gks_set_state(self.h, _vp(_host_ptr(W, self.shape)), GKS_HOST_PINNED_ASYNC))
+
+    def get_state_async(self, out):
+        """Enqueue the copy-out into out (page-locked host memory, state
+        shape) on the solver's stream and return at once; out is valid once
+        the stream has passed the copy."""
+        self._check(lib().gks_get_state(self.h, _vp(_host_ptr(out, self.shape)), GKS_HOST_PINNED_ASYNC))
 
     def get_state(self, out=None):
         if out is not None and hasattr(out, "data_ptr"):

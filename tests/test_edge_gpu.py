@@ -102,3 +102,42 @@ def test_refused_arguments(gks):
         S.set_state(np.zeros(5))  # wrong size
     S.step(0.0)                 # still usable
     assert np.isfinite(S.get_state()).all()
+
+
+def test_async_pinned_state_copies_match_the_synchronous_ones(gks):
+    """GKS_HOST_PINNED_ASYNC: the state copied in from page-locked memory and
+    stepped on two contexts with their own streams, alternating, gives the
+    same bits as the synchronous calls on one context; the async mode is
+    refused where it is not supported (gks_get_buffer) and an unknown mode
+    anywhere."""
+    import ctypes
+    import torch
+    s = WL.riemann2d(96, split=0.8, t_end=0.8)
+    S = gks.solver_for(s, "fp32")
+    S.set_state(s.W)
+    S.step(0.0)
+    ref = S.get_state()
+    host_in = torch.from_numpy(np.ascontiguousarray(s.W)).pin_memory()
+    pipe = []
+    for _ in range(2):
+        st = torch.cuda.Stream()
+        P = gks.solver_for(s, "fp32")
+        P.set_stream(st.cuda_stream)
+        pipe.append((P, torch.empty_like(host_in).pin_memory()))
+    for k in range(4):
+        P, out = pipe[k % 2]
+        P.set_state_async(host_in)
+        P.step(0.0)
+        P.get_state_async(out)
+    torch.cuda.synchronize()
+    for P, out in pipe:
+        assert np.array_equal(out.numpy(), ref)
+        d = P.diagnostics()
+        assert d.steps == 1 and d.t > 0
+        buf = np.empty(S.shape)
+        st = gks.lib().gks_get_buffer(P.h, 0, buf.ctypes.data_as(ctypes.c_void_p), gks.GKS_HOST_PINNED_ASYNC)
+        assert st == gks.GKS_EINVAL
+        st = gks.lib().gks_set_state(P.h, buf.ctypes.data_as(ctypes.c_void_p), 3)
+        assert st == gks.GKS_EINVAL
+        P.close()
+    S.close()
