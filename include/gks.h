@@ -44,7 +44,7 @@ typedef enum {
     GKS_ECUDA = 3,           /* a CUDA runtime call failed */
     GKS_ENONPHYSICAL = 4,    /* rho <= 0, p <= 0 or non-finite state seen by a kernel */
     GKS_ETIMEOUT = 5,        /* a bounded device-side wait gave up */
-    GKS_EUNSUPPORTED = 6     /* valid request this build does not implement */
+    GKS_EUNSUPPORTED = 6     /* valid request the library does not implement */
 } gks_status;
 
 /* ghost-layer boundary conditions (paper Sec. 5: periodic, non-reflecting,
