@@ -239,19 +239,22 @@ __global__ void __launch_bounds__(TN + 2) k1d_stage(GridDev g, Stage1DArgs a, Fl
     const int slot[3] = {0, 1, 3};
 
     const int pl = (int)g.plane;  // a 1-D plane is one ghosted row
-    for (int k = tid; k < 3 * (TN + 6); k += NT) {
-        const int v = k / (TN + 6), c = k % (TN + 6);
-        const int gi = i0 + c;  // ghosted index of cell i0 - 3 + c
-        T val = T(0);
-        if (gi < gx) {
-            if constexpr (sizeof(T) == 4) {
-                if (a.srcf) val = a.srcf[v * pl + gi];
-                else val = (T)a.src[v * pl + gi];
-            } else {
-                val = a.src[v * pl + gi];
-            }
+    // one loop per source type: a per-element choice between the float32
+    // and the converted float64 source was compiled as both, and every
+    // element then paid a float64 -> float32 conversion on the slow float64
+    // pipe whichever source it took
+    auto load = [&](auto src) {
+        for (int k = tid; k < 3 * (TN + 6); k += NT) {
+            const int v = k / (TN + 6), c = k % (TN + 6);
+            const int gi = i0 + c;  // ghosted index of cell i0 - 3 + c
+            sq[v][c] = gi < gx ? (T)src[v * pl + gi] : T(0);
         }
-        sq[v][c] = val;
+    };
+    if constexpr (sizeof(T) == 4) {
+        if (a.srcf) load(a.srcf);
+        else load(a.src);
+    } else {
+        load(a.src);
     }
     __syncthreads();
     fp.dt = s_scal[0];
